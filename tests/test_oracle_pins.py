@@ -1,0 +1,490 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test names the part of the method it pins and the closed form, invariant
+or paper statement it checks.  None of them compares the oracle with itself:
+the expected values are closed forms, conservation laws, the paper's printed
+trends, or convergence orders.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_16843_gb300 import inputs
+
+INF = float("inf")
+
+
+def make2d(nx, ny, Lx=1.0, rho=(1.0, 1.0), mu=(0.1, 0.1), sigma=0.0, eps=None,
+           gamma=0.0, theta=math.pi / 2, beta=(INF, INF), U=(0.0, 0.0)):
+    h = Lx / nx
+    o = oracle.Oracle(2, (nx, ny), (Lx, ny * h))
+    o.set_fluids(rho[0], rho[1], mu[0], mu[1], sigma, h if eps is None else eps, gamma)
+    o.set_wall(0, theta, beta[0], beta[1], U[0])
+    o.set_wall(1, theta, beta[0], beta[1], U[1])
+    return o, h
+
+
+# ---------------------------------------------------------------------------
+# a1: psi and derived quantities (Eq. psi, Eq. curvature, Eq. chemical potential)
+# ---------------------------------------------------------------------------
+
+def test_psi_is_signed_distance_of_tanh_profile():
+    """Eq. (psi): for phi = (1 + tanh((x-x0)/(2 eps)))/2, psi = x - x0 exactly;
+    then grad psi = (1, 0), lap psi = 0, kappa = 0 and mu_c = 0 (Eq. curvature
+    and Eq. chemical potential at phase-field equilibrium)."""
+    nx, ny = 256, 8
+    o, h = make2d(nx, ny, Lx=4.0, sigma=1.0, eps=0.05)
+    phi = inputs.couette_phi_2d(nx, ny, h, 1.0, 3.0, 0.05)
+    out = o.eval_psi(phi)
+    x = inputs.cell_centres(nx, h)
+    near = np.abs(x - 1.0) <= 6 * 0.05   # the far interface adds e^-34 here
+    assert np.allclose(out["psi"][:, near], (x[near] - 1.0)[None, :], atol=1e-12, rtol=0)
+    inner = np.abs(x - 1.0) <= 8 * 0.05
+    assert np.allclose(out["gx"][:, inner], 1.0, atol=1e-9)
+    assert np.abs(out["gy"][:, inner]).max() < 1e-13  # one-sided stencils of a y-constant field
+    assert np.abs(out["kappa"][:, inner]).max() < 1e-6
+    assert np.abs(out["muc"][:, inner]).max() < 1e-6
+
+
+def test_curvature_and_chemical_potential_of_circle_converge_second_order():
+    """For a circular tanh interface, psi = R - r so |grad psi| = 1 and
+    lap psi = -1/r: kappa -> 1/r and mu_c -> 6 sigma phi(1-phi)/r (Eqs. curvature,
+    chemical potential).  The discrete values converge at second order."""
+    errs_k, errs_m = [], []
+    R, eps = 0.25, 0.04
+    for n in (32, 64, 128):
+        o, h = make2d(n, n, sigma=1.0, eps=eps)
+        x = inputs.cell_centres(n, h)
+        X, Y = np.meshgrid(x, x)
+        r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+        phi = 0.5 * (1 + np.tanh((R - r) / (2 * eps)))
+        out = o.eval_psi(phi)
+        band = np.abs(r - R) < 2 * eps
+        errs_k.append(np.abs(out["kappa"][band] - 1 / r[band]).max())
+        errs_m.append(np.abs(out["muc"][band] - 6 * phi[band] * (1 - phi[band]) / r[band]).max())
+    for e in (errs_k, errs_m):
+        assert e[0] / e[1] > 3.3 and e[1] / e[2] > 3.3, e
+
+
+# ---------------------------------------------------------------------------
+# a3: phi flux (Eq. CDI) and wall no-flux (Eq. no-flux BC)
+# ---------------------------------------------------------------------------
+
+def test_stationary_tanh_profile_rhs_converges_second_order():
+    """eps grad phi = phi(1-phi) n holds exactly for the tanh profile (Eq. CDI
+    at rest), so the discrete regularisation flux divergence falls as h^2."""
+    errs = []
+    eps = 0.02
+    for nx in (64, 128, 256):
+        o, h = make2d(nx, 8, sigma=0.0, eps=eps, gamma=1.0)
+        o.set_state(inputs.couette_phi_2d(nx, 8, h, 0.25, 0.75, eps))
+        rphi, _ = o.eval_rhs(gamma=1.0)
+        errs.append(np.abs(rphi).max())
+    assert errs[0] / errs[1] > 3.6 and errs[1] / errs[2] > 3.8, errs
+
+
+def test_central_advection_modified_wavenumber():
+    """With gamma = 0 the phi flux is u phi_f; for phi = 0.5 + 0.1 sin(kx) and
+    uniform u, -div F = -U 0.1 cos(k x_i) sin(k h)/h exactly."""
+    nx, ny, U = 64, 8, 0.7
+    o, h = make2d(nx, ny, gamma=0.0, U=(U, U))
+    x = inputs.cell_centres(nx, h)
+    k = 2 * math.pi * 3
+    phi = np.repeat((0.5 + 0.1 * np.sin(k * x))[None, :], ny, axis=0)
+    u = np.full((ny, nx), U)
+    v = np.zeros((ny + 1, nx))
+    o.set_state(phi, [u, v])
+    rphi, _ = o.eval_rhs(gamma=0.0)
+    exact = -U * 0.1 * np.cos(k * x) * math.sin(k * h) / h
+    assert np.abs(rphi - exact[None, :]).max() < 1e-12 * np.abs(exact).max()
+
+
+def test_mass_conserved_to_roundoff_equilibrium_drop():
+    """Sec. 2: no-flux and no-penetration walls plus periodic sides conserve
+    the phi integral; the flux form telescopes, so only round-off remains."""
+    wl = inputs.drop_2d()
+    o = oracle.from_workload(wl)
+    m0 = o.mass()
+    o.step(wl.dt, 30)
+    assert abs(o.mass() - m0) / m0 < 1e-13
+
+
+def test_mass_conserved_density_ratio_adaptive_gamma():
+    """Same invariant with density ratio 10, viscosity ratio 10, noisy phi and
+    gamma = 2.5 |u|_max (Sec. 5.1)."""
+    nx, ny = 32, 16
+    h = 1.0 / nx
+    o = oracle.Oracle(2, (nx, ny), (1.0, ny * h))
+    o.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, -0.5)
+    o.set_wall_slip_length(2, math.radians(120), h)
+    phi = inputs.add_noise(inputs.cap_phi_2d(nx, ny, h, 0.25, math.pi / 2, 0.5, h), 1e-3, 7)
+    o.set_state(phi)
+    m0 = o.mass()
+    o.step(5e-5, 20)
+    assert abs(o.mass() - m0) / m0 < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# a4 + a5: momentum right-hand side and RK4
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_viscous_mode_decays_with_rk4_amplification(m):
+    """Single fluid, no-slip walls at rest: u = sin(m pi y/H) is an exact
+    eigenvector of the discrete viscous operator with the ghost-cell wall
+    (eigenvalue -(4 nu/h^2) sin^2(m pi h / 2H)); classical RK4 (Sec. 4)
+    multiplies it per step by 1 + z + z^2/2 + z^3/6 + z^4/24."""
+    nx, ny = 8, 32
+    o, h = make2d(nx, ny, rho=(2.0, 2.0), mu=(0.05, 0.05))
+    H = ny * h
+    y = inputs.cell_centres(ny, h)
+    u0 = np.repeat(np.sin(m * math.pi * y / H)[:, None], nx, axis=1)
+    o.set_state(np.ones((ny, nx)), [u0, np.zeros((ny + 1, nx))])
+    dt, n = 2e-3, 25
+    o.step(dt, n)
+    _, vel, _ = o.get_state()
+    lam = -(4 * 0.025 / h ** 2) * math.sin(m * math.pi * h / (2 * H)) ** 2
+    z = lam * dt
+    R = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    assert np.abs(vel[0] - R ** n * u0).max() < 1e-13
+    assert np.abs(vel[1]).max() == 0.0
+
+
+@pytest.mark.parametrize("fluid", [0.0, 1.0])
+def test_navier_slip_couette_closed_form_is_discrete_steady_state(fluid):
+    """Eqs. (slip BC, u_slip_v) with u^Y = 0: plane Couette flow between walls
+    at -U and +U with slip length l = mu/beta has u(y) = 2U (y - H/2)/(H + 2l).
+    The staggered stencils and the ghost value are exact for linear profiles,
+    so the closed form is the discrete steady state to round-off."""
+    nx, ny, U = 8, 32, 0.1
+    mu = (0.2, 0.05)
+    ell = 1.5 / 32
+    o, h = make2d(nx, ny, mu=mu, sigma=1.0, beta=(mu[0] / ell, mu[1] / ell), U=(-U, U))
+    H = ny * h
+    y = inputs.cell_centres(ny, h)
+    u = np.repeat((2 * U * (y - H / 2) / (H + 2 * ell))[:, None], nx, axis=1)
+    phi = np.full((ny, nx), fluid)
+    o.set_state(phi, [u, np.zeros((ny + 1, nx))])
+    _, rmom = o.eval_rhs(gamma=0.0)
+    scale = max(mu) * U / h ** 2
+    assert np.abs(rmom[0]).max() < 1e-11 * scale
+    o.step(1e-3, 20)
+    _, vel, _ = o.get_state()
+    assert np.abs(vel[0] - u).max() < 1e-14
+
+
+def test_consistent_mass_momentum_transport_keeps_uniform_flow():
+    """Eq. (NS_momentum) with the regularisation mass flux S = (rho1-rho2) R:
+    with sigma = 0 a drop of density ratio 20 in a uniform stream (walls moving
+    with it) leaves the velocity uniform, because the momentum flux uses the
+    same phi flux as the phi update."""
+    nx, ny, U = 32, 16, 0.3
+    o, h = make2d(nx, ny, rho=(20.0, 1.0), mu=(0.1, 0.01), sigma=0.0, gamma=1.0,
+                  beta=(0.1 / (1 / 32), 0.01 / (1 / 32)), U=(U, U))
+    phi = inputs.cap_phi_2d(nx, ny, h, 0.2, math.radians(70), 0.4, h)
+    o.set_state(phi, [np.full((ny, nx), U), np.zeros((ny + 1, nx))])
+    o.step(1e-3, 10)
+    phi1, vel, _ = o.get_state()
+    assert np.abs(phi1 - phi).max() > 1e-3          # the drop has moved
+    assert np.abs(vel[0] - U).max() < 1e-12
+    assert np.abs(vel[1]).max() < 1e-12
+
+
+def test_laplace_pressure_jump_of_static_drop():
+    """Eq. (EB surface tension) with Eq. (chemical potential): the pressure
+    that balances the surface tension of a circular drop jumps by sigma/R
+    (2D Laplace law) across the interface."""
+    n = 64
+    o, h = make2d(n, n, mu=(0.1, 0.1), sigma=1.0, gamma=1.0, beta=(6.4, 6.4))
+    x = inputs.cell_centres(n, h)
+    X, Y = np.meshgrid(x, x)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    o.set_state(0.5 * (1 + np.tanh((0.25 - r) / (2 * h))))
+    o.step(1e-5, 1)
+    _, _, p = o.get_state()
+    jump = p[n // 2, n // 2] - p[2, 2]
+    assert abs(jump - 4.0) / 4.0 < 0.03
+
+
+# ---------------------------------------------------------------------------
+# a6..a8: pressure Poisson solve and projection
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_poisson_discrete_eigenfunction(dim):
+    """Constant density: cos(2 pi m x/Lx) (periodic) times cos(pi k z/Lz)
+    (Neumann walls, cell centred) is an eigenvector of the discrete operator
+    with eigenvalue -(4/h^2)[sin^2(pi m/nx) + sin^2(pi k/(2 nz))]; the solve
+    must return it to round-off."""
+    rho = 2.0
+    if dim == 2:
+        n = (32, 16)
+    else:
+        n = (16, 8, 8)
+    h = 1.0 / n[0]
+    L = tuple(x * h for x in n)
+    o = oracle.Oracle(dim, n, L)
+    o.set_fluids(rho, rho, 1, 1, 0, h, 0)
+    shape = n[::-1]
+    o.set_state(np.ones(shape))
+    o.set_solver(1e-14, 100, False)
+    xs = inputs.cell_centres(n[0], h)
+    zs = inputs.cell_centres(n[-1], h)
+    m, k = 3, 2
+    if dim == 2:
+        pe = np.cos(2 * np.pi * m * xs[None, :] / L[0]) * np.cos(np.pi * k * zs[:, None] / L[1])
+        lam = -(4 / h ** 2) * (math.sin(math.pi * m / n[0]) ** 2 + math.sin(math.pi * k / (2 * n[1])) ** 2)
+    else:
+        ys = inputs.cell_centres(n[1], h)
+        pe = (np.cos(2 * np.pi * m * xs[None, None, :] / L[0])
+              * np.sin(2 * np.pi * 1 * ys[None, :, None] / L[1])
+              * np.cos(np.pi * k * zs[:, None, None] / L[2]))
+        lam = -(4 / h ** 2) * (math.sin(math.pi * m / n[0]) ** 2 + math.sin(math.pi * 1 / n[1]) ** 2
+                               + math.sin(math.pi * k / (2 * n[2])) ** 2)
+    p, cyc, res = o.poisson(lam / rho * pe)
+    assert cyc < 20
+    assert np.abs(p - pe).max() < 1e-12
+
+
+def test_poisson_manufactured_variable_density_second_order():
+    """div(grad p / rho) = f with rho(x,y) smooth and p = cos(2 pi x) cos(pi y/Ly)
+    (zero normal derivative at the walls): f is written out by hand below; the
+    discrete solution converges to p at second order."""
+    errs = []
+    for nx in (16, 32, 64):
+        ny = nx // 2
+        h = 1.0 / nx
+        Ly = ny * h
+        o = oracle.Oracle(2, (nx, ny), (1.0, Ly))
+        r1, r2 = 3.0, 1.0
+        o.set_fluids(r1, r2, 1, 1, 0, h, 0)
+        x = inputs.cell_centres(nx, h)[None, :]
+        y = inputs.cell_centres(ny, h)[:, None]
+        a, b = 2 * math.pi, math.pi / Ly
+        phi = 0.5 + 0.3 * np.sin(a * x) * np.cos(b * y)
+        o.set_state(phi)
+        o.set_solver(1e-13, 100, False)
+        rho = (r1 - r2) * phi + r2
+        # p = cos(ax) cos(by); rho_x = (r1-r2) 0.3 a cos(ax) cos(by); rho_y = -(r1-r2) 0.3 b sin(ax) sin(by)
+        px = -a * np.sin(a * x) * np.cos(b * y)
+        py = -b * np.cos(a * x) * np.sin(b * y)
+        lap = -(a * a + b * b) * np.cos(a * x) * np.cos(b * y)
+        rx = (r1 - r2) * 0.3 * a * np.cos(a * x) * np.cos(b * y)
+        ry = -(r1 - r2) * 0.3 * b * np.sin(a * x) * np.sin(b * y)
+        f = lap / rho - (rx * px + ry * py) / rho ** 2
+        p, _, _ = o.poisson(f)
+        pe = np.cos(a * x) * np.cos(b * y)
+        pe = pe - pe.mean()
+        errs.append(np.abs(p - pe).max())
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.7, errs
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_multigrid_matches_direct_solve_variable_density(dim):
+    """The multigrid solution equals a dense direct solve of the same system."""
+    n = (16, 8) if dim == 2 else (8, 8, 8)
+    h = 1.0 / n[0]
+    o = oracle.Oracle(dim, n, tuple(x * h for x in n))
+    o.set_fluids(20.0, 1.0, 1, 1, 0, h, 0)
+    rng = np.random.default_rng(3)
+    phi = np.clip(rng.uniform(-0.1, 1.1, size=n[::-1]), 0, 1)
+    o.set_state(phi)
+    o.set_solver(1e-13, 200, False)
+    f = rng.standard_normal(n[::-1])
+    p_mg, cyc, _ = o.poisson(f)
+    p_d = o.poisson_direct(f)
+    assert np.abs(p_mg - p_d).max() < 1e-10 * np.abs(p_d).max()
+    # and the direct solution satisfies the operator equation
+    Lp = o.apply_laplacian(p_d)
+    assert np.abs(Lp - (f - f.mean())).max() < 1e-9 * np.abs(f).max()
+
+
+def test_projection_leaves_discretely_divergence_free_velocity():
+    """Eq. (NS_incompressibility): after a step the discrete divergence is the
+    solver residual, at most tol * |f| * dt."""
+    wl = inputs.drop_2d()
+    o = oracle.from_workload(wl, tol=1e-12)
+    o.step(wl.dt, 3)
+    div = o.divergence()
+    _, vel, _ = o.get_state()
+    assert np.abs(div).max() < 1e-9
+    assert np.abs(vel[1][0]).max() == 0.0 and np.abs(vel[1][-1]).max() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# a2: GNBC slip (Model 4A and the other models of Sec. 3)
+# ---------------------------------------------------------------------------
+
+def _tilted(nx, ny, h, x0, theta, eps):
+    """Planar interface through (x0, 0) at contact angle theta (measured in
+    fluid 1, fluid 1 on the left), clipped to a strip so the field is periodic."""
+    x = inputs.cell_centres(nx, h)[None, :]
+    y = inputs.cell_centres(ny, h)[:, None]
+    nu = (-math.sin(theta), -math.cos(theta))       # unit normal into fluid 1
+    d = nu[0] * (x - x0) + nu[1] * y
+    phi_r = 0.5 * (1 + np.tanh(d / (2 * eps)))
+    d2 = -nu[0] * (x - (x0 - 0.5 * nx * h)) - nu[1] * y  # parallel interface half a period away
+    phi_l = 0.5 * (1 + np.tanh(d2 / (2 * eps)))
+    return phi_r + phi_l - 1.0
+
+
+def test_model4a_planar_interface_zero_slip_at_equilibrium_angle():
+    """A planar interface has psi exactly linear and kappa = 0; at theta =
+    theta_eq the Model 4A bracket P (d_n psi + cos theta_eq) vanishes, so u^Y is
+    zero to round-off (Eq. Model 4A)."""
+    nx, ny = 256, 32
+    for th_deg in (45.0, 60.0, 120.0):
+        th = math.radians(th_deg)
+        o, h = make2d(nx, ny, Lx=2.0, sigma=1.0, eps=2.0 / 128, theta=th, beta=(10.0, 10.0))
+        o.set_state(_tilted(nx, ny, h, 1.4, th, 2.0 / 128))
+        uY, _, _ = o.eval_wall()
+        x = (np.arange(nx)) * h   # u-face positions
+        win = np.abs(x - 1.4) < 0.15
+        scale = 6.0 / 10.0 * 0.0625 / (2.0 / 128)
+        assert np.abs(uY[0, 0, win]).max() < 1e-10 * scale
+
+
+def test_model4a_planar_interface_integral_constraint():
+    """Eq. (integral constraint u_slip): the integral of u^Y over the contact
+    line region equals (sigma/beta)(cos theta - cos theta_eq) in magnitude; for a
+    right contact line with tau = +x its sign is negative.  The discrete sum
+    converges to it at second order as h -> 0 with eps fixed."""
+    th, th_eq = math.radians(70.0), math.radians(50.0)
+    sigma, beta, eps = 1.0, 10.0, 0.02
+    exact = -(sigma / beta) * (math.cos(th) - math.cos(th_eq))
+    errs = []
+    for nx in (128, 256, 512):
+        ny = nx // 8
+        o, h = make2d(nx, ny, Lx=2.0, sigma=sigma, eps=eps, theta=th_eq, beta=(beta, beta))
+        o.set_state(_tilted(nx, ny, h, 1.4, th, eps))
+        uY, _, _ = o.eval_wall()
+        x = np.arange(nx) * h
+        win = np.abs(x - 1.4) < 0.3
+        errs.append(abs(uY[0, 0, win].sum() * h - exact))
+    assert errs[-1] < 0.01 * abs(exact)
+    assert errs[0] / errs[1] > 3.0 and errs[1] / errs[2] > 3.0, errs
+
+
+def test_prescribed_cap_spurious_slip_only_model4_converges(golden):
+    """Sec. 3.1 and Fig. 7: on the prescribed equilibrium cap (theta = theta_eq
+    = 60 deg, R0 = 0.15, eps ~ h^(2/3) from 0.7h to 1.4h), the maximum spurious
+    slip of Models 4A/4B falls slightly faster than first order, while Models
+    1A, 1B, 2A, 2B, 3A and 3B do not converge."""
+    g = golden["prescribed_field"]
+    th = math.radians(g["theta_eq_deg"])
+    sizes = (64, 128, 256, 512)
+    res = {}
+    for model in g["converging_models"] + g["nonconverging_models"]:
+        vals = []
+        for nx in sizes:
+            ny = nx // 2
+            h = g["Lx"] / nx
+            eps = g["eps_over_delta_range"][0] * h * (nx / sizes[0]) ** (1 - g["eps_scaling_exponent"])
+            R = inputs.cap_radius(g["R0"], th)
+            o, _ = make2d(nx, ny, sigma=1.0, eps=eps, theta=th, beta=(10.0, 10.0))
+            o.set_model(model)
+            o.set_state(inputs.cap_phi_2d(nx, ny, h, R, th, 0.5, eps))
+            uY, _, _ = o.eval_wall()
+            vals.append(np.abs(uY[0, 0]).max())
+        res[model] = np.array(vals)
+    for model in g["converging_models"]:
+        r = res[model]
+        assert np.all(r[:-1] / r[1:] > 2.0), (model, r)          # faster than first order
+        assert r[0] / r[-1] > 8.0 * 1.3, (model, r)
+    for model in g["nonconverging_models"]:
+        r = res[model]
+        assert r[0] / r[-1] < 2.0, (model, r)                      # not convergent
+        assert r.min() > 5 * res["4A"][-1], (model, r)
+
+
+def test_model4a_3d_spherical_cap_spurious_slip_decreases():
+    """3D extension of the Sec. 3.1 analysis: on a prescribed spherical cap at
+    theta = theta_eq the Model 4A slip (with kappa_p the in-plane curvature)
+    decreases under refinement."""
+    th = math.radians(60.0)
+    vals = []
+    for n in (24, 48):
+        h = 1.0 / n
+        eps = 1.2 * h
+        R = inputs.cap_radius(0.3, th, dim=3)
+        o = oracle.Oracle(3, (n, n, n // 2), (1.0, 1.0, 0.5))
+        o.set_fluids(1, 1, 0.1, 0.1, 1.0, eps, 1.0)
+        o.set_wall(2, th, 10.0, 10.0)
+        phi = inputs.cap_phi_3d(n, n, n // 2, h, R, th, 0.5, 0.5, eps)
+        o.set_state(phi)
+        uY, _, _ = o.eval_wall()
+        vals.append(np.abs(uY[0]).max())
+    assert vals[0] / vals[1] > 1.8, vals
+
+
+# ---------------------------------------------------------------------------
+# a9: contact angle and wetted length
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("th_deg", [60.0, 90.0, 120.0])
+def test_contact_angle_of_prescribed_cap(th_deg):
+    """Sec. 3.1: theta is the angle of the phi = 0.5 contour with the wall, from
+    cos(theta) = -d_n phi/|grad phi|; the wetted length of a cap of radius R is
+    2 R sin(theta)."""
+    nx, ny = 256, 128
+    th = math.radians(th_deg)
+    o, h = make2d(nx, ny, sigma=1.0, eps=1.0 / 256)
+    R = inputs.cap_radius(0.15, th)
+    o.set_state(inputs.cap_phi_2d(nx, ny, h, R, th, 0.5, 1.0 / 256))
+    theta, L = o.contact_angle(0)
+    assert abs(math.degrees(theta) - th_deg) < 1.5
+    assert abs(L - 2 * R * math.sin(th)) / (2 * R * math.sin(th)) < 0.01
+
+
+def test_equilibrium_drop_relaxes_toward_theta_eq():
+    """Sec. 5.1: a 90 deg half disc with theta_eq = 60 deg spreads: the contact
+    angle falls toward 60 deg and the wetted length grows toward the exact cap
+    of the same area, while mass stays constant."""
+    wl = inputs.drop_2d()
+    o = oracle.from_workload(wl)
+    th0, L0 = o.contact_angle(0)
+    m0 = o.mass()
+    o.step(wl.dt, 60)
+    th1, L1 = o.contact_angle(0)
+    R_eq = inputs.cap_radius(0.2, math.radians(60.0))
+    assert th1 < th0 - math.radians(5) and th1 > math.radians(60.0)
+    assert L0 < L1 < 2 * R_eq * math.sin(math.radians(60.0))
+    assert abs(o.mass() - m0) / m0 < 1e-13
+
+
+def test_printed_asymmetric_angle(golden):
+    """Sec. 5.2 prints theta_eq = acos(0.38) as 67.7 degrees."""
+    g = golden["couette_asymmetric"]
+    assert abs(math.degrees(math.acos(g["cos_theta_eq"])) - g["theta_eq_deg_printed"]) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# 3D extension in the 2D limit
+# ---------------------------------------------------------------------------
+
+def test_3d_step_reproduces_2d_step_for_y_invariant_data():
+    """The 3D step (walls on z) on data that do not depend on y equals the 2D
+    step (walls on y) to round-off, including the GNBC with kappa_p."""
+    nx, nz = 32, 16
+    h = 1.0 / nx
+    phi2 = inputs.cap_phi_2d(nx, nz, h, 0.2, math.radians(80), 0.5, h)
+    o2 = oracle.Oracle(2, (nx, nz), (1.0, nz * h))
+    o3 = oracle.Oracle(3, (nx, 4, nz), (1.0, 4 * h, nz * h))
+    for o in (o2, o3):
+        o.set_fluids(2.0, 1.0, 0.1, 0.05, 1.0, h, 1.0)
+        o.set_wall_slip_length(0, math.radians(60), h, 0.0)
+        o.set_wall_slip_length(1, math.radians(60), h, 0.0)
+        o.set_solver(1e-12, 100, True)
+    o2.set_state(phi2)
+    phi3 = np.repeat(phi2[:, None, :], 4, axis=1)
+    o3.set_state(phi3)
+    o2.step(1e-4, 3)
+    o3.step(1e-4, 3)
+    p2, v2, q2 = o2.get_state()
+    p3, v3, q3 = o3.get_state()
+    assert np.abs(p3 - p2[:, None, :]).max() < 1e-12
+    assert np.abs(v3[0] - v2[0][:, None, :]).max() < 1e-10 * np.abs(v2[0]).max()
+    assert np.abs(v3[2] - v2[1][:, None, :]).max() < 1e-10 * np.abs(v2[0]).max()
+    assert np.abs(v3[1]).max() < 1e-14
