@@ -1,0 +1,194 @@
+/*
+ * cdi.h -- C ABI of libcdi.so: one GPU time step of the conservative diffuse
+ * interface (CDI) two-phase incompressible solver with the GNBC contact-line
+ * treatment of Brown, Mirjalili, Khanwale & Mani, "A mass-conserving contact
+ * line treatment for second-order conservative phase field methods based on
+ * the generalized Navier boundary condition" (arXiv 2412.16843).
+ *
+ * Problem statement (Sec. 2 and Sec. 4 of the paper):
+ *   d(phi)/dt + div(u phi) = div R,  R = gamma [eps grad phi - phi(1-phi) n]   Eq. (CDI)
+ *   d(rho u)/dt + div[(rho u - S) x u] = -grad P + div[mu(grad u + grad u^T)]
+ *                                        + F_ST                               Eq. (NS_momentum)
+ *   div u = 0                                                                   Eq. (NS_incompressibility)
+ *   F_ST = mu_c grad phi, mu_c from psi = eps ln(phi/(1-phi))                  Eqs. (EB), (chemical potential)
+ *   walls: R.n = 0, u.n = 0, u_slip = u_slip^v + u_slip^Y (Model 4A)           Eqs. (no-flux BC), (no-penetration BC),
+ *                                                                               (slip BC), (u_slip_v), (u_slip_Y)
+ * on a uniform staggered grid (phi, p at cell centres, velocity components on
+ * the faces normal to them), second-order central differences inside,
+ * second-order one-sided wall-normal stencils in the wall rows, first-order
+ * linear extrapolation of the slip-model quantities to the wall, classical
+ * RK4 in time (Sec. 4).  The pressure solve is a geometric multigrid.
+ *
+ * Geometry: 2D grids are nx x ny with walls at y = 0 and y = ny*h; 3D grids
+ * are nx x ny x nz with walls at z = 0 and z = nz*h.  All other axes are
+ * periodic.  The spacing h = Lx/nx is uniform and must equal Ly/ny (and Lz/nz).
+ *
+ * Host array layout (every call that copies fields): contiguous, row-major,
+ * x fastest, no halo.  Cell fields hold nx*ny(*nz) doubles.  The velocity
+ * component normal to the walls (v in 2D, w in 3D) holds one extra face
+ * plane: nx*(ny+1) in 2D, nx*ny*(nz+1) in 3D; its first and last planes lie
+ * on the walls and are zero.  The tangential components hold nx*ny(*nz)
+ * values; entry (i, ...) sits on the face between cells i-1 and i.
+ *
+ * Ownership: the library owns the context.  Device memory is ONE workspace
+ * the caller allocates (size from cdi_workspace_bytes) and binds with
+ * cdi_bind_workspace; the library allocates no device memory.  Host arrays
+ * are copied in or out before the call returns; the caller keeps them.
+ * All device work is issued on the stream given to cdi_bind_workspace.
+ *
+ * Errors: every call returns a cdi_status and never aborts, exits or traps.
+ * cdi_last_error() holds a one-line description of the last failure.
+ * No C++ exception crosses this interface.  Calls on one context are not
+ * thread safe.
+ */
+#ifndef CDI_H
+#define CDI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cdi_ctx cdi_ctx;
+
+typedef enum {
+    CDI_OK = 0,
+    CDI_EINVAL = 1,   /* invalid argument (size, range, NaN parameter)            */
+    CDI_ESTATE = 2,   /* call out of order (e.g. step before a workspace is bound) */
+    CDI_ECUDA = 3,    /* a CUDA runtime call failed; the text says which           */
+    CDI_ENOCONV = 4,  /* the pressure solve hit max_vcycles above its tolerance    */
+    CDI_ENAN = 5,     /* a non-finite value appeared in the state                  */
+    CDI_ETIMEOUT = 6  /* a bounded device-side wait gave up                        */
+} cdi_status;
+
+enum { CDI_FP64 = 0, CDI_FP32_MIXED = 1 };
+enum { CDI_WALL_LO = 0, CDI_WALL_HI = 1, CDI_WALL_BOTH = 2 };
+enum { CDI_WARM_PREV = 0, CDI_WARM_ZERO = 1 };
+/* slip models of Sec. 3, Eqs. (Model 1A) .. (Model 4B); 4A is the default */
+enum { CDI_MODEL_1A = 0, CDI_MODEL_1B, CDI_MODEL_2A, CDI_MODEL_2B,
+       CDI_MODEL_3A, CDI_MODEL_3B, CDI_MODEL_4A, CDI_MODEL_4B };
+
+/* Create a context for a dim-D grid (Sec. 4: uniform staggered Cartesian grid,
+ * periodic sides, walls on the last axis).  dim is 2 or 3; nz is ignored in
+ * 2D.  Every periodic extent must be even and >= 2, the wall extent >= 4;
+ * multigrid coarsens all axes by 2 while every extent stays even and >= 2 and
+ * the coarsest grid must hold at most 64 cells.  precision is CDI_FP64 or
+ * CDI_FP32_MIXED (FP32 state and stencils, FP64 reductions, residuals and
+ * coarse solve).  wall_mask must be 3 (both walls present).
+ * On success *out owns a new context; on failure *out is NULL. */
+cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz,
+                         double Lx, double Ly, double Lz, unsigned wall_mask,
+                         int precision);
+
+/* Bytes of device workspace the context needs (256-byte aligned start). */
+cdi_status cdi_workspace_bytes(const cdi_ctx* ctx, size_t* bytes);
+
+/* Bind the caller's device workspace (at least cdi_workspace_bytes, 256-byte
+ * aligned) and the CUDA stream (a cudaStream_t, NULL for the legacy default
+ * stream) all later work runs on.  Zeroes the state (phi = 0, u = 0, p = 0). */
+cdi_status cdi_bind_workspace(cdi_ctx* ctx, void* dev_ptr, size_t bytes,
+                              void* cuda_stream);
+
+/* Fluid properties: rho = (rho1-rho2) phi + rho2, mu = (mu1-mu2) phi + mu2
+ * (Sec. 2), surface tension sigma (Eq. chemical potential), interface
+ * thickness eps and regularisation strength gamma (Eq. CDI).  gamma >= 0 is
+ * used as given; gamma < 0 selects gamma = max(2.5 |u|_max, -gamma) with
+ * |u|_max the largest face velocity magnitude at the start of each step
+ * (Sec. 5.1).  rho1, rho2 > 0; mu1, mu2 >= 0; eps > 0. */
+cdi_status cdi_set_fluids(cdi_ctx* ctx, double rho1, double rho2, double mu1,
+                          double mu2, double sigma, double eps, double gamma);
+
+/* Wall properties (Eqs. slip BC, u_slip_v, u_slip_Y): equilibrium contact
+ * angle theta_eq (radians, in (0, pi)), slip length l >= 0 giving the
+ * friction beta_i = mu_i / l of each fluid (l = 0: no slip), and the wall's
+ * x velocity U_wall (the tangential direction is +x on both walls).
+ * wall is CDI_WALL_LO, CDI_WALL_HI or CDI_WALL_BOTH.  Call after
+ * cdi_set_fluids (beta uses mu_i). */
+cdi_status cdi_set_wall(cdi_ctx* ctx, int wall, double theta_eq_rad,
+                        double slip_length, double U_wall);
+
+/* The paper's own form of the wall friction: beta = (beta1-beta2) phi + beta2
+ * (Sec. 2), beta1, beta2 > 0, or both +inf for no slip. */
+cdi_status cdi_set_wall_beta(cdi_ctx* ctx, int wall, double beta1, double beta2);
+
+/* Tangential wall velocity (Ux, Uy); Uy is used in 3D only. */
+cdi_status cdi_set_wall_velocity(cdi_ctx* ctx, int wall, double Ux, double Uy);
+
+/* Slip model of Sec. 3 (CDI_MODEL_*); Model 4A (Eq. u_slip_Y) by default. */
+cdi_status cdi_set_model(cdi_ctx* ctx, int model);
+
+/* Copy the phase field from host memory (cell layout above). */
+cdi_status cdi_set_phi(cdi_ctx* ctx, const double* phi_host);
+
+/* Copy the face velocities from host memory (face layouts above); w is
+ * ignored in 2D.  The wall planes of the wall-normal component are forced to
+ * zero (Eq. no-penetration BC). */
+cdi_status cdi_set_velocity(cdi_ctx* ctx, const double* u, const double* v,
+                            const double* w);
+
+/* Pressure solve controls: relative residual tolerance ||f - A p||_2 <=
+ * tol ||f||_2, cap on V-cycles per solve, and the first guess (previous
+ * pressure or zero). */
+cdi_status cdi_set_solver(cdi_ctx* ctx, double tol, int max_vcycles, int warm);
+
+/* Advance nsteps RK4 steps of size dt (Sec. 4): each stage evaluates the phi
+ * flux, wall rows, momentum right-hand side, and projects the stage velocity
+ * (4 pressure solves per step).  Returns CDI_ENOCONV, CDI_ENAN or
+ * CDI_ETIMEOUT on the first failing step, which leaves the state undefined. */
+cdi_status cdi_step(cdi_ctx* ctx, double dt, int nsteps);
+
+/* Total phase volume sum(phi) h^dim, summed in FP64 in a fixed order
+ * (Sec. 2: conserved by the no-flux and no-penetration walls). */
+cdi_status cdi_mass(cdi_ctx* ctx, double* mass_out);
+
+/* Contact angle and wetted length on one wall (Sec. 3.1: angle of the
+ * phi = 0.5 contour with the wall, cos(theta) = -d_n psi / |grad psi|; Sec. 5.1:
+ * wetted length).  phi and the psi gradient are linearly extrapolated to the
+ * wall; the crossings of phi_w = 0.5 are found by linear interpolation,
+ * scanning +x from the column of smallest phi_w.  2D: theta is the mean of
+ * the two crossings and *wetted_len = x_R - x_L.  3D: theta is the mean over
+ * every x line of the wall plane and *wetted_len is the diameter of the disc
+ * of the wetted area.  No crossing: theta = NaN, wetted_len = 0. */
+cdi_status cdi_contact_angle(cdi_ctx* ctx, int wall, double* theta_rad,
+                             double* wetted_len);
+
+/* Copy the state to host memory (any pointer may be NULL). */
+cdi_status cdi_get_fields(cdi_ctx* ctx, double* phi, double* u, double* v,
+                          double* w, double* p);
+
+/* Stage-level evaluations on the current state (used by the parity tests):
+ * right-hand sides of phi (cell layout) and of the face momentum (face
+ * layouts) for the given gamma (gamma < 0: the step's rule). */
+cdi_status cdi_eval_rhs(cdi_ctx* ctx, double gamma, double* rhs_phi,
+                        double* rhs_u, double* rhs_v, double* rhs_w);
+
+/* GNBC quantities on the current state: u^Y and the ghost velocity of every
+ * tangential component, layout [wall][component][wall-plane position]
+ * (wall-plane positions: nx in 2D, nx*ny in 3D, x fastest). */
+cdi_status cdi_eval_wall(cdi_ctx* ctx, double* uY, double* ghost);
+
+/* Pressure solve alone with the current phi: div(grad p / rho_f) = f - mean(f);
+ * p holds the first guess on entry and the zero-mean solution on exit. */
+cdi_status cdi_solve_pressure(cdi_ctx* ctx, const double* f, double* p);
+
+/* Statistics of the last pressure solve: V-cycles, relative residual; and
+ * of the last cdi_step call: largest V-cycle count of one solve. */
+cdi_status cdi_last_stats(cdi_ctx* ctx, int* vcycles, double* resid,
+                          int* max_vcycles_step);
+
+/* Number of kernel launches the last cdi_step issued per time step. */
+cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
+
+/* Text of the last error on this context ("" if none); NULL ctx gives the
+ * last error of cdi_init_grid. */
+const char* cdi_last_error(const cdi_ctx* ctx);
+
+/* Release the context (not the caller's workspace). NULL is accepted. */
+void cdi_destroy(cdi_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDI_H */

@@ -1,0 +1,713 @@
+// C ABI of libcdi.so (declared in include/cdi.h): argument checking, the
+// workspace layout, and the host-side driver of one RK4 time step.
+//
+// One step (Sec. 4: classical RK4; every stage value and the final value are
+// projected, so four pressure solves per step):
+//   for stage k = 1..4:
+//       right-hand side on the stage state        (k_psi, k_cell, k_wall, k_phi_rhs, k_mom)
+//       stage update of phi and rho_f u, u* = M/rho_f   (k_stage_phi, k_stage_mom)
+//       projection: f = div u*/(c dt), multigrid, u = u* - c dt grad p/rho_f
+// The new state lands in the stage buffers, whose role is then swapped with
+// the state buffers.
+#include "cdi_internal.cuh"
+#include "../../include/cdi.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+using namespace cdi;
+
+struct cdi_ctx {
+    Geom g{};
+    double L[3] = {0, 0, 0};
+    int precision = CDI_FP64;
+    // physics
+    PhysDev ph{};
+    double gamma = 0.0;
+    double wall_slip_length[2] = {-1.0, -1.0};
+    bool fluids_set = false;
+    // solver
+    double tol = 1e-10;
+    int max_vcycles = 100;
+    int warm = CDI_WARM_PREV;
+    int npre = 2, npost = 2;
+    // workspace
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool bound = false;
+    // fields (element type double or float, see precision)
+    void* phi_s = nullptr;
+    void* u_s[3] = {nullptr, nullptr, nullptr};
+    void* phi_k = nullptr;
+    void* u_k[3] = {nullptr, nullptr, nullptr};
+    void* acc_phi = nullptr;
+    void* acc_m[3] = {nullptr, nullptr, nullptr};
+    void* rphi = nullptr;
+    void* rm[3] = {nullptr, nullptr, nullptr};
+    void* psi = nullptr;
+    void* nh[3] = {nullptr, nullptr, nullptr};
+    void* muc = nullptr;
+    void* m[3] = {nullptr, nullptr, nullptr};
+    void* wuY = nullptr;
+    void* wghost = nullptr;
+    void* wmuw = nullptr;
+    double* cols = nullptr;
+    double* xfer = nullptr;  // FP64 staging of one face field for host copies
+    MG mg{};
+    double* host_scal = nullptr;
+    // statistics
+    int last_cycles = 0;
+    double last_resid = 0.0;
+    int max_cycles_step = 0;
+    long launches_per_step = 0;
+    std::string err;
+};
+
+namespace {
+
+std::string g_init_error;
+
+cdi_status fail(cdi_ctx* c, cdi_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return st;
+}
+
+cdi_status cuda_check(cdi_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return CDI_OK;
+    return fail(c, CDI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t esize(const cdi_ctx* c) { return c->precision == CDI_FP64 ? sizeof(double) : sizeof(float); }
+
+long nface(const Geom& g, int a) { return g.N + (a == g.W ? g.NP : 0); }
+
+// Fixed-order carving of the workspace; the same walk computes the size.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    void* take(size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+void carve(cdi_ctx* c, char* base, size_t* total) {
+    Carver cv{base};
+    const Geom& g = c->g;
+    const size_t es = esize(c);
+    auto cell = [&]() { return cv.take(g.N * es); };
+    auto face = [&](int a) { return cv.take(nface(g, a) * es); };
+    c->phi_s = cell();
+    c->phi_k = cell();
+    c->acc_phi = cell();
+    c->rphi = cell();
+    c->psi = cell();
+    c->muc = cell();
+    for (int a = 0; a < 3; ++a) {
+        bool on = a < g.D;
+        c->u_s[a] = on ? face(a) : nullptr;
+        c->u_k[a] = on ? face(a) : nullptr;
+        c->acc_m[a] = on ? face(a) : nullptr;
+        c->rm[a] = on ? face(a) : nullptr;
+        c->m[a] = on ? face(a) : nullptr;
+        c->nh[a] = on ? cell() : nullptr;
+    }
+    const size_t nw = (size_t)2 * (g.D - 1) * g.NP;
+    c->wuY = cv.take(nw * es);
+    c->wghost = cv.take(nw * es);
+    c->wmuw = cv.take(nw * es);
+    c->cols = (double*)cv.take((size_t)2 * 3 * g.NP * sizeof(double));
+    c->xfer = (double*)cv.take((size_t)(g.N + g.NP) * sizeof(double));
+    MG& mg = c->mg;
+    for (int l = 0; l < mg.nlev; ++l) {
+        MGLevel& L = mg.lv[l];
+        L.p = (double*)cv.take(L.N * sizeof(double));
+        L.f = (double*)cv.take(L.N * sizeof(double));
+        for (int a = 0; a < 3; ++a)
+            L.beta[a] = (a < g.D) ? (double*)cv.take((L.N + (a == g.W ? L.NP : 0)) * sizeof(double)) : nullptr;
+    }
+    mg.partials = (double*)cv.take(kPartials * sizeof(double));
+    mg.scal = (double*)cv.take(S_NSCAL * sizeof(double));
+    *total = cv.off + 256;
+}
+
+template <typename T>
+__global__ void k_to_double(long n, const T* __restrict__ src, double* __restrict__ dst) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+template <typename T>
+__global__ void k_from_double(long n, const double* __restrict__ src, T* __restrict__ dst) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (T)src[i];
+}
+__global__ void k_set_scalar(double* p, double v) { *p = v; }
+template <typename T>
+__global__ void k_zero_wall_planes(long N, long NP, T* __restrict__ w) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < NP) {
+        w[i] = T(0);
+        w[N + i] = T(0);
+    }
+}
+
+unsigned nblk(long n) { return (unsigned)((n + 255) / 256); }
+
+// copy a host double array into a device field of the context's precision
+cdi_status upload(cdi_ctx* c, void* dst, const double* src, long n) {
+    if (c->precision == CDI_FP64) {
+        cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                                   "cudaMemcpyAsync(H2D)");
+        if (st) return st;
+    } else {
+        cdi_status st = cuda_check(c, cudaMemcpyAsync(c->xfer, src, n * sizeof(double), cudaMemcpyHostToDevice,
+                                                      c->stream), "cudaMemcpyAsync(H2D)");
+        if (st) return st;
+        k_from_double<float><<<nblk(n), 256, 0, c->stream>>>(n, c->xfer, (float*)dst);
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "upload");
+}
+
+cdi_status download(cdi_ctx* c, double* dst, const void* src, long n) {
+    if (!dst) return CDI_OK;
+    if (c->precision == CDI_FP64) {
+        cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                                   "cudaMemcpyAsync(D2H)");
+        if (st) return st;
+    } else {
+        k_to_double<float><<<nblk(n), 256, 0, c->stream>>>(n, (const float*)src, c->xfer);
+        cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, c->xfer, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                                      c->stream), "cudaMemcpyAsync(D2H)");
+        if (st) return st;
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "download");
+}
+
+cdi_status read_scalars(cdi_ctx* c) {
+    cdi_status st = cuda_check(c, cudaMemcpyAsync(c->host_scal, c->mg.scal, S_NSCAL * sizeof(double),
+                                                  cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync(scalars)");
+    if (st) return st;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+}
+
+cdi_status need_bound(cdi_ctx* c) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (!c->bound) return fail(c, CDI_ESTATE, "no workspace bound");
+    return CDI_OK;
+}
+
+// Multigrid solve of div(beta grad p) = f on level 0 (f already mean-free,
+// its norm in S_FNORM, coefficients set); p holds the first guess.
+cdi_status mg_solve(cdi_ctx* c) {
+    const Geom& g = c->g;
+    cudaStream_t s = c->stream;
+    MG& mg = c->mg;
+    launch_resid_norm(g, mg, s);
+    cdi_status st = read_scalars(c);
+    if (st) return st;
+    const double fn = c->host_scal[S_FNORM];
+    double rn = c->host_scal[S_RNORM];
+    int cyc = 0;
+    if (!std::isfinite(fn) || !std::isfinite(rn)) return fail(c, CDI_ENAN, "non-finite pressure right-hand side");
+    if (fn == 0.0) {
+        cudaMemsetAsync(mg.lv[0].p, 0, g.N * sizeof(double), s);
+        c->last_cycles = 0;
+        c->last_resid = 0.0;
+        return CDI_OK;
+    }
+    while (rn > c->tol * fn && cyc < c->max_vcycles) {
+        launch_vcycle(g, mg, c->npre, c->npost, s);
+        launch_resid_norm(g, mg, s);
+        st = read_scalars(c);
+        if (st) return st;
+        rn = c->host_scal[S_RNORM];
+        ++cyc;
+        if (!std::isfinite(rn)) return fail(c, CDI_ENAN, "non-finite pressure residual");
+    }
+    c->last_cycles = cyc;
+    c->last_resid = rn / fn;
+    if (cyc > c->max_cycles_step) c->max_cycles_step = cyc;
+    if (rn > c->tol * fn) {
+        char b[160];
+        snprintf(b, sizeof b, "pressure solve: %d V-cycles left relative residual %.3e > tol %.3e", cyc, rn / fn,
+                 c->tol);
+        return fail(c, CDI_ENOCONV, b);
+    }
+    launch_p_mean_remove(g, mg, s);
+    return CDI_OK;
+}
+
+template <typename T>
+cdi_status project(cdi_ctx* c, const T* phi, T* const* u, double cdt) {
+    const Geom& g = c->g;
+    cudaStream_t s = c->stream;
+    const T* uc[3] = {u[0], u[1], u[2]};
+    launch_div<T>(g, uc, 1.0 / cdt, c->mg, s);
+    launch_sub_mean_and_norm(g, c->mg, s);
+    launch_mg_coef<T>(g, c->ph, phi, c->mg, s);
+    if (c->warm == CDI_WARM_ZERO) cudaMemsetAsync(c->mg.lv[0].p, 0, g.N * sizeof(double), s);
+    cdi_status st = mg_solve(c);
+    if (st) return st;
+    launch_project<T>(g, c->ph, phi, u, cdt, c->mg.lv[0].p, s);
+    return CDI_OK;
+}
+
+template <typename T>
+StageFields<T> stage_fields(cdi_ctx* c, const void* phi, void* const* u) {
+    StageFields<T> f{};
+    f.phi = (const T*)phi;
+    for (int a = 0; a < 3; ++a) {
+        f.u[a] = (const T*)u[a];
+        f.nh[a] = (T*)c->nh[a];
+        f.m[a] = (T*)c->m[a];
+        f.rm[a] = (T*)c->rm[a];
+    }
+    f.psi = (T*)c->psi;
+    f.muc = (T*)c->muc;
+    f.rphi = (T*)c->rphi;
+    f.wuY = (T*)c->wuY;
+    f.wghost = (T*)c->wghost;
+    f.wmuw = (T*)c->wmuw;
+    f.gamma = c->mg.scal + S_GAMMA;
+    return f;
+}
+
+template <typename T>
+void set_gamma(cdi_ctx* c, const void* const* u, double gamma_arg) {
+    if (gamma_arg >= 0.0) {
+        k_set_scalar<<<1, 1, 0, c->stream>>>(c->mg.scal + S_GAMMA, gamma_arg);
+        ++g_launches;
+    } else {
+        const T* uc[3] = {(const T*)u[0], (const T*)u[1], (const T*)u[2]};
+        launch_gamma<T>(c->g, uc, gamma_arg, c->mg, c->stream);
+    }
+}
+
+template <typename T>
+cdi_status step_once(cdi_ctx* c, double dt) {
+    const Geom& g = c->g;
+    cudaStream_t s = c->stream;
+    set_gamma<T>(c, c->u_s, c->gamma);
+    const double ck[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int st = 0; st < 4; ++st) {
+        const void* phi = st == 0 ? c->phi_s : c->phi_k;
+        void* const* u = st == 0 ? c->u_s : c->u_k;
+        StageFields<T> f = stage_fields<T>(c, phi, u);
+        launch_rhs<T>(g, c->ph, f, s);
+        const T* u0[3] = {(const T*)c->u_s[0], (const T*)c->u_s[1], (const T*)c->u_s[2]};
+        const T* rmc[3] = {(const T*)c->rm[0], (const T*)c->rm[1], (const T*)c->rm[2]};
+        T* accm[3] = {(T*)c->acc_m[0], (T*)c->acc_m[1], (T*)c->acc_m[2]};
+        T* uk[3] = {(T*)c->u_k[0], (T*)c->u_k[1], (T*)c->u_k[2]};
+        launch_stage_update<T>(g, c->ph, st, dt, (const T*)c->phi_s, u0, (const T*)c->rphi, rmc, (T*)c->acc_phi, accm,
+                               (T*)c->phi_k, uk, s);
+        const double cdt = (st == 3 ? 1.0 : ck[st + 1]) * dt;
+        cdi_status stt = project<T>(c, (const T*)c->phi_k, uk, cdt);
+        if (stt) return stt;
+    }
+    std::swap(c->phi_s, c->phi_k);
+    for (int a = 0; a < 3; ++a) std::swap(c->u_s[a], c->u_k[a]);
+    return cuda_check(c, cudaGetLastError(), "kernel launch");
+}
+
+cdi_status check_wall(cdi_ctx* c, int wall) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (wall < 0 || wall > 2) return fail(c, CDI_EINVAL, "wall must be CDI_WALL_LO, CDI_WALL_HI or CDI_WALL_BOTH");
+    return CDI_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double Lx, double Ly, double Lz,
+                         unsigned wall_mask, int precision) {
+    if (!out) return fail(nullptr, CDI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(nullptr, CDI_EINVAL, "dim must be 2 or 3");
+    if (wall_mask != 3u) return fail(nullptr, CDI_EINVAL, "wall_mask must be 3 (walls on both ends of the last axis)");
+    if (precision != CDI_FP64 && precision != CDI_FP32_MIXED) return fail(nullptr, CDI_EINVAL, "bad precision");
+    int n[3] = {nx, ny, dim == 3 ? nz : 1};
+    double L[3] = {Lx, Ly, dim == 3 ? Lz : 0.0};
+    const int W = dim - 1;
+    for (int a = 0; a < dim; ++a) {
+        if (a == W) {
+            if (n[a] < 4) return fail(nullptr, CDI_EINVAL, "the wall axis needs at least 4 cells");
+        } else if (n[a] < 2 || n[a] % 2) {
+            return fail(nullptr, CDI_EINVAL, "periodic extents must be even and >= 2");
+        }
+        if (!(L[a] > 0.0) || !std::isfinite(L[a])) return fail(nullptr, CDI_EINVAL, "domain lengths must be > 0");
+    }
+    const double h = Lx / nx;
+    for (int a = 1; a < dim; ++a)
+        if (std::fabs(L[a] / n[a] - h) > 1e-12 * h) return fail(nullptr, CDI_EINVAL, "the spacing must be uniform");
+    const long N = (long)n[0] * n[1] * n[2];
+    if (N > (1L << 31)) return fail(nullptr, CDI_EINVAL, "grid too large");
+    cdi_ctx* c = new (std::nothrow) cdi_ctx();
+    if (!c) return fail(nullptr, CDI_EINVAL, "out of host memory");
+    c->g.D = dim;
+    for (int a = 0; a < 3; ++a) c->g.n[a] = n[a];
+    c->g.W = W;
+    c->g.N = N;
+    c->g.NP = (dim == 2) ? (long)n[0] : (long)n[0] * n[1];
+    c->g.h = h;
+    for (int a = 0; a < 3; ++a) c->L[a] = L[a];
+    c->precision = precision;
+    c->ph.delta = precision == CDI_FP64 ? 1e-12 : 1e-6;
+    c->ph.tau = precision == CDI_FP64 ? 1e-12 : 1e-6;
+    c->ph.model = M4A;
+    for (int s = 0; s < 2; ++s) {
+        c->ph.wall[s].costh = 0.0;
+        c->ph.wall[s].beta1 = c->ph.wall[s].beta2 = INFINITY;
+        c->ph.wall[s].noslip = 1;
+    }
+    // multigrid hierarchy: halve every axis while all extents stay even and >= 2
+    MG& mg = c->mg;
+    mg.nlev = 1;
+    int ln[3] = {n[0], n[1], n[2]};
+    double lh = h;
+    auto set_level = [&](int l) {
+        MGLevel& Lv = mg.lv[l];
+        for (int a = 0; a < 3; ++a) Lv.n[a] = ln[a];
+        Lv.N = (long)ln[0] * ln[1] * ln[2];
+        Lv.NP = (dim == 2) ? ln[0] : (long)ln[0] * ln[1];
+        Lv.h = lh;
+    };
+    set_level(0);
+    for (;;) {
+        bool ok = mg.nlev < kMaxLevels;
+        for (int a = 0; a < dim; ++a)
+            if (ln[a] % 2 || ln[a] / 2 < 2) ok = false;
+        if (!ok) break;
+        for (int a = 0; a < dim; ++a) ln[a] /= 2;
+        lh *= 2.0;
+        set_level(mg.nlev++);
+    }
+    if (mg.lv[mg.nlev - 1].N > kMaxCoarse) {
+        delete c;
+        return fail(nullptr, CDI_EINVAL, "the coarsest multigrid level has more than 64 cells; use extents with more "
+                                         "factors of two");
+    }
+    size_t total = 0;
+    carve(c, nullptr, &total);
+    c->ws_bytes = total;
+    *out = c;
+    return CDI_OK;
+}
+
+cdi_status cdi_workspace_bytes(const cdi_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return fail(nullptr, CDI_EINVAL, "null argument");
+    *bytes = c->ws_bytes;
+    return CDI_OK;
+}
+
+cdi_status cdi_bind_workspace(cdi_ctx* c, void* dev_ptr, size_t bytes, void* stream) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (!dev_ptr) return fail(c, CDI_EINVAL, "workspace pointer is NULL");
+    if (bytes < c->ws_bytes) return fail(c, CDI_EINVAL, "workspace too small");
+    if (((uintptr_t)dev_ptr) & 255u) return fail(c, CDI_EINVAL, "workspace must be 256-byte aligned");
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, dev_ptr) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(c, CDI_EINVAL, "workspace is not device memory");
+    }
+    c->ws = (char*)dev_ptr;
+    c->stream = (cudaStream_t)stream;
+    size_t total = 0;
+    carve(c, c->ws, &total);
+    if (!c->host_scal) {
+        cdi_status st = cuda_check(c, cudaMallocHost((void**)&c->host_scal, S_NSCAL * sizeof(double)),
+                                   "cudaMallocHost");
+        if (st) return st;
+    }
+    cdi_status st = cuda_check(c, cudaMemsetAsync(c->ws, 0, c->ws_bytes - 256, c->stream), "cudaMemsetAsync");
+    if (st) return st;
+    st = cuda_check(c, cudaStreamSynchronize(c->stream), "bind");
+    if (st) return st;
+    c->bound = true;
+    return CDI_OK;
+}
+
+cdi_status cdi_set_fluids(cdi_ctx* c, double rho1, double rho2, double mu1, double mu2, double sigma, double eps,
+                          double gamma) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    double v[7] = {rho1, rho2, mu1, mu2, sigma, eps, gamma};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(c, CDI_EINVAL, "fluid parameters must be finite");
+    if (!(rho1 > 0) || !(rho2 > 0)) return fail(c, CDI_EINVAL, "densities must be > 0");
+    if (mu1 < 0 || mu2 < 0) return fail(c, CDI_EINVAL, "viscosities must be >= 0");
+    if (!(eps > 0)) return fail(c, CDI_EINVAL, "eps must be > 0");
+    c->ph.rho1 = rho1; c->ph.rho2 = rho2; c->ph.mu1 = mu1; c->ph.mu2 = mu2;
+    c->ph.sigma = sigma; c->ph.eps = eps;
+    c->gamma = gamma;
+    c->fluids_set = true;
+    for (int s = 0; s < 2; ++s)
+        if (c->wall_slip_length[s] > 0.0) {
+            c->ph.wall[s].beta1 = mu1 / c->wall_slip_length[s];
+            c->ph.wall[s].beta2 = mu2 / c->wall_slip_length[s];
+        }
+    return CDI_OK;
+}
+
+cdi_status cdi_set_wall(cdi_ctx* c, int wall, double theta_eq, double slip_length, double U_wall) {
+    cdi_status st = check_wall(c, wall);
+    if (st) return st;
+    if (!(theta_eq > 0.0 && theta_eq < M_PI)) return fail(c, CDI_EINVAL, "theta_eq must lie in (0, pi)");
+    if (!(slip_length >= 0.0) || !std::isfinite(slip_length)) return fail(c, CDI_EINVAL, "slip length must be >= 0");
+    if (!std::isfinite(U_wall)) return fail(c, CDI_EINVAL, "wall velocity must be finite");
+    if (!c->fluids_set) return fail(c, CDI_ESTATE, "call cdi_set_fluids before cdi_set_wall");
+    for (int s = 0; s < 2; ++s) {
+        if (wall != 2 && wall != s) continue;
+        WallDev& w = c->ph.wall[s];
+        w.costh = std::cos(theta_eq);
+        w.U[0] = U_wall;
+        c->wall_slip_length[s] = slip_length;
+        if (slip_length == 0.0) {
+            w.noslip = 1;
+            w.beta1 = w.beta2 = INFINITY;
+        } else {
+            w.noslip = 0;
+            w.beta1 = c->ph.mu1 / slip_length;
+            w.beta2 = c->ph.mu2 / slip_length;
+            if (!(w.beta1 > 0) || !(w.beta2 > 0))
+                return fail(c, CDI_EINVAL, "slip length form needs mu1, mu2 > 0 (use cdi_set_wall_beta)");
+        }
+    }
+    return CDI_OK;
+}
+
+cdi_status cdi_set_wall_beta(cdi_ctx* c, int wall, double beta1, double beta2) {
+    cdi_status st = check_wall(c, wall);
+    if (st) return st;
+    const bool inf1 = std::isinf(beta1) && beta1 > 0, inf2 = std::isinf(beta2) && beta2 > 0;
+    if (inf1 != inf2) return fail(c, CDI_EINVAL, "beta1 and beta2 must both be finite or both +inf");
+    if (!inf1 && (!(beta1 > 0) || !(beta2 > 0) || !std::isfinite(beta1) || !std::isfinite(beta2)))
+        return fail(c, CDI_EINVAL, "beta must be > 0");
+    for (int s = 0; s < 2; ++s) {
+        if (wall != 2 && wall != s) continue;
+        WallDev& w = c->ph.wall[s];
+        w.beta1 = beta1;
+        w.beta2 = beta2;
+        w.noslip = inf1 ? 1 : 0;
+        c->wall_slip_length[s] = -1.0;
+    }
+    return CDI_OK;
+}
+
+cdi_status cdi_set_wall_velocity(cdi_ctx* c, int wall, double Ux, double Uy) {
+    cdi_status st = check_wall(c, wall);
+    if (st) return st;
+    if (!std::isfinite(Ux) || !std::isfinite(Uy)) return fail(c, CDI_EINVAL, "wall velocity must be finite");
+    for (int s = 0; s < 2; ++s) {
+        if (wall != 2 && wall != s) continue;
+        c->ph.wall[s].U[0] = Ux;
+        c->ph.wall[s].U[1] = Uy;
+    }
+    return CDI_OK;
+}
+
+cdi_status cdi_set_model(cdi_ctx* c, int model) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (model < CDI_MODEL_1A || model > CDI_MODEL_4B) return fail(c, CDI_EINVAL, "unknown slip model");
+    c->ph.model = model;
+    return CDI_OK;
+}
+
+cdi_status cdi_set_phi(cdi_ctx* c, const double* phi) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    if (!phi) return fail(c, CDI_EINVAL, "phi is NULL");
+    for (long i = 0; i < c->g.N; ++i)
+        if (!std::isfinite(phi[i])) return fail(c, CDI_ENAN, "phi holds a non-finite value");
+    return upload(c, c->phi_s, phi, c->g.N);
+}
+
+cdi_status cdi_set_velocity(cdi_ctx* c, const double* u, const double* v, const double* w) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    const double* comps[3] = {u, v, w};
+    for (int a = 0; a < c->g.D; ++a) {
+        if (!comps[a]) return fail(c, CDI_EINVAL, "velocity component is NULL");
+        const long n = nface(c->g, a);
+        for (long i = 0; i < n; ++i)
+            if (!std::isfinite(comps[a][i])) return fail(c, CDI_ENAN, "velocity holds a non-finite value");
+        st = upload(c, c->u_s[a], comps[a], n);
+        if (st) return st;
+    }
+    // no penetration: the wall planes of the wall-normal component are zero
+    void* wn = c->u_s[c->g.W];
+    if (c->precision == CDI_FP64)
+        k_zero_wall_planes<double><<<nblk(c->g.NP), 256, 0, c->stream>>>(c->g.N, c->g.NP, (double*)wn);
+    else
+        k_zero_wall_planes<float><<<nblk(c->g.NP), 256, 0, c->stream>>>(c->g.N, c->g.NP, (float*)wn);
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "set_velocity");
+}
+
+cdi_status cdi_set_solver(cdi_ctx* c, double tol, int max_vcycles, int warm) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(c, CDI_EINVAL, "tol must be > 0");
+    if (max_vcycles < 1) return fail(c, CDI_EINVAL, "max_vcycles must be >= 1");
+    if (warm != CDI_WARM_PREV && warm != CDI_WARM_ZERO) return fail(c, CDI_EINVAL, "bad warm-start mode");
+    c->tol = tol;
+    c->max_vcycles = max_vcycles;
+    c->warm = warm;
+    return CDI_OK;
+}
+
+cdi_status cdi_step(cdi_ctx* c, double dt, int nsteps) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, CDI_EINVAL, "dt must be > 0");
+    if (nsteps < 0) return fail(c, CDI_EINVAL, "nsteps must be >= 0");
+    if (!c->fluids_set) return fail(c, CDI_ESTATE, "fluids not set");
+    c->max_cycles_step = 0;
+    const long l0 = g_launches;
+    for (int n = 0; n < nsteps; ++n) {
+        st = (c->precision == CDI_FP64) ? step_once<double>(c, dt) : step_once<float>(c, dt);
+        if (st) return st;
+    }
+    if (nsteps > 0) c->launches_per_step = (g_launches - l0) / nsteps;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "cdi_step");
+}
+
+cdi_status cdi_mass(cdi_ctx* c, double* mass_out) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    if (!mass_out) return fail(c, CDI_EINVAL, "mass_out is NULL");
+    if (c->precision == CDI_FP64) launch_mass<double>(c->g, (const double*)c->phi_s, c->mg, c->stream);
+    else launch_mass<float>(c->g, (const float*)c->phi_s, c->mg, c->stream);
+    st = read_scalars(c);
+    if (st) return st;
+    *mass_out = c->host_scal[S_MASS];
+    return CDI_OK;
+}
+
+cdi_status cdi_contact_angle(cdi_ctx* c, int wall, double* theta, double* wetted) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    if (wall != 0 && wall != 1) return fail(c, CDI_EINVAL, "wall must be CDI_WALL_LO or CDI_WALL_HI");
+    if (!theta || !wetted) return fail(c, CDI_EINVAL, "null output");
+    if (c->precision == CDI_FP64)
+        launch_wall_columns<double>(c->g, c->ph, (const double*)c->phi_s, (double*)c->psi, c->cols, c->stream);
+    else
+        launch_wall_columns<float>(c->g, c->ph, (const float*)c->phi_s, (float*)c->psi, c->cols, c->stream);
+    launch_contact_line(c->g, wall, c->cols, c->mg, c->stream);
+    st = read_scalars(c);
+    if (st) return st;
+    *theta = c->host_scal[S_THETA];
+    *wetted = c->host_scal[S_WETTED];
+    return CDI_OK;
+}
+
+cdi_status cdi_get_fields(cdi_ctx* c, double* phi, double* u, double* v, double* w, double* p) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    st = download(c, phi, c->phi_s, c->g.N);
+    if (st) return st;
+    double* comps[3] = {u, v, w};
+    for (int a = 0; a < c->g.D; ++a) {
+        st = download(c, comps[a], c->u_s[a], nface(c->g, a));
+        if (st) return st;
+    }
+    if (p) {
+        st = cuda_check(c, cudaMemcpyAsync(p, c->mg.lv[0].p, c->g.N * sizeof(double), cudaMemcpyDeviceToHost,
+                                           c->stream), "cudaMemcpyAsync(p)");
+        if (st) return st;
+        st = cuda_check(c, cudaStreamSynchronize(c->stream), "get_fields");
+    }
+    return st;
+}
+
+cdi_status cdi_eval_rhs(cdi_ctx* c, double gamma, double* rphi, double* ru, double* rv, double* rw) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    if (c->precision == CDI_FP64) {
+        set_gamma<double>(c, c->u_s, gamma >= 0 ? gamma : c->gamma);
+        launch_rhs<double>(c->g, c->ph, stage_fields<double>(c, c->phi_s, c->u_s), c->stream);
+    } else {
+        set_gamma<float>(c, c->u_s, gamma >= 0 ? gamma : c->gamma);
+        launch_rhs<float>(c->g, c->ph, stage_fields<float>(c, c->phi_s, c->u_s), c->stream);
+    }
+    st = cuda_check(c, cudaGetLastError(), "eval_rhs launch");
+    if (st) return st;
+    st = download(c, rphi, c->rphi, c->g.N);
+    if (st) return st;
+    double* comps[3] = {ru, rv, rw};
+    for (int a = 0; a < c->g.D; ++a) {
+        st = download(c, comps[a], c->rm[a], nface(c->g, a));
+        if (st) return st;
+    }
+    return CDI_OK;
+}
+
+cdi_status cdi_eval_wall(cdi_ctx* c, double* uY, double* ghost) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    if (c->precision == CDI_FP64) {
+        set_gamma<double>(c, c->u_s, c->gamma >= 0 ? c->gamma : 0.0);
+        launch_rhs<double>(c->g, c->ph, stage_fields<double>(c, c->phi_s, c->u_s), c->stream);
+    } else {
+        set_gamma<float>(c, c->u_s, c->gamma >= 0 ? c->gamma : 0.0);
+        launch_rhs<float>(c->g, c->ph, stage_fields<float>(c, c->phi_s, c->u_s), c->stream);
+    }
+    const long nw = 2L * (c->g.D - 1) * c->g.NP;
+    st = download(c, uY, c->wuY, nw);
+    if (st) return st;
+    return download(c, ghost, c->wghost, nw);
+}
+
+cdi_status cdi_solve_pressure(cdi_ctx* c, const double* f, double* p) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    if (!f || !p) return fail(c, CDI_EINVAL, "null array");
+    const Geom& g = c->g;
+    MG& mg = c->mg;
+    cudaStream_t s = c->stream;
+    st = cuda_check(c, cudaMemcpyAsync(mg.lv[0].f, f, g.N * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
+    if (st) return st;
+    st = cuda_check(c, cudaMemcpyAsync(mg.lv[0].p, p, g.N * sizeof(double), cudaMemcpyHostToDevice, s), "copy p");
+    if (st) return st;
+    launch_sum_f(g, mg, s);
+    launch_sub_mean_and_norm(g, mg, s);
+    if (c->precision == CDI_FP64) launch_mg_coef<double>(g, c->ph, (const double*)c->phi_s, mg, s);
+    else launch_mg_coef<float>(g, c->ph, (const float*)c->phi_s, mg, s);
+    st = mg_solve(c);
+    if (st) return st;
+    st = cuda_check(c, cudaMemcpyAsync(p, mg.lv[0].p, g.N * sizeof(double), cudaMemcpyDeviceToHost, s), "copy p");
+    if (st) return st;
+    return cuda_check(c, cudaStreamSynchronize(s), "solve_pressure");
+}
+
+cdi_status cdi_last_stats(cdi_ctx* c, int* vcycles, double* resid, int* max_vcycles_step) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (vcycles) *vcycles = c->last_cycles;
+    if (resid) *resid = c->last_resid;
+    if (max_vcycles_step) *max_vcycles_step = c->max_cycles_step;
+    return CDI_OK;
+}
+
+cdi_status cdi_launches_per_step(cdi_ctx* c, long* launches) {
+    if (!c || !launches) return fail(c, CDI_EINVAL, "null argument");
+    *launches = c->launches_per_step;
+    return CDI_OK;
+}
+
+const char* cdi_last_error(const cdi_ctx* c) {
+    if (!c) return g_init_error.c_str();
+    return c->err.c_str();
+}
+
+void cdi_destroy(cdi_ctx* c) {
+    if (!c) return;
+    if (c->host_scal) cudaFreeHost(c->host_scal);
+    delete c;
+}
+
+}  // extern "C"

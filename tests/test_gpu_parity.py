@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Per-call checks compare every element of a stage result; time-stepping checks
+compare every field after many steps.  FP64 bar: 1e-12 relative per call and
+1e-10 relative (max-norm difference over the field's max norm, p zero-mean)
+after 1000 steps.  The two sides differ only in rounding order (fused
+multiply-add, reduction order, libm).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_16843_gb300 import cdi, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2412_16843_gb300 import build
+    build.build()
+    cdi.load()
+
+
+def rel(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return np.abs(a - b).max() / scale
+
+
+def pair(wl, tol=1e-12, precision=cdi.FP64):
+    g = cdi.from_workload(wl, precision=precision, tol=tol)
+    o = oracle.from_workload(wl, tol=tol)
+    return g, o
+
+
+def moving_state(wl, nsteps=5):
+    """A state with a nonzero velocity: the oracle's state after a few steps."""
+    o = oracle.from_workload(wl, tol=1e-12)
+    o.step(wl.dt, nsteps)
+    return o.get_state()
+
+
+# ---------------------------------------------------------------------------
+# per-call parity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("model", ["4A", "1A", "2B", "3B", "4B"])
+def test_rhs_and_wall_parity_2d(model):
+    wl = inputs.drop_2d(64, 32)
+    phi, vel, p = moving_state(wl)
+    g, o = pair(wl)
+    g.set_model(model)
+    o.set_model(model)
+    g.set_state(phi, vel)
+    o.set_state(phi, vel, p)
+    rg, mg = g.eval_rhs(gamma=1.0)
+    ro, mo = o.eval_rhs(gamma=1.0)
+    assert rel(rg, ro) < 1e-12
+    for a in range(2):
+        assert rel(mg[a], mo[a]) < 1e-12, a
+    uYg, ghg = g.eval_wall()
+    uYo, gho, _ = o.eval_wall()
+    assert rel(uYg, uYo) < 1e-12
+    assert rel(ghg, gho) < 1e-12
+
+
+def test_rhs_and_wall_parity_3d():
+    n = (16, 8, 12)
+    h = 1.0 / 16
+    L = tuple(x * h for x in n)
+    rng = np.random.default_rng(11)
+    phi = inputs.add_noise(inputs.cap_phi_3d(*n, h, 0.3, math.radians(80), 0.5, 0.25, 1.3 * h), 1e-3, 5)
+    vel = [0.05 * rng.standard_normal((n[2], n[1], n[0])), 0.05 * rng.standard_normal((n[2], n[1], n[0])),
+           0.05 * rng.standard_normal((n[2] + 1, n[1], n[0]))]
+    vel[2][0] = 0.0
+    vel[2][-1] = 0.0
+    g = cdi.Solver(3, n, L)
+    o = oracle.Oracle(3, n, L)
+    for s in (g, o):
+        s.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, 1.3 * h, 1.0)
+    g.set_wall(cdi.WALL_LO, math.radians(60), h, 0.02)
+    g.set_wall(cdi.WALL_HI, math.radians(120), 2 * h, -0.03)
+    g.set_wall_velocity(cdi.WALL_LO, 0.02, 0.01)
+    o.set_wall_slip_length(0, math.radians(60), h, 0.02, 0.01)
+    o.set_wall_slip_length(1, math.radians(120), 2 * h, -0.03)
+    g.set_state(phi, vel)
+    o.set_state(phi, vel)
+    rg, mg = g.eval_rhs(gamma=1.0)
+    ro, mo = o.eval_rhs(gamma=1.0)
+    assert rel(rg, ro) < 1e-12
+    for a in range(3):
+        assert rel(mg[a], mo[a]) < 1e-12, a
+    uYg, ghg = g.eval_wall()
+    uYo, gho, _ = o.eval_wall()
+    assert rel(uYg, uYo) < 1e-12
+    assert rel(ghg, gho) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pressure_solve_parity(dim):
+    n = (64, 32) if dim == 2 else (16, 16, 8)
+    h = 1.0 / n[0]
+    L = tuple(x * h for x in n)
+    rng = np.random.default_rng(2)
+    phi = np.clip(rng.uniform(-0.2, 1.2, size=n[::-1]), 0, 1)
+    f = rng.standard_normal(n[::-1])
+    g = cdi.Solver(dim, n, L)
+    o = oracle.Oracle(dim, n, L)
+    for s in (g, o):
+        s.set_fluids(20.0, 1.0, 0.1, 0.1, 0.0, h, 0.0)
+    g.set_solver(1e-12, 100, cdi.WARM_ZERO)
+    o.set_solver(1e-12, 100, False)
+    g.set_state(phi)
+    o.set_state(phi)
+    pg = g.solve_pressure(f)
+    po, cyc, _ = o.poisson(f)
+    assert g.last_stats()["cycles"] == cyc
+    assert rel(pg, po) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# time-stepping parity
+# ---------------------------------------------------------------------------
+
+def test_step_parity_drop_1000_steps():
+    """64x32 equilibrium drop (FP64 plain method), 1000 steps: every field
+    within 1e-10 relative of the oracle; mass conserved to round-off."""
+    wl = inputs.drop_2d(64, 32)
+    g, o = pair(wl, tol=1e-12)
+    m0 = g.mass()
+    assert abs(m0 - o.mass()) < 1e-15
+    g.step(wl.dt, 1000)
+    o.step(wl.dt, 1000)
+    phi_g, vel_g, p_g = g.get_fields()
+    phi_o, vel_o, p_o = o.get_state()
+    assert rel(phi_g, phi_o) < 1e-10
+    for a in range(2):
+        assert rel(vel_g[a], vel_o[a]) < 1e-10, a
+    assert rel(p_g - p_g.mean(), p_o - p_o.mean()) < 1e-10
+    assert abs(g.mass() - m0) / m0 < 1e-13
+    tg, Lg = g.contact_angle(0)
+    to, Lo = o.contact_angle(0)
+    assert abs(tg - to) < 1e-9 and abs(Lg - Lo) < 1e-9
+
+
+def test_step_parity_couette_cut():
+    """128x32 cut of the two-phase Couette case (moving walls, slip length dx)."""
+    wl = inputs.couette_2d(128, 32, 1.0)
+    g, o = pair(wl, tol=1e-12)
+    g.step(wl.dt, 100)
+    o.step(wl.dt, 100)
+    phi_g, vel_g, p_g = g.get_fields()
+    phi_o, vel_o, p_o = o.get_state()
+    assert rel(phi_g, phi_o) < 1e-11
+    for a in range(2):
+        assert rel(vel_g[a], vel_o[a]) < 1e-10, a
+
+
+def test_step_parity_3d_drop():
+    """16x16x12 3D drop with density ratio 10 and noise, 10 steps."""
+    n = (16, 16, 12)
+    h = 1.0 / 16
+    L = tuple(x * h for x in n)
+    phi = inputs.add_noise(inputs.cap_phi_3d(*n, h, 0.3, math.pi / 2, 0.5, 0.5, h), 1e-3, 12345)
+    g = cdi.Solver(3, n, L)
+    o = oracle.Oracle(3, n, L)
+    for s in (g, o):
+        s.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, 1.0)
+        s.set_solver(1e-12, 100)
+    g.set_wall(cdi.WALL_BOTH, math.radians(60), h, 0.0)
+    o.set_wall_slip_length(2, math.radians(60), h, 0.0)
+    g.set_state(phi)
+    o.set_state(phi)
+    g.step(5e-5, 10)
+    o.step(5e-5, 10)
+    phi_g, vel_g, _ = g.get_fields()
+    phi_o, vel_o, _ = o.get_state()
+    assert rel(phi_g, phi_o) < 1e-11
+    for a in range(3):
+        assert rel(vel_g[a], vel_o[a]) < 1e-10, a
+
+
+def test_couette_full_size_512x128_parity():
+    """The full 512x128 Couette workload in the launch configuration the bench
+    times (FP64, tol 1e-10, warm start): 3 steps, every field vs the oracle."""
+    wl = inputs.couette_2d(512, 128, 1.0)
+    g, o = pair(wl, tol=1e-10)
+    g.step(wl.dt, 3)
+    o.step(wl.dt, 3)
+    phi_g, vel_g, _ = g.get_fields()
+    phi_o, vel_o, _ = o.get_state()
+    assert rel(phi_g, phi_o) < 1e-11
+    for a in range(2):
+        assert rel(vel_g[a], vel_o[a]) < 1e-9, a
+
+
+# ---------------------------------------------------------------------------
+# invariants and error paths on the GPU
+# ---------------------------------------------------------------------------
+
+def test_contact_angle_of_prescribed_cap_gpu():
+    nx, ny = 256, 128
+    h = 1.0 / nx
+    th = math.radians(60)
+    R = inputs.cap_radius(0.15, th)
+    phi = inputs.cap_phi_2d(nx, ny, h, R, th, 0.5, h)
+    g = cdi.Solver(2, (nx, ny), (1.0, ny * h))
+    g.set_fluids(1, 1, 0.1, 0.1, 1.0, h, 1.0)
+    g.set_state(phi)
+    o = oracle.Oracle(2, (nx, ny), (1.0, ny * h))
+    o.set_fluids(1, 1, 0.1, 0.1, 1.0, h, 1.0)
+    o.set_state(phi)
+    tg, Lg = g.contact_angle(0)
+    to, Lo = o.contact_angle(0)
+    assert abs(tg - to) < 1e-12 and abs(Lg - Lo) < 1e-12
+    assert abs(math.degrees(tg) - 60) < 1.5
+
+
+def test_no_convergence_is_reported():
+    wl = inputs.drop_2d(64, 32)
+    g = cdi.from_workload(wl, tol=1e-14, max_vcycles=1)
+    with pytest.raises(cdi.CdiError) as e:
+        g.step(wl.dt, 1)
+    assert e.value.status == 4
+
+
+def test_nan_input_is_rejected():
+    wl = inputs.drop_2d(64, 32)
+    g = cdi.from_workload(wl)
+    bad = wl.phi0.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(cdi.CdiError) as e:
+        g.set_phi(bad)
+    assert e.value.status == 5
