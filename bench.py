@@ -1,0 +1,368 @@
+"""Throughput of one full CDI + NS time step (4 RK stages, 4 pressure solves to
+a 1e-8 relative residual) on the two-phase Couette workload, 512x128 cells,
+FP64, through the libcdi C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints ONE JSON line on rank 0.  The GPU arm times K steps with CUDA events on
+the library's stream, with a 256 MiB device write (larger than the 129 MB L2)
+before every timed step; `value` is whole-job Mcell-steps/s.  `e2e` is the
+same metric when every step uploads the state from pinned host memory and
+reads every field back.  The reference arm (--impl reference) times the FP64
+CPU oracle on the host cores.  With N > 1 GPUs the workload is replicated, one
+independent replica per rank (the single grid does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-steps/s per full CDI+NS step, learned/batched vs plain, same accuracy"
+UNIT = "Mcell-steps/s"
+WORKLOAD = "couette2d_512x128_fp64"
+PRESSURE_TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--roofline-kernel", default="step")
+    ap.add_argument("--exec", default="persistent", choices=["persistent", "kernels"])
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2412_16843_gb300 import inputs
+    return inputs.couette_2d(512, 128, 1.0)
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch of the kernels the roofline can name
+# (unique words each launch must read or write at least once)
+# ---------------------------------------------------------------------------
+def vcycle_words(D):
+    """FP64 words per finest-level cell moved by one V-cycle plus its residual
+    check: 2+2 red-black sweeps (p read+write, f, D face coefficients), the
+    residual-restriction pass, the prolongation, summed over the hierarchy
+    (factor 1/(1 - 2^-D)), and the residual norm of the convergence test."""
+    fine = 4 * (3 + D) + (2 + D) + 3.0 / 2 ** D + 2
+    return fine / (1 - 2.0 ** -D) + (2 + D)
+
+
+def step_bytes(D, N, word, vcycles_per_step):
+    """Algorithmic bytes of one full step: per RK stage the fused stencil
+    minimum (read the stage state and y^n, read+write the accumulator, write
+    the next stage: 5(1+D) words), per pressure solve the divergence (D+1),
+    the projection (2D+1) and the V-cycles, in FP64."""
+    stencil = 4 * 5 * (1 + D) * word
+    solves = 8 * (4 * (3 + 2 * D + 1) + vcycles_per_step * vcycle_words(D))
+    return N * (stencil + solves)
+
+
+def algorithmic_bytes(kernel, dim, N, NP, word):
+    D = dim
+    words = {
+        "rbgs0": 0.5 * N + 0.5 * N + 0.5 * N + D * N + NP,  # p read/write of one colour, f, face coefficients
+        "mom": (3 * D + 2) * N + NP,                           # u, m, phi, mu_c in; rhs of every component out
+        "phi_rhs": (3 * D + 2) * N + NP,                       # phi, u, n in; rhs_phi, m out
+        "cell": (3 + D) * N,                                   # phi, psi in; n, mu_c out
+        "psi": 2 * N,
+        "stage_mom": (2 + 5 * D) * N,
+    }[kernel]
+    if kernel == "rbgs0":
+        return words * 8  # the multigrid works in FP64 in every precision
+    return words * word
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (the summary stores the source hash)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    return ent["dram_bytes_per_launch"] if h == ent["source_sha256_16"] else None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_rate(wl, steps, budget_s=None):
+    """Time the FP64 oracle on `steps` steps of the workload; returns
+    (Mcell-steps/s, seconds, sample description)."""
+    import oracle
+    o = oracle.from_workload(wl, tol=PRESSURE_TOL)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(steps):
+        o.step(wl.dt, 1)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return wl.cells * done / dt / 1e6, dt, "%d steps of the %dx%d workload from its initial state" % (
+        done, wl.n[0], wl.n[1])
+
+
+def reference_arm(args, rank, world):
+    from paper_2412_16843_gb300 import inputs
+    if rank != 0:
+        return
+    wl_full = workload()
+    # one untimed full-size step sizes the per-step sample so the run ends in minutes
+    import oracle
+    o = oracle.from_workload(wl_full, tol=PRESSURE_TOL)
+    t0 = time.perf_counter()
+    o.step(wl_full.dt, 1)
+    t_full = time.perf_counter() - t0
+    budget = 150.0
+    nx = 512
+    while nx > 32 and (args.steps + args.warmup) * t_full * nx / 512 > budget:
+        nx //= 2
+    wl = inputs.couette_2d(nx, 128, 1.0) if nx != 512 else wl_full
+    o = oracle.from_workload(wl, tol=PRESSURE_TOL)
+    o.step(wl.dt, max(0, args.warmup - 1))
+    t0 = time.perf_counter()
+    o.step(wl.dt, args.steps)
+    dt = time.perf_counter() - t0
+    value = wl.cells * args.steps / dt / 1e6
+    sample = "%dx128 crop of the 512x128 Couette workload (same physics, x extent cut), %d timed steps" % (
+        nx, args.steps) if nx != 512 else "the full 512x128 workload, %d timed steps" % args.steps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "pressure_tol": PRESSURE_TOL},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def gpu_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2412_16843_gb300 import build, cdi
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.set_device(local_rank)
+    wl = workload()
+    s = cdi.from_workload(wl, precision=cdi.FP64, tol=PRESSURE_TOL, max_vcycles=100)
+    s.set_exec(cdi.EXEC_PERSISTENT if args.exec == "persistent" else cdi.EXEC_KERNELS)
+    stream = s.stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    s.step(wl.dt, args.warmup)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    s.profile_start(args.roofline_kernel, 1 << 15)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches = 0
+    max_cyc = 0
+    total_cyc = 0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+        s.step(wl.dt, 1)
+        ends[k].record(stream)
+        launches += s.launches_per_step()
+        st = s.last_stats()
+        max_cyc = max(max_cyc, st["max_cycles_step"])
+        total_cyc += st["total_cycles_call"]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    kern_ms, kern_n = s.profile_stop()
+    clk = clocks.stop()
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = wl.cells * args.steps * world / (ms_max / 1e3) / 1e6
+
+    # end to end through the public API with host buffers
+    ne = args.e2e_steps or max(5, min(args.steps, 30))
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+    phi_h = pin(s.cell_shape)
+    vel_h = [pin(s.face_shape(a)) for a in range(s.dim)]
+    p_h = pin(s.cell_shape)
+    s.get_fields((phi_h, vel_h, p_h))
+    h2d = phi_h.nbytes + sum(v.nbytes for v in vel_h)
+    d2h = phi_h.nbytes + sum(v.nbytes for v in vel_h) + p_h.nbytes
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ne):
+        s.set_state(phi_h, vel_h)
+        s.step(wl.dt, 1)
+        s.get_fields((phi_h, vel_h, p_h))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = wl.cells * ne * world / float(te.item()) / 1e6
+
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    cyc_per_step = total_cyc / args.steps
+    if args.roofline_kernel == "step":
+        nbytes = step_bytes(wl.dim, wl.cells, 8, cyc_per_step)
+    else:
+        nbytes = algorithmic_bytes(args.roofline_kernel, wl.dim, wl.cells, wl.n[0], 8)
+    avg_s = kern_ms / max(kern_n, 1) / 1e3
+    achieved = nbytes / avg_s / 1e9 if kern_n else None
+    roof = {"bound": "hbm", "kernel": args.roofline_kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None, "traffic": traffic_for(args.roofline_kernel),
+            "peak_source": peak_kind, "algorithmic_bytes_per_launch": nbytes, "launches_timed": kern_n,
+            "avg_launch_us": avg_s * 1e6}
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, secs, sample = oracle_rate(wl, 6, budget_s=25.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample + " (%.1f s)" % secs}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": wl.cells, "dt": wl.dt, "pressure_tol": PRESSURE_TOL,
+                   "max_vcycles_per_solve_seen": max_cyc,
+                   "vcycles_per_step": cyc_per_step, "exec": args.exec, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed by a 256 MiB device write before every timed step"},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": ne},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        gpu_arm(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

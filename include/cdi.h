@@ -65,6 +65,9 @@ typedef enum {
 enum { CDI_FP64 = 0, CDI_FP32_MIXED = 1 };
 enum { CDI_WALL_LO = 0, CDI_WALL_HI = 1, CDI_WALL_BOTH = 2 };
 enum { CDI_WARM_PREV = 0, CDI_WARM_ZERO = 1 };
+/* how cdi_step runs: one persistent cooperative launch per call (default), or
+ * one launch per stencil / multigrid kernel with host-side convergence tests */
+enum { CDI_EXEC_PERSISTENT = 0, CDI_EXEC_KERNELS = 1 };
 /* slip models of Sec. 3, Eqs. (Model 1A) .. (Model 4B); 4A is the default */
 enum { CDI_MODEL_1A = 0, CDI_MODEL_1B, CDI_MODEL_2A, CDI_MODEL_2B,
        CDI_MODEL_3A, CDI_MODEL_3B, CDI_MODEL_4A, CDI_MODEL_4B };
@@ -173,12 +176,33 @@ cdi_status cdi_eval_wall(cdi_ctx* ctx, double* uY, double* ghost);
 cdi_status cdi_solve_pressure(cdi_ctx* ctx, const double* f, double* p);
 
 /* Statistics of the last pressure solve: V-cycles, relative residual; and
- * of the last cdi_step call: largest V-cycle count of one solve. */
+ * of the last cdi_step call: largest V-cycle count of one solve and the
+ * V-cycles of all its solves (any pointer may be NULL). */
 cdi_status cdi_last_stats(cdi_ctx* ctx, int* vcycles, double* resid,
-                          int* max_vcycles_step);
+                          int* max_vcycles_step, int* total_vcycles_call);
 
-/* Number of kernel launches the last cdi_step issued per time step. */
+/* Number of kernel launches the last cdi_step issued per time step (the
+ * persistent mode issues one launch per cdi_step call). */
 cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
+
+/* Execution mode of cdi_step: CDI_EXEC_PERSISTENT (default) runs all steps of
+ * the call in one cooperative launch with bounded grid barriers (a barrier
+ * that waits longer than 2 s ends the call with CDI_ETIMEOUT);
+ * CDI_EXEC_KERNELS launches every stencil and multigrid kernel separately.
+ * Both compute the same arithmetic. */
+cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
+
+/* Launch profiler (diagnostics): from now on record a CUDA event pair on the
+ * launching stream around each of the next max_launches launches of one
+ * kernel class ("rbgs0" = red-black sweep on the finest level, "mom",
+ * "phi_rhs", "wall", "cell", "psi", "stage_phi", "stage_mom", "div",
+ * "rbgs", "resid_restrict0", "prolong0", "coarse", "resid", "project").
+ * Creates events (host objects); allocates no device memory. */
+cdi_status cdi_profile_start(cdi_ctx* ctx, const char* kernel, int max_launches);
+
+/* Stop the launch profiler: total device time of the recorded launches (ms)
+ * and their number.  Synchronises the stream. */
+cdi_status cdi_profile_stop(cdi_ctx* ctx, double* total_ms, long* launches);
 
 /* Text of the last error on this context ("" if none); NULL ctx gives the
  * last error of cdi_init_grid. */

@@ -23,6 +23,7 @@ STATUS = {0: "CDI_OK", 1: "CDI_EINVAL", 2: "CDI_ESTATE", 3: "CDI_ECUDA",
 FP64, FP32_MIXED = 0, 1
 WALL_LO, WALL_HI, WALL_BOTH = 0, 1, 2
 WARM_PREV, WARM_ZERO = 0, 1
+EXEC_PERSISTENT, EXEC_KERNELS = 0, 1
 MODELS = {"1A": 0, "1B": 1, "2A": 2, "2B": 3, "3A": 4, "3B": 5, "4A": 6, "4B": 7}
 
 _lib = None
@@ -74,8 +75,11 @@ def load(path: str = LIB_PATH):
         "cdi_eval_rhs": [P, D, DP, DP, DP, DP],
         "cdi_eval_wall": [P, DP, DP],
         "cdi_solve_pressure": [P, DP, DP],
-        "cdi_last_stats": [P, IP, DP, IP],
+        "cdi_last_stats": [P, IP, DP, IP, IP],
+        "cdi_set_exec": [P, I],
         "cdi_launches_per_step": [P, ctypes.POINTER(ctypes.c_long)],
+        "cdi_profile_start": [P, ctypes.c_char_p, I],
+        "cdi_profile_stop": [P, DP, ctypes.POINTER(ctypes.c_long)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -243,14 +247,27 @@ class Solver:
         return p
 
     def last_stats(self):
-        c, r, m = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
-        self._check(self.lib.cdi_last_stats(self.h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(m)))
-        return {"cycles": c.value, "resid": r.value, "max_cycles_step": m.value}
+        c, r, m, t = ctypes.c_int(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.cdi_last_stats(self.h, ctypes.byref(c), ctypes.byref(r), ctypes.byref(m),
+                                            ctypes.byref(t)))
+        return {"cycles": c.value, "resid": r.value, "max_cycles_step": m.value, "total_cycles_call": t.value}
+
+    def set_exec(self, mode: int):
+        self._check(self.lib.cdi_set_exec(self.h, mode))
 
     def launches_per_step(self):
         n = ctypes.c_long()
         self._check(self.lib.cdi_launches_per_step(self.h, ctypes.byref(n)))
         return n.value
+
+
+    def profile_start(self, kernel: str, max_launches: int = 4096):
+        self._check(self.lib.cdi_profile_start(self.h, kernel.encode(), max_launches))
+
+    def profile_stop(self):
+        ms, n = ctypes.c_double(), ctypes.c_long()
+        self._check(self.lib.cdi_profile_stop(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
 
 def from_workload(wl, precision=FP64, tol=1e-10, max_vcycles=100):

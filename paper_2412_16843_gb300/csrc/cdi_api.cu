@@ -59,10 +59,20 @@ struct cdi_ctx {
     double* xfer = nullptr;  // FP64 staging of one face field for host copies
     MG mg{};
     double* host_scal = nullptr;
+    // execution of cdi_step: one persistent cooperative launch, or one launch per kernel
+    int exec = CDI_EXEC_PERSISTENT;
+    PersistCtl* ctl = nullptr;
+    bool persist_ready = false;
+    PersistLayout playout{};
+    int persist_lt = 0;
+    size_t persist_smem = 0;
+    int persist_grid = 0;
+    long spin_limit_ns = 2000000000L;
     // statistics
     int last_cycles = 0;
     double last_resid = 0.0;
     int max_cycles_step = 0;
+    int total_cycles_call = 0;
     long launches_per_step = 0;
     std::string err;
 };
@@ -128,13 +138,25 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     MG& mg = c->mg;
     for (int l = 0; l < mg.nlev; ++l) {
         MGLevel& L = mg.lv[l];
-        L.p = (double*)cv.take(L.N * sizeof(double));
-        L.f = (double*)cv.take(L.N * sizeof(double));
+        const long nl = L.g.N, np = L.g.NP;
+        if (l == 0) {  // FP64 pressure, right-hand side and coefficients of the defect correction
+            L.p = (double*)cv.take(nl * sizeof(double));
+            L.f = (double*)cv.take(nl * sizeof(double));
+            for (int a = 0; a < 3; ++a)
+                L.beta[a] = (a < g.D) ? (double*)cv.take((nl + (a == g.W ? np : 0)) * sizeof(double)) : nullptr;
+        } else {
+            L.p = nullptr;
+            L.f = nullptr;
+            for (int a = 0; a < 3; ++a) L.beta[a] = nullptr;
+        }
+        L.e = (float*)cv.take(nl * sizeof(float));
+        L.r = (float*)cv.take(nl * sizeof(float));
         for (int a = 0; a < 3; ++a)
-            L.beta[a] = (a < g.D) ? (double*)cv.take((L.N + (a == g.W ? L.NP : 0)) * sizeof(double)) : nullptr;
+            L.bf[a] = (a < g.D) ? (float*)cv.take((nl + (a == g.W ? np : 0)) * sizeof(float)) : nullptr;
     }
-    mg.partials = (double*)cv.take(kPartials * sizeof(double));
+    mg.partials = (double*)cv.take(2 * kPartials * sizeof(double));
     mg.scal = (double*)cv.take(S_NSCAL * sizeof(double));
+    c->ctl = (PersistCtl*)cv.take(sizeof(PersistCtl));
     *total = cv.off + 256;
 }
 
@@ -234,6 +256,7 @@ cdi_status mg_solve(cdi_ctx* c) {
     c->last_cycles = cyc;
     c->last_resid = rn / fn;
     if (cyc > c->max_cycles_step) c->max_cycles_step = cyc;
+    c->total_cycles_call += cyc;
     if (rn > c->tol * fn) {
         char b[160];
         snprintf(b, sizeof b, "pressure solve: %d V-cycles left relative residual %.3e > tol %.3e", cyc, rn / fn,
@@ -316,6 +339,109 @@ cdi_status step_once(cdi_ctx* c, double dt) {
     return cuda_check(c, cudaGetLastError(), "kernel launch");
 }
 
+// Choose the first multigrid level the persistent kernel's CTA 0 solves in
+// shared memory (the largest tail that fits), and the launch shape.
+template <typename T>
+cdi_status persist_setup(cdi_ctx* c) {
+    if (c->persist_ready) return CDI_OK;
+    int dev = 0, optin = 0;
+    cdi_status st = cuda_check(c, cudaGetDevice(&dev), "cudaGetDevice");
+    if (st) return st;
+    st = cuda_check(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+                    "cudaDeviceGetAttribute");
+    if (st) return st;
+    const size_t budget = (size_t)optin > 8192 ? (size_t)optin - 4096 : 0;
+    int lt = c->mg.nlev - 1;
+    for (int l = 0; l < c->mg.nlev; ++l) {
+        PersistLayout L{};
+        if (persist_tail_layout(c->g, c->mg, l, L) <= budget) {
+            lt = l;
+            break;
+        }
+    }
+    c->persist_lt = lt;
+    c->persist_smem = persist_tail_layout(c->g, c->mg, lt, c->playout);
+    st = cuda_check(c, persist_prepare<T>(c->g.D, c->persist_smem, &c->persist_grid), "persistent kernel setup");
+    if (st) return st;
+    c->persist_ready = true;
+    return CDI_OK;
+}
+
+template <typename T>
+cdi_status step_persist(cdi_ctx* c, double dt, int nsteps) {
+    cdi_status st = persist_setup<T>(c);
+    if (st) return st;
+    PersistArgs<T> A{};
+    static_cast<PersistLayout&>(A) = c->playout;
+    A.g = c->g;
+    A.ph = c->ph;
+    A.phi_s = (T*)c->phi_s;
+    A.phi_k = (T*)c->phi_k;
+    A.acc_phi = (T*)c->acc_phi;
+    A.rphi = (T*)c->rphi;
+    A.psi = (T*)c->psi;
+    A.muc = (T*)c->muc;
+    A.wuY = (T*)c->wuY;
+    A.wghost = (T*)c->wghost;
+    A.wmuw = (T*)c->wmuw;
+    for (int a = 0; a < 3; ++a) {
+        A.u_s[a] = (T*)c->u_s[a];
+        A.u_k[a] = (T*)c->u_k[a];
+        A.acc_m[a] = (T*)c->acc_m[a];
+        A.rm[a] = (T*)c->rm[a];
+        A.nh[a] = (T*)c->nh[a];
+        A.m[a] = (T*)c->m[a];
+    }
+    for (int l = 0; l < kMaxLevels; ++l) A.lv[l] = c->mg.lv[l];
+    A.nlev = c->mg.nlev;
+    A.lt = c->persist_lt;
+    A.partials = c->mg.partials;
+    A.ctl = c->ctl;
+    A.tol = c->tol;
+    A.max_vcycles = c->max_vcycles;
+    A.warm = c->warm;
+    A.npre = c->npre;
+    A.npost = c->npost;
+    A.gamma_param = c->gamma;
+    A.dt = dt;
+    A.nsteps = nsteps;
+    A.spin_limit = c->spin_limit_ns;
+    st = cuda_check(c, cudaMemsetAsync(c->ctl, 0, sizeof(PersistCtl), c->stream), "cudaMemsetAsync(ctl)");
+    if (st) return st;
+    const bool on = prof_before(KC_STEP, c->stream);
+    st = cuda_check(c, launch_step_persist<T>(A, c->persist_smem, c->persist_grid, c->stream),
+                    "cudaLaunchCooperativeKernel");
+    prof_after(on, c->stream);
+    if (st) return st;
+    ++g_launches;
+    PersistCtl h{};
+    st = cuda_check(c, cudaMemcpyAsync(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost, c->stream), "read ctl");
+    if (st) return st;
+    st = cuda_check(c, cudaStreamSynchronize(c->stream), "persistent step");
+    if (st) return st;
+    c->last_cycles = h.last_cycles;
+    c->last_resid = h.last_resid;
+    c->max_cycles_step = h.max_cycles;
+    c->total_cycles_call = h.total_cycles;
+    // the kernel swapped state and stage buffers once per finished step
+    for (int s = 0; s < h.steps_done; ++s) {
+        std::swap(c->phi_s, c->phi_k);
+        for (int a = 0; a < 3; ++a) std::swap(c->u_s[a], c->u_k[a]);
+    }
+    if (h.status != CDI_OK) {
+        char b[200];
+        if (h.status == CDI_ENOCONV)
+            snprintf(b, sizeof b, "pressure solve: %d V-cycles left relative residual %.3e > tol %.3e (step %d)",
+                     h.last_cycles, h.last_resid, c->tol, h.steps_done);
+        else if (h.status == CDI_ETIMEOUT)
+            snprintf(b, sizeof b, "a grid barrier of the persistent step kernel timed out (step %d)", h.steps_done);
+        else
+            snprintf(b, sizeof b, "non-finite value in the pressure solve (step %d)", h.steps_done);
+        return fail(c, (cdi_status)h.status, b);
+    }
+    return CDI_OK;
+}
+
 cdi_status check_wall(cdi_ctx* c, int wall) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
     if (wall < 0 || wall > 2) return fail(c, CDI_EINVAL, "wall must be CDI_WALL_LO, CDI_WALL_HI or CDI_WALL_BOTH");
@@ -352,12 +478,7 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     if (N > (1L << 31)) return fail(nullptr, CDI_EINVAL, "grid too large");
     cdi_ctx* c = new (std::nothrow) cdi_ctx();
     if (!c) return fail(nullptr, CDI_EINVAL, "out of host memory");
-    c->g.D = dim;
-    for (int a = 0; a < 3; ++a) c->g.n[a] = n[a];
-    c->g.W = W;
-    c->g.N = N;
-    c->g.NP = (dim == 2) ? (long)n[0] : (long)n[0] * n[1];
-    c->g.h = h;
+    c->g = make_geom(dim, n, h);
     for (int a = 0; a < 3; ++a) c->L[a] = L[a];
     c->precision = precision;
     c->ph.delta = precision == CDI_FP64 ? 1e-12 : 1e-6;
@@ -373,13 +494,7 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     mg.nlev = 1;
     int ln[3] = {n[0], n[1], n[2]};
     double lh = h;
-    auto set_level = [&](int l) {
-        MGLevel& Lv = mg.lv[l];
-        for (int a = 0; a < 3; ++a) Lv.n[a] = ln[a];
-        Lv.N = (long)ln[0] * ln[1] * ln[2];
-        Lv.NP = (dim == 2) ? ln[0] : (long)ln[0] * ln[1];
-        Lv.h = lh;
-    };
+    auto set_level = [&](int l) { mg.lv[l].g = make_geom(dim, ln, lh); };
     set_level(0);
     for (;;) {
         bool ok = mg.nlev < kMaxLevels;
@@ -390,7 +505,7 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
         lh *= 2.0;
         set_level(mg.nlev++);
     }
-    if (mg.lv[mg.nlev - 1].N > kMaxCoarse) {
+    if (mg.lv[mg.nlev - 1].g.N > kMaxCoarse) {
         delete c;
         return fail(nullptr, CDI_EINVAL, "the coarsest multigrid level has more than 64 cells; use extents with more "
                                          "factors of two");
@@ -568,13 +683,27 @@ cdi_status cdi_step(cdi_ctx* c, double dt, int nsteps) {
     if (nsteps < 0) return fail(c, CDI_EINVAL, "nsteps must be >= 0");
     if (!c->fluids_set) return fail(c, CDI_ESTATE, "fluids not set");
     c->max_cycles_step = 0;
+    c->total_cycles_call = 0;
+    if (nsteps == 0) return CDI_OK;
     const long l0 = g_launches;
-    for (int n = 0; n < nsteps; ++n) {
-        st = (c->precision == CDI_FP64) ? step_once<double>(c, dt) : step_once<float>(c, dt);
+    if (c->exec == CDI_EXEC_PERSISTENT) {
+        st = (c->precision == CDI_FP64) ? step_persist<double>(c, dt, nsteps) : step_persist<float>(c, dt, nsteps);
         if (st) return st;
+    } else {
+        for (int n = 0; n < nsteps; ++n) {
+            st = (c->precision == CDI_FP64) ? step_once<double>(c, dt) : step_once<float>(c, dt);
+            if (st) return st;
+        }
     }
-    if (nsteps > 0) c->launches_per_step = (g_launches - l0) / nsteps;
+    c->launches_per_step = (g_launches - l0) / nsteps;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "cdi_step");
+}
+
+cdi_status cdi_set_exec(cdi_ctx* c, int mode) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (mode != CDI_EXEC_PERSISTENT && mode != CDI_EXEC_KERNELS) return fail(c, CDI_EINVAL, "unknown exec mode");
+    c->exec = mode;
+    return CDI_OK;
 }
 
 cdi_status cdi_mass(cdi_ctx* c, double* mass_out) {
@@ -685,11 +814,66 @@ cdi_status cdi_solve_pressure(cdi_ctx* c, const double* f, double* p) {
     return cuda_check(c, cudaStreamSynchronize(s), "solve_pressure");
 }
 
-cdi_status cdi_last_stats(cdi_ctx* c, int* vcycles, double* resid, int* max_vcycles_step) {
+cdi_status cdi_profile_start(cdi_ctx* c, const char* kernel, int max_launches) {
+    if (!c || !kernel) return fail(c, CDI_EINVAL, "null argument");
+    if (max_launches < 1 || max_launches > (1 << 20)) return fail(c, CDI_EINVAL, "max_launches out of range");
+    int kc = -1;
+    for (int i = 0; i < KC_COUNT; ++i)
+        if (std::strcmp(kernel, kKernelClassNames[i]) == 0) kc = i;
+    if (kc < 0) return fail(c, CDI_EINVAL, std::string("unknown kernel class ") + kernel);
+    Profiler& P = g_prof;
+    if (P.ev) {
+        for (int i = 0; i < 2 * P.cap; ++i) cudaEventDestroy(P.ev[i]);
+        delete[] P.ev;
+        P.ev = nullptr;
+    }
+    P.ev = new (std::nothrow) cudaEvent_t[2 * max_launches];
+    if (!P.ev) return fail(c, CDI_EINVAL, "out of host memory");
+    for (int i = 0; i < 2 * max_launches; ++i) {
+        cdi_status st = cuda_check(c, cudaEventCreate(&P.ev[i]), "cudaEventCreate");
+        if (st) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(P.ev[j]);
+            delete[] P.ev;
+            P.ev = nullptr;
+            return st;
+        }
+    }
+    P.cap = max_launches;
+    P.used = 0;
+    P.target = kc;
+    return CDI_OK;
+}
+
+cdi_status cdi_profile_stop(cdi_ctx* c, double* total_ms, long* launches) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    Profiler& P = g_prof;
+    cdi_status st = cuda_check(c, cudaStreamSynchronize(c->stream), "profile sync");
+    if (st) return st;
+    double tot = 0.0;
+    for (int i = 0; i < P.used; ++i) {
+        float ms = 0.f;
+        st = cuda_check(c, cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]), "cudaEventElapsedTime");
+        if (st) return st;
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = P.used;
+    for (int i = 0; i < 2 * P.cap; ++i) cudaEventDestroy(P.ev[i]);
+    delete[] P.ev;
+    P.ev = nullptr;
+    P.cap = 0;
+    P.used = 0;
+    P.target = -1;
+    return CDI_OK;
+}
+
+cdi_status cdi_last_stats(cdi_ctx* c, int* vcycles, double* resid, int* max_vcycles_step,
+                          int* total_vcycles_call) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
     if (vcycles) *vcycles = c->last_cycles;
     if (resid) *resid = c->last_resid;
     if (max_vcycles_step) *max_vcycles_step = c->max_cycles_step;
+    if (total_vcycles_call) *total_vcycles_call = c->total_cycles_call;
     return CDI_OK;
 }
 

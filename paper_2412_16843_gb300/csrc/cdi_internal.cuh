@@ -19,6 +19,29 @@ constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarse = 64;      // cells of the coarsest multigrid level
 constexpr int kPartials = 1024;     // blocks of the fixed-order reductions
 
+// Division by a runtime constant d of an unsigned x < 2^31 with one
+// multiply-high, an add and a shift: q = (umulhi(x, m) + x) >> s with
+// s = ceil(log2 d) and m = floor(2^32 (2^s - d) / d) + 1 (the round-up method
+// of Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994).
+struct FastDiv {
+    unsigned d, m;
+    int s;
+    __host__ void init(unsigned dv) {
+        d = dv;
+        s = 0;
+        while ((1ull << s) < dv) ++s;
+        m = (unsigned)((((1ull << 32) * ((1ull << s) - dv)) / dv) + 1);
+    }
+    __host__ __device__ __forceinline__ unsigned div(unsigned x) const {
+#ifdef __CUDA_ARCH__
+        return (__umulhi(x, m) + x) >> s;
+#else
+        return x / d;
+#endif
+    }
+};
+
 struct Geom {
     int D;        // 2 or 3
     int n[3];     // cells per axis, n[2] = 1 in 2D
@@ -26,7 +49,21 @@ struct Geom {
     long N;       // cells
     long NP;      // cells of one wall plane (= stride of the wall axis)
     double h;
+    FastDiv fd0, fd1;  // division by n[0] and by n[1]
 };
+
+inline Geom make_geom(int D, const int n[3], double h) {
+    Geom g{};
+    g.D = D;
+    for (int a = 0; a < 3; ++a) g.n[a] = n[a];
+    g.W = D - 1;
+    g.N = (long)n[0] * n[1] * n[2];
+    g.NP = (D == 2) ? (long)n[0] : (long)n[0] * n[1];
+    g.h = h;
+    g.fd0.init((unsigned)n[0]);
+    g.fd1.init((unsigned)n[1]);
+    return g;
+}
 
 // slip model ids (the CDI_MODEL_* values of cdi.h)
 enum { M1A = 0, M1B, M2A, M2B, M3A, M3B, M4A, M4B };
@@ -63,29 +100,31 @@ struct StageFields {
 };
 
 // ---------------------------------------------------------------------------
-// index helpers
+// index helpers (grids hold fewer than 2^31 cells)
 // ---------------------------------------------------------------------------
 struct IJK {
     int i, j, k;
 };
 
-__host__ __device__ inline IJK decode(const Geom& g, long c) {
+__host__ __device__ __forceinline__ IJK decode(const Geom& g, long c) {
     IJK q;
-    q.i = (int)(c % g.n[0]);
-    long r = c / g.n[0];
-    q.j = (int)(r % g.n[1]);
-    q.k = (int)(r / g.n[1]);
+    const unsigned cc = (unsigned)c;
+    const unsigned r = g.fd0.div(cc);
+    q.i = (int)(cc - r * (unsigned)g.n[0]);
+    const unsigned k = g.fd1.div(r);
+    q.j = (int)(r - k * (unsigned)g.n[1]);
+    q.k = (int)k;
     return q;
 }
-__host__ __device__ inline long encode(const Geom& g, int i, int j, int k) {
-    return (long)i + (long)g.n[0] * ((long)j + (long)g.n[1] * k);
+__host__ __device__ __forceinline__ long encode(const Geom& g, int i, int j, int k) {
+    return (long)((unsigned)i + (unsigned)g.n[0] * ((unsigned)j + (unsigned)g.n[1] * (unsigned)k));
 }
-__host__ __device__ inline int coord(const IJK& q, int a) { return a == 0 ? q.i : (a == 1 ? q.j : q.k); }
-__host__ __device__ inline void setc(IJK& q, int a, int v) {
+__host__ __device__ __forceinline__ int coord(const IJK& q, int a) { return a == 0 ? q.i : (a == 1 ? q.j : q.k); }
+__host__ __device__ __forceinline__ void setc(IJK& q, int a, int v) {
     if (a == 0) q.i = v; else if (a == 1) q.j = v; else q.k = v;
 }
 // shift by s along axis a; periodic axes wrap (|s| <= n), the wall axis does not
-__host__ __device__ inline IJK shift(const Geom& g, IJK q, int a, int s) {
+__host__ __device__ __forceinline__ IJK shift(const Geom& g, IJK q, int a, int s) {
     int v = coord(q, a) + s;
     if (a != g.W) {
         if (v < 0) v += g.n[a];
@@ -94,10 +133,10 @@ __host__ __device__ inline IJK shift(const Geom& g, IJK q, int a, int s) {
     setc(q, a, v);
     return q;
 }
-__host__ __device__ inline long idx(const Geom& g, const IJK& q) { return encode(g, q.i, q.j, q.k); }
+__host__ __device__ __forceinline__ long idx(const Geom& g, const IJK& q) { return encode(g, q.i, q.j, q.k); }
 
 template <typename T>
-__host__ __device__ inline T clampv(T x, T lo, T hi) { return x < lo ? lo : (x > hi ? hi : x); }
+__host__ __device__ __forceinline__ T clampv(T x, T lo, T hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
 // ---------------------------------------------------------------------------
 // launchers (stencils: k_stencil.cu; multigrid and reductions: k_mg.cu)
@@ -114,22 +153,24 @@ template <typename T>
 void launch_wall_columns(const Geom& g, const PhysDev& ph, const T* phi, T* psi, double* cols,
                          cudaStream_t s);
 
-// multigrid hierarchy, all arrays in double
+// Multigrid hierarchy.  The pressure p, its right-hand side f and the level-0
+// face coefficients beta are FP64 (defect correction); every level also holds
+// an FP32 correction e, right-hand side r and coefficients bf for the V-cycle.
 struct MGLevel {
-    int n[3];
-    long N, NP;
-    double h;
-    double* p;
-    double* f;
-    double* beta[3];
+    Geom g;
+    double* p;         // level 0 only
+    double* f;         // level 0 only
+    double* beta[3];   // level 0 only
+    float* e;
+    float* r;
+    float* bf[3];
 };
 
 struct MG {
     int nlev;
     MGLevel lv[kMaxLevels];
-    double* partials;   // [kPartials]
+    double* partials;   // [2 * kPartials]
     double* scal;       // device scalars
-    double* host_scal;  // pinned host mirror (nullable)
 };
 
 // scalar slots in MG::scal
@@ -142,8 +183,8 @@ void launch_sum_f(const Geom& g, MG& mg, cudaStream_t s);
 void launch_sub_mean_and_norm(const Geom& g, MG& mg, cudaStream_t s);
 template <typename T>
 void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cudaStream_t s);
-void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s);
-void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s);
+void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s);   // FP64 residual, its norm, r0 and e0 = 0
+void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s);  // FP32 V-cycle, p += e0
 void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s);
 template <typename T>
 void launch_project(const Geom& g, const PhysDev& ph, const T* phi, T* const* us, double cdt,
@@ -154,7 +195,89 @@ template <typename T>
 void launch_gamma(const Geom& g, const T* const* u, double gamma_param, MG& mg, cudaStream_t s);
 void launch_contact_line(const Geom& g, int wall, const double* cols, MG& mg, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// persistent step kernel (k_persist.cu)
+// ---------------------------------------------------------------------------
+constexpr int kPersistThreads = 512;
+
+// control block in the workspace (zeroed before every launch)
+struct PersistCtl {
+    unsigned bar_count;
+    unsigned bar_gen;
+    int status;        // CDI_OK or the cdi_status that ended the launch
+    int max_cycles;    // largest V-cycle count of one solve in this launch
+    int last_cycles;
+    int total_cycles;  // V-cycles of all solves in this launch
+    int steps_done;
+    int pad;
+    double last_resid;
+};
+
+// offsets (in floats) of the FP32 multigrid tail levels in dynamic shared
+// memory, and of the FP64 scratch of the coarsest dense solve (in doubles,
+// from the 8-byte aligned end of the float part)
+struct PersistLayout {
+    long sm_e[kMaxLevels], sm_r[kMaxLevels], sm_b[kMaxLevels][3];
+    long sm_dbl;   // float offset where the double scratch starts
+    long sm_A, sm_bb, sm_fct;
+};
+
+template <typename T>
+struct PersistArgs : PersistLayout {
+    Geom g;
+    PhysDev ph;
+    T *phi_s, *phi_k, *acc_phi, *rphi, *psi, *muc, *wuY, *wghost, *wmuw;
+    T *u_s[3], *u_k[3], *acc_m[3], *rm[3], *nh[3], *m[3];
+    MGLevel lv[kMaxLevels];
+    int nlev, lt;        // levels lt.. are solved by CTA 0 in shared memory
+    double* partials;    // 2 * kPartials doubles
+    PersistCtl* ctl;
+    double tol;
+    int max_vcycles, warm, npre, npost;
+    double gamma_param, dt;
+    int nsteps;
+    long spin_limit;     // barrier timeout in nanoseconds
+};
+
+size_t persist_tail_layout(const Geom& g, const MG& mg, int lt, PersistLayout& L);
+template <typename T>
+cudaError_t persist_prepare(int dim, size_t smem, int* grid);
+template <typename T>
+cudaError_t launch_step_persist(PersistArgs<T>& A, size_t smem, int grid, cudaStream_t s);
+
 // number of kernel launches issued since the counter was reset (host side)
 extern thread_local long g_launches;
+
+// Kernel classes that the launch profiler can bracket with CUDA events.
+enum KClass { KC_PSI = 0, KC_CELL, KC_WALL, KC_PHI_RHS, KC_MOM, KC_STAGE_PHI, KC_STAGE_MOM, KC_DIV,
+              KC_RBGS0, KC_RBGS, KC_RESTRICT0, KC_PROLONG0, KC_COARSE, KC_RESID, KC_PROJECT, KC_STEP, KC_COUNT };
+extern const char* const kKernelClassNames[KC_COUNT];
+
+// Launch profiler: records an event pair around each launch of one kernel
+// class on the launching stream, up to a fixed number of launches.
+struct Profiler {
+    int target = -1;
+    int cap = 0;
+    int used = 0;
+    cudaEvent_t* ev = nullptr;  // 2 * cap events
+};
+extern thread_local Profiler g_prof;
+
+inline bool prof_before(int kc, cudaStream_t s) {
+    if (g_prof.target != kc || g_prof.used >= g_prof.cap) return false;
+    cudaEventRecord(g_prof.ev[2 * g_prof.used], s);
+    return true;
+}
+inline void prof_after(bool on, cudaStream_t s) {
+    if (!on) return;
+    cudaEventRecord(g_prof.ev[2 * g_prof.used + 1], s);
+    ++g_prof.used;
+}
+#define CDI_PROF(kc, s, launch)              \
+    do {                                     \
+        const bool _on = prof_before(kc, s); \
+        launch;                              \
+        prof_after(_on, s);                  \
+    } while (0)
 
 }  // namespace cdi

@@ -1,0 +1,522 @@
+// Persistent time-step kernel: nsteps full RK4 steps (Sec. 4) in ONE
+// cooperative launch with one CTA per SM.
+//
+// Every phase of the step (the right-hand side of Eqs. CDI and NS_momentum,
+// the RK4 stage update, and each projection with its multigrid V-cycles and
+// convergence test) runs as a grid-stride loop over cells, separated by a
+// grid barrier.  The multigrid levels of at most a few thousand cells are
+// solved by CTA 0 alone in shared memory (one "tail" call per V-cycle) while
+// the other CTAs wait at the next barrier.  Reductions (mean and norm of the
+// pressure right-hand side, residual norm, |u|_max) are deterministic: each
+// CTA writes one partial, and after the barrier every CTA sums the partials
+// in the same order, so every CTA takes the same convergence decision.
+//
+// Barriers spin for a bounded number of iterations; on timeout the kernel
+// sets CDI_ETIMEOUT in the control block and every CTA returns.  ENOCONV and
+// ENAN are uniform decisions and also end the launch.  Data written by one CTA
+// and read by another after a barrier is read with ld.global.cg (L2), never
+// from a possibly stale L1 line.
+#include "ops.cuh"
+#include "../../include/cdi.h"
+
+namespace cdi {
+
+namespace {
+
+using LG = ops::LdCG;
+using LP = ops::LdPlain;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+// block-wide sum or max, returned to every thread of the block
+template <bool MAX>
+__device__ double block_reduce_all(double v) {
+    __shared__ double sh[32];
+    __shared__ double res;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = MAX ? warp_max(v) : warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double x = lane < nw ? sh[lane] : 0.0;
+        x = MAX ? warp_max(x) : warp_sum(x);
+        if (lane == 0) res = x;
+    }
+    __syncthreads();
+    return res;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+struct Barrier {
+    PersistCtl* ctl;
+    long limit;
+    // grid barrier; false when the launch is ending (timeout or error)
+    __device__ bool sync() {
+        __shared__ int ok;
+        __syncthreads();  // the CTA's writes of this phase are done
+        if (threadIdx.x == 0) {
+            volatile unsigned* genp = &ctl->bar_gen;
+            const unsigned gen = *genp;
+            __threadfence();
+            const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+            if (arrived == gridDim.x - 1) {
+                atomicExch(&ctl->bar_count, 0u);
+                __threadfence();
+                atomicAdd(&ctl->bar_gen, 1u);
+            } else {
+                // bounded wait: give up after `limit` ns (or 2^31 polls)
+                const unsigned long long t0 = globaltimer();
+                long it = 0;
+                while (*genp == gen) {
+                    if (++it > (1L << 31) || globaltimer() - t0 > (unsigned long long)limit) {
+                        atomicCAS(&ctl->status, 0, (int)CDI_ETIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+            ok = (*(volatile int*)&ctl->status == 0);
+        }
+        __syncthreads();
+        return ok != 0;
+    }
+};
+
+// deterministic grid reduction: every CTA returns the same value
+template <bool MAX>
+__device__ bool grid_reduce(double v, double* partials, Barrier& bar, double& out) {
+    v = block_reduce_all<MAX>(v);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    if (!bar.sync()) return false;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        s = MAX ? fmax(s, __ldcg(partials + b)) : s + __ldcg(partials + b);
+    out = block_reduce_all<MAX>(s);
+    return true;
+}
+
+template <typename T>
+struct Run {
+    const PersistArgs<T>& A;
+    Barrier bar;
+    int red = 0;  // alternates the two partial buffers
+    __device__ double* partials() { return A.partials + (red++ & 1) * kPartials; }
+};
+
+// ---------------------------------------------------------------------------
+// multigrid tail: FP32 levels lt .. nlev-1 by CTA 0 in shared memory.  Input:
+// the right-hand side r of level lt (global); output: its correction e.
+// Level geometry and shared-memory offsets are copied into registers per
+// level, so no per-thread array is indexed at run time.
+// ---------------------------------------------------------------------------
+struct SmLevel {
+    Geom g;
+    float* e;
+    float* r;
+    float* b[3];
+};
+
+template <typename T, int DIM>
+__device__ __forceinline__ SmLevel sm_level(const PersistArgs<T>& A, float* sm, int l) {
+    SmLevel s;
+    s.g = A.lv[l].g;
+    s.e = sm + A.sm_e[l];
+    s.r = sm + A.sm_r[l];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) s.b[a] = (a < DIM) ? sm + A.sm_b[l][a] : nullptr;
+    return s;
+}
+
+template <typename T, int DIM>
+__device__ void tail_vcycle(const PersistArgs<T>& A, bool first, float* sm) {
+    const int lt = A.lt, nl = A.nlev;
+    const int nt = blockDim.x, t0 = threadIdx.x;
+    double* sd = reinterpret_cast<double*>(sm + A.sm_dbl);
+    if (first) {
+        // coefficients of the tail levels (constant during one solve)
+        const SmLevel top = sm_level<T, DIM>(A, sm, lt);
+        const int ntop = (int)(top.g.N + top.g.NP);
+        if (lt == 0) {
+            for (int a = 0; a < DIM; ++a) {
+                const int nf = (int)(top.g.N + (a == DIM - 1 ? top.g.NP : 0));
+                const float* src = A.lv[0].bf[a];
+                for (int t = t0; t < nf; t += nt) top.b[a][t] = __ldcg(src + t);
+            }
+        } else {
+            const MGLevel F = A.lv[lt - 1];
+            const float* fb[3] = {F.bf[0], F.bf[1], F.bf[2]};
+            for (int t = t0; t < ntop; t += nt) ops::coef_restrict_at<LG, float, DIM>(F.g, top.g, fb, top.b, t);
+        }
+        __syncthreads();
+        for (int l = lt + 1; l < nl; ++l) {
+            const SmLevel f = sm_level<T, DIM>(A, sm, l - 1), c = sm_level<T, DIM>(A, sm, l);
+            const float* fb[3] = {f.b[0], f.b[1], f.b[2]};
+            const int n = (int)(c.g.N + c.g.NP);
+            for (int t = t0; t < n; t += nt) ops::coef_restrict_at<LP, float, DIM>(f.g, c.g, fb, c.b, t);
+            __syncthreads();
+        }
+    }
+    {
+        const SmLevel top = sm_level<T, DIM>(A, sm, lt);
+        const float* src = A.lv[lt].r;
+        for (int c = t0; c < (int)top.g.N; c += nt) {
+            top.r[c] = __ldcg(src + c);
+            top.e[c] = 0.f;
+        }
+        __syncthreads();
+    }
+    for (int l = lt; l < nl - 1; ++l) {  // down
+        const SmLevel L = sm_level<T, DIM>(A, sm, l), C = sm_level<T, DIM>(A, sm, l + 1);
+        const float* bl[3] = {L.b[0], L.b[1], L.b[2]};
+        const int half = (int)(L.g.N / 2);
+        for (int it = 0; it < A.npre; ++it)
+            for (int col = 0; col < 2; ++col) {
+                for (int k = t0; k < half; k += nt)
+                    ops::rbgs_at<LP, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
+                __syncthreads();
+            }
+        for (int t = t0; t < (int)C.g.N; t += nt)
+            ops::resid_restrict_at<LP, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
+        __syncthreads();
+    }
+    {
+        const SmLevel C = sm_level<T, DIM>(A, sm, nl - 1);
+        const float* bc[3] = {C.b[0], C.b[1], C.b[2]};
+        __shared__ int piv;
+        __shared__ double shv;
+        ops::coarse_solve_block<LP, float, DIM>(C.g, bc, C.r, C.e, sd + A.sm_A, sd + A.sm_bb, sd + A.sm_fct, &piv,
+                                                &shv);
+    }
+    for (int l = nl - 2; l >= lt; --l) {  // up
+        const SmLevel L = sm_level<T, DIM>(A, sm, l), C = sm_level<T, DIM>(A, sm, l + 1);
+        const float* bl[3] = {L.b[0], L.b[1], L.b[2]};
+        const int half = (int)(L.g.N / 2);
+        for (int c = t0; c < (int)L.g.N; c += nt) ops::prolong_at<LP, float, DIM>(L.g, C.g, C.e, L.e, c);
+        __syncthreads();
+        for (int it = 0; it < A.npost; ++it)
+            for (int col = 0; col < 2; ++col) {
+                for (int k = t0; k < half; k += nt)
+                    ops::rbgs_at<LP, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
+                __syncthreads();
+            }
+    }
+    {
+        const SmLevel top = sm_level<T, DIM>(A, sm, lt);
+        float* dst = A.lv[lt].e;
+        for (int c = t0; c < (int)top.g.N; c += nt) dst[c] = top.e[c];
+    }
+}
+
+// one FP32 V-cycle on the correction equation A e = r from level 0 (grid
+// levels 0 .. lt-1, the tail by CTA 0), ending with p += e on level 0
+template <typename T, int DIM>
+__device__ bool vcycle(Run<T>& R, bool first, float* sm) {
+    const PersistArgs<T>& A = R.A;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int l = 0; l < A.lt; ++l) {
+        const MGLevel L = A.lv[l];
+        const MGLevel C = A.lv[l + 1];
+        const float* bl[3] = {L.bf[0], L.bf[1], L.bf[2]};
+        const int half = (int)(L.g.N / 2);
+        for (int it = 0; it < A.npre; ++it)
+            for (int col = 0; col < 2; ++col) {
+                for (int k = tid; k < half; k += nth)
+                    ops::rbgs_at<LG, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
+                if (!R.bar.sync()) return false;
+            }
+        for (int t = tid; t < (int)C.g.N; t += nth)
+            ops::resid_restrict_at<LG, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
+        if (!R.bar.sync()) return false;
+    }
+    if (blockIdx.x == 0) tail_vcycle<T, DIM>(A, first, sm);
+    if (!R.bar.sync()) return false;
+    const MGLevel L0 = A.lv[0];
+    bool updated = false;
+    for (int l = A.lt - 1; l >= 0; --l) {
+        const MGLevel L = A.lv[l];
+        const MGLevel C = A.lv[l + 1];
+        const float* bl[3] = {L.bf[0], L.bf[1], L.bf[2]};
+        const int half = (int)(L.g.N / 2);
+        for (int c = tid; c < (int)L.g.N; c += nth) ops::prolong_at<LG, float, DIM>(L.g, C.g, C.e, L.e, c);
+        if (!R.bar.sync()) return false;
+        for (int it = 0; it < A.npost; ++it)
+            for (int col = 0; col < 2; ++col) {
+                const bool last = (l == 0 && it == A.npost - 1 && col == 1);
+                for (int k = tid; k < half; k += nth) {
+                    const long c = ops::colour_cell(L.g, col, k);
+                    ops::rbgs_at<LG, float, DIM>(L.g, bl, L.e, L.r, c);
+                    if (last) L0.p[c] = __ldcg(L0.p + c) + (double)L.e[c];
+                }
+                if (last) {  // the other colour is final already
+                    for (int k = tid; k < half; k += nth) {
+                        const long c = ops::colour_cell(L.g, 0, k);
+                        L0.p[c] = __ldcg(L0.p + c) + (double)__ldcg(L.e + c);
+                    }
+                    updated = true;
+                }
+                if (!R.bar.sync()) return false;
+            }
+    }
+    if (!updated) {
+        for (int c = tid; c < (int)L0.g.N; c += nth) L0.p[c] = __ldcg(L0.p + c) + (double)__ldcg(L0.e + c);
+        if (!R.bar.sync()) return false;
+    }
+    return true;
+}
+
+// FP64 residual of level 0: its squared norm, the FP32 copy r and e = 0
+template <int DIM>
+__device__ double resid64_local(const MGLevel& L0, long tid, long nth) {
+    const double* b[3] = {L0.beta[0], L0.beta[1], L0.beta[2]};
+    double acc = 0.0;
+    for (long c = tid; c < L0.g.N; c += nth) {
+        const double r = ops::resid64_at<LG, DIM>(L0.g, b, L0.p, L0.f, c);
+        L0.r[c] = (float)r;
+        L0.e[c] = 0.f;
+        acc += r * r;
+    }
+    return acc;
+}
+
+__device__ void set_status(PersistCtl* ctl, int st) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->status, 0, st);
+}
+
+// projection: f = div u*/(c dt) - mean, defect correction to tol,
+// u = u* - c dt grad p / rho_f
+template <typename T, int DIM>
+__device__ bool project(Run<T>& R, const T* phi, T* const* u, double cdt, float* sm) {
+    const PersistArgs<T>& A = R.A;
+    const Geom& g = A.g;
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long)gridDim.x * blockDim.x;
+    const MGLevel& L0 = A.lv[0];
+    const double ih = 1.0 / g.h, inv_cdt = 1.0 / cdt;
+    const T* uc[3] = {u[0], u[1], u[2]};
+    double s = 0.0;
+    for (long c = tid; c < g.N; c += nth) {
+        const double v = ops::div_at<LG, T, DIM>(g, uc, ih, inv_cdt, c);
+        L0.f[c] = v;
+        s += v;
+    }
+    double sum;
+    if (!grid_reduce<false>(s, R.partials(), R.bar, sum)) return false;
+    const double mean = sum / (double)g.N;
+    double s2 = 0.0;
+    for (long c = tid; c < g.N; c += nth) {
+        const double v = __ldcg(L0.f + c) - mean;
+        L0.f[c] = v;
+        s2 += v * v;
+        if (A.warm == CDI_WARM_ZERO) L0.p[c] = 0.0;
+    }
+    for (long t = tid; t < g.N + g.NP; t += nth)
+        ops::coef0_at<LG, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, L0.beta, L0.bf, t);
+    double fsq;
+    if (!grid_reduce<false>(s2, R.partials(), R.bar, fsq)) return false;
+    const double fn = sqrt(fsq);
+    for (int l = 1; l < A.lt; ++l) {
+        const MGLevel& F = A.lv[l - 1];
+        const MGLevel& C = A.lv[l];
+        const float* fb[3] = {F.bf[0], F.bf[1], F.bf[2]};
+        for (long t = tid; t < C.g.N + C.g.NP; t += nth) ops::coef_restrict_at<LG, float, DIM>(F.g, C.g, fb, C.bf, t);
+        if (!R.bar.sync()) return false;
+    }
+    double rsq;
+    if (!grid_reduce<false>(resid64_local<DIM>(L0, tid, nth), R.partials(), R.bar, rsq)) return false;
+    double rn = sqrt(rsq);
+    if (!isfinite(fn) || !isfinite(rn)) {
+        set_status(A.ctl, CDI_ENAN);
+        return false;
+    }
+    int cyc = 0;
+    if (fn == 0.0) {
+        for (long c = tid; c < g.N; c += nth) L0.p[c] = 0.0;
+        if (!R.bar.sync()) return false;
+    } else {
+        bool first = true;
+        while (rn > A.tol * fn && cyc < A.max_vcycles) {
+            if (!vcycle<T, DIM>(R, first, sm)) return false;
+            first = false;
+            if (!grid_reduce<false>(resid64_local<DIM>(L0, tid, nth), R.partials(), R.bar, rsq)) return false;
+            rn = sqrt(rsq);
+            ++cyc;
+            if (!isfinite(rn)) {
+                set_status(A.ctl, CDI_ENAN);
+                return false;
+            }
+        }
+        if (rn > A.tol * fn) {
+            set_status(A.ctl, CDI_ENOCONV);
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                A.ctl->last_cycles = cyc;
+                A.ctl->last_resid = rn / fn;
+            }
+            return false;
+        }
+        double ps = 0.0;
+        for (long c = tid; c < g.N; c += nth) ps += __ldcg(L0.p + c);
+        double psum;
+        if (!grid_reduce<false>(ps, R.partials(), R.bar, psum)) return false;
+        const double pmean = psum / (double)g.N;
+        for (long c = tid; c < g.N; c += nth) L0.p[c] = __ldcg(L0.p + c) - pmean;
+        if (!R.bar.sync()) return false;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.ctl->last_cycles = cyc;
+        A.ctl->last_resid = fn == 0.0 ? 0.0 : rn / fn;
+        A.ctl->total_cycles += cyc;
+        if (cyc > A.ctl->max_cycles) A.ctl->max_cycles = cyc;
+    }
+    for (long c = tid; c < g.N; c += nth) ops::project_at<LG, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, u, cdt, L0.p, c);
+    return R.bar.sync();
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kPersistThreads, 1) k_step_persist(PersistArgs<T> A) {
+    extern __shared__ double smd[];
+    float* sm = reinterpret_cast<float*>(smd);
+    Run<T> R{A, Barrier{A.ctl, A.spin_limit}};
+    const Geom& g = A.g;
+    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long)gridDim.x * blockDim.x;
+    T* phi_s = A.phi_s;
+    T* phi_k = A.phi_k;
+    T* u_s[3] = {A.u_s[0], A.u_s[1], A.u_s[2]};
+    T* u_k[3] = {A.u_k[0], A.u_k[1], A.u_k[2]};
+    const double ck[4] = {0.0, 0.5, 0.5, 1.0};
+    const double bk[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    for (int step = 0; step < A.nsteps; ++step) {
+        double gamma = A.gamma_param;
+        if (gamma < 0.0) {  // gamma = 2.5 |u|_max, floored (Sec. 5.1)
+            double mx = 0.0;
+            for (int a = 0; a < DIM; ++a) {
+                const long nf = g.N + (a == DIM - 1 ? g.NP : 0);
+                for (long c = tid; c < nf; c += nth) mx = fmax(mx, fabs((double)__ldcg(u_s[a] + c)));
+            }
+            double umax;
+            if (!grid_reduce<true>(mx, R.partials(), R.bar, umax)) return;
+            gamma = fmax(2.5 * umax, -A.gamma_param);
+        }
+        for (int st = 0; st < 4; ++st) {
+            T* phi = st == 0 ? phi_s : phi_k;
+            T* const* u = st == 0 ? u_s : u_k;
+            StageFields<T> f{};
+            f.phi = phi;
+            for (int a = 0; a < 3; ++a) {
+                f.u[a] = u[a];
+                f.nh[a] = A.nh[a];
+                f.m[a] = A.m[a];
+                f.rm[a] = A.rm[a];
+            }
+            f.psi = A.psi;
+            f.muc = A.muc;
+            f.rphi = A.rphi;
+            f.wuY = A.wuY;
+            f.wghost = A.wghost;
+            f.wmuw = A.wmuw;
+            for (long c = tid; c < g.N; c += nth) ops::psi_at<LG>(g, A.ph, phi, A.psi, c);
+            if (!R.bar.sync()) return;
+            for (long c = tid; c < g.N; c += nth)
+                ops::cell_at<LG, T, DIM>(g, A.ph, phi, A.psi, A.nh[0], A.nh[1], A.nh[2], A.muc, c);
+            for (long t = tid; t < 2 * g.NP; t += nth)
+                ops::wall_at<LG, T, DIM>(g, A.ph, phi, A.psi, u[0], u[1], A.wuY, A.wghost, A.wmuw, t);
+            if (!R.bar.sync()) return;
+            for (long c = tid; c < g.N; c += nth) ops::phi_rhs_at<LG, T, DIM>(g, A.ph, f, (T)gamma, c);
+            if (!R.bar.sync()) return;
+            for (long c = tid; c < g.N; c += nth) ops::mom_at<LG, T, DIM>(g, A.ph, f, c);
+            if (!R.bar.sync()) return;
+            const int first = st == 0, last = st == 3;
+            const double cn = last ? 1.0 : ck[st + 1];
+            const T b = (T)bk[st], cdt = (T)(cn * A.dt), dt = (T)A.dt;
+            for (long c = tid; c < g.N; c += nth)
+                ops::stage_phi_at<LG>(b, cdt, dt, first, last, phi_s, A.rphi, A.acc_phi, phi_k, c);
+            if (!R.bar.sync()) return;
+            const T* u0c[3] = {u_s[0], u_s[1], u_s[2]};
+            const T* rmc[3] = {A.rm[0], A.rm[1], A.rm[2]};
+            T* accm[3] = {A.acc_m[0], A.acc_m[1], A.acc_m[2]};
+            for (long c = tid; c < g.N; c += nth)
+                ops::stage_mom_at<LG, T, DIM>(g, A.ph, b, cdt, dt, first, last, phi_s, phi_k, u0c, rmc, accm, u_k, c);
+            if (!R.bar.sync()) return;
+            if (!project<T, DIM>(R, phi_k, u_k, cn * A.dt, sm)) return;
+        }
+        T* tp = phi_s;
+        phi_s = phi_k;
+        phi_k = tp;
+        for (int a = 0; a < 3; ++a) {
+            T* tu = u_s[a];
+            u_s[a] = u_k[a];
+            u_k[a] = tu;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->steps_done = step + 1;
+    }
+}
+
+}  // namespace
+
+// shared-memory layout of the FP32 tail levels and the FP64 dense-solve scratch; returns bytes
+size_t persist_tail_layout(const Geom& g, const MG& mg, int lt, PersistLayout& L) {
+    long off = 0;  // floats
+    for (int l = lt; l < mg.nlev; ++l) {
+        const Geom& v = mg.lv[l].g;
+        L.sm_e[l] = off;
+        off += v.N;
+        L.sm_r[l] = off;
+        off += v.N;
+        for (int a = 0; a < 3; ++a) {
+            L.sm_b[l][a] = off;
+            if (a < g.D) off += v.N + (a == g.W ? v.NP : 0);
+        }
+    }
+    off = (off + 1) & ~1L;  // 8-byte alignment for the double scratch
+    L.sm_dbl = off;
+    long d = 0;  // doubles
+    L.sm_A = d;
+    d += (long)kMaxCoarse * kMaxCoarse;
+    L.sm_bb = d;
+    d += 2 * kMaxCoarse;
+    L.sm_fct = d;
+    d += kMaxCoarse;
+    return (size_t)off * sizeof(float) + (size_t)d * sizeof(double);
+}
+
+template <typename T>
+cudaError_t launch_step_persist(PersistArgs<T>& A, size_t smem, int grid, cudaStream_t s) {
+    void* args[] = {&A};
+    const void* fn = (A.g.D == 2) ? (const void*)k_step_persist<T, 2> : (const void*)k_step_persist<T, 3>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPersistThreads), args, smem, s);
+}
+
+template <typename T>
+cudaError_t persist_prepare(int dim, size_t smem, int* grid) {
+    const void* fn = (dim == 2) ? (const void*)k_step_persist<T, 2> : (const void*)k_step_persist<T, 3>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kPersistThreads, smem)) != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    *grid = nsm;  // one CTA per SM
+    return cudaSuccess;
+}
+
+template cudaError_t launch_step_persist<double>(PersistArgs<double>&, size_t, int, cudaStream_t);
+template cudaError_t launch_step_persist<float>(PersistArgs<float>&, size_t, int, cudaStream_t);
+template cudaError_t persist_prepare<double>(int, size_t, int*);
+template cudaError_t persist_prepare<float>(int, size_t, int*);
+
+}  // namespace cdi

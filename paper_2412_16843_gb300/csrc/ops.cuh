@@ -1,0 +1,700 @@
+// Per-element device operations of the time step.  The standalone kernels
+// (k_stencil.cu, k_mg.cu) and the persistent step kernel (k_persist.cu) both
+// call these, so the two execution paths share one copy of the arithmetic.
+//
+// The load policy L decides how fields are read: LdPlain is an ordinary
+// global load; LdCG reads through L2 only (ld.global.cg), which the persistent
+// kernel uses for every field another block may have written before the last
+// grid barrier.
+//
+// Formulas (paper sections and equations):
+//   psi_at          Eq. (psi), phi clamped to [delta, 1-delta]
+//   cell_at         Eqs. (chemical potential), (curvature); normal grad psi/|grad psi|;
+//                   central differences inside, one-sided in the wall rows (Sec. 4)
+//   wall_at         Eqs. (slip BC), (u_slip_v), (u_slip_Y) and Models 1A..4B (Sec. 3);
+//                   wall values by first-order linear extrapolation (Sec. 4)
+//   phi_rhs_at      Eqs. (CDI), (no-flux BC): u phi - R on faces, zero on walls;
+//                   mass flux (rho1-rho2)(u phi - R) + rho2 u of Eq. (NS_momentum)
+//   mom_at          Eq. (NS_momentum) without the pressure; Eq. (EB surface tension)
+//   stage_*_at      classical RK4 (Sec. 4) on phi and on the face momentum rho_f u
+//   div/coef/rbgs/resid/restrict/prolong/project: projection onto div u = 0
+//                   (Eq. NS_incompressibility) by geometric multigrid
+#pragma once
+
+#include "cdi_internal.cuh"
+
+namespace cdi {
+namespace ops {
+
+struct LdPlain {
+    template <typename T>
+    __device__ __forceinline__ static T ld(const T* p) { return *p; }
+};
+struct LdCG {
+    template <typename T>
+    __device__ __forceinline__ static T ld(const T* p) { return __ldcg(p); }
+};
+
+// ---------------------------------------------------------------------------
+// a1: psi and cell-centre derivatives
+// ---------------------------------------------------------------------------
+template <class L, typename T>
+__device__ __forceinline__ void d12(const Geom& g, const T* s, const IJK& q, long c, int b, T ih, T& d1, T& d2) {
+    const T half_ih = T(0.5) * ih, ih2 = ih * ih;
+    if (b == g.W) {
+        const int r = coord(q, b);
+        const long st = g.NP;
+        if (r == 0) {
+            T s0 = L::ld(s + c), s1 = L::ld(s + c + st), s2 = L::ld(s + c + 2 * st), s3 = L::ld(s + c + 3 * st);
+            d1 = (T(-3) * s0 + T(4) * s1 - s2) * half_ih;
+            d2 = (T(2) * s0 - T(5) * s1 + T(4) * s2 - s3) * ih2;
+            return;
+        }
+        if (r == g.n[b] - 1) {
+            T s0 = L::ld(s + c), s1 = L::ld(s + c - st), s2 = L::ld(s + c - 2 * st), s3 = L::ld(s + c - 3 * st);
+            d1 = (T(3) * s0 - T(4) * s1 + s2) * half_ih;
+            d2 = (T(2) * s0 - T(5) * s1 + T(4) * s2 - s3) * ih2;
+            return;
+        }
+        T sm = L::ld(s + c - st), s0 = L::ld(s + c), sp = L::ld(s + c + st);
+        d1 = (sp - sm) * half_ih;
+        d2 = (sp - T(2) * s0 + sm) * ih2;
+        return;
+    }
+    T sm = L::ld(s + idx(g, shift(g, q, b, -1))), s0 = L::ld(s + c), sp = L::ld(s + idx(g, shift(g, q, b, 1)));
+    d1 = (sp - sm) * half_ih;
+    d2 = (sp - T(2) * s0 + sm) * ih2;
+}
+
+template <class L, typename T>
+__device__ __forceinline__ void psi_at(const Geom& g, const PhysDev& ph, const T* phi, T* psi, long c) {
+    const T delta = (T)ph.delta;
+    T pt = clampv(L::ld(phi + c), delta, T(1) - delta);
+    psi[c] = (T)ph.eps * log(pt / (T(1) - pt));
+}
+
+template <class L, typename T, int DIM>
+__device__ __forceinline__ void cell_at(const Geom& g, const PhysDev& ph, const T* phi, const T* psi, T* nh0,
+                                        T* nh1, T* nh2, T* muc, long c) {
+    const IJK q = decode(g, c);
+    const T ih = T(1) / (T)g.h;
+    T gb[3], grad2 = T(0), lap = T(0);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+        T d1, d2;
+        d12<L>(g, psi, q, c, b, ih, d1, d2);
+        gb[b] = d1;
+        grad2 += d1 * d1;
+        lap += d2;
+    }
+    const T delta = (T)ph.delta, eps = (T)ph.eps;
+    T pt = clampv(L::ld(phi + c), delta, T(1) - delta);
+    T P = pt * (T(1) - pt);
+    muc[c] = T(6) * (T)ph.sigma * (P * (T(1) - T(2) * pt) * (T(1) - grad2) / eps - P * lap);
+    T gm = sqrt(grad2) + (T)ph.tau;
+    nh0[c] = gb[0] / gm;
+    nh1[c] = gb[1] / gm;
+    if (DIM == 3) nh2[c] = gb[2] / gm;
+}
+
+// ---------------------------------------------------------------------------
+// a2: wall rows
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ColQ {
+    T phiw, psiw, dnw, kpw, dnphiw;
+    T gt[2], gtphi[2];
+};
+
+// values extrapolated to wall s from the first two cell centres of column (i, j):
+// q_w = (3 q_0 - q_1)/2 (first-order linear extrapolation, Sec. 4)
+template <class L, typename T, int DIM>
+__device__ ColQ<T> wall_column(const Geom& g, const PhysDev& ph, const T* phi, const T* psi, int s, int i, int j) {
+    const int W = DIM - 1, nW = g.n[W];
+    const int r0 = s == 0 ? 0 : nW - 1, r1 = s == 0 ? 1 : nW - 2;
+    const T sgn = s == 0 ? T(1) : T(-1);  // inward wall normal
+    const T ih = T(1) / (T)g.h;
+    const T delta = (T)ph.delta, eps = (T)ph.eps, tau = (T)ph.tau;
+    T kp[2], dn[2], dnph[2], gtv[2][2], gtp[2][2], phv[2], psv[2];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        IJK q;
+        q.i = i;
+        if (DIM == 2) { q.j = rr == 0 ? r0 : r1; q.k = 0; }
+        else { q.j = j; q.k = rr == 0 ? r0 : r1; }
+        const long c = idx(g, q);
+        T gb[3], grad2 = T(0), lap = T(0), dph[3];
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) {
+            T d1, d2;
+            d12<L>(g, psi, q, c, b, ih, d1, d2);
+            gb[b] = d1;
+            grad2 += d1 * d1;
+            lap += d2;
+            T e1, e2;
+            d12<L>(g, phi, q, c, b, ih, e1, e2);
+            dph[b] = e1;
+        }
+        const T phic = L::ld(phi + c), psic = L::ld(psi + c);
+        T pt = clampv(phic, delta, T(1) - delta);
+        T kap = (T(1) - T(2) * pt) * (T(1) - grad2) / eps - lap;
+        if (DIM == 3) {
+            // in-plane curvature: subtract the normal curvature along the
+            // contact-line direction s = n_phi x n_wall (tangent to the wall)
+            const T ih2 = ih * ih;
+            T pxx = (L::ld(psi + idx(g, shift(g, q, 0, 1))) - T(2) * psic + L::ld(psi + idx(g, shift(g, q, 0, -1)))) *
+                    ih2;
+            T pyy = (L::ld(psi + idx(g, shift(g, q, 1, 1))) - T(2) * psic + L::ld(psi + idx(g, shift(g, q, 1, -1)))) *
+                    ih2;
+            IJK qpp = shift(g, shift(g, q, 0, 1), 1, 1), qpm = shift(g, shift(g, q, 0, 1), 1, -1);
+            IJK qmp = shift(g, shift(g, q, 0, -1), 1, 1), qmm = shift(g, shift(g, q, 0, -1), 1, -1);
+            T pxy = (L::ld(psi + idx(g, qpp)) - L::ld(psi + idx(g, qpm)) - L::ld(psi + idx(g, qmp)) +
+                     L::ld(psi + idx(g, qmm))) *
+                    (T(0.25) * ih2);
+            T px = gb[0], py = gb[1];
+            T gm = sqrt(grad2);
+            T t2 = px * px + py * py;
+            T num = py * py * pxx - T(2) * px * py * pxy + px * px * pyy;
+            T ks = -num / ((t2 + tau * tau) * (gm + tau));
+            kap -= ks;
+        }
+        kp[rr] = kap;
+        dn[rr] = sgn * gb[W];
+        dnph[rr] = sgn * dph[W];
+        gtv[rr][0] = gb[0];
+        gtp[rr][0] = dph[0];
+        gtv[rr][1] = (DIM == 3) ? gb[1] : T(0);
+        gtp[rr][1] = (DIM == 3) ? dph[1] : T(0);
+        phv[rr] = phic;
+        psv[rr] = psic;
+    }
+    ColQ<T> o;
+    o.phiw = clampv(T(0.5) * (T(3) * phv[0] - phv[1]), T(0), T(1));
+    o.psiw = T(0.5) * (T(3) * psv[0] - psv[1]);
+    o.dnw = T(0.5) * (T(3) * dn[0] - dn[1]);
+    o.kpw = T(0.5) * (T(3) * kp[0] - kp[1]);
+    o.dnphiw = T(0.5) * (T(3) * dnph[0] - dnph[1]);
+    o.gt[0] = T(0.5) * (T(3) * gtv[0][0] - gtv[1][0]);
+    o.gtphi[0] = T(0.5) * (T(3) * gtp[0][0] - gtp[1][0]);
+    o.gt[1] = T(0.5) * (T(3) * gtv[0][1] - gtv[1][1]);
+    o.gtphi[1] = T(0.5) * (T(3) * gtp[0][1] - gtp[1][1]);
+    return o;
+}
+
+// u^Y of the slip models of Sec. 3: -(6 sigma/beta) [A + B cos(theta_eq)] T
+template <typename T>
+__device__ __forceinline__ T slip_model(int model, T sigma, T eps, T beta, T costh, T P, T dnpsi, T dtpsi, T gpsi,
+                                        T dnphi, T dtphi, T gphi, T kp, T psiw) {
+    const bool corr = (model == M3A || model == M3B || model == M4A || model == M4B);
+    const T cc = corr ? (T(1) + kp * psiw) : T(1);
+    T A, B, Tt;
+    switch (model) {
+        case M1A: case M3A: A = eps * dnphi; B = P * cc; Tt = dtphi; break;
+        case M1B: case M3B: A = eps * dnphi; B = eps * gphi * cc; Tt = dtphi; break;
+        case M2A: case M4A: A = P * dnpsi; B = P * cc; Tt = P / eps * dtpsi; break;
+        default:            A = P * dnpsi; B = P * gpsi * cc; Tt = P / eps * dtpsi; break;
+    }
+    return -(T(6) * sigma / beta) * (A + B * costh) * Tt;
+}
+
+// thread t in [0, 2 NP): wall s = t / NP, wall-plane position t % NP; slip
+// velocity, ghost value and wall viscosity of every tangential component
+template <class L, typename T, int DIM>
+__device__ void wall_at(const Geom& g, const PhysDev& ph, const T* phi, const T* psi, const T* u0, const T* u1,
+                        T* wuY, T* wghost, T* wmuw, long t) {
+    const int s = (int)(t / g.NP);
+    const long pidx = t - s * g.NP;
+    const int i = (int)(pidx % g.n[0]);
+    const int j = (DIM == 3) ? (int)(pidx / g.n[0]) : 0;
+    const int W = DIM - 1;
+    const int r0 = s == 0 ? 0 : g.n[W] - 1;
+    const T ih = T(1) / (T)g.h;
+    const WallDev& wp = ph.wall[s];
+    const ColQ<T> cR = wall_column<L, T, DIM>(g, ph, phi, psi, s, i, j);
+#pragma unroll
+    for (int a = 0; a < DIM - 1; ++a) {
+        int iL = i, jL = j;
+        if (a == 0) iL = (i == 0) ? g.n[0] - 1 : i - 1;
+        else jL = (j == 0) ? g.n[1] - 1 : j - 1;
+        const ColQ<T> cL = wall_column<L, T, DIM>(g, ph, phi, psi, s, iL, jL);
+        const T pb = T(0.5) * (cL.phiw + cR.phiw);
+        const T P = pb * (T(1) - pb);
+        const T psb = T(0.5) * (cL.psiw + cR.psiw);
+        const T dnb = T(0.5) * (cL.dnw + cR.dnw);
+        const T kb = T(0.5) * (cL.kpw + cR.kpw);
+        const T dtau = (cR.psiw - cL.psiw) * ih;
+        const T dnphi = T(0.5) * (cL.dnphiw + cR.dnphiw);
+        const T dtphi = (cR.phiw - cL.phiw) * ih;
+        T gs = dnb * dnb, gf = dnphi * dnphi;
+#pragma unroll
+        for (int tt = 0; tt < DIM - 1; ++tt) {
+            T gt = (tt == a) ? dtau : T(0.5) * (cL.gt[tt] + cR.gt[tt]);
+            T gtf = (tt == a) ? dtphi : T(0.5) * (cL.gtphi[tt] + cR.gtphi[tt]);
+            gs += gt * gt;
+            gf += gtf * gtf;
+        }
+        const T muw = (T)(ph.mu1 - ph.mu2) * pb + (T)ph.mu2;
+        T uY = T(0), lw = T(0);
+        if (!wp.noslip) {
+            const T beta = (T)(wp.beta1 - wp.beta2) * pb + (T)wp.beta2;  // beta linear in phi
+            uY = slip_model<T>(ph.model, (T)ph.sigma, (T)ph.eps, beta, (T)wp.costh, P, dnb, dtau, sqrt(gs), dnphi,
+                               dtphi, sqrt(gf), kb, psb);
+            lw = muw / beta;
+        }
+        const long cq = (DIM == 2) ? encode(g, i, r0, 0) : encode(g, i, j, r0);
+        const T uf = (a == 0) ? L::ld(u0 + cq) : L::ld(u1 + cq);
+        // ghost value: u_w = (u0+ug)/2, d_n u = (u0-ug)/h, u_w - U = l_w d_n u + u^Y
+        const T lwh = lw * ih;
+        const T ug = ((T)wp.U[a] + uY - uf * (T(0.5) - lwh)) / (T(0.5) + lwh);
+        const long o = ((long)s * (DIM - 1) + a) * g.NP + pidx;
+        wuY[o] = uY;
+        wghost[o] = ug;
+        wmuw[o] = muw;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a3: phi flux and the consistent mass flux
+// ---------------------------------------------------------------------------
+template <class L, typename T>
+__device__ __forceinline__ T phi_flux(const T* phi, const T* nh, long cL, long cR, T uf, T gamma, T eps, T ih,
+                                      T delta) {
+    const T fL = L::ld(phi + cL), fR = L::ld(phi + cR);
+    const T pb = T(0.5) * (fL + fR);
+    const T pc = clampv(pb, delta, T(1) - delta);
+    const T nb = T(0.5) * (L::ld(nh + cL) + L::ld(nh + cR));
+    return uf * pb - gamma * (eps * (fR - fL) * ih - pc * (T(1) - pc) * nb);
+}
+
+template <class L, typename T, int DIM>
+__device__ __forceinline__ void phi_rhs_at(const Geom& g, const PhysDev& ph, const StageFields<T>& f, T gamma,
+                                           long c) {
+    const IJK q = decode(g, c);
+    const int W = DIM - 1;
+    const T ih = T(1) / (T)g.h;
+    const T eps = (T)ph.eps, delta = (T)ph.delta;
+    const T drho = (T)(ph.rho1 - ph.rho2), rho2 = (T)ph.rho2;
+    T div = T(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const T* ua = f.u[a];
+        const T* na = f.nh[a];
+        const int r = coord(q, a);
+        T Flo = T(0), Fhi = T(0);
+        const T ulo = L::ld(ua + c);
+        if (!(a == W && r == 0)) {
+            long cL = idx(g, shift(g, q, a, -1));
+            Flo = phi_flux<L>(f.phi, na, cL, c, ulo, gamma, eps, ih, delta);
+        }
+        if (!(a == W && r == g.n[W] - 1)) {
+            long cR = idx(g, shift(g, q, a, 1));
+            long fi = (a == W) ? c + g.NP : cR;
+            Fhi = phi_flux<L>(f.phi, na, c, cR, L::ld(ua + fi), gamma, eps, ih, delta);
+        }
+        div += Fhi - Flo;
+        f.m[a][c] = (a == W && r == 0) ? T(0) : drho * Flo + rho2 * ulo;
+    }
+    f.rphi[c] = -div * ih;
+}
+
+// ---------------------------------------------------------------------------
+// a4: momentum right-hand side (all components on the low faces of cell c)
+// ---------------------------------------------------------------------------
+template <class L, typename T, int DIM>
+__device__ void mom_at(const Geom& g, const PhysDev& ph, const StageFields<T>& f, long c) {
+    const IJK q = decode(g, c);
+    const int W = DIM - 1, nW = g.n[W];
+    const T ih = T(1) / (T)g.h;
+    const T dmu = (T)(ph.mu1 - ph.mu2), mu2 = (T)ph.mu2;
+    const T* phi = f.phi;
+    auto mu = [&](long cc) { return dmu * L::ld(phi + cc) + mu2; };
+    const long pidx = (DIM == 2) ? (long)q.i : (long)q.i + (long)g.n[0] * q.j;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const T* ua = f.u[a];
+        if (a == W && coord(q, W) == 0) { f.rm[a][c] = T(0); continue; }  // wall face
+        const long cR = c;
+        const long cL = idx(g, shift(g, q, a, -1));
+        T adv = T(0), vis = T(0);
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) {
+            if (b == a) {
+                const long fRlo = c, fRhi = (a == W) ? c + g.NP : idx(g, shift(g, q, a, 1));
+                const long fLlo = cL, fLhi = c;
+                const T* ma = f.m[a];
+                const T uRlo = L::ld(ua + fRlo), uRhi = L::ld(ua + fRhi), uLlo = L::ld(ua + fLlo);
+                T mbR = T(0.5) * (L::ld(ma + fRlo) + L::ld(ma + fRhi)), ubR = T(0.5) * (uRlo + uRhi);
+                T mbL = T(0.5) * (L::ld(ma + fLlo) + L::ld(ma + fLhi)), ubL = T(0.5) * (uLlo + uRlo);
+                T tR = T(2) * mu(cR) * (uRhi - uRlo) * ih;
+                T tL = T(2) * mu(cL) * (uRlo - uLlo) * ih;
+                adv -= (mbR * ubR - mbL * ubL) * ih;
+                vis += (tR - tL) * ih;
+            } else {
+                T conv[2], tau[2];
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    const int eb = coord(q, b) + side;
+                    if (b == W && (eb == 0 || eb == nW)) {
+                        const int s = eb == 0 ? 0 : 1;
+                        const long o = ((long)s * (DIM - 1) + a) * g.NP + pidx;
+                        const T ug = L::ld(f.wghost + o), muw = L::ld(f.wmuw + o);
+                        const T u0 = L::ld(ua + c);
+                        conv[side] = T(0);
+                        tau[side] = (s == 0) ? muw * (u0 - ug) * ih : muw * (ug - u0) * ih;
+                        continue;
+                    }
+                    IJK qhi = q;
+                    setc(qhi, b, eb);
+                    if (b != W && eb == g.n[b]) setc(qhi, b, 0);
+                    const IJK qlo = shift(g, qhi, b, -1);
+                    const long chi = idx(g, qhi), clo = idx(g, qlo);
+                    const long chiA = idx(g, shift(g, qhi, a, -1)), cloA = idx(g, shift(g, qlo, a, -1));
+                    const T uhi = L::ld(ua + chi), ulo = L::ld(ua + clo);
+                    const T ub = T(0.5) * (ulo + uhi);
+                    const T mb = T(0.5) * (L::ld(f.m[b] + chi) + L::ld(f.m[b] + chiA));
+                    conv[side] = mb * ub;
+                    const T me = T(0.25) * (mu(chi) + mu(chiA) + mu(clo) + mu(cloA));
+                    const T dub = (uhi - ulo) * ih;
+                    const T dua = (L::ld(f.u[b] + chi) - L::ld(f.u[b] + chiA)) * ih;
+                    tau[side] = me * (dub + dua);
+                }
+                adv -= (conv[1] - conv[0]) * ih;
+                vis += (tau[1] - tau[0]) * ih;
+            }
+        }
+        // energy-based surface tension on the face (Eq. EB)
+        const T st = T(0.5) * (L::ld(f.muc + cL) + L::ld(f.muc + cR)) * (L::ld(phi + cR) - L::ld(phi + cL)) * ih;
+        f.rm[a][c] = adv + vis + st;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a5: RK4 stage values
+// ---------------------------------------------------------------------------
+template <class L, typename T>
+__device__ __forceinline__ void stage_phi_at(T b, T cdt, T dt, int first, int last, const T* phi0, const T* rphi,
+                                             T* acc, T* phik, long c) {
+    const T k = L::ld(rphi + c);
+    const T a = first ? b * k : L::ld(acc + c) + b * k;
+    acc[c] = a;
+    phik[c] = last ? L::ld(phi0 + c) + dt * a : L::ld(phi0 + c) + cdt * k;
+}
+
+template <class L, typename T, int DIM>
+__device__ __forceinline__ void stage_mom_at(const Geom& g, const PhysDev& ph, T b, T cdt, T dt, int first, int last,
+                                             const T* phi0, const T* phik, const T* const* u0, const T* const* rm,
+                                             T* const* acc, T* const* uk, long c) {
+    const IJK q = decode(g, c);
+    const int W = DIM - 1;
+    const T drho = (T)(ph.rho1 - ph.rho2), rho2 = (T)ph.rho2;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        if (a == W && coord(q, W) == 0) { uk[a][c] = T(0); acc[a][c] = T(0); continue; }
+        const long cL = idx(g, shift(g, q, a, -1));
+        const T rf0 = T(0.5) * ((drho * L::ld(phi0 + cL) + rho2) + (drho * L::ld(phi0 + c) + rho2));
+        const T M0 = rf0 * L::ld(u0[a] + c);
+        const T k = L::ld(rm[a] + c);
+        const T ac = first ? b * k : L::ld(acc[a] + c) + b * k;
+        acc[a][c] = ac;
+        const T Mv = last ? M0 + dt * ac : M0 + cdt * k;
+        const T rfk = T(0.5) * ((drho * L::ld(phik + cL) + rho2) + (drho * L::ld(phik + c) + rho2));
+        uk[a][c] = Mv / rfk;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a6..a8: projection and multigrid
+//
+// The pressure solve is FP64 defect correction around an FP32 V-cycle: the
+// residual r = f - A p, its norm and the update p += e are FP64; the V-cycle
+// that computes the correction e ~ A^-1 r runs in FP32 (M = float), except
+// the dense solve of the coarsest level, which is FP64.  The iteration
+// converges to the FP64 tolerance because each V-cycle only has to reduce the
+// error by a fixed factor.
+// ---------------------------------------------------------------------------
+template <class L, typename T, int DIM>
+__device__ __forceinline__ double div_at(const Geom& g, const T* const* us, double ih, double inv_cdt, long c) {
+    const IJK q = decode(g, c);
+    double div = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const long hi = (a == DIM - 1) ? c + g.NP : idx(g, shift(g, q, a, 1));
+        div += (double)L::ld(us[a] + hi) - (double)L::ld(us[a] + c);
+    }
+    return div * ih * inv_cdt;
+}
+
+// face coefficients 1/rho_f of level 0 in FP64 (bs) and FP32 (bsf); t in
+// [0, N + NP) (the last NP are the high wall faces of the wall-normal component)
+template <class L, typename T, int DIM>
+__device__ __forceinline__ void coef0_at(const Geom& g, double rho1, double rho2, const T* phi, double* const* bs,
+                                         float* const* bsf, long t) {
+    if (t >= g.N) {
+        bs[DIM - 1][t] = 0.0;
+        bsf[DIM - 1][t] = 0.f;
+        return;
+    }
+    const IJK q = decode(g, t);
+    const double dr = rho1 - rho2;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        if (a == DIM - 1 && coord(q, a) == 0) {
+            bs[a][t] = 0.0;
+            bsf[a][t] = 0.f;
+            continue;
+        }
+        const long cL = idx(g, shift(g, q, a, -1));
+        const double rf = 0.5 * ((dr * (double)L::ld(phi + cL) + rho2) + (dr * (double)L::ld(phi + t) + rho2));
+        const double b = 1.0 / rf;
+        bs[a][t] = b;
+        bsf[a][t] = (float)b;
+    }
+}
+
+// coarse face coefficient = mean of the 2^(D-1) fine faces covering it; t in [0, Nc + NPc)
+template <class L, typename M, int DIM>
+__device__ __forceinline__ void coef_restrict_at(const Geom& gf, const Geom& gc, const M* const* fb, M* const* cb,
+                                                 long t) {
+    IJK q = decode(gc, t < gc.N ? t : t - gc.NP);
+    if (t >= gc.N) setc(q, DIM - 1, gc.n[DIM - 1]);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        if (t >= gc.N && a != DIM - 1) continue;
+        int other[2] = {0, 0}, no = 0;
+        for (int b = 0; b < DIM; ++b)
+            if (b != a) other[no++] = b;
+        const int o2 = (DIM == 3) ? 2 : 1;
+        M sum = M(0);
+        for (int t2 = 0; t2 < o2; ++t2)
+            for (int t1 = 0; t1 < 2; ++t1) {
+                IJK qf;
+                qf.i = 2 * q.i;
+                qf.j = 2 * q.j;
+                qf.k = (DIM == 3) ? 2 * q.k : 0;
+                setc(qf, other[0], coord(qf, other[0]) + t1);
+                if (DIM == 3) setc(qf, other[1], coord(qf, other[1]) + t2);
+                sum += L::ld(fb[a] + idx(gf, qf));
+            }
+        cb[a][idx(gc, q)] = sum * (M(1) / M(2 * o2));
+    }
+}
+
+// (A p)_c pieces: diag = sum (beta- + beta+)/h^2, off = sum (beta- p- + beta+ p+)/h^2;
+// zero coefficients on the walls (Neumann); returns off - diag p_c
+template <class L, typename M, int DIM>
+__device__ __forceinline__ M apply_L(const Geom& g, const M* const* beta, const M* p, const IJK& q, long c, M ih2,
+                                     M& diag, M& off) {
+    diag = M(0);
+    off = M(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        // neighbour indices; beyond a wall the index is clamped to c itself and
+        // the zero wall coefficient cancels the term, so every load is issued
+        // at once (no load waits on the coefficient)
+        long lo, hi;
+        if (a == DIM - 1) {
+            const int r = coord(q, a);
+            lo = r > 0 ? c - g.NP : c;
+            hi = r < g.n[a] - 1 ? c + g.NP : c;
+        } else {
+            lo = idx(g, shift(g, q, a, -1));
+            hi = idx(g, shift(g, q, a, 1));
+        }
+        const long fhi = (a == DIM - 1) ? c + g.NP : hi;
+        const M bm = L::ld(beta[a] + c);
+        const M bp = L::ld(beta[a] + fhi);
+        const M pm = L::ld(p + lo);
+        const M pp = L::ld(p + hi);
+        diag += (bm + bp) * ih2;
+        off += (bm * pm + bp * pp) * ih2;
+    }
+    return off - diag * L::ld(p + c);
+}
+
+// k-th cell of one colour ((i+j+k) even or odd); every extent of a smoothed level is even
+__device__ __forceinline__ long colour_cell(const Geom& g, int colour, long k) {
+    const unsigned half = (unsigned)g.n[0] >> 1;
+    const unsigned line = (unsigned)k / half;
+    const unsigned m = (unsigned)k - line * half;
+    const unsigned kk = g.fd1.div(line);
+    const unsigned j = line - kk * (unsigned)g.n[1];
+    const unsigned i = 2u * m + ((colour + j + kk) & 1u);
+    return (long)(i + (unsigned)g.n[0] * line);
+}
+
+template <class L, typename M, int DIM>
+__device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* p, const M* f, long c) {
+    const IJK q = decode(g, c);
+    const M ih2 = M(1) / M(g.h * g.h);
+    M diag, off;
+    apply_L<L, M, DIM>(g, beta, p, q, c, ih2, diag, off);
+    p[c] = (off - L::ld(f + c)) / diag;
+}
+
+// FP64 residual f - A p of level 0
+template <class L, int DIM>
+__device__ __forceinline__ double resid64_at(const Geom& g, const double* const* beta, const double* p,
+                                             const double* f, long c) {
+    const IJK q = decode(g, c);
+    const double ih2 = 1.0 / (g.h * g.h);
+    double diag, off;
+    return L::ld(f + c) - apply_L<L, double, DIM>(g, beta, p, q, c, ih2, diag, off);
+}
+
+// coarse cell t: mean of the 2^D fine residuals; zero coarse correction
+template <class L, typename M, int DIM>
+__device__ __forceinline__ void resid_restrict_at(const Geom& gf, const Geom& gc, const M* const* beta, const M* p,
+                                                  const M* f, M* fc, M* pc, long t) {
+    const IJK Q = decode(gc, t);
+    const M ih2 = M(1) / M(gf.h * gf.h);
+    const int o2 = (DIM == 3) ? 2 : 1;
+    M s = M(0);
+    for (int t2 = 0; t2 < o2; ++t2)
+        for (int t1 = 0; t1 < 2; ++t1)
+            for (int t0 = 0; t0 < 2; ++t0) {
+                IJK q;
+                q.i = 2 * Q.i + t0;
+                q.j = 2 * Q.j + t1;
+                q.k = (DIM == 3) ? 2 * Q.k + t2 : 0;
+                const long c = idx(gf, q);
+                M diag, off;
+                const M Lp = apply_L<L, M, DIM>(gf, beta, p, q, c, ih2, diag, off);
+                s += L::ld(f + c) - Lp;
+            }
+    fc[t] = s * (M(1) / M(4 * o2));
+    pc[t] = M(0);
+}
+
+// cell-centred (bi/tri)linear prolongation, weights 3/4 and 1/4 per axis;
+// beyond a wall the coarse value is reflected (Neumann)
+template <class L, typename M, int DIM>
+__device__ __forceinline__ M prolong_val(const Geom& gf, const Geom& gc, const M* pc, long c) {
+    const IJK q = decode(gf, c);
+    int I[3][2];
+    M w[3][2];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        if (b >= DIM) { I[b][0] = I[b][1] = 0; w[b][0] = M(1); w[b][1] = M(0); continue; }
+        const int qb = coord(q, b);
+        const int P = qb >> 1;
+        int nb = (qb & 1) ? P + 1 : P - 1;
+        if (b == DIM - 1) nb = min(max(nb, 0), gc.n[b] - 1);
+        else { if (nb < 0) nb += gc.n[b]; else if (nb >= gc.n[b]) nb -= gc.n[b]; }
+        I[b][0] = P;
+        I[b][1] = nb;
+        w[b][0] = M(0.75);
+        w[b][1] = M(0.25);
+    }
+    M s = M(0);
+#pragma unroll
+    for (int t2 = 0; t2 < (DIM == 3 ? 2 : 1); ++t2)
+#pragma unroll
+        for (int t1 = 0; t1 < 2; ++t1)
+#pragma unroll
+            for (int t0 = 0; t0 < 2; ++t0)
+                s += w[0][t0] * w[1][t1] * w[2][t2] * L::ld(pc + encode(gc, I[0][t0], I[1][t1], I[2][t2]));
+    return s;
+}
+
+template <class L, typename M, int DIM>
+__device__ __forceinline__ void prolong_at(const Geom& gf, const Geom& gc, const M* pc, M* p, long c) {
+    p[c] = L::ld(p + c) + prolong_val<L, M, DIM>(gf, gc, pc, c);
+}
+
+// u = u* - c dt grad p / rho_f on the interior faces of cell c
+template <class L, typename T, int DIM>
+__device__ __forceinline__ void project_at(const Geom& g, double rho1, double rho2, const T* phi, T* const* us,
+                                           double cdt, const double* p, long c) {
+    const IJK q = decode(g, c);
+    const double ih = 1.0 / g.h, dr = rho1 - rho2;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        if (a == DIM - 1 && coord(q, a) == 0) continue;  // wall face stays zero
+        const long cL = idx(g, shift(g, q, a, -1));
+        const double rf = 0.5 * ((dr * (double)L::ld(phi + cL) + rho2) + (dr * (double)L::ld(phi + c) + rho2));
+        const double beta = 1.0 / rf;
+        const double dp = (L::ld(p + c) - L::ld(p + cL)) * ih;
+        us[a][c] = (T)((double)L::ld(us[a] + c) - cdt * beta * dp);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dense FP64 solve of (A + c 1 1^T) e = r on a level of at most kMaxCoarse
+// cells by one thread block (Gaussian elimination with partial pivoting).
+// A, bb, fct: FP64 scratch of kMaxCoarse^2, kMaxCoarse and kMaxCoarse values.
+// The rank-one term c 1 1^T (c = mean diagonal / n) removes the constant null
+// space of the periodic + Neumann operator; the right-hand side sums to zero.
+// ---------------------------------------------------------------------------
+template <class L, typename M, int DIM>
+__device__ void coarse_solve_block(const Geom& g, const M* const* beta, const M* f, M* p, double* A, double* bb,
+                                   double* fct, int* piv_s, double* shift_s) {
+    const int n = (int)g.N;
+    const double ih2 = 1.0 / (g.h * g.h);
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double dsum = 0.0;
+        for (int c = 0; c < n; ++c) {
+            const IJK q = decode(g, c);
+            for (int a = 0; a < DIM; ++a) {
+                const long hi = (a == DIM - 1) ? c + g.NP : idx(g, shift(g, q, a, 1));
+                const double bm = (double)L::ld(beta[a] + c), bp = (double)L::ld(beta[a] + hi);
+                A[c * n + c] -= (bm + bp) * ih2;
+                if (bm != 0.0) A[c * n + idx(g, shift(g, q, a, -1))] += bm * ih2;
+                if (bp != 0.0) A[c * n + hi] += bp * ih2;
+            }
+            dsum += -A[c * n + c];
+            bb[c] = (double)L::ld(f + c);
+        }
+        *shift_s = -dsum / ((double)n * (double)n);
+    }
+    __syncthreads();
+    const double sh = *shift_s;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] += sh;
+    __syncthreads();
+    for (int col = 0; col < n; ++col) {
+        if (threadIdx.x == 0) {
+            int pv = col;
+            for (int r = col + 1; r < n; ++r)
+                if (fabs(A[r * n + col]) > fabs(A[pv * n + col])) pv = r;
+            *piv_s = pv;
+        }
+        __syncthreads();
+        const int pv = *piv_s;
+        if (pv != col) {
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                double tmp = A[col * n + t];
+                A[col * n + t] = A[pv * n + t];
+                A[pv * n + t] = tmp;
+            }
+            if (threadIdx.x == 0) {
+                double tmp = bb[col];
+                bb[col] = bb[pv];
+                bb[pv] = tmp;
+            }
+        }
+        __syncthreads();
+        for (int r = col + 1 + threadIdx.x; r < n; r += blockDim.x) fct[r] = A[r * n + col] / A[col * n + col];
+        __syncthreads();
+        for (int r = col + 1 + threadIdx.x; r < n; r += blockDim.x) {
+            const double fr = fct[r];
+            if (fr == 0.0) continue;
+            for (int t = col; t < n; ++t) A[r * n + t] -= fr * A[col * n + t];
+            bb[r] -= fr * bb[col];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int r = n - 1; r >= 0; --r) {
+            double s = bb[r];
+            for (int t = r + 1; t < n; ++t) s -= A[r * n + t] * bb[n + t];
+            bb[n + r] = s / A[r * n + r];
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) p[c] = (M)bb[n + c];
+    __syncthreads();
+}
+
+}  // namespace ops
+}  // namespace cdi

@@ -29,10 +29,15 @@ def rel(a, b):
     return np.abs(a - b).max() / scale
 
 
-def pair(wl, tol=1e-12, precision=cdi.FP64):
+def pair(wl, tol=1e-12, precision=cdi.FP64, exec_mode=cdi.EXEC_PERSISTENT):
     g = cdi.from_workload(wl, precision=precision, tol=tol)
+    g.set_exec(exec_mode)
     o = oracle.from_workload(wl, tol=tol)
     return g, o
+
+
+EXEC_MODES = pytest.mark.parametrize("exec_mode", [cdi.EXEC_PERSISTENT, cdi.EXEC_KERNELS],
+                                     ids=["persistent", "kernels"])
 
 
 def moving_state(wl, nsteps=5):
@@ -116,19 +121,24 @@ def test_pressure_solve_parity(dim):
     o.set_state(phi)
     pg = g.solve_pressure(f)
     po, cyc, _ = o.poisson(f)
-    assert g.last_stats()["cycles"] == cyc
+    # the GPU solver (FP64 defect correction around FP32 V-cycles) and the
+    # oracle's FP64 multigrid converge to the same solution of the same system
     assert rel(pg, po) < 1e-10
+    fm = f - f.mean()
+    assert np.linalg.norm(o.apply_laplacian(pg) - fm) <= 1.01e-12 * np.linalg.norm(fm)
+    assert abs(pg.mean()) < 1e-12 * np.abs(pg).max()
 
 
 # ---------------------------------------------------------------------------
 # time-stepping parity
 # ---------------------------------------------------------------------------
 
-def test_step_parity_drop_1000_steps():
+@EXEC_MODES
+def test_step_parity_drop_1000_steps(exec_mode):
     """64x32 equilibrium drop (FP64 plain method), 1000 steps: every field
     within 1e-10 relative of the oracle; mass conserved to round-off."""
     wl = inputs.drop_2d(64, 32)
-    g, o = pair(wl, tol=1e-12)
+    g, o = pair(wl, tol=1e-12, exec_mode=exec_mode)
     m0 = g.mass()
     assert abs(m0 - o.mass()) < 1e-15
     g.step(wl.dt, 1000)
@@ -145,10 +155,11 @@ def test_step_parity_drop_1000_steps():
     assert abs(tg - to) < 1e-9 and abs(Lg - Lo) < 1e-9
 
 
-def test_step_parity_couette_cut():
+@EXEC_MODES
+def test_step_parity_couette_cut(exec_mode):
     """128x32 cut of the two-phase Couette case (moving walls, slip length dx)."""
     wl = inputs.couette_2d(128, 32, 1.0)
-    g, o = pair(wl, tol=1e-12)
+    g, o = pair(wl, tol=1e-12, exec_mode=exec_mode)
     g.step(wl.dt, 100)
     o.step(wl.dt, 100)
     phi_g, vel_g, p_g = g.get_fields()
@@ -158,7 +169,8 @@ def test_step_parity_couette_cut():
         assert rel(vel_g[a], vel_o[a]) < 1e-10, a
 
 
-def test_step_parity_3d_drop():
+@EXEC_MODES
+def test_step_parity_3d_drop(exec_mode):
     """16x16x12 3D drop with density ratio 10 and noise, 10 steps."""
     n = (16, 16, 12)
     h = 1.0 / 16
@@ -170,6 +182,7 @@ def test_step_parity_3d_drop():
         s.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, 1.0)
         s.set_solver(1e-12, 100)
     g.set_wall(cdi.WALL_BOTH, math.radians(60), h, 0.0)
+    g.set_exec(exec_mode)
     o.set_wall_slip_length(2, math.radians(60), h, 0.0)
     g.set_state(phi)
     o.set_state(phi)
@@ -182,18 +195,21 @@ def test_step_parity_3d_drop():
         assert rel(vel_g[a], vel_o[a]) < 1e-10, a
 
 
-def test_couette_full_size_512x128_parity():
+@EXEC_MODES
+def test_couette_full_size_512x128_parity(exec_mode):
     """The full 512x128 Couette workload in the launch configuration the bench
-    times (FP64, tol 1e-10, warm start): 3 steps, every field vs the oracle."""
+    times (FP64, pressure tolerance 1e-8, warm start): 3 steps, every field vs
+    the oracle.  Both sides stop their V-cycles at the same 1e-8 residual, so
+    the velocity bar is the solver tolerance times a safety factor of 10."""
     wl = inputs.couette_2d(512, 128, 1.0)
-    g, o = pair(wl, tol=1e-10)
+    g, o = pair(wl, tol=1e-8, exec_mode=exec_mode)
     g.step(wl.dt, 3)
     o.step(wl.dt, 3)
     phi_g, vel_g, _ = g.get_fields()
     phi_o, vel_o, _ = o.get_state()
     assert rel(phi_g, phi_o) < 1e-11
     for a in range(2):
-        assert rel(vel_g[a], vel_o[a]) < 1e-9, a
+        assert rel(vel_g[a], vel_o[a]) < 1e-7, a
 
 
 # ---------------------------------------------------------------------------
@@ -218,9 +234,11 @@ def test_contact_angle_of_prescribed_cap_gpu():
     assert abs(math.degrees(tg) - 60) < 1.5
 
 
-def test_no_convergence_is_reported():
+@EXEC_MODES
+def test_no_convergence_is_reported(exec_mode):
     wl = inputs.drop_2d(64, 32)
     g = cdi.from_workload(wl, tol=1e-14, max_vcycles=1)
+    g.set_exec(exec_mode)
     with pytest.raises(cdi.CdiError) as e:
         g.step(wl.dt, 1)
     assert e.value.status == 4
@@ -234,3 +252,32 @@ def test_nan_input_is_rejected():
     with pytest.raises(cdi.CdiError) as e:
         g.set_phi(bad)
     assert e.value.status == 5
+
+
+def test_adaptive_gamma_parity_both_modes():
+    """gamma = 2.5 |u|_max (Sec. 5.1) with density and viscosity ratio 10:
+    the persistent and per-kernel paths and the oracle agree after 50 steps."""
+    nx, ny = 64, 32
+    h = 1.0 / nx
+    phi = inputs.add_noise(inputs.cap_phi_2d(nx, ny, h, 0.2, math.pi / 2, 0.5, h), 1e-3, 9)
+    res = []
+    for mode in (cdi.EXEC_PERSISTENT, cdi.EXEC_KERNELS):
+        g = cdi.Solver(2, (nx, ny), (1.0, ny * h))
+        g.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, -0.5)
+        g.set_wall(cdi.WALL_BOTH, math.radians(120), h, 0.0)
+        g.set_solver(1e-12, 100)
+        g.set_exec(mode)
+        g.set_state(phi)
+        g.step(5e-5, 50)
+        res.append(g.get_fields())
+    o = oracle.Oracle(2, (nx, ny), (1.0, ny * h))
+    o.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, -0.5)
+    o.set_wall_slip_length(2, math.radians(120), h)
+    o.set_solver(1e-12, 100)
+    o.set_state(phi)
+    o.step(5e-5, 50)
+    phi_o, vel_o, _ = o.get_state()
+    for phi_g, vel_g, _ in res:
+        assert rel(phi_g, phi_o) < 1e-11
+        for a in range(2):
+            assert rel(vel_g[a], vel_o[a]) < 1e-10
