@@ -109,12 +109,14 @@ def traffic_for(kernel):
     ent = d.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, ent["source"])
-    if not os.path.exists(src):
-        return None
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
-    return ent["dram_bytes_per_launch"] if h == ent["source_sha256_16"] else None
+    h = hashlib.sha256()
+    for rel in ent["sources"]:
+        src = os.path.join(ROOT, rel)
+        if not os.path.exists(src):
+            return None
+        with open(src, "rb") as f:
+            h.update(f.read())
+    return ent["dram_bytes_per_launch"] if h.hexdigest()[:16] == ent["sources_sha256_16"] else None
 
 
 # ---------------------------------------------------------------------------

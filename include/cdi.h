@@ -211,6 +211,27 @@ const char* cdi_last_error(const cdi_ctx* ctx);
 /* Release the context (not the caller's workspace). NULL is accepted. */
 void cdi_destroy(cdi_ctx* ctx);
 
+/* Total phase volume sum(phi) * cell_volume of n doubles at phi_dev (device
+ * memory), written as one double to mass_dev (device memory), with work
+ * issued on cuda_stream (a cudaStream_t, NULL for the legacy default stream).
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code running inside an allocator or
+ * memory-pool callback, or in a program whose device memory is all reserved
+ * up front -- and so cannot supply the workspace a context needs.  It
+ * allocates nothing: its scratch (one FP64 partial per 8192 elements) is a
+ * fixed 32 KiB array inside the library, present on every GPU that loads the
+ * library until the process exits.  Hence n must lie in [1, 33554432];
+ * other n returns CDI_EINVAL.  The first call on a device looks up the
+ * scratch address on that device (make that first call before any stream
+ * capture).  Every call on a device shares the scratch and leaves its partial
+ * sums there; calls whose kernels overlap on the GPU race with each other.
+ * Blocks sum fixed chunks in a fixed order, so the result is deterministic.
+ * On failure a one-line message is copied into err (err_len bytes, may be
+ * NULL). */
+cdi_status cdi_mass_noalloc(const double* phi_dev, long long n, double cell_volume,
+                            double* mass_dev, void* cuda_stream, char* err,
+                            size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif
