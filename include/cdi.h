@@ -192,6 +192,11 @@ cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
  * Both compute the same arithmetic. */
 cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
 
+/* Longest wait (nanoseconds, 0 .. 6e10; default 2e9) of a grid barrier in the
+ * persistent step kernel before the call ends with CDI_ETIMEOUT.  A timed-out
+ * call leaves the state undefined but the context and the device usable. */
+cdi_status cdi_set_barrier_timeout(cdi_ctx* ctx, long long ns);
+
 /* Launch profiler (diagnostics): from now on record a CUDA event pair on the
  * launching stream around each of the next max_launches launches of one
  * kernel class ("rbgs0" = red-black sweep on the finest level, "mom",

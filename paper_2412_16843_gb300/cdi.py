@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         "cdi_solve_pressure": [P, DP, DP],
         "cdi_last_stats": [P, IP, DP, IP, IP],
         "cdi_set_exec": [P, I],
+        "cdi_set_barrier_timeout": [P, ctypes.c_longlong],
         "cdi_launches_per_step": [P, ctypes.POINTER(ctypes.c_long)],
         "cdi_profile_start": [P, ctypes.c_char_p, I],
         "cdi_profile_stop": [P, DP, ctypes.POINTER(ctypes.c_long)],
@@ -254,6 +255,9 @@ class Solver:
 
     def set_exec(self, mode: int):
         self._check(self.lib.cdi_set_exec(self.h, mode))
+
+    def set_barrier_timeout(self, ns: int):
+        self._check(self.lib.cdi_set_barrier_timeout(self.h, int(ns)))
 
     def launches_per_step(self):
         n = ctypes.c_long()

@@ -699,6 +699,13 @@ cdi_status cdi_step(cdi_ctx* c, double dt, int nsteps) {
     return cuda_check(c, cudaStreamSynchronize(c->stream), "cdi_step");
 }
 
+cdi_status cdi_set_barrier_timeout(cdi_ctx* c, long long ns) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (ns < 0 || ns > 60000000000LL) return fail(c, CDI_EINVAL, "barrier timeout must lie in [0, 60 s]");
+    c->spin_limit_ns = (long)ns;
+    return CDI_OK;
+}
+
 cdi_status cdi_set_exec(cdi_ctx* c, int mode) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
     if (mode != CDI_EXEC_PERSISTENT && mode != CDI_EXEC_KERNELS) return fail(c, CDI_EINVAL, "unknown exec mode");
