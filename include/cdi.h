@@ -216,6 +216,54 @@ const char* cdi_last_error(const cdi_ctx* ctx);
 /* Release the context (not the caller's workspace). NULL is accepted. */
 void cdi_destroy(cdi_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Batched sweep: many independent problems (e.g. a theta_eq / slip length /
+ * capillary number sweep) advanced together by ONE kernel launch.  Each
+ * problem is an ordinary context (initialised, parameters set, workspace
+ * bound, state set); the batch only schedules them: one CTA takes one
+ * instance (largest first) and runs all its steps, so instances never wait
+ * for each other.  The arithmetic of every instance is exactly that of
+ * cdi_step (Sec. 4 time step), so results equal those of stepping each
+ * context alone.  All instances need the same dimension and precision and
+ * must stay alive while the batch exists.
+ * ------------------------------------------------------------------------- */
+typedef struct cdi_batch cdi_batch;
+
+/* Create a batch over n contexts (the batch does not own them). */
+cdi_status cdi_batch_create(cdi_batch** out, int n, cdi_ctx* const* instances);
+
+/* Device workspace of the batch itself (instance descriptors and outcomes;
+ * about 4 KB per instance). */
+cdi_status cdi_batch_workspace_bytes(const cdi_batch* b, size_t* bytes);
+
+/* Bind the batch workspace (256-byte aligned) and the stream of its launches. */
+cdi_status cdi_batch_bind_workspace(cdi_batch* b, void* dev_ptr, size_t bytes,
+                                    void* cuda_stream);
+
+/* Advance every instance by nsteps RK4 steps; dt[i] is instance i's step.
+ * Returns the first failing instance's status (its context holds the text). */
+cdi_status cdi_batch_step(cdi_batch* b, const double* dt, int nsteps);
+
+/* Threads per CTA of the batched kernel: 256, 512 (default) or 1024. */
+cdi_status cdi_batch_set_threads(cdi_batch* b, int threads);
+
+/* Autotuner: time trial_steps steps of the whole batch with each CTA size
+ * (256, 512, 1024) and keep the fastest; ms_out (3 entries, may be NULL)
+ * receives the times.  The trial steps advance the instances. */
+cdi_status cdi_batch_autotune(cdi_batch* b, const double* dt, int trial_steps,
+                              int* threads_out, double* ms_out);
+
+/* Outcome of instance i in the last cdi_batch_step: status, largest V-cycle
+ * count of one solve, total V-cycles; and the launch's device time (ms). */
+cdi_status cdi_batch_stats(cdi_batch* b, int i, int* status, int* max_vcycles,
+                           int* total_vcycles, float* last_ms);
+
+/* Last error of the batch (NULL: of the last failed cdi_batch_create). */
+const char* cdi_batch_last_error(const cdi_batch* b);
+
+/* Release the batch (not its contexts or workspace). NULL is accepted. */
+void cdi_batch_destroy(cdi_batch* b);
+
 /* Total phase volume sum(phi) * cell_volume of n doubles at phi_dev (device
  * memory), written as one double to mass_dev (device memory), with work
  * issued on cuda_stream (a cudaStream_t, NULL for the legacy default stream).

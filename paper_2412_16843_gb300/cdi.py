@@ -82,10 +82,23 @@ def load(path: str = LIB_PATH):
         "cdi_profile_start": [P, ctypes.c_char_p, I],
         "cdi_profile_stop": [P, DP, ctypes.POINTER(ctypes.c_long)],
     }
+    sig.update({
+        "cdi_batch_create": [ctypes.POINTER(P), I, ctypes.POINTER(P)],
+        "cdi_batch_workspace_bytes": [P, ctypes.POINTER(S)],
+        "cdi_batch_bind_workspace": [P, P, S, P],
+        "cdi_batch_step": [P, DP, I],
+        "cdi_batch_set_threads": [P, I],
+        "cdi_batch_autotune": [P, DP, I, IP, DP],
+        "cdi_batch_stats": [P, I, IP, IP, IP, ctypes.POINTER(ctypes.c_float)],
+    })
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = I
+    lib.cdi_batch_last_error.argtypes = [P]
+    lib.cdi_batch_last_error.restype = ctypes.c_char_p
+    lib.cdi_batch_destroy.argtypes = [P]
+    lib.cdi_batch_destroy.restype = None
     lib.cdi_last_error.argtypes = [P]
     lib.cdi_last_error.restype = ctypes.c_char_p
     lib.cdi_destroy.argtypes = [P]
@@ -272,6 +285,64 @@ class Solver:
         ms, n = ctypes.c_double(), ctypes.c_long()
         self._check(self.lib.cdi_profile_stop(self.h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+class Batch:
+    """Many Solvers advanced by one batched launch (cdi_batch_* in cdi.h)."""
+
+    def __init__(self, solvers):
+        import torch
+
+        self.lib = load()
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        arr = (ctypes.c_void_p * n)(*[s.h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        self._check(self.lib.cdi_batch_create(ctypes.byref(h), n, arr), None)
+        self.h = h
+        nbytes = ctypes.c_size_t()
+        self._check(self.lib.cdi_batch_workspace_bytes(self.h, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+        self.stream = self.solvers[0].stream
+        self._check(self.lib.cdi_batch_bind_workspace(self.h, ctypes.c_void_p(self.workspace.data_ptr()),
+                                                      nbytes.value, ctypes.c_void_p(self.stream.cuda_stream)))
+
+    def _check(self, st, h="self"):
+        if st != 0:
+            msg = self.lib.cdi_batch_last_error(self.h if h == "self" else None)
+            raise CdiError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cdi_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, dts, nsteps=1):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        assert d.shape == (len(self.solvers),)
+        self._check(self.lib.cdi_batch_step(self.h, _dp(d), nsteps))
+
+    def set_threads(self, threads):
+        self._check(self.lib.cdi_batch_set_threads(self.h, threads))
+
+    def autotune(self, dts, trial_steps=1):
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        best = ctypes.c_int()
+        ms = np.zeros(3)
+        self._check(self.lib.cdi_batch_autotune(self.h, _dp(d), trial_steps, ctypes.byref(best), _dp(ms)))
+        return best.value, ms
+
+    def stats(self, i):
+        st, mx, tot, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        self._check(self.lib.cdi_batch_stats(self.h, i, ctypes.byref(st), ctypes.byref(mx), ctypes.byref(tot),
+                                             ctypes.byref(ms)))
+        return {"status": st.value, "max_cycles": mx.value, "total_cycles": tot.value, "last_ms": ms.value}
 
 
 def from_workload(wl, precision=FP64, tol=1e-10, max_vcycles=100):

@@ -17,6 +17,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
+#include <algorithm>
 
 using namespace cdi;
 
@@ -339,40 +341,50 @@ cdi_status step_once(cdi_ctx* c, double dt) {
     return cuda_check(c, cudaGetLastError(), "kernel launch");
 }
 
-// Choose the first multigrid level the persistent kernel's CTA 0 solves in
-// shared memory (the largest tail that fits), and the launch shape.
-template <typename T>
-cdi_status persist_setup(cdi_ctx* c) {
-    if (c->persist_ready) return CDI_OK;
+// First multigrid level that one CTA solves in shared memory (the largest
+// FP32 tail that fits the budget) and its layout.
+size_t pick_tail(const cdi_ctx* c, size_t budget, int* lt_out, PersistLayout* L) {
+    int lt = c->mg.nlev - 1;
+    for (int l = 0; l < c->mg.nlev; ++l) {
+        PersistLayout t{};
+        if (persist_tail_layout(c->g, c->mg, l, t) <= budget) {
+            lt = l;
+            break;
+        }
+    }
+    *lt_out = lt;
+    return persist_tail_layout(c->g, c->mg, lt, *L);
+}
+
+cdi_status smem_optin(cdi_ctx* c, size_t* bytes) {
     int dev = 0, optin = 0;
     cdi_status st = cuda_check(c, cudaGetDevice(&dev), "cudaGetDevice");
     if (st) return st;
     st = cuda_check(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
                     "cudaDeviceGetAttribute");
     if (st) return st;
-    const size_t budget = (size_t)optin > 8192 ? (size_t)optin - 4096 : 0;
-    int lt = c->mg.nlev - 1;
-    for (int l = 0; l < c->mg.nlev; ++l) {
-        PersistLayout L{};
-        if (persist_tail_layout(c->g, c->mg, l, L) <= budget) {
-            lt = l;
-            break;
-        }
-    }
-    c->persist_lt = lt;
-    c->persist_smem = persist_tail_layout(c->g, c->mg, lt, c->playout);
+    *bytes = (size_t)optin;
+    return CDI_OK;
+}
+
+template <typename T>
+cdi_status persist_setup(cdi_ctx* c) {
+    if (c->persist_ready) return CDI_OK;
+    size_t optin = 0;
+    cdi_status st = smem_optin(c, &optin);
+    if (st) return st;
+    const size_t budget = optin > 8192 ? optin - 4096 : 0;
+    c->persist_smem = pick_tail(c, budget, &c->persist_lt, &c->playout);
     st = cuda_check(c, persist_prepare<T>(c->g.D, c->persist_smem, &c->persist_grid), "persistent kernel setup");
     if (st) return st;
     c->persist_ready = true;
     return CDI_OK;
 }
 
+// the descriptor of this context's next steps (current state pointers)
 template <typename T>
-cdi_status step_persist(cdi_ctx* c, double dt, int nsteps) {
-    cdi_status st = persist_setup<T>(c);
-    if (st) return st;
-    PersistArgs<T> A{};
-    static_cast<PersistLayout&>(A) = c->playout;
+void fill_inst(const cdi_ctx* c, InstArgs<T>& A, int lt, const PersistLayout& lay, double dt) {
+    static_cast<PersistLayout&>(A) = lay;
     A.g = c->g;
     A.ph = c->ph;
     A.phi_s = (T*)c->phi_s;
@@ -394,9 +406,7 @@ cdi_status step_persist(cdi_ctx* c, double dt, int nsteps) {
     }
     for (int l = 0; l < kMaxLevels; ++l) A.lv[l] = c->mg.lv[l];
     A.nlev = c->mg.nlev;
-    A.lt = c->persist_lt;
-    A.partials = c->mg.partials;
-    A.ctl = c->ctl;
+    A.lt = lt;
     A.tol = c->tol;
     A.max_vcycles = c->max_vcycles;
     A.warm = c->warm;
@@ -404,6 +414,39 @@ cdi_status step_persist(cdi_ctx* c, double dt, int nsteps) {
     A.npost = c->npost;
     A.gamma_param = c->gamma;
     A.dt = dt;
+}
+
+// record one launch's outcome on the context; the kernel swapped the state
+// and stage buffers once per finished step
+cdi_status apply_stats(cdi_ctx* c, const InstStats& h, const char* who) {
+    c->last_cycles = h.last_cycles;
+    c->last_resid = h.last_resid;
+    c->max_cycles_step = h.max_cycles;
+    c->total_cycles_call = h.total_cycles;
+    for (int s = 0; s < h.steps_done; ++s) {
+        std::swap(c->phi_s, c->phi_k);
+        for (int a = 0; a < 3; ++a) std::swap(c->u_s[a], c->u_k[a]);
+    }
+    if (h.status == CDI_OK) return CDI_OK;
+    char b[240];
+    if (h.status == CDI_ENOCONV)
+        snprintf(b, sizeof b, "%spressure solve: %d V-cycles left relative residual %.3e > tol %.3e (step %d)", who,
+                 h.last_cycles, h.last_resid, c->tol, h.steps_done);
+    else if (h.status == CDI_ETIMEOUT)
+        snprintf(b, sizeof b, "%sa grid barrier of the persistent step kernel timed out (step %d)", who, h.steps_done);
+    else
+        snprintf(b, sizeof b, "%snon-finite value in the pressure solve (step %d)", who, h.steps_done);
+    return fail(c, (cdi_status)h.status, b);
+}
+
+template <typename T>
+cdi_status step_persist(cdi_ctx* c, double dt, int nsteps) {
+    cdi_status st = persist_setup<T>(c);
+    if (st) return st;
+    PersistArgs<T> A{};
+    fill_inst<T>(c, A.I, c->persist_lt, c->playout, dt);
+    A.partials = c->mg.partials;
+    A.ctl = c->ctl;
     A.nsteps = nsteps;
     A.spin_limit = c->spin_limit_ns;
     st = cuda_check(c, cudaMemsetAsync(c->ctl, 0, sizeof(PersistCtl), c->stream), "cudaMemsetAsync(ctl)");
@@ -419,27 +462,7 @@ cdi_status step_persist(cdi_ctx* c, double dt, int nsteps) {
     if (st) return st;
     st = cuda_check(c, cudaStreamSynchronize(c->stream), "persistent step");
     if (st) return st;
-    c->last_cycles = h.last_cycles;
-    c->last_resid = h.last_resid;
-    c->max_cycles_step = h.max_cycles;
-    c->total_cycles_call = h.total_cycles;
-    // the kernel swapped state and stage buffers once per finished step
-    for (int s = 0; s < h.steps_done; ++s) {
-        std::swap(c->phi_s, c->phi_k);
-        for (int a = 0; a < 3; ++a) std::swap(c->u_s[a], c->u_k[a]);
-    }
-    if (h.status != CDI_OK) {
-        char b[200];
-        if (h.status == CDI_ENOCONV)
-            snprintf(b, sizeof b, "pressure solve: %d V-cycles left relative residual %.3e > tol %.3e (step %d)",
-                     h.last_cycles, h.last_resid, c->tol, h.steps_done);
-        else if (h.status == CDI_ETIMEOUT)
-            snprintf(b, sizeof b, "a grid barrier of the persistent step kernel timed out (step %d)", h.steps_done);
-        else
-            snprintf(b, sizeof b, "non-finite value in the pressure solve (step %d)", h.steps_done);
-        return fail(c, (cdi_status)h.status, b);
-    }
-    return CDI_OK;
+    return apply_stats(c, h.st, "");
 }
 
 cdi_status check_wall(cdi_ctx* c, int wall) {
@@ -900,5 +923,253 @@ void cdi_destroy(cdi_ctx* c) {
     if (c->host_scal) cudaFreeHost(c->host_scal);
     delete c;
 }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched sweep: many independent contexts advanced by one launch
+// ===========================================================================
+struct cdi_batch {
+    int n = 0;
+    int dim = 2;
+    int precision = CDI_FP64;
+    std::vector<cdi_ctx*> inst;
+    std::vector<int> order;        // instance indices by decreasing cell count
+    std::vector<int> lt;           // per instance: first level solved in shared memory
+    std::vector<PersistLayout> lay;
+    size_t smem = 0;               // dynamic shared memory of the launch
+    int threads = 512;
+    int grid = 0;
+    bool prepared = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    void* d_insts = nullptr;
+    InstStats* d_stats = nullptr;
+    int* d_counter = nullptr;
+    std::vector<InstStats> stats;  // last launch, caller's order
+    float last_ms = 0.f;
+    std::string err;
+};
+
+namespace {
+
+std::string g_batch_error;
+
+cdi_status bfail(cdi_batch* b, cdi_status st, const std::string& msg) {
+    if (b) b->err = msg;
+    else g_batch_error = msg;
+    return st;
+}
+
+size_t inst_bytes(int precision) {
+    return precision == CDI_FP64 ? sizeof(InstArgs<double>) : sizeof(InstArgs<float>);
+}
+
+void batch_carve(cdi_batch* b, char* base, size_t* total) {
+    Carver cv{base};
+    b->d_insts = cv.take((size_t)b->n * inst_bytes(b->precision));
+    b->d_stats = (InstStats*)cv.take((size_t)b->n * sizeof(InstStats));
+    b->d_counter = (int*)cv.take(sizeof(int));
+    *total = cv.off + 256;
+}
+
+template <typename T>
+cdi_status batch_launch(cdi_batch* b, const double* dt, int nsteps, float* ms) {
+    cdi_status st;
+    if (!b->prepared) {
+        cudaError_t e = batch_prepare<T>(b->dim, b->threads, b->smem, &b->grid);
+        if (e != cudaSuccess) return bfail(b, CDI_ECUDA, std::string("batched kernel setup: ") + cudaGetErrorString(e));
+        b->prepared = true;
+    }
+    std::vector<InstArgs<T>> h(b->n);
+    for (int k = 0; k < b->n; ++k) {
+        const int i = b->order[k];
+        fill_inst<T>(b->inst[i], h[k], b->lt[i], b->lay[i], dt[i]);
+    }
+    cudaStream_t s = b->stream;
+    cudaError_t e = cudaMemcpyAsync(b->d_insts, h.data(), h.size() * sizeof(InstArgs<T>), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_stats, 0, (size_t)b->n * sizeof(InstStats), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return bfail(b, CDI_ECUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+    BatchArgs<T> B{(const InstArgs<T>*)b->d_insts, b->d_stats, b->d_counter, b->n, nsteps};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ms) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+    }
+    const bool on = prof_before(KC_STEP, s);
+    e = launch_batch_persist<T>(B, b->dim, b->threads, b->smem, b->grid, s);
+    prof_after(on, s);
+    if (ms) cudaEventRecord(e1, s);
+    if (e != cudaSuccess) return bfail(b, CDI_ECUDA, std::string("batched launch: ") + cudaGetErrorString(e));
+    ++g_launches;
+    std::vector<InstStats> hs(b->n);
+    e = cudaMemcpyAsync(hs.data(), b->d_stats, hs.size() * sizeof(InstStats), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return bfail(b, CDI_ECUDA, std::string("batched step: ") + cudaGetErrorString(e));
+    if (ms) {
+        cudaEventElapsedTime(ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    cdi_status first = CDI_OK;
+    for (int k = 0; k < b->n; ++k) {
+        const int i = b->order[k];
+        b->stats[i] = hs[k];
+        char who[48];
+        snprintf(who, sizeof who, "instance %d: ", i);
+        st = apply_stats(b->inst[i], hs[k], who);
+        if (st && first == CDI_OK) {
+            first = st;
+            b->err = b->inst[i]->err;
+        }
+    }
+    return first;
+}
+
+}  // namespace
+
+extern "C" {
+
+cdi_status cdi_batch_create(cdi_batch** out, int n, cdi_ctx* const* instances) {
+    if (!out) return bfail(nullptr, CDI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !instances) return bfail(nullptr, CDI_EINVAL, "need at least one instance");
+    cdi_batch* b = new (std::nothrow) cdi_batch();
+    if (!b) return bfail(nullptr, CDI_EINVAL, "out of host memory");
+    b->n = n;
+    b->inst.assign(instances, instances + n);
+    for (int i = 0; i < n; ++i) {
+        cdi_ctx* c = b->inst[i];
+        if (!c || !c->bound || !c->fluids_set) {
+            delete b;
+            return bfail(nullptr, CDI_ESTATE, "every instance must be initialised, bound and have its fluids set");
+        }
+        if (c->precision != b->inst[0]->precision || c->g.D != b->inst[0]->g.D) {
+            delete b;
+            return bfail(nullptr, CDI_EINVAL, "all instances need the same dimension and precision");
+        }
+        for (int j = 0; j < i; ++j)
+            if (b->inst[j] == c) {
+                delete b;
+                return bfail(nullptr, CDI_EINVAL, "an instance appears twice");
+            }
+    }
+    b->dim = b->inst[0]->g.D;
+    b->precision = b->inst[0]->precision;
+    b->stream = b->inst[0]->stream;
+    b->order.resize(n);
+    for (int i = 0; i < n; ++i) b->order[i] = i;
+    std::stable_sort(b->order.begin(), b->order.end(),
+                     [&](int x, int y) { return b->inst[x]->g.N > b->inst[y]->g.N; });
+    // shared-memory tail per instance under a budget that leaves room for two
+    // CTAs per SM; the launch uses the largest
+    size_t optin = 0;
+    cdi_status st = smem_optin(b->inst[0], &optin);
+    if (st) {
+        delete b;
+        return bfail(nullptr, st, "cannot query the device");
+    }
+    const size_t budget = std::min<size_t>(optin > 8192 ? optin - 4096 : 0, 100 * 1024);
+    b->lt.resize(n);
+    b->lay.resize(n);
+    b->stats.assign(n, InstStats{});
+    for (int i = 0; i < n; ++i) {
+        const size_t sm = pick_tail(b->inst[i], budget, &b->lt[i], &b->lay[i]);
+        b->smem = std::max(b->smem, sm);
+    }
+    size_t total = 0;
+    batch_carve(b, nullptr, &total);
+    b->ws_bytes = total;
+    *out = b;
+    return CDI_OK;
+}
+
+cdi_status cdi_batch_workspace_bytes(const cdi_batch* b, size_t* bytes) {
+    if (!b || !bytes) return bfail(nullptr, CDI_EINVAL, "null argument");
+    *bytes = b->ws_bytes;
+    return CDI_OK;
+}
+
+cdi_status cdi_batch_bind_workspace(cdi_batch* b, void* dev_ptr, size_t bytes, void* stream) {
+    if (!b) return bfail(nullptr, CDI_EINVAL, "null batch");
+    if (!dev_ptr || bytes < b->ws_bytes) return bfail(b, CDI_EINVAL, "workspace missing or too small");
+    if (((uintptr_t)dev_ptr) & 255u) return bfail(b, CDI_EINVAL, "workspace must be 256-byte aligned");
+    b->ws = (char*)dev_ptr;
+    b->stream = (cudaStream_t)stream;
+    size_t total = 0;
+    batch_carve(b, b->ws, &total);
+    return CDI_OK;
+}
+
+cdi_status cdi_batch_set_threads(cdi_batch* b, int threads) {
+    if (!b) return bfail(nullptr, CDI_EINVAL, "null batch");
+    if (threads != 256 && threads != 512 && threads != 1024) return bfail(b, CDI_EINVAL, "threads must be 256, 512 or 1024");
+    if (threads != b->threads) b->prepared = false;
+    b->threads = threads;
+    return CDI_OK;
+}
+
+cdi_status cdi_batch_step(cdi_batch* b, const double* dt, int nsteps) {
+    if (!b) return bfail(nullptr, CDI_EINVAL, "null batch");
+    if (!b->ws) return bfail(b, CDI_ESTATE, "no workspace bound");
+    if (!dt) return bfail(b, CDI_EINVAL, "dt is NULL");
+    if (nsteps < 0) return bfail(b, CDI_EINVAL, "nsteps must be >= 0");
+    for (int i = 0; i < b->n; ++i)
+        if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return bfail(b, CDI_EINVAL, "every dt must be > 0");
+    if (nsteps == 0) return CDI_OK;
+    return b->precision == CDI_FP64 ? batch_launch<double>(b, dt, nsteps, &b->last_ms)
+                                    : batch_launch<float>(b, dt, nsteps, &b->last_ms);
+}
+
+cdi_status cdi_batch_autotune(cdi_batch* b, const double* dt, int trial_steps, int* threads_out, double* ms_out) {
+    if (!b) return bfail(nullptr, CDI_EINVAL, "null batch");
+    if (trial_steps < 1) return bfail(b, CDI_EINVAL, "trial_steps must be >= 1");
+    const int cand[3] = {256, 512, 1024};
+    int best = b->threads;
+    float best_ms = 1e30f;
+    for (int k = 0; k < 3; ++k) {
+        cdi_status st = cdi_batch_set_threads(b, cand[k]);
+        if (st) return st;
+        {  // the candidate must fit one CTA per SM with the batch's shared memory
+            int grid = 0;
+            cudaError_t e = b->precision == CDI_FP64 ? batch_prepare<double>(b->dim, cand[k], b->smem, &grid)
+                                                     : batch_prepare<float>(b->dim, cand[k], b->smem, &grid);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+        }
+        st = cdi_batch_step(b, dt, trial_steps);
+        if (st) return st;
+        if (ms_out) ms_out[k] = b->last_ms;
+        if (b->last_ms < best_ms) {
+            best_ms = b->last_ms;
+            best = cand[k];
+        }
+    }
+    cdi_batch_set_threads(b, best);
+    if (threads_out) *threads_out = best;
+    return CDI_OK;
+}
+
+cdi_status cdi_batch_stats(cdi_batch* b, int i, int* status, int* max_vcycles, int* total_vcycles, float* last_ms) {
+    if (!b) return bfail(nullptr, CDI_EINVAL, "null batch");
+    if (i < 0 || i >= b->n) return bfail(b, CDI_EINVAL, "instance index out of range");
+    if (status) *status = b->stats[i].status;
+    if (max_vcycles) *max_vcycles = b->stats[i].max_cycles;
+    if (total_vcycles) *total_vcycles = b->stats[i].total_cycles;
+    if (last_ms) *last_ms = b->last_ms;
+    return CDI_OK;
+}
+
+const char* cdi_batch_last_error(const cdi_batch* b) {
+    if (!b) return g_batch_error.c_str();
+    return b->err.c_str();
+}
+
+void cdi_batch_destroy(cdi_batch* b) { delete b; }
 
 }  // extern "C"

@@ -200,17 +200,22 @@ void launch_contact_line(const Geom& g, int wall, const double* cols, MG& mg, cu
 // ---------------------------------------------------------------------------
 constexpr int kPersistThreads = 512;
 
-// control block in the workspace (zeroed before every launch)
-struct PersistCtl {
-    unsigned bar_count;
-    unsigned bar_gen;
-    int status;        // CDI_OK or the cdi_status that ended the launch
+// per-instance outcome of one launch (zeroed before every launch)
+struct InstStats {
+    int status;        // CDI_OK or the cdi_status that ended the instance's steps
     int max_cycles;    // largest V-cycle count of one solve in this launch
     int last_cycles;
     int total_cycles;  // V-cycles of all solves in this launch
     int steps_done;
     int pad;
     double last_resid;
+};
+
+// control block of the single-grid persistent kernel in the workspace
+struct PersistCtl {
+    unsigned bar_count;
+    unsigned bar_gen;
+    InstStats st;
 };
 
 // offsets (in floats) of the FP32 multigrid tail levels in dynamic shared
@@ -222,21 +227,37 @@ struct PersistLayout {
     long sm_A, sm_bb, sm_fct;
 };
 
+// everything one instance's steps need (copied by value into the kernel
+// parameters, or into shared memory by the batched kernel)
 template <typename T>
-struct PersistArgs : PersistLayout {
+struct __align__(16) InstArgs : PersistLayout {
     Geom g;
     PhysDev ph;
     T *phi_s, *phi_k, *acc_phi, *rphi, *psi, *muc, *wuY, *wghost, *wmuw;
     T *u_s[3], *u_k[3], *acc_m[3], *rm[3], *nh[3], *m[3];
     MGLevel lv[kMaxLevels];
-    int nlev, lt;        // levels lt.. are solved by CTA 0 in shared memory
-    double* partials;    // 2 * kPartials doubles
-    PersistCtl* ctl;
+    int nlev, lt;        // levels lt.. are solved by one CTA in shared memory
     double tol;
     int max_vcycles, warm, npre, npost;
     double gamma_param, dt;
+};
+
+template <typename T>
+struct PersistArgs {
+    InstArgs<T> I;
+    PersistCtl* ctl;
+    double* partials;    // 2 * kPartials doubles
     int nsteps;
     long spin_limit;     // barrier timeout in nanoseconds
+};
+
+template <typename T>
+struct BatchArgs {
+    const InstArgs<T>* insts;  // sorted by decreasing cell count
+    InstStats* stats;
+    int* counter;              // next instance to take (zeroed before the launch)
+    int n_inst;
+    int nsteps;
 };
 
 size_t persist_tail_layout(const Geom& g, const MG& mg, int lt, PersistLayout& L);
@@ -244,6 +265,10 @@ template <typename T>
 cudaError_t persist_prepare(int dim, size_t smem, int* grid);
 template <typename T>
 cudaError_t launch_step_persist(PersistArgs<T>& A, size_t smem, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t batch_prepare(int dim, int threads, size_t smem, int* grid);
+template <typename T>
+cudaError_t launch_batch_persist(BatchArgs<T>& B, int dim, int threads, size_t smem, int grid, cudaStream_t s);
 
 // number of kernel launches issued since the counter was reset (host side)
 extern thread_local long g_launches;

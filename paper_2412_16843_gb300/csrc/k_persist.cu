@@ -1,21 +1,23 @@
-// Persistent time-step kernel: nsteps full RK4 steps (Sec. 4) in ONE
-// cooperative launch with one CTA per SM.
+// Persistent time-step kernels.
 //
-// Every phase of the step (the right-hand side of Eqs. CDI and NS_momentum,
-// the RK4 stage update, and each projection with its multigrid V-cycles and
-// convergence test) runs as a grid-stride loop over cells, separated by a
-// grid barrier.  The multigrid levels of at most a few thousand cells are
-// solved by CTA 0 alone in shared memory (one "tail" call per V-cycle) while
-// the other CTAs wait at the next barrier.  Reductions (mean and norm of the
-// pressure right-hand side, residual norm, |u|_max) are deterministic: each
-// CTA writes one partial, and after the barrier every CTA sums the partials
-// in the same order, so every CTA takes the same convergence decision.
+// k_step_persist: nsteps full RK4 steps (Sec. 4) of ONE grid in one
+//   cooperative launch with one CTA per SM.  Every phase (the right-hand side
+//   of Eqs. CDI and NS_momentum, the RK4 stage update, each projection with its
+//   multigrid V-cycles and convergence test) is a grid-stride loop between
+//   grid barriers.  Barriers wait a bounded time, then set CDI_ETIMEOUT and
+//   every CTA returns.  Reductions are deterministic: each CTA writes one
+//   partial and every CTA sums the partials in the same order, so all take the
+//   same convergence decision.  Data another CTA wrote before the last barrier
+//   is read with ld.global.cg (L2), never from a possibly stale L1 line.
 //
-// Barriers spin for a bounded number of iterations; on timeout the kernel
-// sets CDI_ETIMEOUT in the control block and every CTA returns.  ENOCONV and
-// ENAN are uniform decisions and also end the launch.  Data written by one CTA
-// and read by another after a barrier is read with ld.global.cg (L2), never
-// from a possibly stale L1 line.
+// k_batch_persist: many independent grids (a parameter sweep) in one launch.
+//   Each CTA takes the largest instance not yet taken (atomic counter over a
+//   size-sorted descriptor array) and runs all its steps alone, so every
+//   barrier is a __syncthreads and no CTA ever waits for another.
+//
+// Both run the same step code, written once against an executor X that
+// supplies the thread range, the barrier and the reductions.  In both, the
+// multigrid levels that fit in shared memory are solved by one CTA there.
 #include "ops.cuh"
 #include "../../include/cdi.h"
 
@@ -62,9 +64,19 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-struct Barrier {
+// ---------------------------------------------------------------------------
+// executors
+// ---------------------------------------------------------------------------
+struct GridX {
     PersistCtl* ctl;
-    long limit;
+    double* partials;  // 2 * kPartials
+    long limit;        // barrier timeout, ns
+    int red;
+    using Ld = LG;
+    __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ int nth() const { return gridDim.x * blockDim.x; }
+    __device__ bool tail_cta() const { return blockIdx.x == 0; }
+    __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
     // grid barrier; false when the launch is ending (timeout or error)
     __device__ bool sync() {
         __shared__ int ok;
@@ -84,44 +96,52 @@ struct Barrier {
                 long it = 0;
                 while (*genp == gen) {
                     if (++it > (1L << 31) || globaltimer() - t0 > (unsigned long long)limit) {
-                        atomicCAS(&ctl->status, 0, (int)CDI_ETIMEOUT);
+                        atomicCAS(&ctl->st.status, 0, (int)CDI_ETIMEOUT);
                         break;
                     }
                     __nanosleep(32);
                 }
             }
             __threadfence();
-            ok = (*(volatile int*)&ctl->status == 0);
+            ok = (*(volatile int*)&ctl->st.status == 0);
         }
         __syncthreads();
         return ok != 0;
     }
+    template <bool MAX>
+    __device__ bool reduce(double v, double& out) {
+        double* part = partials + (red++ & 1) * kPartials;
+        v = block_reduce_all<MAX>(v);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+        if (!sync()) return false;
+        double s = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            s = MAX ? fmax(s, __ldcg(part + b)) : s + __ldcg(part + b);
+        out = block_reduce_all<MAX>(s);
+        return true;
+    }
 };
 
-// deterministic grid reduction: every CTA returns the same value
-template <bool MAX>
-__device__ bool grid_reduce(double v, double* partials, Barrier& bar, double& out) {
-    v = block_reduce_all<MAX>(v);
-    if (threadIdx.x == 0) partials[blockIdx.x] = v;
-    if (!bar.sync()) return false;
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        s = MAX ? fmax(s, __ldcg(partials + b)) : s + __ldcg(partials + b);
-    out = block_reduce_all<MAX>(s);
-    return true;
-}
-
-template <typename T>
-struct Run {
-    const PersistArgs<T>& A;
-    Barrier bar;
-    int red = 0;  // alternates the two partial buffers
-    __device__ double* partials() { return A.partials + (red++ & 1) * kPartials; }
+struct BlockX {
+    using Ld = LP;  // one CTA owns the instance: its own writes are visible after __syncthreads
+    __device__ int tid() const { return threadIdx.x; }
+    __device__ int nth() const { return blockDim.x; }
+    __device__ bool tail_cta() const { return true; }
+    __device__ bool leader() const { return threadIdx.x == 0; }
+    __device__ bool sync() {
+        __syncthreads();
+        return true;
+    }
+    template <bool MAX>
+    __device__ bool reduce(double v, double& out) {
+        out = block_reduce_all<MAX>(v);
+        return true;
+    }
 };
 
 // ---------------------------------------------------------------------------
-// multigrid tail: FP32 levels lt .. nlev-1 by CTA 0 in shared memory.  Input:
-// the right-hand side r of level lt (global); output: its correction e.
+// multigrid tail: FP32 levels lt .. nlev-1 by one CTA in shared memory.
+// Input: the right-hand side r of level lt (global); output: its correction e.
 // Level geometry and shared-memory offsets are copied into registers per
 // level, so no per-thread array is indexed at run time.
 // ---------------------------------------------------------------------------
@@ -133,7 +153,7 @@ struct SmLevel {
 };
 
 template <typename T, int DIM>
-__device__ __forceinline__ SmLevel sm_level(const PersistArgs<T>& A, float* sm, int l) {
+__device__ __forceinline__ SmLevel sm_level(const InstArgs<T>& A, float* sm, int l) {
     SmLevel s;
     s.g = A.lv[l].g;
     s.e = sm + A.sm_e[l];
@@ -144,7 +164,7 @@ __device__ __forceinline__ SmLevel sm_level(const PersistArgs<T>& A, float* sm, 
 }
 
 template <typename T, int DIM>
-__device__ void tail_vcycle(const PersistArgs<T>& A, bool first, float* sm) {
+__device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
     const int lt = A.lt, nl = A.nlev;
     const int nt = blockDim.x, t0 = threadIdx.x;
     double* sd = reinterpret_cast<double*>(sm + A.sm_dbl);
@@ -223,12 +243,12 @@ __device__ void tail_vcycle(const PersistArgs<T>& A, bool first, float* sm) {
     }
 }
 
-// one FP32 V-cycle on the correction equation A e = r from level 0 (grid
-// levels 0 .. lt-1, the tail by CTA 0), ending with p += e on level 0
-template <typename T, int DIM>
-__device__ bool vcycle(Run<T>& R, bool first, float* sm) {
-    const PersistArgs<T>& A = R.A;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+// one FP32 V-cycle on the correction equation A e = r from level 0 (levels
+// 0 .. lt-1 by the executor's threads, the tail by one CTA), ending with p += e
+template <typename T, int DIM, class X>
+__device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
+    using L_ = typename X::Ld;
+    const int tid = x.tid(), nth = x.nth();
     for (int l = 0; l < A.lt; ++l) {
         const MGLevel L = A.lv[l];
         const MGLevel C = A.lv[l + 1];
@@ -237,15 +257,15 @@ __device__ bool vcycle(Run<T>& R, bool first, float* sm) {
         for (int it = 0; it < A.npre; ++it)
             for (int col = 0; col < 2; ++col) {
                 for (int k = tid; k < half; k += nth)
-                    ops::rbgs_at<LG, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
-                if (!R.bar.sync()) return false;
+                    ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
+                if (!x.sync()) return false;
             }
         for (int t = tid; t < (int)C.g.N; t += nth)
-            ops::resid_restrict_at<LG, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
-        if (!R.bar.sync()) return false;
+            ops::resid_restrict_at<L_, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
+        if (!x.sync()) return false;
     }
-    if (blockIdx.x == 0) tail_vcycle<T, DIM>(A, first, sm);
-    if (!R.bar.sync()) return false;
+    if (x.tail_cta()) tail_vcycle<T, DIM>(A, first, sm);
+    if (!x.sync()) return false;
     const MGLevel L0 = A.lv[0];
     bool updated = false;
     for (int l = A.lt - 1; l >= 0; --l) {
@@ -253,40 +273,40 @@ __device__ bool vcycle(Run<T>& R, bool first, float* sm) {
         const MGLevel C = A.lv[l + 1];
         const float* bl[3] = {L.bf[0], L.bf[1], L.bf[2]};
         const int half = (int)(L.g.N / 2);
-        for (int c = tid; c < (int)L.g.N; c += nth) ops::prolong_at<LG, float, DIM>(L.g, C.g, C.e, L.e, c);
-        if (!R.bar.sync()) return false;
+        for (int c = tid; c < (int)L.g.N; c += nth) ops::prolong_at<L_, float, DIM>(L.g, C.g, C.e, L.e, c);
+        if (!x.sync()) return false;
         for (int it = 0; it < A.npost; ++it)
             for (int col = 0; col < 2; ++col) {
                 const bool last = (l == 0 && it == A.npost - 1 && col == 1);
                 for (int k = tid; k < half; k += nth) {
                     const long c = ops::colour_cell(L.g, col, k);
-                    ops::rbgs_at<LG, float, DIM>(L.g, bl, L.e, L.r, c);
-                    if (last) L0.p[c] = __ldcg(L0.p + c) + (double)L.e[c];
+                    ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
+                    if (last) L0.p[c] = L_::ld(L0.p + c) + (double)L.e[c];
                 }
                 if (last) {  // the other colour is final already
                     for (int k = tid; k < half; k += nth) {
                         const long c = ops::colour_cell(L.g, 0, k);
-                        L0.p[c] = __ldcg(L0.p + c) + (double)__ldcg(L.e + c);
+                        L0.p[c] = L_::ld(L0.p + c) + (double)L_::ld(L.e + c);
                     }
                     updated = true;
                 }
-                if (!R.bar.sync()) return false;
+                if (!x.sync()) return false;
             }
     }
     if (!updated) {
-        for (int c = tid; c < (int)L0.g.N; c += nth) L0.p[c] = __ldcg(L0.p + c) + (double)__ldcg(L0.e + c);
-        if (!R.bar.sync()) return false;
+        for (int c = tid; c < (int)L0.g.N; c += nth) L0.p[c] = L_::ld(L0.p + c) + (double)L_::ld(L0.e + c);
+        if (!x.sync()) return false;
     }
     return true;
 }
 
 // FP64 residual of level 0: its squared norm, the FP32 copy r and e = 0
-template <int DIM>
-__device__ double resid64_local(const MGLevel& L0, long tid, long nth) {
+template <class Ld, int DIM>
+__device__ double resid64_local(const MGLevel& L0, int tid, int nth) {
     const double* b[3] = {L0.beta[0], L0.beta[1], L0.beta[2]};
     double acc = 0.0;
-    for (long c = tid; c < L0.g.N; c += nth) {
-        const double r = ops::resid64_at<LG, DIM>(L0.g, b, L0.p, L0.f, c);
+    for (int c = tid; c < (int)L0.g.N; c += nth) {
+        const double r = ops::resid64_at<Ld, DIM>(L0.g, b, L0.p, L0.f, c);
         L0.r[c] = (float)r;
         L0.e[c] = 0.f;
         acc += r * r;
@@ -294,121 +314,122 @@ __device__ double resid64_local(const MGLevel& L0, long tid, long nth) {
     return acc;
 }
 
-__device__ void set_status(PersistCtl* ctl, int st) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl->status, 0, st);
+template <class X>
+__device__ void set_status(X& x, InstStats* S, int st) {
+    if (x.leader()) atomicCAS(&S->status, 0, st);
 }
 
 // projection: f = div u*/(c dt) - mean, defect correction to tol,
 // u = u* - c dt grad p / rho_f
-template <typename T, int DIM>
-__device__ bool project(Run<T>& R, const T* phi, T* const* u, double cdt, float* sm) {
-    const PersistArgs<T>& A = R.A;
+template <typename T, int DIM, class X>
+__device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, T* const* u, double cdt, float* sm) {
+    using L_ = typename X::Ld;
     const Geom& g = A.g;
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long)gridDim.x * blockDim.x;
-    const MGLevel& L0 = A.lv[0];
+    const int tid = x.tid(), nth = x.nth();
+    const MGLevel L0 = A.lv[0];
     const double ih = 1.0 / g.h, inv_cdt = 1.0 / cdt;
     const T* uc[3] = {u[0], u[1], u[2]};
     double s = 0.0;
-    for (long c = tid; c < g.N; c += nth) {
-        const double v = ops::div_at<LG, T, DIM>(g, uc, ih, inv_cdt, c);
+    for (int c = tid; c < (int)g.N; c += nth) {
+        const double v = ops::div_at<L_, T, DIM>(g, uc, ih, inv_cdt, c);
         L0.f[c] = v;
         s += v;
     }
     double sum;
-    if (!grid_reduce<false>(s, R.partials(), R.bar, sum)) return false;
+    if (!x.template reduce<false>(s, sum)) return false;
     const double mean = sum / (double)g.N;
     double s2 = 0.0;
-    for (long c = tid; c < g.N; c += nth) {
-        const double v = __ldcg(L0.f + c) - mean;
+    for (int c = tid; c < (int)g.N; c += nth) {
+        const double v = L_::ld(L0.f + c) - mean;
         L0.f[c] = v;
         s2 += v * v;
         if (A.warm == CDI_WARM_ZERO) L0.p[c] = 0.0;
     }
-    for (long t = tid; t < g.N + g.NP; t += nth)
-        ops::coef0_at<LG, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, L0.beta, L0.bf, t);
+    for (int t = tid; t < (int)(g.N + g.NP); t += nth)
+        ops::coef0_at<L_, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, L0.beta, L0.bf, t);
     double fsq;
-    if (!grid_reduce<false>(s2, R.partials(), R.bar, fsq)) return false;
+    if (!x.template reduce<false>(s2, fsq)) return false;
     const double fn = sqrt(fsq);
     for (int l = 1; l < A.lt; ++l) {
-        const MGLevel& F = A.lv[l - 1];
-        const MGLevel& C = A.lv[l];
+        const MGLevel F = A.lv[l - 1];
+        const MGLevel C = A.lv[l];
         const float* fb[3] = {F.bf[0], F.bf[1], F.bf[2]};
-        for (long t = tid; t < C.g.N + C.g.NP; t += nth) ops::coef_restrict_at<LG, float, DIM>(F.g, C.g, fb, C.bf, t);
-        if (!R.bar.sync()) return false;
+        for (int t = tid; t < (int)(C.g.N + C.g.NP); t += nth)
+            ops::coef_restrict_at<L_, float, DIM>(F.g, C.g, fb, C.bf, t);
+        if (!x.sync()) return false;
     }
     double rsq;
-    if (!grid_reduce<false>(resid64_local<DIM>(L0, tid, nth), R.partials(), R.bar, rsq)) return false;
+    if (!x.template reduce<false>(resid64_local<L_, DIM>(L0, tid, nth), rsq)) return false;
     double rn = sqrt(rsq);
     if (!isfinite(fn) || !isfinite(rn)) {
-        set_status(A.ctl, CDI_ENAN);
+        set_status(x, S, CDI_ENAN);
         return false;
     }
     int cyc = 0;
     if (fn == 0.0) {
-        for (long c = tid; c < g.N; c += nth) L0.p[c] = 0.0;
-        if (!R.bar.sync()) return false;
+        for (int c = tid; c < (int)g.N; c += nth) L0.p[c] = 0.0;
+        if (!x.sync()) return false;
     } else {
         bool first = true;
         while (rn > A.tol * fn && cyc < A.max_vcycles) {
-            if (!vcycle<T, DIM>(R, first, sm)) return false;
+            if (!vcycle<T, DIM>(A, x, first, sm)) return false;
             first = false;
-            if (!grid_reduce<false>(resid64_local<DIM>(L0, tid, nth), R.partials(), R.bar, rsq)) return false;
+            if (!x.template reduce<false>(resid64_local<L_, DIM>(L0, tid, nth), rsq)) return false;
             rn = sqrt(rsq);
             ++cyc;
             if (!isfinite(rn)) {
-                set_status(A.ctl, CDI_ENAN);
+                set_status(x, S, CDI_ENAN);
                 return false;
             }
         }
         if (rn > A.tol * fn) {
-            set_status(A.ctl, CDI_ENOCONV);
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                A.ctl->last_cycles = cyc;
-                A.ctl->last_resid = rn / fn;
+            set_status(x, S, CDI_ENOCONV);
+            if (x.leader()) {
+                S->last_cycles = cyc;
+                S->last_resid = rn / fn;
             }
             return false;
         }
         double ps = 0.0;
-        for (long c = tid; c < g.N; c += nth) ps += __ldcg(L0.p + c);
+        for (int c = tid; c < (int)g.N; c += nth) ps += L_::ld(L0.p + c);
         double psum;
-        if (!grid_reduce<false>(ps, R.partials(), R.bar, psum)) return false;
+        if (!x.template reduce<false>(ps, psum)) return false;
         const double pmean = psum / (double)g.N;
-        for (long c = tid; c < g.N; c += nth) L0.p[c] = __ldcg(L0.p + c) - pmean;
-        if (!R.bar.sync()) return false;
+        for (int c = tid; c < (int)g.N; c += nth) L0.p[c] = L_::ld(L0.p + c) - pmean;
+        if (!x.sync()) return false;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        A.ctl->last_cycles = cyc;
-        A.ctl->last_resid = fn == 0.0 ? 0.0 : rn / fn;
-        A.ctl->total_cycles += cyc;
-        if (cyc > A.ctl->max_cycles) A.ctl->max_cycles = cyc;
+    if (x.leader()) {
+        S->last_cycles = cyc;
+        S->last_resid = fn == 0.0 ? 0.0 : rn / fn;
+        S->total_cycles += cyc;
+        if (cyc > S->max_cycles) S->max_cycles = cyc;
     }
-    for (long c = tid; c < g.N; c += nth) ops::project_at<LG, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, u, cdt, L0.p, c);
-    return R.bar.sync();
+    for (int c = tid; c < (int)g.N; c += nth) ops::project_at<L_, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, u, cdt, L0.p, c);
+    return x.sync();
 }
 
-template <typename T, int DIM>
-__global__ void __launch_bounds__(kPersistThreads, 1) k_step_persist(PersistArgs<T> A) {
-    extern __shared__ double smd[];
-    float* sm = reinterpret_cast<float*>(smd);
-    Run<T> R{A, Barrier{A.ctl, A.spin_limit}};
+// nsteps RK4 steps of one instance; the state pointers swap once per step
+template <typename T, int DIM, class X>
+__device__ void run_steps(const InstArgs<T>& A, X& x, int nsteps, InstStats* S, float* sm) {
+    using L_ = typename X::Ld;
     const Geom& g = A.g;
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x, nth = (long)gridDim.x * blockDim.x;
+    const int tid = x.tid(), nth = x.nth();
     T* phi_s = A.phi_s;
     T* phi_k = A.phi_k;
     T* u_s[3] = {A.u_s[0], A.u_s[1], A.u_s[2]};
     T* u_k[3] = {A.u_k[0], A.u_k[1], A.u_k[2]};
     const double ck[4] = {0.0, 0.5, 0.5, 1.0};
     const double bk[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-    for (int step = 0; step < A.nsteps; ++step) {
+    for (int step = 0; step < nsteps; ++step) {
         double gamma = A.gamma_param;
         if (gamma < 0.0) {  // gamma = 2.5 |u|_max, floored (Sec. 5.1)
             double mx = 0.0;
             for (int a = 0; a < DIM; ++a) {
-                const long nf = g.N + (a == DIM - 1 ? g.NP : 0);
-                for (long c = tid; c < nf; c += nth) mx = fmax(mx, fabs((double)__ldcg(u_s[a] + c)));
+                const int nf = (int)(g.N + (a == DIM - 1 ? g.NP : 0));
+                for (int c = tid; c < nf; c += nth) mx = fmax(mx, fabs((double)L_::ld(u_s[a] + c)));
             }
             double umax;
-            if (!grid_reduce<true>(mx, R.partials(), R.bar, umax)) return;
+            if (!x.template reduce<true>(mx, umax)) return;
             gamma = fmax(2.5 * umax, -A.gamma_param);
         }
         for (int st = 0; st < 4; ++st) {
@@ -428,30 +449,30 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_step_persist(PersistArgs
             f.wuY = A.wuY;
             f.wghost = A.wghost;
             f.wmuw = A.wmuw;
-            for (long c = tid; c < g.N; c += nth) ops::psi_at<LG>(g, A.ph, phi, A.psi, c);
-            if (!R.bar.sync()) return;
-            for (long c = tid; c < g.N; c += nth)
-                ops::cell_at<LG, T, DIM>(g, A.ph, phi, A.psi, A.nh[0], A.nh[1], A.nh[2], A.muc, c);
-            for (long t = tid; t < 2 * g.NP; t += nth)
-                ops::wall_at<LG, T, DIM>(g, A.ph, phi, A.psi, u[0], u[1], A.wuY, A.wghost, A.wmuw, t);
-            if (!R.bar.sync()) return;
-            for (long c = tid; c < g.N; c += nth) ops::phi_rhs_at<LG, T, DIM>(g, A.ph, f, (T)gamma, c);
-            if (!R.bar.sync()) return;
-            for (long c = tid; c < g.N; c += nth) ops::mom_at<LG, T, DIM>(g, A.ph, f, c);
-            if (!R.bar.sync()) return;
+            for (int c = tid; c < (int)g.N; c += nth) ops::psi_at<L_>(g, A.ph, phi, A.psi, c);
+            if (!x.sync()) return;
+            for (int c = tid; c < (int)g.N; c += nth)
+                ops::cell_at<L_, T, DIM>(g, A.ph, phi, A.psi, A.nh[0], A.nh[1], A.nh[2], A.muc, c);
+            for (int t = tid; t < (int)(2 * g.NP); t += nth)
+                ops::wall_at<L_, T, DIM>(g, A.ph, phi, A.psi, u[0], u[1], A.wuY, A.wghost, A.wmuw, t);
+            if (!x.sync()) return;
+            for (int c = tid; c < (int)g.N; c += nth) ops::phi_rhs_at<L_, T, DIM>(g, A.ph, f, (T)gamma, c);
+            if (!x.sync()) return;
+            for (int c = tid; c < (int)g.N; c += nth) ops::mom_at<L_, T, DIM>(g, A.ph, f, c);
+            if (!x.sync()) return;
             const int first = st == 0, last = st == 3;
             const double cn = last ? 1.0 : ck[st + 1];
             const T b = (T)bk[st], cdt = (T)(cn * A.dt), dt = (T)A.dt;
-            for (long c = tid; c < g.N; c += nth)
-                ops::stage_phi_at<LG>(b, cdt, dt, first, last, phi_s, A.rphi, A.acc_phi, phi_k, c);
-            if (!R.bar.sync()) return;
+            for (int c = tid; c < (int)g.N; c += nth)
+                ops::stage_phi_at<L_>(b, cdt, dt, first, last, phi_s, A.rphi, A.acc_phi, phi_k, c);
+            if (!x.sync()) return;
             const T* u0c[3] = {u_s[0], u_s[1], u_s[2]};
             const T* rmc[3] = {A.rm[0], A.rm[1], A.rm[2]};
             T* accm[3] = {A.acc_m[0], A.acc_m[1], A.acc_m[2]};
-            for (long c = tid; c < g.N; c += nth)
-                ops::stage_mom_at<LG, T, DIM>(g, A.ph, b, cdt, dt, first, last, phi_s, phi_k, u0c, rmc, accm, u_k, c);
-            if (!R.bar.sync()) return;
-            if (!project<T, DIM>(R, phi_k, u_k, cn * A.dt, sm)) return;
+            for (int c = tid; c < (int)g.N; c += nth)
+                ops::stage_mom_at<L_, T, DIM>(g, A.ph, b, cdt, dt, first, last, phi_s, phi_k, u0c, rmc, accm, u_k, c);
+            if (!x.sync()) return;
+            if (!project<T, DIM>(A, x, S, phi_k, u_k, cn * A.dt, sm)) return;
         }
         T* tp = phi_s;
         phi_s = phi_k;
@@ -461,7 +482,37 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_step_persist(PersistArgs
             u_s[a] = u_k[a];
             u_k[a] = tu;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) A.ctl->steps_done = step + 1;
+        if (x.leader()) S->steps_done = step + 1;
+    }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kPersistThreads, 1) k_step_persist(PersistArgs<T> P) {
+    extern __shared__ double smd[];
+    float* sm = reinterpret_cast<float*>(smd);
+    GridX x{P.ctl, P.partials, P.spin_limit, 0};
+    run_steps<T, DIM>(P.I, x, P.nsteps, &P.ctl->st, sm);
+}
+
+template <typename T, int DIM, int NT>
+__global__ void __launch_bounds__(NT, 1) k_batch_persist(BatchArgs<T> B) {
+    extern __shared__ double smd[];
+    float* sm = reinterpret_cast<float*>(smd);
+    __shared__ int s_inst;
+    __shared__ __align__(16) InstArgs<T> sA;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_inst = atomicAdd(B.counter, 1);
+        __syncthreads();
+        const int i = s_inst;
+        if (i >= B.n_inst) return;
+        // the instance descriptor into shared memory (16-byte words)
+        const int4* src = reinterpret_cast<const int4*>(B.insts + i);
+        int4* dst = reinterpret_cast<int4*>(&sA);
+        for (int w = threadIdx.x; w < (int)(sizeof(InstArgs<T>) / sizeof(int4)); w += blockDim.x) dst[w] = src[w];
+        __syncthreads();
+        BlockX x;
+        run_steps<T, DIM>(sA, x, B.nsteps, B.stats + i, sm);
     }
 }
 
@@ -496,7 +547,7 @@ size_t persist_tail_layout(const Geom& g, const MG& mg, int lt, PersistLayout& L
 template <typename T>
 cudaError_t launch_step_persist(PersistArgs<T>& A, size_t smem, int grid, cudaStream_t s) {
     void* args[] = {&A};
-    const void* fn = (A.g.D == 2) ? (const void*)k_step_persist<T, 2> : (const void*)k_step_persist<T, 3>;
+    const void* fn = (A.I.g.D == 2) ? (const void*)k_step_persist<T, 2> : (const void*)k_step_persist<T, 3>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPersistThreads), args, smem, s);
 }
 
@@ -514,9 +565,46 @@ cudaError_t persist_prepare(int dim, size_t smem, int* grid) {
     return cudaSuccess;
 }
 
+template <typename T, int NT>
+static const void* batch_fn(int dim) {
+    return (dim == 2) ? (const void*)k_batch_persist<T, 2, NT> : (const void*)k_batch_persist<T, 3, NT>;
+}
+template <typename T>
+static const void* batch_fn_threads(int dim, int threads) {
+    switch (threads) {
+        case 256: return batch_fn<T, 256>(dim);
+        case 1024: return batch_fn<T, 1024>(dim);
+        default: return batch_fn<T, 512>(dim);
+    }
+}
+
+template <typename T>
+cudaError_t batch_prepare(int dim, int threads, size_t smem, int* grid) {
+    const void* fn = batch_fn_threads<T>(dim, threads);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 0, per = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem)) != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    *grid = nsm * per;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_batch_persist(BatchArgs<T>& B, int dim, int threads, size_t smem, int grid, cudaStream_t s) {
+    void* args[] = {&B};
+    return cudaLaunchKernel(batch_fn_threads<T>(dim, threads), dim3(grid), dim3(threads), args, smem, s);
+}
+
 template cudaError_t launch_step_persist<double>(PersistArgs<double>&, size_t, int, cudaStream_t);
 template cudaError_t launch_step_persist<float>(PersistArgs<float>&, size_t, int, cudaStream_t);
 template cudaError_t persist_prepare<double>(int, size_t, int*);
 template cudaError_t persist_prepare<float>(int, size_t, int*);
+template cudaError_t batch_prepare<double>(int, int, size_t, int*);
+template cudaError_t batch_prepare<float>(int, int, size_t, int*);
+template cudaError_t launch_batch_persist<double>(BatchArgs<double>&, int, int, size_t, int, cudaStream_t);
+template cudaError_t launch_batch_persist<float>(BatchArgs<float>&, int, int, size_t, int, cudaStream_t);
 
 }  // namespace cdi

@@ -182,6 +182,62 @@ def drop_3d(n: int = 256, theta_eq_deg: float = 60.0, seed: int = 12345,
                     math.radians(theta_eq_deg), h, 0.0, 0.0, 3.5e-5, 5000, phi)
 
 
+SWEEP_SIZES = (64, 96, 128, 192, 256, 384, 512)
+
+
+def stable_dt(wl: Workload, safety: float = 0.4) -> float:
+    """A step inside the explicit limits of the RK4 step: viscous
+    (0.35 h^2 rho_min / mu_max in 2D, 0.23 h^2 rho_min / mu_max in 3D),
+    capillary (sqrt((rho1+rho2) h^3 / (4 pi sigma))) and advective
+    (h / (|U_wall| + 0.5)), times a safety factor."""
+    h = wl.h
+    rmin = min(wl.rho1, wl.rho2)
+    mmax = max(wl.mu1, wl.mu2, 1e-30)
+    visc = (0.35 if wl.dim == 2 else 0.23) * h * h * rmin / mmax
+    cap = math.sqrt((wl.rho1 + wl.rho2) * h ** 3 / (4.0 * math.pi * max(wl.sigma, 1e-30)))
+    adv = h / (max(abs(wl.U_lo), abs(wl.U_hi)) + 0.5)
+    return safety * min(visc, cap, adv)
+
+
+def sweep_2d(n_inst: int = 512, seed: int = 2024, steps: int = 2000) -> list:
+    """Parameter sweep of uneven 2D instances (half drops, half Couette):
+    nx drawn log-uniformly in [64, 512] and rounded (in log) to the nearest of
+    SWEEP_SIZES (extents whose multigrid coarsens to at most 64 cells), ny =
+    nx/2, h = 1/64; theta_eq ~ U[30, 150] deg, slip length ~ U[0.5, 4] h,
+    Ca ~ U[0.01, 0.1], density ratio rho1/rho2 ~ U[1, 20] (rho2 = 1),
+    mu = 0.1 in both fluids; Couette walls at -/+0.1 (sigma = mu U / Ca), drops
+    with sigma = 1 start as a 90 deg cap of radius 0.3 Ly; per-instance dt =
+    0.4 x the smallest explicit limit."""
+    rng = np.random.default_rng(seed)
+    logs = np.log(np.array(SWEEP_SIZES, dtype=float))
+    out = []
+    h = 1.0 / 64
+    for i in range(n_inst):
+        s = rng.uniform(math.log(64), math.log(512))
+        nx = SWEEP_SIZES[int(np.argmin(np.abs(logs - s)))]
+        ny = nx // 2
+        th = math.radians(rng.uniform(30.0, 150.0))
+        ell = rng.uniform(0.5, 4.0) * h
+        ca = rng.uniform(0.01, 0.1)
+        ratio = rng.uniform(1.0, 20.0)
+        mu = 0.1
+        Lx, Ly = nx * h, ny * h
+        if i % 2 == 0:
+            sigma, U, gamma = 1.0, 0.0, 1.0
+            phi = cap_phi_2d(nx, ny, h, 0.3 * Ly, math.pi / 2, 0.5 * Lx, h)
+            name = "sweep%03d_drop_%dx%d" % (i, nx, ny)
+        else:
+            U = 0.1
+            sigma, gamma = mu * U / ca, 2.5 * U
+            phi = couette_phi_2d(nx, ny, h, Lx / 4, 3 * Lx / 4, h)
+            name = "sweep%03d_couette_%dx%d" % (i, nx, ny)
+        wl = Workload(name, 2, (nx, ny), (Lx, Ly), ratio, 1.0, mu, mu, sigma, h, gamma, th, ell,
+                      -U, U, 0.0, steps, phi)
+        wl.dt = stable_dt(wl)
+        out.append(wl)
+    return out
+
+
 def workload(name: str) -> Workload:
     table = {
         "drop2d_64x32": lambda: drop_2d(64, 32),
