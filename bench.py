@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--exec", default="persistent", choices=["persistent", "kernels"])
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     return ap.parse_args()
 
 
@@ -245,6 +246,7 @@ def gpu_arm(args, rank, world, local_rank):
     wl = workload()
     s = cdi.from_workload(wl, precision=cdi.FP64, tol=PRESSURE_TOL, max_vcycles=100)
     s.set_exec(cdi.EXEC_PERSISTENT if args.exec == "persistent" else cdi.EXEC_KERNELS)
+    s.set_solver(PRESSURE_TOL, 100, cdi.WARM_EXTRAP)
     stream = s.stream
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -324,6 +326,9 @@ def gpu_arm(args, rank, world, local_rank):
             "frac": (achieved / hbm) if achieved else None, "traffic": traffic_for(args.roofline_kernel),
             "peak_source": peak_kind, "algorithmic_bytes_per_launch": nbytes, "launches_timed": kern_n,
             "avg_launch_us": avg_s * 1e6}
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = forms_report(args.steps)
     cpu = None
     if not args.no_cpu_baseline:
         rate, secs, sample = oracle_rate(wl, 6, budget_s=25.0)
@@ -334,7 +339,7 @@ def gpu_arm(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": wl.cells, "dt": wl.dt, "pressure_tol": PRESSURE_TOL,
                    "max_vcycles_per_solve_seen": max_cyc,
-                   "vcycles_per_step": cyc_per_step, "exec": args.exec, "parallelism": "replicas" if world > 1 else "single",
+                   "vcycles_per_step": cyc_per_step, "exec": args.exec, "warm_start": "extrapolated", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed by a 256 MiB device write before every timed step"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -342,8 +347,83 @@ def gpu_arm(args, rank, world, local_rank):
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
+
+
+def _timed_steps(step_fn, nsteps, flush):
+    """Device time (ms) of nsteps calls of step_fn, each after an L2 flush."""
+    import torch
+    total = 0.0
+    for k in range(nsteps):
+        flush.fill_(k & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        step_fn()
+        b.record()
+        torch.cuda.synchronize()
+        total += a.elapsed_time(b)
+    return total
+
+
+def forms_report(steps):
+    """The added forms on their own workloads (one GPU): FP32-mixed Couette,
+    the batched sweep of 512 uneven 2D instances against looping the
+    single-grid step over the same instances, and the 3D 256^3 drop."""
+    import numpy as np
+    import torch
+
+    from paper_2412_16843_gb300 import cdi, inputs
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    # FP32-mixed Couette 512x128
+    wl = inputs.couette_2d(512, 128, 1.0)
+    s = cdi.from_workload(wl, precision=cdi.FP32_MIXED, tol=PRESSURE_TOL)
+    s.set_solver(PRESSURE_TOL, 100, cdi.WARM_EXTRAP)
+    s.step(wl.dt, 3)
+    ms = _timed_steps(lambda: s.step(wl.dt, 1), steps, flush)
+    out["fp32_mixed_couette2d_512x128"] = {"value": wl.cells * steps / (ms / 1e3) / 1e6, "unit": UNIT,
+                                           "ms_per_step": ms / steps, "pressure_tol": PRESSURE_TOL}
+    del s
+    # batched sweep vs looping the single-grid step
+    wls = inputs.sweep_2d()
+    cells = sum(w.cells for w in wls)
+    solvers = []
+    for w in wls:
+        sv = cdi.from_workload(w, precision=cdi.FP32_MIXED, tol=PRESSURE_TOL)
+        sv.set_solver(PRESSURE_TOL, 100, cdi.WARM_EXTRAP)
+        solvers.append(sv)
+    b = cdi.Batch(solvers)
+    dts = np.array([w.dt for w in wls])
+    best, tune_ms = b.autotune(dts, 1)
+    b.step(dts, 2)
+    kb = max(2, min(steps, 5))
+    ms_b = _timed_steps(lambda: b.step(dts, 1), kb, flush)
+    loop_ms = _timed_steps(lambda: [sv.step(w.dt, 1) for sv, w in zip(solvers, wls)], 1, flush)
+    cyc = [b.stats(i)["total_cycles"] for i in range(len(wls))]
+    out["batched_sweep_512_fp32"] = {
+        "value": cells * kb / (ms_b / 1e3) / 1e6, "unit": UNIT, "instances": len(wls), "cells": cells,
+        "ms_per_step": ms_b / kb, "looped_single_grid_value": cells / (loop_ms / 1e3) / 1e6,
+        "speedup_vs_looped": (loop_ms) / (ms_b / kb), "autotuned_threads": best,
+        "autotune_ms": [float(x) for x in tune_ms], "mean_vcycles_per_step": float(np.mean(cyc)),
+        "pressure_tol": PRESSURE_TOL}
+    del b, solvers
+    torch.cuda.empty_cache()
+    # 3D drop 256^3, FP32-mixed
+    wl = inputs.drop_3d(256)
+    s = cdi.from_workload(wl, precision=cdi.FP32_MIXED, tol=PRESSURE_TOL)
+    s.set_solver(PRESSURE_TOL, 100, cdi.WARM_EXTRAP)
+    s.step(wl.dt, 2)
+    k3 = max(2, min(steps, 5))
+    ms3 = _timed_steps(lambda: s.step(wl.dt, 1), k3, flush)
+    out["fp32_mixed_drop3d_256"] = {"value": wl.cells * k3 / (ms3 / 1e3) / 1e6, "unit": UNIT,
+                                    "ms_per_step": ms3 / k3, "vcycles_last_step": s.last_stats()["total_cycles_call"],
+                                    "pressure_tol": PRESSURE_TOL}
+    del s
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():

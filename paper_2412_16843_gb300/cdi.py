@@ -22,7 +22,7 @@ STATUS = {0: "CDI_OK", 1: "CDI_EINVAL", 2: "CDI_ESTATE", 3: "CDI_ECUDA",
           4: "CDI_ENOCONV", 5: "CDI_ENAN", 6: "CDI_ETIMEOUT"}
 FP64, FP32_MIXED = 0, 1
 WALL_LO, WALL_HI, WALL_BOTH = 0, 1, 2
-WARM_PREV, WARM_ZERO = 0, 1
+WARM_PREV, WARM_ZERO, WARM_EXTRAP = 0, 1, 2
 EXEC_PERSISTENT, EXEC_KERNELS = 0, 1
 MODELS = {"1A": 0, "1B": 1, "2A": 2, "2B": 3, "3A": 4, "3B": 5, "4A": 6, "4B": 7}
 

@@ -35,6 +35,8 @@ struct cdi_ctx {
     double tol = 1e-10;
     int max_vcycles = 100;
     int warm = CDI_WARM_PREV;
+    double* hist[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    long hist_steps = 0;  // steps whose stage pressures are in hist
     int npre = 2, npost = 2;
     // workspace
     char* ws = nullptr;
@@ -159,6 +161,8 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     mg.partials = (double*)cv.take(2 * kPartials * sizeof(double));
     mg.scal = (double*)cv.take(S_NSCAL * sizeof(double));
     c->ctl = (PersistCtl*)cv.take(sizeof(PersistCtl));
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 2; ++j) c->hist[k][j] = (double*)cv.take((size_t)g.N * sizeof(double));
     *total = cv.off + 256;
 }
 
@@ -414,6 +418,9 @@ void fill_inst(const cdi_ctx* c, InstArgs<T>& A, int lt, const PersistLayout& la
     A.npost = c->npost;
     A.gamma_param = c->gamma;
     A.dt = dt;
+    for (int k = 0; k < 4; ++k)
+        for (int j = 0; j < 2; ++j) A.hist[k][j] = c->hist[k][j];
+    A.hist_step0 = c->hist_steps;
 }
 
 // record one launch's outcome on the context; the kernel swapped the state
@@ -423,6 +430,7 @@ cdi_status apply_stats(cdi_ctx* c, const InstStats& h, const char* who) {
     c->last_resid = h.last_resid;
     c->max_cycles_step = h.max_cycles;
     c->total_cycles_call = h.total_cycles;
+    c->hist_steps += h.steps_done;
     for (int s = 0; s < h.steps_done; ++s) {
         std::swap(c->phi_s, c->phi_k);
         for (int a = 0; a < 3; ++a) std::swap(c->u_s[a], c->u_k[a]);
@@ -664,6 +672,7 @@ cdi_status cdi_set_phi(cdi_ctx* c, const double* phi) {
     if (!phi) return fail(c, CDI_EINVAL, "phi is NULL");
     for (long i = 0; i < c->g.N; ++i)
         if (!std::isfinite(phi[i])) return fail(c, CDI_ENAN, "phi holds a non-finite value");
+    c->hist_steps = 0;
     return upload(c, c->phi_s, phi, c->g.N);
 }
 
@@ -679,6 +688,7 @@ cdi_status cdi_set_velocity(cdi_ctx* c, const double* u, const double* v, const 
         st = upload(c, c->u_s[a], comps[a], n);
         if (st) return st;
     }
+    c->hist_steps = 0;
     // no penetration: the wall planes of the wall-normal component are zero
     void* wn = c->u_s[c->g.W];
     if (c->precision == CDI_FP64)
@@ -692,10 +702,12 @@ cdi_status cdi_set_solver(cdi_ctx* c, double tol, int max_vcycles, int warm) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(c, CDI_EINVAL, "tol must be > 0");
     if (max_vcycles < 1) return fail(c, CDI_EINVAL, "max_vcycles must be >= 1");
-    if (warm != CDI_WARM_PREV && warm != CDI_WARM_ZERO) return fail(c, CDI_EINVAL, "bad warm-start mode");
+    if (warm != CDI_WARM_PREV && warm != CDI_WARM_ZERO && warm != CDI_WARM_EXTRAP)
+        return fail(c, CDI_EINVAL, "bad warm-start mode");
     c->tol = tol;
     c->max_vcycles = max_vcycles;
     c->warm = warm;
+    c->hist_steps = 0;
     return CDI_OK;
 }
 

@@ -240,6 +240,10 @@ struct __align__(16) InstArgs : PersistLayout {
     double tol;
     int max_vcycles, warm, npre, npost;
     double gamma_param, dt;
+    // first guess by extrapolation in time (CDI_WARM_EXTRAP): the pressure of
+    // RK stage k of the last two steps, hist[k][s & 1] written at step s
+    double* hist[4][2];
+    long hist_step0;   // steps stored before this launch
 };
 
 template <typename T>

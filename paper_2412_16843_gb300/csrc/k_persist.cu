@@ -322,7 +322,8 @@ __device__ void set_status(X& x, InstStats* S, int st) {
 // projection: f = div u*/(c dt) - mean, defect correction to tol,
 // u = u* - c dt grad p / rho_f
 template <typename T, int DIM, class X>
-__device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, T* const* u, double cdt, float* sm) {
+__device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, T* const* u, double cdt, float* sm,
+                        int stage, long sg) {
     using L_ = typename X::Ld;
     const Geom& g = A.g;
     const int tid = x.tid(), nth = x.nth();
@@ -339,11 +340,17 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
     if (!x.template reduce<false>(s, sum)) return false;
     const double mean = sum / (double)g.N;
     double s2 = 0.0;
+    // first guess: zero, the last solve's pressure, or the same RK stage of the
+    // last two steps extrapolated linearly in time (2 p_(n-1) - p_(n-2))
+    const bool extrap = (A.warm == CDI_WARM_EXTRAP);
+    const double* hnew = extrap ? A.hist[stage][(sg - 1) & 1] : nullptr;
+    const double* hold = extrap ? A.hist[stage][sg & 1] : nullptr;
     for (int c = tid; c < (int)g.N; c += nth) {
         const double v = L_::ld(L0.f + c) - mean;
         L0.f[c] = v;
         s2 += v * v;
         if (A.warm == CDI_WARM_ZERO) L0.p[c] = 0.0;
+        else if (extrap && sg >= 2) L0.p[c] = 2.0 * L_::ld(hnew + c) - L_::ld(hold + c);
     }
     for (int t = tid; t < (int)(g.N + g.NP); t += nth)
         ops::coef0_at<L_, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, L0.beta, L0.bf, t);
@@ -366,8 +373,12 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
         return false;
     }
     int cyc = 0;
+    double* hput = extrap ? A.hist[stage][sg & 1] : nullptr;
     if (fn == 0.0) {
-        for (int c = tid; c < (int)g.N; c += nth) L0.p[c] = 0.0;
+        for (int c = tid; c < (int)g.N; c += nth) {
+            L0.p[c] = 0.0;
+            if (extrap) hput[c] = 0.0;
+        }
         if (!x.sync()) return false;
     } else {
         bool first = true;
@@ -395,7 +406,11 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
         double psum;
         if (!x.template reduce<false>(ps, psum)) return false;
         const double pmean = psum / (double)g.N;
-        for (int c = tid; c < (int)g.N; c += nth) L0.p[c] = L_::ld(L0.p + c) - pmean;
+        for (int c = tid; c < (int)g.N; c += nth) {
+            const double v = L_::ld(L0.p + c) - pmean;
+            L0.p[c] = v;
+            if (extrap) hput[c] = v;
+        }
         if (!x.sync()) return false;
     }
     if (x.leader()) {
@@ -472,7 +487,7 @@ __device__ void run_steps(const InstArgs<T>& A, X& x, int nsteps, InstStats* S, 
             for (int c = tid; c < (int)g.N; c += nth)
                 ops::stage_mom_at<L_, T, DIM>(g, A.ph, b, cdt, dt, first, last, phi_s, phi_k, u0c, rmc, accm, u_k, c);
             if (!x.sync()) return;
-            if (!project<T, DIM>(A, x, S, phi_k, u_k, cn * A.dt, sm)) return;
+            if (!project<T, DIM>(A, x, S, phi_k, u_k, cn * A.dt, sm, st, A.hist_step0 + step)) return;
         }
         T* tp = phi_s;
         phi_s = phi_k;

@@ -203,6 +203,8 @@ def test_couette_full_size_512x128_parity(exec_mode):
     the velocity bar is the solver tolerance times a safety factor of 10."""
     wl = inputs.couette_2d(512, 128, 1.0)
     g, o = pair(wl, tol=1e-8, exec_mode=exec_mode)
+    g.set_solver(1e-8, 100, cdi.WARM_EXTRAP)
+    g.set_state(wl.phi0)
     g.step(wl.dt, 3)
     o.step(wl.dt, 3)
     phi_g, vel_g, _ = g.get_fields()
@@ -281,3 +283,32 @@ def test_adaptive_gamma_parity_both_modes():
         assert rel(phi_g, phi_o) < 1e-11
         for a in range(2):
             assert rel(vel_g[a], vel_o[a]) < 1e-10
+
+
+@pytest.mark.parametrize("exec_mode", [cdi.EXEC_PERSISTENT], ids=["persistent"])
+def test_extrapolated_warm_start_parity_and_fewer_cycles(exec_mode):
+    """First guess by linear extrapolation in time of each RK stage's pressure:
+    same solution as the oracle (whose first guess is the last solve's
+    pressure) within the FP64 bar, with fewer V-cycles than the plain guess."""
+    wl = inputs.couette_2d(128, 32, 1.0)
+    g_prev = cdi.from_workload(wl, tol=1e-12)
+    g_ext = cdi.from_workload(wl, tol=1e-12)
+    g_ext.set_solver(1e-12, 100, cdi.WARM_EXTRAP)
+    g_ext.set_state(wl.phi0)
+    for g in (g_prev, g_ext):
+        g.set_exec(exec_mode)
+        g.step(wl.dt, 20)
+    o = oracle.from_workload(wl, tol=1e-12)
+    o.step(wl.dt, 20)
+    cyc_prev = g_prev.last_stats()["total_cycles_call"]
+    g_prev.step(wl.dt, 20)
+    g_ext.step(wl.dt, 20)
+    o.step(wl.dt, 20)
+    cyc_prev = g_prev.last_stats()["total_cycles_call"]
+    cyc_ext = g_ext.last_stats()["total_cycles_call"]
+    phi_g, vel_g, _ = g_ext.get_fields()
+    phi_o, vel_o, _ = o.get_state()
+    assert rel(phi_g, phi_o) < 1e-11
+    for a in range(2):
+        assert rel(vel_g[a], vel_o[a]) < 1e-10
+    assert cyc_ext < cyc_prev, (cyc_ext, cyc_prev)
