@@ -1,0 +1,77 @@
+"""Pins of the FP64 reference network (oracle/unet.py): gradients against
+central differences, closed forms of the convolution and of the first Adam
+step, and the exact parameter count."""
+import numpy as np
+
+from oracle import unet
+
+
+def test_parameter_count():
+    # 27 (2*16 + 16*32 + 32*64 + 64*128 + 192*64 + 96*32 + 48*16) + 16*1 weights + biases
+    assert unet.param_count() == 27 * 26912 + 16 + (16 + 32 + 64 + 128 + 64 + 32 + 16 + 1)
+
+
+def test_conv_closed_forms():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((4, 5, 6, 3))
+    # only the centre tap: a per-voxel matrix product
+    w = np.zeros((27, 2, 3))
+    w[13] = rng.standard_normal((2, 3))
+    b = np.array([0.5, -1.0])
+    assert np.allclose(unet.conv(x, w, b), x @ w[13].T + b, atol=1e-14)
+    # all-ones kernel on a constant field: 27 * Cin * c inside, fewer taps at the zero-padded faces
+    ones = np.ones((27, 1, 3))
+    y = unet.conv(np.full((4, 5, 6, 3), 2.0), ones, np.zeros(1))
+    assert np.allclose(y[1:-1, 1:-1, 1:-1, 0], 27 * 3 * 2.0)
+    assert np.allclose(y[0, 0, 0, 0], 8 * 3 * 2.0)           # corner: 2x2x2 neighbours
+    # a tap moves the field by one cell: tap (dz,dy,dx) = (0,0,+1) reads x[.., i+1]
+    w = np.zeros((27, 3, 3))
+    w[(0 + 1) * 9 + (0 + 1) * 3 + (1 + 1)] = np.eye(3)
+    y = unet.conv(x, w, np.zeros(3))
+    assert np.allclose(y[:, :, :-1], x[:, :, 1:]) and np.allclose(y[:, :, -1], 0.0)
+
+
+def test_pool_up_adjoint():
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal((4, 4, 4, 2))
+    b = rng.standard_normal((2, 2, 2, 2))
+    # <pool(a), b> = <a, pool^T(b)> and <up(b), a> = <b, up^T(a)>
+    assert np.isclose(np.sum(unet.pool(a) * b), np.sum(a * unet.pool_backward(b)))
+    assert np.isclose(np.sum(unet.up(b) * a), np.sum(b * unet.up_backward(a)))
+
+
+def test_gradients_match_central_differences():
+    rng = np.random.default_rng(2)
+    P = unet.init_params(3)
+    for k in P:
+        if k.endswith(".b"):
+            P[k] = 0.1 * rng.standard_normal(P[k].shape)
+    x = rng.standard_normal((8, 8, 8, 2))
+    t = rng.standard_normal((8, 8, 8, 1))
+    y, c = unet.forward(P, x)
+    G = unet.backward(P, c, y, t)
+    h = 1e-6
+    checked = 0
+    for k in sorted(P):
+        flat = P[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = unet.loss(unet.forward(P, x)[0], t)
+            flat[idx] = old - h
+            lm = unet.loss(unet.forward(P, x)[0], t)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            g = G[k].reshape(-1)[idx]
+            assert abs(fd - g) <= 1e-6 * max(abs(fd), abs(g)) + 1e-10, (k, idx, fd, g)
+            checked += 1
+    assert checked >= 60
+
+
+def test_first_adam_step_closed_form():
+    P = {"w": np.array([1.0, -2.0, 3.0])}
+    G = {"w": np.array([0.5, -4.0, 0.0])}
+    st = {}
+    unet.adam_step(P, G, st, lr=0.01)
+    # first step: m_hat = g, v_hat = g^2, so the update is -lr g / (|g| + eps)
+    assert np.allclose(P["w"], [1.0 - 0.01 * 0.5 / (0.5 + 1e-8), -2.0 + 0.01 * 4.0 / (4.0 + 1e-8), 3.0])
