@@ -64,10 +64,11 @@ typedef enum {
 
 enum { CDI_FP64 = 0, CDI_FP32_MIXED = 1 };
 enum { CDI_WALL_LO = 0, CDI_WALL_HI = 1, CDI_WALL_BOTH = 2 };
-/* first guess of each pressure solve: the last solve's pressure, zero, or
+/* first guess of each pressure solve: the last solve's pressure, zero,
  * (persistent and batched execution) the same RK stage of the two previous
- * steps extrapolated linearly in time */
-enum { CDI_WARM_PREV = 0, CDI_WARM_ZERO = 1, CDI_WARM_EXTRAP = 2 };
+ * steps extrapolated linearly in time, or the prediction of the network
+ * attached with cdi_set_warm_unet (launch-per-kernel execution) */
+enum { CDI_WARM_PREV = 0, CDI_WARM_ZERO = 1, CDI_WARM_EXTRAP = 2, CDI_WARM_UNET = 3 };
 /* how cdi_step runs: one persistent cooperative launch per call (default), or
  * one launch per stencil / multigrid kernel with host-side convergence tests */
 enum { CDI_EXEC_PERSISTENT = 0, CDI_EXEC_KERNELS = 1 };
@@ -269,6 +270,69 @@ const char* cdi_batch_last_error(const cdi_batch* b);
 
 /* Release the batch (not its contexts or workspace). NULL is accepted. */
 void cdi_batch_destroy(cdi_batch* b);
+
+/* ---------------------------------------------------------------------------
+ * Learned first guess of the pressure solve (a form of the solver; the paper
+ * has no network).  A 3D U-Net with four levels (16, 32, 64, 128 channels,
+ * one 3x3x3 convolution per level with zero padding and ReLU, 2x2x2 average
+ * pooling, nearest upsampling, skip connections by concatenation, a 1x1x1
+ * head; 726,993 parameters) maps (f / rms(f), rho_f / max(rho1, rho2)) to
+ * p / (rms(f) max(rho1, rho2) h^2) (h: grid spacing) for the pressure equation
+ * div(grad p / rho_f) = f of the projection (Sec. 4).  Convolutions run on the
+ * tensor cores with BF16 weights and activations and FP32 accumulation;
+ * master weights and Adam moments are FP32.  Arrays are channels-last with x
+ * fastest: input [nz][ny][nx][2], output [nz][ny][nx].  The prediction only
+ * starts the multigrid solve, which still iterates to its tolerance.
+ * ------------------------------------------------------------------------- */
+typedef struct cdi_unet cdi_unet;
+
+/* Create a network for nx*ny*nz grids; every extent a multiple of 8 and the
+ * grid at most 2^28 voxels. */
+cdi_status cdi_unet_create(cdi_unet** out, int nx, int ny, int nz);
+
+/* Device workspace (parameters, gradients, Adam moments, activations). */
+cdi_status cdi_unet_workspace_bytes(const cdi_unet* net, size_t* bytes);
+
+/* Bind the workspace (256-byte aligned, cleared here) and the stream. */
+cdi_status cdi_unet_bind_workspace(cdi_unet* net, void* dev_ptr, size_t bytes,
+                                   void* cuda_stream);
+
+/* Number of parameters (726,993). */
+cdi_status cdi_unet_param_count(size_t* n);
+
+/* Copy the parameters from / to host memory (n doubles, stored as FP32 on
+ * the device).  Flat order: for the layers e0, e1, e2, b, d2, d1, d0, head,
+ * the weights [taps][Cout][Cin] (tap (dz+1)*9 + (dy+1)*3 + (dx+1)) then the
+ * biases [Cout].  Setting the parameters resets the Adam moments. */
+cdi_status cdi_unet_set_params(cdi_unet* net, const double* params, size_t n);
+cdi_status cdi_unet_get_params(cdi_unet* net, double* params, size_t n);
+
+/* Forward pass on host arrays: x [N][2] -> y [N]. */
+cdi_status cdi_unet_forward(cdi_unet* net, const double* x, double* y);
+
+/* One training step on host arrays x [N][2], target [N]: forward, the mean
+ * squared error (written to loss before the update, may be NULL), the
+ * gradients of every parameter (written to grads in the flat order when not
+ * NULL) and, when lr > 0, one Adam step (b1 0.9, b2 0.999, eps 1e-8). */
+cdi_status cdi_unet_train_step(cdi_unet* net, const double* x, const double* target,
+                               double lr, double* loss, double* grads);
+
+/* Last error of the network (NULL: of the last failed cdi_unet_create). */
+const char* cdi_unet_last_error(const cdi_unet* net);
+
+/* Release the network (not its workspace). NULL is accepted. */
+void cdi_unet_destroy(cdi_unet* net);
+
+/* Attach a network (NULL detaches) whose extents equal the context's grid
+ * (3D only).  With CDI_WARM_UNET every pressure solve of cdi_step starts from
+ * the network's prediction; cdi_step then launches kernel by kernel.  The
+ * network must stay alive while attached and share the context's stream. */
+cdi_status cdi_set_warm_unet(cdi_ctx* ctx, cdi_unet* net);
+
+/* The right-hand side (mean removed) and the solution of the last pressure
+ * solve of cdi_step or cdi_solve_pressure, cell layout (either pointer may
+ * be NULL): training pairs for the network. */
+cdi_status cdi_last_pressure(cdi_ctx* ctx, double* f, double* p);
 
 /* Total phase volume sum(phi) * cell_volume of n doubles at phi_dev (device
  * memory), written as one double to mass_dev (device memory), with work

@@ -1,10 +1,10 @@
 """FP64 reference of the multigrid warm-start network (TEST INFRASTRUCTURE ONLY).
 
 A 3D U-Net maps the normalised pressure right-hand side and density,
-(f / rms(f), rho / max(rho)), to the normalised pressure p / (rms(f) max(rho) L^2)
-(L: the domain's x length).  The paper has no network; this is the learned
-first guess of the pressure solve that the build adds (a form of the solver,
-not of the method).  Only tests/ and the bench's CPU legs use this module.
+(f / rms(f), rho / max(rho)), to the normalised pressure p / (rms(f) max(rho) h^2)
+(h: the grid spacing).  The paper has no network; this is a learned
+first guess for the pressure solve (a form of the solver, not of the
+method).  Only tests/ and the bench's CPU legs use this module.
 
 Architecture (one 3x3x3 convolution per level, zero padding, ReLU after every
 convolution but the last, 2x2x2 average pooling down, nearest upsampling up,
@@ -22,6 +22,16 @@ Arrays are channels-last: an activation is (nz, ny, nx, C); a 3x3x3 weight is
 Everything here is plain FP64 numpy written from the definitions: a
 convolution is a sum over the 27 shifted inputs, its gradients are the
 transposed sums.
+
+Storage precision.  forward() and backward() take an optional `store`
+function applied to every array the GPU network keeps in memory (the input,
+each convolution's activated output, each pooled array, the loss gradient,
+each data gradient and each accumulated skip gradient).  With store=None the
+network is plain FP64.  With store=bf16_round the stored values, and with them
+the ReLU decisions (y > 0) that select which gradients flow, are those of a
+network that keeps its activations in bfloat16, so that comparisons with such
+a network compare arithmetic rather than the discontinuous ReLU masks.  The
+arithmetic between storage points stays FP64.
 """
 from __future__ import annotations
 
@@ -31,6 +41,20 @@ LAYERS = [  # name, Cin, Cout, taps
     ("e0", 2, 16, 27), ("e1", 16, 32, 27), ("e2", 32, 64, 27), ("b", 64, 128, 27),
     ("d2", 192, 64, 27), ("d1", 96, 32, 27), ("d0", 48, 16, 27), ("head", 16, 1, 1),
 ]
+
+
+def bf16_round(a):
+    """Round to bfloat16 (8 exponent bits, 7 stored mantissa bits) by
+    round-to-nearest, ties-to-even, of the FP32 value; returned as FP64.
+    The FP32 bit pattern keeps its top 16 bits after adding 0x7FFF plus the
+    lowest kept bit (the tie breaker).  Finite inputs only."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _identity(a):
+    return a
 
 
 def param_count() -> int:
@@ -101,24 +125,25 @@ def up_backward(dy):
     return dy.reshape(nz // 2, 2, ny // 2, 2, nx // 2, 2, c).sum(axis=(1, 3, 5))
 
 
-def forward(P, x):
+def forward(P, x, store=None):
     """x: (nz, ny, nx, 2); extents divisible by 8.  Returns y (nz, ny, nx, 1)
-    and the cache the backward pass needs."""
-    c = {"x": x}
+    and the cache the backward pass needs.  store: see the module docstring."""
+    S = store or _identity
+    c = {"x": S(x)}
     relu = lambda a: np.maximum(a, 0.0)
-    c["e0"] = relu(conv(x, P["e0.w"], P["e0.b"]))
-    c["p0"] = pool(c["e0"])
-    c["e1"] = relu(conv(c["p0"], P["e1.w"], P["e1.b"]))
-    c["p1"] = pool(c["e1"])
-    c["e2"] = relu(conv(c["p1"], P["e2.w"], P["e2.b"]))
-    c["p2"] = pool(c["e2"])
-    c["b"] = relu(conv(c["p2"], P["b.w"], P["b.b"]))
+    c["e0"] = S(relu(conv(c["x"], P["e0.w"], P["e0.b"])))
+    c["p0"] = S(pool(c["e0"]))
+    c["e1"] = S(relu(conv(c["p0"], P["e1.w"], P["e1.b"])))
+    c["p1"] = S(pool(c["e1"]))
+    c["e2"] = S(relu(conv(c["p1"], P["e2.w"], P["e2.b"])))
+    c["p2"] = S(pool(c["e2"]))
+    c["b"] = S(relu(conv(c["p2"], P["b.w"], P["b.b"])))
     c["c2"] = np.concatenate([up(c["b"]), c["e2"]], axis=3)
-    c["d2"] = relu(conv(c["c2"], P["d2.w"], P["d2.b"]))
+    c["d2"] = S(relu(conv(c["c2"], P["d2.w"], P["d2.b"])))
     c["c1"] = np.concatenate([up(c["d2"]), c["e1"]], axis=3)
-    c["d1"] = relu(conv(c["c1"], P["d1.w"], P["d1.b"]))
+    c["d1"] = S(relu(conv(c["c1"], P["d1.w"], P["d1.b"])))
     c["c0"] = np.concatenate([up(c["d1"]), c["e0"]], axis=3)
-    c["d0"] = relu(conv(c["c0"], P["d0.w"], P["d0.b"]))
+    c["d0"] = S(relu(conv(c["c0"], P["d0.w"], P["d0.b"])))
     y = conv(c["d0"], P["head.w"], P["head.b"])
     return y, c
 
@@ -128,30 +153,37 @@ def loss(y, t):
     return float(np.mean((y - t) ** 2))
 
 
-def backward(P, c, y, t):
-    """Gradients of the mean squared error with respect to every parameter."""
+def backward(P, c, y, t, store=None):
+    """Gradients of the mean squared error with respect to every parameter.
+    store: see the module docstring."""
+    S = store or _identity
     G = {}
-    dy = 2.0 * (y - t) / y.size
-    dd0, G["head.w"], G["head.b"] = conv_backward(c["d0"], P["head.w"], dy)
+    dy = S(2.0 * (y - t) / y.size)
+
+    def cb(x, w, g):
+        dx, dw, db = conv_backward(x, w, g)
+        return S(dx), dw, db
+
+    dd0, G["head.w"], G["head.b"] = cb(c["d0"], P["head.w"], dy)
     dd0 = dd0 * (c["d0"] > 0)
-    dc0, G["d0.w"], G["d0.b"] = conv_backward(c["c0"], P["d0.w"], dd0)
+    dc0, G["d0.w"], G["d0.b"] = cb(c["c0"], P["d0.w"], dd0)
     k = c["d1"].shape[3]
-    dd1 = up_backward(dc0[..., :k]) * (c["d1"] > 0)
+    dd1 = S(up_backward(dc0[..., :k])) * (c["d1"] > 0)
     de0 = dc0[..., k:]
-    dc1, G["d1.w"], G["d1.b"] = conv_backward(c["c1"], P["d1.w"], dd1)
+    dc1, G["d1.w"], G["d1.b"] = cb(c["c1"], P["d1.w"], dd1)
     k = c["d2"].shape[3]
-    dd2 = up_backward(dc1[..., :k]) * (c["d2"] > 0)
+    dd2 = S(up_backward(dc1[..., :k])) * (c["d2"] > 0)
     de1 = dc1[..., k:]
-    dc2, G["d2.w"], G["d2.b"] = conv_backward(c["c2"], P["d2.w"], dd2)
+    dc2, G["d2.w"], G["d2.b"] = cb(c["c2"], P["d2.w"], dd2)
     k = c["b"].shape[3]
-    db_ = up_backward(dc2[..., :k]) * (c["b"] > 0)
+    db_ = S(up_backward(dc2[..., :k])) * (c["b"] > 0)
     de2 = dc2[..., k:]
-    dp2, G["b.w"], G["b.b"] = conv_backward(c["p2"], P["b.w"], db_)
-    de2 = (de2 + pool_backward(dp2)) * (c["e2"] > 0)
-    dp1, G["e2.w"], G["e2.b"] = conv_backward(c["p1"], P["e2.w"], de2)
-    de1 = (de1 + pool_backward(dp1)) * (c["e1"] > 0)
-    dp0, G["e1.w"], G["e1.b"] = conv_backward(c["p0"], P["e1.w"], de1)
-    de0 = (de0 + pool_backward(dp0)) * (c["e0"] > 0)
+    dp2, G["b.w"], G["b.b"] = cb(c["p2"], P["b.w"], db_)
+    de2 = S(de2 + pool_backward(dp2)) * (c["e2"] > 0)
+    dp1, G["e2.w"], G["e2.b"] = cb(c["p1"], P["e2.w"], de2)
+    de1 = S(de1 + pool_backward(dp1)) * (c["e1"] > 0)
+    dp0, G["e1.w"], G["e1.b"] = cb(c["p0"], P["e1.w"], de1)
+    de0 = S(de0 + pool_backward(dp0)) * (c["e0"] > 0)
     _, G["e0.w"], G["e0.b"] = conv_backward(c["x"], P["e0.w"], de0)
     return G
 

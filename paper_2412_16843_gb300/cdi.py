@@ -22,7 +22,7 @@ STATUS = {0: "CDI_OK", 1: "CDI_EINVAL", 2: "CDI_ESTATE", 3: "CDI_ECUDA",
           4: "CDI_ENOCONV", 5: "CDI_ENAN", 6: "CDI_ETIMEOUT"}
 FP64, FP32_MIXED = 0, 1
 WALL_LO, WALL_HI, WALL_BOTH = 0, 1, 2
-WARM_PREV, WARM_ZERO, WARM_EXTRAP = 0, 1, 2
+WARM_PREV, WARM_ZERO, WARM_EXTRAP, WARM_UNET = 0, 1, 2, 3
 EXEC_PERSISTENT, EXEC_KERNELS = 0, 1
 MODELS = {"1A": 0, "1B": 1, "2A": 2, "2B": 3, "3A": 4, "3B": 5, "4A": 6, "4B": 7}
 
@@ -90,6 +90,16 @@ def load(path: str = LIB_PATH):
         "cdi_batch_set_threads": [P, I],
         "cdi_batch_autotune": [P, DP, I, IP, DP],
         "cdi_batch_stats": [P, I, IP, IP, IP, ctypes.POINTER(ctypes.c_float)],
+        "cdi_unet_create": [ctypes.POINTER(P), I, I, I],
+        "cdi_unet_workspace_bytes": [P, ctypes.POINTER(S)],
+        "cdi_unet_bind_workspace": [P, P, S, P],
+        "cdi_unet_param_count": [ctypes.POINTER(S)],
+        "cdi_unet_set_params": [P, DP, S],
+        "cdi_unet_get_params": [P, DP, S],
+        "cdi_unet_forward": [P, DP, DP],
+        "cdi_unet_train_step": [P, DP, DP, D, DP, DP],
+        "cdi_set_warm_unet": [P, P],
+        "cdi_last_pressure": [P, DP, DP],
     })
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -99,6 +109,10 @@ def load(path: str = LIB_PATH):
     lib.cdi_batch_last_error.restype = ctypes.c_char_p
     lib.cdi_batch_destroy.argtypes = [P]
     lib.cdi_batch_destroy.restype = None
+    lib.cdi_unet_last_error.argtypes = [P]
+    lib.cdi_unet_last_error.restype = ctypes.c_char_p
+    lib.cdi_unet_destroy.argtypes = [P]
+    lib.cdi_unet_destroy.restype = None
     lib.cdi_last_error.argtypes = [P]
     lib.cdi_last_error.restype = ctypes.c_char_p
     lib.cdi_destroy.argtypes = [P]
@@ -278,6 +292,18 @@ class Solver:
         return n.value
 
 
+    def set_warm_unet(self, net):
+        """Attach a Unet (None detaches) for WARM_UNET first guesses."""
+        self._unet = net
+        self._check(self.lib.cdi_set_warm_unet(self.h, None if net is None else net.h))
+
+    def last_pressure(self):
+        """(f, p) of the last pressure solve, cell layout."""
+        f = np.empty(self.cell_shape)
+        p = np.empty(self.cell_shape)
+        self._check(self.lib.cdi_last_pressure(self.h, _dp(f), _dp(p)))
+        return f, p
+
     def profile_start(self, kernel: str, max_launches: int = 4096):
         self._check(self.lib.cdi_profile_start(self.h, kernel.encode(), max_launches))
 
@@ -343,6 +369,78 @@ class Batch:
         self._check(self.lib.cdi_batch_stats(self.h, i, ctypes.byref(st), ctypes.byref(mx), ctypes.byref(tot),
                                              ctypes.byref(ms)))
         return {"status": st.value, "max_cycles": mx.value, "total_cycles": tot.value, "last_ms": ms.value}
+
+
+class Unet:
+    """Warm-start U-Net on the GPU (cdi_unet_* in cdi.h).  Arrays are
+    channels-last (nz, ny, nx, C) float64; parameters are a flat vector in the
+    order of cdi_unet_set_params."""
+
+    def __init__(self, n, stream=None):
+        import torch
+
+        self.lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libcdi needs a CUDA device; there is no CPU path")
+        self.n = tuple(int(x) for x in n)
+        h = ctypes.c_void_p()
+        self._check(self.lib.cdi_unet_create(ctypes.byref(h), *self.n), None)
+        self.h = h
+        nbytes = ctypes.c_size_t()
+        self._check(self.lib.cdi_unet_workspace_bytes(self.h, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._check(self.lib.cdi_unet_bind_workspace(self.h, ctypes.c_void_p(self.workspace.data_ptr()),
+                                                     nbytes.value, ctypes.c_void_p(self.stream.cuda_stream)))
+        c = ctypes.c_size_t()
+        self._check(self.lib.cdi_unet_param_count(ctypes.byref(c)))
+        self.nparams = int(c.value)
+
+    def _check(self, st, h="self"):
+        if st != 0:
+            msg = self.lib.cdi_unet_last_error(self.h if h == "self" else None)
+            raise CdiError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cdi_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.n[2], self.n[1], self.n[0])
+
+    def set_params(self, flat):
+        a = _f64(flat)
+        assert a.shape == (self.nparams,)
+        self._check(self.lib.cdi_unet_set_params(self.h, _dp(a), a.size))
+
+    def get_params(self):
+        a = np.empty(self.nparams)
+        self._check(self.lib.cdi_unet_get_params(self.h, _dp(a), a.size))
+        return a
+
+    def forward(self, x):
+        xa = _f64(x)
+        assert xa.shape == self.shape + (2,)
+        y = np.empty(self.shape)
+        self._check(self.lib.cdi_unet_forward(self.h, _dp(xa), _dp(y)))
+        return y
+
+    def train_step(self, x, target, lr=0.0, want_grads=False):
+        """Loss before the update and (optionally) the flat gradients."""
+        xa, ta = _f64(x), _f64(target)
+        assert xa.shape == self.shape + (2,) and ta.size == xa.size // 2
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams) if want_grads else None
+        self._check(self.lib.cdi_unet_train_step(self.h, _dp(xa), _dp(ta), float(lr), ctypes.byref(loss), _dp(g)))
+        return (loss.value, g) if want_grads else loss.value
 
 
 def from_workload(wl, precision=FP64, tol=1e-10, max_vcycles=100):

@@ -10,6 +10,7 @@
 // The new state lands in the stage buffers, whose role is then swapped with
 // the state buffers.
 #include "cdi_internal.cuh"
+#include "unet.cuh"
 #include "../../include/cdi.h"
 
 #include <cmath>
@@ -35,6 +36,7 @@ struct cdi_ctx {
     double tol = 1e-10;
     int max_vcycles = 100;
     int warm = CDI_WARM_PREV;
+    cdi_unet* unet = nullptr;  // learned first guess (CDI_WARM_UNET)
     double* hist[4][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
     long hist_steps = 0;  // steps whose stage pressures are in hist
     int npre = 2, npost = 2;
@@ -282,6 +284,11 @@ cdi_status project(cdi_ctx* c, const T* phi, T* const* u, double cdt) {
     launch_sub_mean_and_norm(g, c->mg, s);
     launch_mg_coef<T>(g, c->ph, phi, c->mg, s);
     if (c->warm == CDI_WARM_ZERO) cudaMemsetAsync(c->mg.lv[0].p, 0, g.N * sizeof(double), s);
+    if (c->warm == CDI_WARM_UNET) {
+        const cudaError_t e = unet_predict_device<T>(c->unet, c->mg.lv[0].f, phi, c->ph.rho1, c->ph.rho2,
+                                                     c->mg.scal + S_FNORM, c->g.h, c->mg.lv[0].p, s);
+        if (e != cudaSuccess) return cuda_check(c, e, "network first guess");
+    }
     cdi_status st = mg_solve(c);
     if (st) return st;
     launch_project<T>(g, c->ph, phi, u, cdt, c->mg.lv[0].p, s);
@@ -702,7 +709,7 @@ cdi_status cdi_set_solver(cdi_ctx* c, double tol, int max_vcycles, int warm) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
     if (!(tol > 0.0) || !std::isfinite(tol)) return fail(c, CDI_EINVAL, "tol must be > 0");
     if (max_vcycles < 1) return fail(c, CDI_EINVAL, "max_vcycles must be >= 1");
-    if (warm != CDI_WARM_PREV && warm != CDI_WARM_ZERO && warm != CDI_WARM_EXTRAP)
+    if (warm != CDI_WARM_PREV && warm != CDI_WARM_ZERO && warm != CDI_WARM_EXTRAP && warm != CDI_WARM_UNET)
         return fail(c, CDI_EINVAL, "bad warm-start mode");
     c->tol = tol;
     c->max_vcycles = max_vcycles;
@@ -720,8 +727,9 @@ cdi_status cdi_step(cdi_ctx* c, double dt, int nsteps) {
     c->max_cycles_step = 0;
     c->total_cycles_call = 0;
     if (nsteps == 0) return CDI_OK;
+    if (c->warm == CDI_WARM_UNET && !c->unet) return fail(c, CDI_ESTATE, "CDI_WARM_UNET without an attached network");
     const long l0 = g_launches;
-    if (c->exec == CDI_EXEC_PERSISTENT) {
+    if (c->exec == CDI_EXEC_PERSISTENT && c->warm != CDI_WARM_UNET) {
         st = (c->precision == CDI_FP64) ? step_persist<double>(c, dt, nsteps) : step_persist<float>(c, dt, nsteps);
         if (st) return st;
     } else {
@@ -732,6 +740,36 @@ cdi_status cdi_step(cdi_ctx* c, double dt, int nsteps) {
     }
     c->launches_per_step = (g_launches - l0) / nsteps;
     return cuda_check(c, cudaStreamSynchronize(c->stream), "cdi_step");
+}
+
+cdi_status cdi_set_warm_unet(cdi_ctx* c, cdi_unet* net) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (net) {
+        if (c->g.D != 3) return fail(c, CDI_EINVAL, "the network needs a 3D grid");
+        int n[3];
+        unet_extents(net, n);
+        if (n[0] != c->g.n[0] || n[1] != c->g.n[1] || n[2] != c->g.n[2])
+            return fail(c, CDI_EINVAL, "network extents differ from the grid");
+    }
+    c->unet = net;
+    return CDI_OK;
+}
+
+cdi_status cdi_last_pressure(cdi_ctx* c, double* f, double* p) {
+    cdi_status st = need_bound(c);
+    if (st) return st;
+    const long N = c->g.N;
+    if (f) {
+        st = cuda_check(c, cudaMemcpyAsync(f, c->mg.lv[0].f, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                        "copy f");
+        if (st) return st;
+    }
+    if (p) {
+        st = cuda_check(c, cudaMemcpyAsync(p, c->mg.lv[0].p, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                        "copy p");
+        if (st) return st;
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "last_pressure");
 }
 
 cdi_status cdi_set_barrier_timeout(cdi_ctx* c, long long ns) {
@@ -1129,8 +1167,11 @@ cdi_status cdi_batch_step(cdi_batch* b, const double* dt, int nsteps) {
     if (!b->ws) return bfail(b, CDI_ESTATE, "no workspace bound");
     if (!dt) return bfail(b, CDI_EINVAL, "dt is NULL");
     if (nsteps < 0) return bfail(b, CDI_EINVAL, "nsteps must be >= 0");
-    for (int i = 0; i < b->n; ++i)
+    for (int i = 0; i < b->n; ++i) {
         if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return bfail(b, CDI_EINVAL, "every dt must be > 0");
+        if (b->inst[i]->warm == CDI_WARM_UNET)
+            return bfail(b, CDI_EINVAL, "CDI_WARM_UNET is not available in batched execution");
+    }
     if (nsteps == 0) return CDI_OK;
     return b->precision == CDI_FP64 ? batch_launch<double>(b, dt, nsteps, &b->last_ms)
                                     : batch_launch<float>(b, dt, nsteps, &b->last_ms);

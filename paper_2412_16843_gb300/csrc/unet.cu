@@ -1,0 +1,809 @@
+// Warm-start U-Net on the tensor cores: forward, backward and Adam.
+//
+// Convolutions are implicit GEMMs on channels-last BF16 activations
+// [voxel][channel] with mma.sync m16n8k16 (BF16 in, FP32 accumulate):
+//   forward      y[v][co] = b[co] + sum_t sum_ci x[v + off(t)][ci] W[t][co][ci]
+//                (M = 16 voxels per warp, N = all output channels, K = 27 taps x Cin)
+//   data grad    dx = forward(dy) with the taps flipped and W transposed,
+//                because the adjoint of a zero-padded correlation is the
+//                correlation with the mirrored kernel
+//   weight grad  dW[t][co][ci] = sum_v dy[v][co] x[v + off(t)][ci]
+//                (M = 16 output channels, N = input channels, K = voxels;
+//                partial sums of voxel chunks are added with atomics)
+// Pooling (2x2x2 mean), nearest upsampling, channel concatenation, ReLU
+// masks, the mean-squared-error loss and Adam are elementwise kernels.
+// Master weights and Adam moments are FP32; the tensor cores see BF16 copies.
+#include "unet.cuh"
+#include "../../include/cdi.h"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace cdi {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+struct CG {
+    int nx, ny, nz, N;
+};
+
+constexpr int kLayers = 8;
+// name order e0, e1, e2, b, d2, d1, d0, head: Cin, Cout, taps
+constexpr int kCin[kLayers] = {2, 16, 32, 64, 192, 96, 48, 16};
+constexpr int kCout[kLayers] = {16, 32, 64, 128, 64, 32, 16, 1};
+constexpr int kTaps[kLayers] = {27, 27, 27, 27, 27, 27, 27, 1};
+
+inline int pad16(int c) { return (c + 15) / 16 * 16; }
+
+__device__ __forceinline__ unsigned ld_pair(const bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
+__device__ __forceinline__ unsigned pack2(bf16 lo, bf16 hi) {
+    return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+__device__ __forceinline__ void mma_bf16(float* c, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// tap t = (dz+1)*9 + (dy+1)*3 + (dx+1); a 1-tap layer is the centre only
+__device__ __forceinline__ void tap_off(int tap, int ntaps, int& dz, int& dy, int& dx) {
+    if (ntaps == 1) {
+        dz = dy = dx = 0;
+        return;
+    }
+    dz = tap / 9 - 1;
+    dy = (tap / 3) % 3 - 1;
+    dx = tap % 3 - 1;
+}
+
+struct Vox {
+    int x, y, z;
+    bool in;
+};
+__device__ __forceinline__ Vox vox(const CG& g, int v) {
+    Vox o;
+    o.in = v < g.N;
+    const int vv = o.in ? v : 0;
+    o.x = vv % g.nx;
+    const int r = vv / g.nx;
+    o.y = r % g.ny;
+    o.z = r / g.ny;
+    return o;
+}
+// neighbour index or -1 (zero padding)
+__device__ __forceinline__ int nbr(const CG& g, const Vox& p, int dz, int dy, int dx) {
+    const int x = p.x + dx, y = p.y + dy, z = p.z + dz;
+    if (!p.in || x < 0 || x >= g.nx || y < 0 || y >= g.ny || z < 0 || z >= g.nz) return -1;
+    return x + g.nx * (y + g.ny * z);
+}
+
+// forward convolution (also the data gradient with flipped, transposed W)
+template <int NF, bool OUTF32>
+__global__ void __launch_bounds__(128) k_conv(CG g, const bf16* __restrict__ in, int cin_pad,
+                                              const bf16* __restrict__ w, int cout_pad, const float* __restrict__ bias,
+                                              int cout, void* out, int out_stride, int out_off, int relu, int ntaps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    const int r0 = (blockIdx.x * 4 + warp) * 16 + gid, r1 = r0 + 8;
+    const Vox v0 = vox(g, r0), v1 = vox(g, r1);
+    float acc[NF][4];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int tap = 0; tap < ntaps; ++tap) {
+        int dz, dy, dx;
+        tap_off(tap, ntaps, dz, dy, dx);
+        const int n0 = nbr(g, v0, dz, dy, dx), n1 = nbr(g, v1, dz, dy, dx);
+        const bf16* p0 = in + (size_t)(n0 < 0 ? 0 : n0) * cin_pad + 2 * tig;
+        const bf16* p1 = in + (size_t)(n1 < 0 ? 0 : n1) * cin_pad + 2 * tig;
+        const bf16* wt = w + ((size_t)tap * cout_pad + gid) * cin_pad + 2 * tig;
+        for (int k0 = 0; k0 < cin_pad; k0 += 16) {
+            const unsigned a0 = n0 >= 0 ? ld_pair(p0 + k0) : 0u;
+            const unsigned a1 = n1 >= 0 ? ld_pair(p1 + k0) : 0u;
+            const unsigned a2 = n0 >= 0 ? ld_pair(p0 + k0 + 8) : 0u;
+            const unsigned a3 = n1 >= 0 ? ld_pair(p1 + k0 + 8) : 0u;
+#pragma unroll
+            for (int j = 0; j < NF; ++j) {
+                const bf16* wj = wt + (size_t)j * 8 * cin_pad + k0;
+                mma_bf16(acc[j], a0, a1, a2, a3, ld_pair(wj), ld_pair(wj + 8));
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = h ? r1 : r0;
+            if (r >= g.N) continue;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int co = j * 8 + 2 * tig + e;
+                if (co >= cout) continue;
+                float v = acc[j][2 * h + e] + (bias ? bias[co] : 0.f);
+                if (relu) v = fmaxf(v, 0.f);
+                const size_t o = (size_t)r * out_stride + out_off + co;
+                if (OUTF32) reinterpret_cast<float*>(out)[o] = v;
+                else reinterpret_cast<bf16*>(out)[o] = __float2bfloat16(v);
+            }
+        }
+}
+
+// weight gradient: dW[t][co][ci] += sum over a voxel chunk of dy[v][co] x[v+off(t)][ci]
+template <int NF>
+__global__ void __launch_bounds__(128) k_wgrad(CG g, const bf16* __restrict__ in, int cin_pad,
+                                               const bf16* __restrict__ dyv, int cout_pad, float* dW, int cout, int cin,
+                                               int ntaps, int chunk) {
+    const int tap = blockIdx.x, co0 = blockIdx.y * 16;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+    int dz, dy, dx;
+    tap_off(tap, ntaps, dz, dy, dx);
+    float acc[NF][4];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int per_warp = chunk / 4;
+    const int vbeg = blockIdx.z * chunk + warp * per_warp;
+    const int vend = min(vbeg + per_warp, g.N);
+    const bf16 zero = __float2bfloat16(0.f);
+    auto dyat = [&](int v, int co) { return (v < g.N && co < cout_pad) ? dyv[(size_t)v * cout_pad + co] : zero; };
+    for (int vb = vbeg; vb < vend; vb += 16) {
+        const int vk[4] = {vb + 2 * tig, vb + 2 * tig + 1, vb + 2 * tig + 8, vb + 2 * tig + 9};
+        const int ca = co0 + gid, cb = co0 + gid + 8;
+        const unsigned a0 = pack2(dyat(vk[0], ca), dyat(vk[1], ca));
+        const unsigned a1 = pack2(dyat(vk[0], cb), dyat(vk[1], cb));
+        const unsigned a2 = pack2(dyat(vk[2], ca), dyat(vk[3], ca));
+        const unsigned a3 = pack2(dyat(vk[2], cb), dyat(vk[3], cb));
+        int nb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) nb[i] = (vk[i] < vend) ? nbr(g, vox(g, vk[i]), dz, dy, dx) : -1;
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            const int ci = j * 8 + gid;
+            auto xin = [&](int n) { return n >= 0 ? in[(size_t)n * cin_pad + ci] : zero; };
+            mma_bf16(acc[j], a0, a1, a2, a3, pack2(xin(nb[0]), xin(nb[1])), pack2(xin(nb[2]), xin(nb[3])));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int co = co0 + gid + 8 * h, ci = j * 8 + 2 * tig + e;
+                if (co < cout && ci < cin) atomicAdd(&dW[((size_t)tap * cout + co) * cin + ci], acc[j][2 * h + e]);
+            }
+}
+
+__global__ void k_bias_grad(int N, const bf16* dy, int stride, int C, float* db) {
+    const int c = blockIdx.y;
+    float s = 0.f;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x)
+        s += __bfloat162float(dy[(size_t)v * stride + c]);
+    __shared__ float sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(&db[c], sh[0]);
+}
+
+// 2x2x2 mean of the fine grid gf into the coarse grid
+__global__ void k_pool(CG gf, const bf16* in, int C, bf16* out) {
+    const int Nc = gf.N / 8;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)Nc * C) return;
+    const int c = (int)(t % C), V = (int)(t / C);
+    const int cx = gf.nx / 2, cy = gf.ny / 2;
+    const int X = V % cx, Y = (V / cx) % cy, Z = V / (cx * cy);
+    float s = 0.f;
+    for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < 2; ++j)
+            for (int i = 0; i < 2; ++i)
+                s += __bfloat162float(in[(size_t)((2 * X + i) + gf.nx * ((2 * Y + j) + gf.ny * (2 * Z + k))) * C + c]);
+    out[t] = __float2bfloat16(0.125f * s);
+}
+
+// din[v][off+c] += dout[parent(v)][c] / 8 on the fine grid gf
+__global__ void k_pool_bwd_add(CG gf, const bf16* dout, int C, bf16* din, int stride, int off) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)gf.N * C) return;
+    const int c = (int)(t % C), v = (int)(t / C);
+    const int x = v % gf.nx, y = (v / gf.nx) % gf.ny, z = v / (gf.nx * gf.ny);
+    const int P = (x / 2) + (gf.nx / 2) * ((y / 2) + (gf.ny / 2) * (z / 2));
+    const size_t o = (size_t)v * stride + off + c;
+    din[o] = __float2bfloat16(__bfloat162float(din[o]) + 0.125f * __bfloat162float(dout[(size_t)P * C + c]));
+}
+
+// nearest upsampling of the coarse input into channels [off, off+C) of the fine output
+__global__ void k_up(CG gf, const bf16* in, int C, bf16* out, int stride, int off) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)gf.N * C) return;
+    const int c = (int)(t % C), v = (int)(t / C);
+    const int x = v % gf.nx, y = (v / gf.nx) % gf.ny, z = v / (gf.nx * gf.ny);
+    const int P = (x / 2) + (gf.nx / 2) * ((y / 2) + (gf.ny / 2) * (z / 2));
+    out[(size_t)v * stride + off + c] = in[(size_t)P * C + c];
+}
+
+// adjoint of k_up: din[V][c] = sum of the 8 children dout[child][off+c]
+__global__ void k_up_bwd(CG gf, const bf16* dout, int stride, int off, int C, bf16* din) {
+    const int Nc = gf.N / 8;
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)Nc * C) return;
+    const int c = (int)(t % C), V = (int)(t / C);
+    const int cx = gf.nx / 2, cy = gf.ny / 2;
+    const int X = V % cx, Y = (V / cx) % cy, Z = V / (cx * cy);
+    float s = 0.f;
+    for (int k = 0; k < 2; ++k)
+        for (int j = 0; j < 2; ++j)
+            for (int i = 0; i < 2; ++i)
+                s += __bfloat162float(
+                    dout[(size_t)((2 * X + i) + gf.nx * ((2 * Y + j) + gf.ny * (2 * Z + k))) * stride + off + c]);
+    din[t] = __float2bfloat16(s);
+}
+
+__global__ void k_copy_ch(int N, const bf16* src, int sstride, int soff, bf16* dst, int dstride, int doff, int C) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)N * C) return;
+    const int c = (int)(t % C), v = (int)(t / C);
+    dst[(size_t)v * dstride + doff + c] = src[(size_t)v * sstride + soff + c];
+}
+
+// g *= (y > 0) (ReLU backward), both [N][C] contiguous
+__global__ void k_relu_mask(long n, bf16* g, const bf16* y) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n && !(__bfloat162float(y[t]) > 0.f)) g[t] = __float2bfloat16(0.f);
+}
+
+// mean squared error: partial sums of (y-t)^2 and the BF16 gradient 2(y-t)/N in channel 0 of 16
+__global__ void k_loss(int N, const float* y, const float* t, bf16* gy, float* part) {
+    float s = 0.f;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        const float d = y[v] - t[v];
+        s += d * d;
+        gy[(size_t)v * 16] = __float2bfloat16(2.f * d / (float)N);
+    }
+    __shared__ float sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(part, sh[0]);
+}
+
+// Adam (Kingma and Ba, 2015) with bias corrections bc1 = 1 - b1^t, bc2 = 1 - b2^t
+__global__ void k_adam(long n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                       float bc1, float bc2) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+// BF16 copies: wb[t][co_pad][ci_pad] = W[t][co][ci]; wt[t][ci_pad][co_pad] = W[T-1-t][co][ci]
+__global__ void k_weights_bf16(const float* W, int taps, int cout, int cin, int co_pad, int ci_pad, bf16* wb,
+                               bf16* wt) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = (long)taps * co_pad * ci_pad;
+    if (i >= n) return;
+    const int ci = (int)(i % ci_pad), co = (int)((i / ci_pad) % co_pad), t = (int)(i / ((long)ci_pad * co_pad));
+    const float val = (co < cout && ci < cin) ? W[((size_t)t * cout + co) * cin + ci] : 0.f;
+    wb[i] = __float2bfloat16(val);
+    const int tf = taps - 1 - t;
+    wt[((size_t)tf * ci_pad + ci) * co_pad + co] = __float2bfloat16(val);
+}
+
+__global__ void k_input_host(int N, const double* x2, bf16* x) {  // x2: [N][2] from the host
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)N * 16) return;
+    const int c = (int)(t % 16), v = (int)(t / 16);
+    x[t] = __float2bfloat16(c < 2 ? (float)x2[(size_t)v * 2 + c] : 0.f);
+}
+
+template <typename T>
+__global__ void k_input_solver(int N, const double* f, const T* phi, double rho1, double rho2, const double* fnorm,
+                               bf16* x) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)N * 16) return;
+    const int c = (int)(t % 16), v = (int)(t / 16);
+    float val = 0.f;
+    if (c == 0) {
+        const double fr = *fnorm / sqrt((double)N);
+        val = fr > 0.0 ? (float)(f[v] / fr) : 0.f;
+    } else if (c == 1) {
+        val = (float)(((rho1 - rho2) * (double)phi[v] + rho2) / fmax(rho1, rho2));
+    }
+    x[t] = __float2bfloat16(val);
+}
+
+__global__ void k_output_solver(int N, const float* y, const double* fnorm, double scale, double* p) {
+    const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    p[v] = (double)y[v] * (*fnorm / sqrt((double)N)) * scale;
+}
+
+unsigned blocks(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace cdi
+
+using namespace cdi;
+
+struct cdi_unet {
+    int n[3] = {0, 0, 0};
+    CG g[4];  // levels 0..3
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    // parameters
+    float *W[kLayers], *B[kLayers], *gW[kLayers], *gB[kLayers];
+    float *mW[kLayers], *vW[kLayers], *mB[kLayers], *vB[kLayers];
+    bf16 *Wb[kLayers], *Wt[kLayers];
+    int ci_pad[kLayers], co_pad[kLayers];
+    // activations and gradients (BF16, channels last)
+    bf16 *x, *e0, *p0, *e1, *p1, *e2, *p2, *b, *c2, *d2, *c1, *d1, *c0, *d0;
+    bf16 *gy, *gd0, *gc0, *gd1, *gc1, *gd2, *gc2, *gb, *gp2, *ge2, *gp1, *ge1, *gp0, *ge0;
+    float *y, *t, *part;
+    double* x2;  // host-input staging [N][2]
+    long adam_t = 0;
+    bool weights_ready = false;
+    std::string err;
+};
+
+namespace {
+
+std::string g_unet_error;
+
+cdi_status ufail(cdi_unet* u, cdi_status st, const std::string& m) {
+    if (u) u->err = m;
+    else g_unet_error = m;
+    return st;
+}
+
+struct UCarver {
+    char* base;
+    size_t off = 0;
+    void* take(size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+void unet_carve(cdi_unet* u, char* base, size_t* total) {
+    UCarver cv{base};
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kTaps[l] * kCout[l] * kCin[l], nb = kCout[l];
+        u->ci_pad[l] = pad16(kCin[l]);
+        u->co_pad[l] = pad16(kCout[l]);
+        u->W[l] = (float*)cv.take(nw * 4);
+        u->B[l] = (float*)cv.take(nb * 4);
+        u->gW[l] = (float*)cv.take(nw * 4);
+        u->gB[l] = (float*)cv.take(nb * 4);
+        u->mW[l] = (float*)cv.take(nw * 4);
+        u->vW[l] = (float*)cv.take(nw * 4);
+        u->mB[l] = (float*)cv.take(nb * 4);
+        u->vB[l] = (float*)cv.take(nb * 4);
+        const size_t np = (size_t)kTaps[l] * u->ci_pad[l] * u->co_pad[l];
+        u->Wb[l] = (bf16*)cv.take(np * 2);
+        u->Wt[l] = (bf16*)cv.take(np * 2);
+    }
+    const long N0 = u->g[0].N, N1 = u->g[1].N, N2 = u->g[2].N, N3 = u->g[3].N;
+    auto act = [&](long n, int c) { return (bf16*)cv.take((size_t)n * c * 2); };
+    u->x = act(N0, 16);
+    u->e0 = act(N0, 16);
+    u->p0 = act(N1, 16);
+    u->e1 = act(N1, 32);
+    u->p1 = act(N2, 32);
+    u->e2 = act(N2, 64);
+    u->p2 = act(N3, 64);
+    u->b = act(N3, 128);
+    u->c2 = act(N2, 192);
+    u->d2 = act(N2, 64);
+    u->c1 = act(N1, 96);
+    u->d1 = act(N1, 32);
+    u->c0 = act(N0, 48);
+    u->d0 = act(N0, 16);
+    u->gy = act(N0, 16);
+    u->gd0 = act(N0, 16);
+    u->gc0 = act(N0, 48);
+    u->gd1 = act(N1, 32);
+    u->gc1 = act(N1, 96);
+    u->gd2 = act(N2, 64);
+    u->gc2 = act(N2, 192);
+    u->gb = act(N3, 128);
+    u->gp2 = act(N3, 64);
+    u->ge2 = act(N2, 64);
+    u->gp1 = act(N2, 32);
+    u->ge1 = act(N1, 32);
+    u->gp0 = act(N1, 16);
+    u->ge0 = act(N0, 16);
+    u->y = (float*)cv.take((size_t)N0 * 4);
+    u->t = (float*)cv.take((size_t)N0 * 4);
+    u->part = (float*)cv.take(256);
+    u->x2 = (double*)cv.take((size_t)N0 * 2 * 8);
+    *total = cv.off + 256;
+}
+
+// y = conv(in) for layer l on level grid gl into out (stride, offset)
+template <bool OUTF32>
+void conv_fwd(cdi_unet* u, int l, const CG& gl, const bf16* in, void* out, int stride, int off, bool relu) {
+    const unsigned gb = (unsigned)((gl.N + 63) / 64);
+    const int nf = u->co_pad[l] / 8;
+    const int cin = u->ci_pad[l], cop = u->co_pad[l];
+    cudaStream_t s = u->stream;
+#define CONV_CASE(NFV)                                                                                          \
+    case NFV:                                                                                                   \
+        k_conv<NFV, OUTF32><<<gb, 128, 0, s>>>(gl, in, cin, u->Wb[l], cop, u->B[l], kCout[l], out, stride, off, \
+                                                relu ? 1 : 0, kTaps[l]);                                        \
+        break;
+    switch (nf) {
+        CONV_CASE(2)
+        CONV_CASE(4)
+        CONV_CASE(8)
+        CONV_CASE(16)
+        default: break;
+    }
+#undef CONV_CASE
+}
+
+// dx (BF16 [N][ci_pad]) = adjoint of layer l applied to dy (BF16 [N][co_pad])
+void conv_dgrad(cdi_unet* u, int l, const CG& gl, const bf16* dy, bf16* dx) {
+    const unsigned gb = (unsigned)((gl.N + 63) / 64);
+    const int nf = u->ci_pad[l] / 8;
+    cudaStream_t s = u->stream;
+#define DG_CASE(NFV)                                                                                              \
+    case NFV:                                                                                                     \
+        k_conv<NFV, false><<<gb, 128, 0, s>>>(gl, dy, u->co_pad[l], u->Wt[l], u->ci_pad[l], nullptr,             \
+                                               u->ci_pad[l], dx, u->ci_pad[l], 0, 0, kTaps[l]);                   \
+        break;
+    switch (nf) {
+        DG_CASE(2)
+        DG_CASE(4)
+        DG_CASE(6)
+        DG_CASE(8)
+        DG_CASE(12)
+        DG_CASE(24)
+        default: break;
+    }
+#undef DG_CASE
+}
+
+void conv_wgrad(cdi_unet* u, int l, const CG& gl, const bf16* in, const bf16* dy) {
+    const int chunk = 1024;
+    dim3 grid((unsigned)kTaps[l], (unsigned)((u->co_pad[l] + 15) / 16), (unsigned)((gl.N + chunk - 1) / chunk));
+    const int nf = u->ci_pad[l] / 8;
+    cudaStream_t s = u->stream;
+#define WG_CASE(NFV)                                                                                                \
+    case NFV:                                                                                                       \
+        k_wgrad<NFV><<<grid, 128, 0, s>>>(gl, in, u->ci_pad[l], dy, u->co_pad[l], u->gW[l], kCout[l], kCin[l],     \
+                                           kTaps[l], chunk);                                                        \
+        break;
+    switch (nf) {
+        WG_CASE(2)
+        WG_CASE(4)
+        WG_CASE(6)
+        WG_CASE(8)
+        WG_CASE(12)
+        WG_CASE(24)
+        default: break;
+    }
+#undef WG_CASE
+    k_bias_grad<<<dim3(64, (unsigned)kCout[l]), 256, 0, s>>>(gl.N, dy, u->co_pad[l], kCout[l], u->gB[l]);
+}
+
+void refresh_weights(cdi_unet* u) {
+    for (int l = 0; l < kLayers; ++l) {
+        const long n = (long)kTaps[l] * u->co_pad[l] * u->ci_pad[l];
+        k_weights_bf16<<<blocks(n), 256, 0, u->stream>>>(u->W[l], kTaps[l], kCout[l], kCin[l], u->co_pad[l],
+                                                          u->ci_pad[l], u->Wb[l], u->Wt[l]);
+    }
+    u->weights_ready = true;
+}
+
+// forward pass from u->x to u->y (FP32)
+void forward(cdi_unet* u) {
+    const CG *g = u->g;
+    cudaStream_t s = u->stream;
+    conv_fwd<false>(u, 0, g[0], u->x, u->e0, 16, 0, true);
+    k_pool<<<blocks(g[1].N * 16L), 256, 0, s>>>(g[0], u->e0, 16, u->p0);
+    conv_fwd<false>(u, 1, g[1], u->p0, u->e1, 32, 0, true);
+    k_pool<<<blocks(g[2].N * 32L), 256, 0, s>>>(g[1], u->e1, 32, u->p1);
+    conv_fwd<false>(u, 2, g[2], u->p1, u->e2, 64, 0, true);
+    k_pool<<<blocks(g[3].N * 64L), 256, 0, s>>>(g[2], u->e2, 64, u->p2);
+    conv_fwd<false>(u, 3, g[3], u->p2, u->b, 128, 0, true);
+    k_up<<<blocks(g[2].N * 128L), 256, 0, s>>>(g[2], u->b, 128, u->c2, 192, 0);
+    k_copy_ch<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2].N, u->e2, 64, 0, u->c2, 192, 128, 64);
+    conv_fwd<false>(u, 4, g[2], u->c2, u->d2, 64, 0, true);
+    k_up<<<blocks(g[1].N * 64L), 256, 0, s>>>(g[1], u->d2, 64, u->c1, 96, 0);
+    k_copy_ch<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1].N, u->e1, 32, 0, u->c1, 96, 64, 32);
+    conv_fwd<false>(u, 5, g[1], u->c1, u->d1, 32, 0, true);
+    k_up<<<blocks(g[0].N * 32L), 256, 0, s>>>(g[0], u->d1, 32, u->c0, 48, 0);
+    k_copy_ch<<<blocks(g[0].N * 16L), 256, 0, s>>>(g[0].N, u->e0, 16, 0, u->c0, 48, 32, 16);
+    conv_fwd<false>(u, 6, g[0], u->c0, u->d0, 16, 0, true);
+    conv_fwd<true>(u, 7, g[0], u->d0, u->y, 1, 0, false);
+    g_launches += 22;
+}
+
+// gradients of the mean squared error (u->y against u->t) into gW, gB
+void backward(cdi_unet* u) {
+    const CG* g = u->g;
+    cudaStream_t s = u->stream;
+    for (int l = 0; l < kLayers; ++l) {
+        cudaMemsetAsync(u->gW[l], 0, (size_t)kTaps[l] * kCout[l] * kCin[l] * 4, s);
+        cudaMemsetAsync(u->gB[l], 0, (size_t)kCout[l] * 4, s);
+    }
+    cudaMemsetAsync(u->gy, 0, (size_t)g[0].N * 16 * 2, s);
+    cudaMemsetAsync(u->part, 0, 4, s);
+    k_loss<<<256, 256, 0, s>>>(g[0].N, u->y, u->t, u->gy, u->part);
+    // head and d0
+    conv_wgrad(u, 7, g[0], u->d0, u->gy);
+    conv_dgrad(u, 7, g[0], u->gy, u->gd0);
+    k_relu_mask<<<blocks(g[0].N * 16L), 256, 0, s>>>(g[0].N * 16L, u->gd0, u->d0);
+    conv_wgrad(u, 6, g[0], u->c0, u->gd0);
+    conv_dgrad(u, 6, g[0], u->gd0, u->gc0);
+    k_up_bwd<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[0], u->gc0, 48, 0, 32, u->gd1);
+    k_relu_mask<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1].N * 32L, u->gd1, u->d1);
+    k_copy_ch<<<blocks(g[0].N * 16L), 256, 0, s>>>(g[0].N, u->gc0, 48, 32, u->ge0, 16, 0, 16);
+    // d1
+    conv_wgrad(u, 5, g[1], u->c1, u->gd1);
+    conv_dgrad(u, 5, g[1], u->gd1, u->gc1);
+    k_up_bwd<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[1], u->gc1, 96, 0, 64, u->gd2);
+    k_relu_mask<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2].N * 64L, u->gd2, u->d2);
+    k_copy_ch<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1].N, u->gc1, 96, 64, u->ge1, 32, 0, 32);
+    // d2
+    conv_wgrad(u, 4, g[2], u->c2, u->gd2);
+    conv_dgrad(u, 4, g[2], u->gd2, u->gc2);
+    k_up_bwd<<<blocks(g[3].N * 128L), 256, 0, s>>>(g[2], u->gc2, 192, 0, 128, u->gb);
+    k_relu_mask<<<blocks(g[3].N * 128L), 256, 0, s>>>(g[3].N * 128L, u->gb, u->b);
+    k_copy_ch<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2].N, u->gc2, 192, 128, u->ge2, 64, 0, 64);
+    // bottleneck
+    conv_wgrad(u, 3, g[3], u->p2, u->gb);
+    conv_dgrad(u, 3, g[3], u->gb, u->gp2);
+    k_pool_bwd_add<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2], u->gp2, 64, u->ge2, 64, 0);
+    k_relu_mask<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2].N * 64L, u->ge2, u->e2);
+    // e2
+    conv_wgrad(u, 2, g[2], u->p1, u->ge2);
+    conv_dgrad(u, 2, g[2], u->ge2, u->gp1);
+    k_pool_bwd_add<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1], u->gp1, 32, u->ge1, 32, 0);
+    k_relu_mask<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1].N * 32L, u->ge1, u->e1);
+    // e1
+    conv_wgrad(u, 1, g[1], u->p0, u->ge1);
+    conv_dgrad(u, 1, g[1], u->ge1, u->gp0);
+    k_pool_bwd_add<<<blocks(g[0].N * 16L), 256, 0, s>>>(g[0], u->gp0, 16, u->ge0, 16, 0);
+    k_relu_mask<<<blocks(g[0].N * 16L), 256, 0, s>>>(g[0].N * 16L, u->ge0, u->e0);
+    // e0
+    conv_wgrad(u, 0, g[0], u->x, u->ge0);
+    g_launches += 50;
+}
+
+void adam(cdi_unet* u, double lr) {
+    ++u->adam_t;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float bc1 = (float)(1.0 - std::pow(0.9, (double)u->adam_t));
+    const float bc2 = (float)(1.0 - std::pow(0.999, (double)u->adam_t));
+    for (int l = 0; l < kLayers; ++l) {
+        const long nw = (long)kTaps[l] * kCout[l] * kCin[l];
+        k_adam<<<blocks(nw), 256, 0, u->stream>>>(nw, u->W[l], u->gW[l], u->mW[l], u->vW[l], (float)lr, b1, b2, eps,
+                                                   bc1, bc2);
+        k_adam<<<blocks(kCout[l]), 256, 0, u->stream>>>(kCout[l], u->B[l], u->gB[l], u->mB[l], u->vB[l], (float)lr,
+                                                         b1, b2, eps, bc1, bc2);
+    }
+    refresh_weights(u);
+}
+
+size_t param_count() {
+    size_t n = 0;
+    for (int l = 0; l < kLayers; ++l) n += (size_t)kTaps[l] * kCout[l] * kCin[l] + kCout[l];
+    return n;
+}
+
+cdi_status upload_x(cdi_unet* u, const double* x_host) {
+    const long N = u->g[0].N;
+    if (cudaMemcpyAsync(u->x2, x_host, (size_t)N * 2 * 8, cudaMemcpyHostToDevice, u->stream) != cudaSuccess)
+        return ufail(u, CDI_ECUDA, "input upload failed");
+    k_input_host<<<blocks(N * 16), 256, 0, u->stream>>>((int)N, u->x2, u->x);
+    return CDI_OK;
+}
+
+}  // namespace
+
+namespace cdi {
+
+template <typename T>
+cudaError_t unet_predict_device(cdi_unet* u, const double* f_dev, const T* phi_dev, double rho1, double rho2,
+                                const double* fnorm_dev, double h, double* p_dev, cudaStream_t s) {
+    cudaStream_t keep = u->stream;
+    u->stream = s;
+    if (!u->weights_ready) refresh_weights(u);
+    const long N = u->g[0].N;
+    k_input_solver<T><<<blocks(N * 16), 256, 0, s>>>((int)N, f_dev, phi_dev, rho1, rho2, fnorm_dev, u->x);
+    forward(u);
+    k_output_solver<<<blocks(N), 256, 0, s>>>((int)N, u->y, fnorm_dev, fmax(rho1, rho2) * h * h, p_dev);
+    g_launches += 2;
+    u->stream = keep;
+    return cudaGetLastError();
+}
+
+void unet_extents(const cdi_unet* u, int* n) {
+    n[0] = u->n[0];
+    n[1] = u->n[1];
+    n[2] = u->n[2];
+}
+
+template cudaError_t unet_predict_device<double>(cdi_unet*, const double*, const double*, double, double,
+                                                 const double*, double, double*, cudaStream_t);
+template cudaError_t unet_predict_device<float>(cdi_unet*, const double*, const float*, double, double, const double*,
+                                                double, double*, cudaStream_t);
+
+}  // namespace cdi
+
+extern "C" {
+
+cdi_status cdi_unet_create(cdi_unet** out, int nx, int ny, int nz) {
+    if (!out) return ufail(nullptr, CDI_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 8 || ny < 8 || nz < 8 || nx % 8 || ny % 8 || nz % 8)
+        return ufail(nullptr, CDI_EINVAL, "network extents must be multiples of 8 (three 2x2x2 poolings)");
+    if ((long)nx * ny * nz > (1L << 28)) return ufail(nullptr, CDI_EINVAL, "grid too large for the network");
+    cdi_unet* u = new (std::nothrow) cdi_unet();
+    if (!u) return ufail(nullptr, CDI_EINVAL, "out of host memory");
+    u->n[0] = nx;
+    u->n[1] = ny;
+    u->n[2] = nz;
+    for (int l = 0; l < 4; ++l) {
+        u->g[l].nx = nx >> l;
+        u->g[l].ny = ny >> l;
+        u->g[l].nz = nz >> l;
+        u->g[l].N = u->g[l].nx * u->g[l].ny * u->g[l].nz;
+    }
+    size_t total = 0;
+    unet_carve(u, nullptr, &total);
+    u->ws_bytes = total;
+    *out = u;
+    return CDI_OK;
+}
+
+cdi_status cdi_unet_workspace_bytes(const cdi_unet* u, size_t* bytes) {
+    if (!u || !bytes) return ufail(nullptr, CDI_EINVAL, "null argument");
+    *bytes = u->ws_bytes;
+    return CDI_OK;
+}
+
+cdi_status cdi_unet_bind_workspace(cdi_unet* u, void* dev_ptr, size_t bytes, void* stream) {
+    if (!u) return ufail(nullptr, CDI_EINVAL, "null network");
+    if (!dev_ptr || bytes < u->ws_bytes) return ufail(u, CDI_EINVAL, "workspace missing or too small");
+    if (((uintptr_t)dev_ptr) & 255u) return ufail(u, CDI_EINVAL, "workspace must be 256-byte aligned");
+    u->ws = (char*)dev_ptr;
+    u->stream = (cudaStream_t)stream;
+    size_t total = 0;
+    unet_carve(u, u->ws, &total);
+    if (cudaMemsetAsync(u->ws, 0, u->ws_bytes - 256, u->stream) != cudaSuccess ||
+        cudaStreamSynchronize(u->stream) != cudaSuccess)
+        return ufail(u, CDI_ECUDA, "workspace clear failed");
+    u->adam_t = 0;
+    u->weights_ready = false;
+    return CDI_OK;
+}
+
+cdi_status cdi_unet_param_count(size_t* n) {
+    if (!n) return ufail(nullptr, CDI_EINVAL, "null argument");
+    *n = param_count();
+    return CDI_OK;
+}
+
+// flat parameter order: for each layer (e0, e1, e2, b, d2, d1, d0, head) the
+// weights [taps][Cout][Cin] then the biases [Cout]
+cdi_status cdi_unet_set_params(cdi_unet* u, const double* host, size_t n) {
+    if (!u || !u->ws) return ufail(u, CDI_ESTATE, "network workspace not bound");
+    if (!host || n != param_count()) return ufail(u, CDI_EINVAL, "parameter array has the wrong length");
+    std::vector<float> tmp(host, host + n);
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kTaps[l] * kCout[l] * kCin[l];
+        cudaMemcpyAsync(u->W[l], tmp.data() + o, nw * 4, cudaMemcpyHostToDevice, u->stream);
+        o += nw;
+        cudaMemcpyAsync(u->B[l], tmp.data() + o, (size_t)kCout[l] * 4, cudaMemcpyHostToDevice, u->stream);
+        o += kCout[l];
+        cudaMemsetAsync(u->mW[l], 0, nw * 4, u->stream);
+        cudaMemsetAsync(u->vW[l], 0, nw * 4, u->stream);
+        cudaMemsetAsync(u->mB[l], 0, (size_t)kCout[l] * 4, u->stream);
+        cudaMemsetAsync(u->vB[l], 0, (size_t)kCout[l] * 4, u->stream);
+    }
+    u->adam_t = 0;
+    refresh_weights(u);
+    if (cudaStreamSynchronize(u->stream) != cudaSuccess) return ufail(u, CDI_ECUDA, "parameter upload failed");
+    return CDI_OK;
+}
+
+cdi_status cdi_unet_get_params(cdi_unet* u, double* host, size_t n) {
+    if (!u || !u->ws) return ufail(u, CDI_ESTATE, "network workspace not bound");
+    if (!host || n != param_count()) return ufail(u, CDI_EINVAL, "parameter array has the wrong length");
+    std::vector<float> tmp(n);
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const size_t nw = (size_t)kTaps[l] * kCout[l] * kCin[l];
+        cudaMemcpyAsync(tmp.data() + o, u->W[l], nw * 4, cudaMemcpyDeviceToHost, u->stream);
+        o += nw;
+        cudaMemcpyAsync(tmp.data() + o, u->B[l], (size_t)kCout[l] * 4, cudaMemcpyDeviceToHost, u->stream);
+        o += kCout[l];
+    }
+    if (cudaStreamSynchronize(u->stream) != cudaSuccess) return ufail(u, CDI_ECUDA, "parameter download failed");
+    for (size_t i = 0; i < n; ++i) host[i] = tmp[i];
+    return CDI_OK;
+}
+
+// x_host: [N][2] (channels last), y_host: [N]
+cdi_status cdi_unet_forward(cdi_unet* u, const double* x_host, double* y_host) {
+    if (!u || !u->ws) return ufail(u, CDI_ESTATE, "network workspace not bound");
+    if (!x_host || !y_host) return ufail(u, CDI_EINVAL, "null array");
+    if (!u->weights_ready) refresh_weights(u);
+    cdi_status st = upload_x(u, x_host);
+    if (st) return st;
+    forward(u);
+    const long N = u->g[0].N;
+    std::vector<float> y(N);
+    if (cudaMemcpyAsync(y.data(), u->y, (size_t)N * 4, cudaMemcpyDeviceToHost, u->stream) != cudaSuccess ||
+        cudaStreamSynchronize(u->stream) != cudaSuccess)
+        return ufail(u, CDI_ECUDA, std::string("forward: ") + cudaGetErrorString(cudaGetLastError()));
+    for (long i = 0; i < N; ++i) y_host[i] = y[i];
+    return CDI_OK;
+}
+
+// one training step on (x, target): loss before the update; grads (FP32,
+// flat parameter order) if grads_host is not NULL; Adam update if lr > 0
+cdi_status cdi_unet_train_step(cdi_unet* u, const double* x_host, const double* t_host, double lr, double* loss,
+                               double* grads_host) {
+    if (!u || !u->ws) return ufail(u, CDI_ESTATE, "network workspace not bound");
+    if (!x_host || !t_host) return ufail(u, CDI_EINVAL, "null array");
+    if (!(lr >= 0.0) || !std::isfinite(lr)) return ufail(u, CDI_EINVAL, "lr must be >= 0");
+    if (!u->weights_ready) refresh_weights(u);
+    const long N = u->g[0].N;
+    cdi_status st = upload_x(u, x_host);
+    if (st) return st;
+    std::vector<float> t(t_host, t_host + N);
+    cudaMemcpyAsync(u->t, t.data(), (size_t)N * 4, cudaMemcpyHostToDevice, u->stream);
+    forward(u);
+    backward(u);
+    float part = 0.f;
+    cudaMemcpyAsync(&part, u->part, 4, cudaMemcpyDeviceToHost, u->stream);
+    if (grads_host) {
+        std::vector<float> g(param_count());
+        size_t o = 0;
+        for (int l = 0; l < kLayers; ++l) {
+            const size_t nw = (size_t)kTaps[l] * kCout[l] * kCin[l];
+            cudaMemcpyAsync(g.data() + o, u->gW[l], nw * 4, cudaMemcpyDeviceToHost, u->stream);
+            o += nw;
+            cudaMemcpyAsync(g.data() + o, u->gB[l], (size_t)kCout[l] * 4, cudaMemcpyDeviceToHost, u->stream);
+            o += kCout[l];
+        }
+        if (cudaStreamSynchronize(u->stream) != cudaSuccess) return ufail(u, CDI_ECUDA, "gradient download failed");
+        for (size_t i = 0; i < g.size(); ++i) grads_host[i] = g[i];
+    }
+    if (lr > 0.0) adam(u, lr);
+    if (cudaStreamSynchronize(u->stream) != cudaSuccess)
+        return ufail(u, CDI_ECUDA, std::string("train step: ") + cudaGetErrorString(cudaGetLastError()));
+    if (loss) *loss = (double)part / (double)N;
+    return CDI_OK;
+}
+
+const char* cdi_unet_last_error(const cdi_unet* u) { return u ? u->err.c_str() : g_unet_error.c_str(); }
+
+void cdi_unet_destroy(cdi_unet* u) { delete u; }
+
+}  // extern "C"

@@ -63,3 +63,30 @@ def test_init_and_host_side_setters(lib):
     assert lib.cdi_mass(h, ctypes.byref(m)) == 2
     lib.cdi_destroy(h)
     lib.cdi_destroy(None)
+
+
+def test_unet_host_side_checks(lib):
+    n = ctypes.c_size_t()
+    assert lib.cdi_unet_param_count(ctypes.byref(n)) == 0 and n.value == 726993
+    u = ctypes.c_void_p()
+    assert lib.cdi_unet_create(ctypes.byref(u), 12, 16, 16) == 1 and not u.value   # not a multiple of 8
+    assert len(lib.cdi_unet_last_error(None)) > 0
+    assert lib.cdi_unet_create(ctypes.byref(u), 16, 16, 8) == 0 and u.value
+    nbytes = ctypes.c_size_t()
+    assert lib.cdi_unet_workspace_bytes(u, ctypes.byref(nbytes)) == 0
+    assert nbytes.value > 726993 * (4 * 4 + 2 * 2)  # FP32 weights, gradients, two Adam moments; two BF16 copies
+    x = (ctypes.c_double * (16 * 16 * 8 * 2))()
+    y = (ctypes.c_double * (16 * 16 * 8))()
+    assert lib.cdi_unet_forward(u, x, y) == 2      # no workspace bound
+    # the network attaches only to a 3D context of the same extents
+    st, h2 = _init(lib, 2, 64, 32, 1, 1.0, 0.5, 0.0)
+    assert st == 0 and lib.cdi_set_warm_unet(h2, u) == 1
+    st, h3 = _init(lib, 3, 16, 16, 16, 1.0, 1.0, 1.0)
+    assert st == 0 and lib.cdi_set_warm_unet(h3, u) == 1
+    assert lib.cdi_set_warm_unet(h3, None) == 0
+    assert lib.cdi_set_solver(h3, 1e-8, 10, 3) == 0   # CDI_WARM_UNET
+    assert lib.cdi_set_solver(h3, 1e-8, 10, 4) == 1
+    for h in (h2, h3):
+        lib.cdi_destroy(h)
+    lib.cdi_unet_destroy(u)
+    lib.cdi_unet_destroy(None)

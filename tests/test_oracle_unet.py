@@ -75,3 +75,37 @@ def test_first_adam_step_closed_form():
     unet.adam_step(P, G, st, lr=0.01)
     # first step: m_hat = g, v_hat = g^2, so the update is -lr g / (|g| + eps)
     assert np.allclose(P["w"], [1.0 - 0.01 * 0.5 / (0.5 + 1e-8), -2.0 + 0.01 * 4.0 / (4.0 + 1e-8), 3.0])
+
+
+def test_bf16_round_ties_and_bounds():
+    e = 2.0 ** -8          # half the bfloat16 spacing at 1
+    vals = np.array([1.0, 3.0, 1 + e, 1 + 3 * e, 1 + e + 2.0 ** -20, -(1 + e), 2.0 ** -130, 65504.0])
+    want = np.array([1.0, 3.0, 1.0, 1 + 4 * e, 1 + 2 * e, -1.0, 2.0 ** -130, 65536.0])
+    assert np.array_equal(unet.bf16_round(vals), want)
+    # relative rounding error at most half a unit in the 8th bit, and idempotent
+    x = np.random.default_rng(4).standard_normal(10000) * 10.0 ** np.random.default_rng(5).uniform(-5, 5, 10000)
+    r = unet.bf16_round(x)
+    assert np.all(np.abs(r - np.float32(x)) <= 2.0 ** -8 * np.abs(np.float32(x)))
+    assert np.array_equal(unet.bf16_round(r), r)
+
+
+def test_bf16_round_matches_torch():
+    torch = __import__("pytest").importorskip("torch")
+    x = np.random.default_rng(6).standard_normal(4096).astype(np.float32)
+    ours = unet.bf16_round(x)
+    lib = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(ours, lib)
+
+
+def test_storage_rounding_is_a_bounded_perturbation():
+    """With every stored array rounded to bfloat16 the output stays within a
+    few bfloat16 units of the FP64 network, and store=None is the FP64 path."""
+    rng = np.random.default_rng(8)
+    P = unet.init_params(9)
+    x = rng.standard_normal((8, 8, 16, 2))
+    y64, c64 = unet.forward(P, x)
+    y_id, _ = unet.forward(P, x, store=lambda a: a)
+    assert np.array_equal(y64, y_id)
+    y16, _ = unet.forward(P, x, store=unet.bf16_round)
+    e = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
+    assert 1e-4 < e < 2e-2
