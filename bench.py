@@ -56,29 +56,40 @@ def workload():
 # algorithmic bytes per launch of the kernels the roofline can name
 # (unique words each launch must read or write at least once)
 # ---------------------------------------------------------------------------
-def vcycle_words(D):
-    """FP64 words per finest-level cell moved by one V-cycle plus its residual
-    check: 2+2 red-black sweeps (p read+write, f, D face coefficients), the
-    residual-restriction pass, the prolongation, summed over the hierarchy
-    (factor 1/(1 - 2^-D)), and the residual norm of the convergence test."""
+def vcycle_bytes(D):
+    """Bytes per finest-level cell of one V-cycle plus its convergence test.
+    The cycle itself runs in FP32 (error e, residual r, D face coefficients):
+    2+2 red-black sweeps each read e, r and the coefficients and write e; the
+    residual-restriction pass reads e, r, the coefficients and writes the
+    coarse r and e; the prolongation reads the coarse e and updates e; all
+    levels together weigh 1/(1 - 2^-D) of the finest one.  The FP64 defect
+    correction adds p += e (read p and e, write p) and the residual of the
+    test (read p, f and the D FP64 coefficients, write the FP32 r)."""
     fine = 4 * (3 + D) + (2 + D) + 3.0 / 2 ** D + 2
-    return fine / (1 - 2.0 ** -D) + (2 + D)
+    return 4 * fine / (1 - 2.0 ** -D) + (8 + 4 + 8) + (8 * (2 + D) + 4)
+
+
+def solve_fixed_bytes(D, word):
+    """Bytes per cell of one pressure solve outside its V-cycles: divergence
+    (read D face velocities, write the FP64 f), coefficients (read phi, write
+    D FP32 and D FP64 face values) and projection (read p, phi and the D
+    velocities, write the D velocities)."""
+    return (D * word + 8) + (word + 12 * D) + (8 + word * (1 + 2 * D))
 
 
 def step_bytes(D, N, word, vcycles_per_step):
     """Algorithmic bytes of one full step: per RK stage the fused stencil
     minimum (read the stage state and y^n, read+write the accumulator, write
-    the next stage: 5(1+D) words), per pressure solve the divergence (D+1),
-    the projection (2D+1) and the V-cycles, in FP64."""
+    the next stage: 5(1+D) words of the state precision), four pressure solves
+    and the V-cycles of the step."""
     stencil = 4 * 5 * (1 + D) * word
-    solves = 8 * (4 * (3 + 2 * D + 1) + vcycles_per_step * vcycle_words(D))
-    return N * (stencil + solves)
+    return N * (stencil + 4 * solve_fixed_bytes(D, word) + vcycles_per_step * vcycle_bytes(D))
 
 
 def algorithmic_bytes(kernel, dim, N, NP, word):
     D = dim
     words = {
-        "rbgs0": 0.5 * N + 0.5 * N + 0.5 * N + D * N + NP,  # p read/write of one colour, f, face coefficients
+        "rbgs0": 0.5 * N + 0.5 * N + 0.5 * N + D * N + NP,  # e read/write of one colour, r, face coefficients
         "mom": (3 * D + 2) * N + NP,                           # u, m, phi, mu_c in; rhs of every component out
         "phi_rhs": (3 * D + 2) * N + NP,                       # phi, u, n in; rhs_phi, m out
         "cell": (3 + D) * N,                                   # phi, psi in; n, mu_c out
@@ -86,7 +97,7 @@ def algorithmic_bytes(kernel, dim, N, NP, word):
         "stage_mom": (2 + 5 * D) * N,
     }[kernel]
     if kernel == "rbgs0":
-        return words * 8  # the multigrid works in FP64 in every precision
+        return words * 4  # the V-cycles work in FP32 in every precision
     return words * word
 
 
@@ -368,10 +379,86 @@ def _timed_steps(step_fn, nsteps, flush):
     return total
 
 
+UNET_FLOPS_PER_VOXEL = sum(2 * t * ci * co / 8 ** lvl for (_, ci, co, t), lvl in
+                           zip((("e0", 2, 16, 27), ("e1", 16, 32, 27), ("e2", 32, 64, 27), ("b", 64, 128, 27),
+                                ("d2", 192, 64, 27), ("d1", 96, 32, 27), ("d0", 48, 16, 27), ("head", 16, 1, 1)),
+                               (0, 1, 2, 3, 2, 1, 0, 0)))
+
+
+def unet_form(flush, n_train=64, pairs=40, iters=800, n_infer=256):
+    """Learned first guess: pairs from the first steps of an n_train^3 drop,
+    Adam on the GPU, then V-cycles per solve and time per step from zero, from
+    the previous pressure and from the network; and the device time of one
+    forward pass at n_infer^3 against the dense BF16 peak."""
+    import numpy as np
+    import torch
+
+    from paper_2412_16843_gb300 import cdi, inputs
+    wl = inputs.drop_3d(n_train)
+    dt = inputs.stable_dt(wl)
+    s = cdi.from_workload(wl, precision=cdi.FP64, tol=PRESSURE_TOL)
+    X, T = [], []
+    for _ in range(pairs):
+        s.step(dt, 1)
+        f, p = s.last_pressure()
+        x, t = inputs.unet_pair(f, p, s.get_fields()[0], wl.rho1, wl.rho2, wl.h)
+        X.append(x)
+        T.append(t)
+    phi, vel, _ = s.get_fields()
+    del s
+    net = cdi.Unet((n_train,) * 3)
+    net.set_params(inputs.unet_initial_params(0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = [net.train_step(X[i % pairs], T[i % pairs], lr=1e-3 if i < 0.6 * iters else 3e-4)
+              for i in range(iters)]
+    train_s = time.perf_counter() - t0
+    res = {"grid": n_train, "pairs": pairs, "adam_steps": iters, "train_ms_per_step": 1e3 * train_s / iters,
+           "loss_first": float(np.mean(losses[:pairs])), "loss_last": float(np.mean(losses[-pairs:])),
+           "pressure_tol": PRESSURE_TOL, "exec": "kernels"}
+    for name, warm in (("zero", cdi.WARM_ZERO), ("previous", cdi.WARM_PREV), ("network", cdi.WARM_UNET)):
+        r = cdi.from_workload(wl, precision=cdi.FP64, tol=PRESSURE_TOL)
+        r.set_exec(cdi.EXEC_KERNELS)
+        r.set_solver(PRESSURE_TOL, 100, warm)
+        if warm == cdi.WARM_UNET:
+            r.set_warm_unet(net)
+        r.set_state(phi, vel)
+        cyc = 0
+        ms = 0.0
+        for _ in range(8):
+            ms += _timed_steps(lambda: r.step(dt, 1), 1, flush)
+            cyc += r.last_stats()["total_cycles_call"]
+        res["vcycles_per_solve_" + name] = cyc / 32.0
+        res["ms_per_step_" + name] = ms / 8
+        del r
+    params = net.get_params()
+    del net
+    torch.cuda.empty_cache()
+    big = cdi.Unet((n_infer,) * 3)
+    big.set_params(params)
+    N = n_infer ** 3
+    x = torch.randn(N * 2, dtype=torch.float32, device="cuda")
+    y = torch.empty(N, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(big.stream):
+        for _ in range(2):
+            big.forward_device(x, y)
+    ms = _timed_steps(lambda: big.forward_device(x, y), 5, flush) / 5
+    flops = UNET_FLOPS_PER_VOXEL * N
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peak = json.load(f).get("bf16_tflops")
+    res["inference"] = {"grid": n_infer, "ms": ms, "flops": flops, "tflops": flops / ms / 1e9,
+                        "bf16_peak_tflops": peak, "frac": flops / ms / 1e9 / peak if peak else None,
+                        "peak_source": "measured (burst)"}
+    del big
+    torch.cuda.empty_cache()
+    return res
+
+
 def forms_report(steps):
     """The added forms on their own workloads (one GPU): FP32-mixed Couette,
     the batched sweep of 512 uneven 2D instances against looping the
-    single-grid step over the same instances, and the 3D 256^3 drop."""
+    single-grid step over the same instances, the 3D 256^3 drop, and the
+    learned first guess."""
     import numpy as np
     import torch
 
@@ -385,7 +472,8 @@ def forms_report(steps):
     s.step(wl.dt, 3)
     ms = _timed_steps(lambda: s.step(wl.dt, 1), steps, flush)
     out["fp32_mixed_couette2d_512x128"] = {"value": wl.cells * steps / (ms / 1e3) / 1e6, "unit": UNIT,
-                                           "ms_per_step": ms / steps, "pressure_tol": PRESSURE_TOL}
+                                           "ms_per_step": ms / steps, "pressure_tol": PRESSURE_TOL,
+                                           "l2_resident": True}
     del s
     # batched sweep vs looping the single-grid step
     wls = inputs.sweep_2d()
@@ -418,11 +506,18 @@ def forms_report(steps):
     s.step(wl.dt, 2)
     k3 = max(2, min(steps, 5))
     ms3 = _timed_steps(lambda: s.step(wl.dt, 1), k3, flush)
+    cyc3 = s.last_stats()["total_cycles_call"]
+    hbm, peak_kind = peaks()
+    ach = step_bytes(3, wl.cells, 4, cyc3) / (ms3 / k3 / 1e3) / 1e9
     out["fp32_mixed_drop3d_256"] = {"value": wl.cells * k3 / (ms3 / 1e3) / 1e6, "unit": UNIT,
-                                    "ms_per_step": ms3 / k3, "vcycles_last_step": s.last_stats()["total_cycles_call"],
-                                    "pressure_tol": PRESSURE_TOL}
+                                    "ms_per_step": ms3 / k3, "vcycles_last_step": cyc3,
+                                    "pressure_tol": PRESSURE_TOL,
+                                    "roofline": {"bound": "hbm", "kernel": "step", "achieved": ach, "peak": hbm,
+                                                 "unit": "GB/s", "frac": ach / hbm, "peak_source": peak_kind,
+                                                 "algorithmic_bytes_per_step": step_bytes(3, wl.cells, 4, cyc3)}}
     del s
     torch.cuda.empty_cache()
+    out["unet_warm_start_drop3d_64"] = unet_form(flush)
     return out
 
 

@@ -310,6 +310,10 @@ cdi_status cdi_unet_get_params(cdi_unet* net, double* params, size_t n);
 /* Forward pass on host arrays: x [N][2] -> y [N]. */
 cdi_status cdi_unet_forward(cdi_unet* net, const double* x, double* y);
 
+/* Forward pass on device arrays, FP32 x [N][2] -> FP32 y [N], issued on the
+ * network's stream without host copies or synchronisation. */
+cdi_status cdi_unet_forward_device(cdi_unet* net, const float* x, float* y);
+
 /* One training step on host arrays x [N][2], target [N]: forward, the mean
  * squared error (written to loss before the update, may be NULL), the
  * gradients of every parameter (written to grads in the flat order when not

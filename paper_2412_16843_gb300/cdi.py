@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "cdi_unet_set_params": [P, DP, S],
         "cdi_unet_get_params": [P, DP, S],
         "cdi_unet_forward": [P, DP, DP],
+        "cdi_unet_forward_device": [P, P, P],
         "cdi_unet_train_step": [P, DP, DP, D, DP, DP],
         "cdi_set_warm_unet": [P, P],
         "cdi_last_pressure": [P, DP, DP],
@@ -432,6 +433,17 @@ class Unet:
         y = np.empty(self.shape)
         self._check(self.lib.cdi_unet_forward(self.h, _dp(xa), _dp(y)))
         return y
+
+    def forward_device(self, x, y):
+        """Device forward pass: torch float32 tensors x (..., 2) and y (...) on
+        the network's device; stream-ordered, no synchronisation."""
+        import torch
+
+        assert x.is_cuda and x.dtype == torch.float32 and y.dtype == torch.float32
+        assert x.numel() == 2 * y.numel() == 2 * int(np.prod(self.n))
+        assert x.is_contiguous() and y.is_contiguous()
+        self._check(self.lib.cdi_unet_forward_device(self.h, ctypes.c_void_p(x.data_ptr()),
+                                                     ctypes.c_void_p(y.data_ptr())))
 
     def train_step(self, x, target, lr=0.0, want_grads=False):
         """Loss before the update and (optionally) the flat gradients."""

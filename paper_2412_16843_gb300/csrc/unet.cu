@@ -314,6 +314,13 @@ __global__ void k_input_host(int N, const double* x2, bf16* x) {  // x2: [N][2] 
     x[t] = __float2bfloat16(c < 2 ? (float)x2[(size_t)v * 2 + c] : 0.f);
 }
 
+__global__ void k_input_dev(int N, const float* x2, bf16* x) {  // x2: [N][2] on the device
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)N * 16) return;
+    const int c = (int)(t % 16), v = (int)(t / 16);
+    x[t] = __float2bfloat16(c < 2 ? x2[(size_t)v * 2 + c] : 0.f);
+}
+
 template <typename T>
 __global__ void k_input_solver(int N, const double* f, const T* phi, double rho1, double rho2, const double* fnorm,
                                bf16* x) {
@@ -762,6 +769,22 @@ cdi_status cdi_unet_forward(cdi_unet* u, const double* x_host, double* y_host) {
         cudaStreamSynchronize(u->stream) != cudaSuccess)
         return ufail(u, CDI_ECUDA, std::string("forward: ") + cudaGetErrorString(cudaGetLastError()));
     for (long i = 0; i < N; ++i) y_host[i] = y[i];
+    return CDI_OK;
+}
+
+// forward pass on device arrays (FP32 [N][2] -> FP32 [N]), stream-ordered, no host copies
+cdi_status cdi_unet_forward_device(cdi_unet* u, const float* x_dev, float* y_dev) {
+    if (!u || !u->ws) return ufail(u, CDI_ESTATE, "network workspace not bound");
+    if (!x_dev || !y_dev) return ufail(u, CDI_EINVAL, "null array");
+    if (!u->weights_ready) refresh_weights(u);
+    const long N = u->g[0].N;
+    k_input_dev<<<blocks(N * 16), 256, 0, u->stream>>>((int)N, x_dev, u->x);
+    forward(u);
+    g_launches += 1;
+    if (cudaMemcpyAsync(y_dev, u->y, (size_t)N * 4, cudaMemcpyDeviceToDevice, u->stream) != cudaSuccess)
+        return ufail(u, CDI_ECUDA, "output copy failed");
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return ufail(u, CDI_ECUDA, std::string("forward_device: ") + cudaGetErrorString(e));
     return CDI_OK;
 }
 

@@ -245,3 +245,29 @@ def workload(name: str) -> Workload:
         "drop3d_256": lambda: drop_3d(256),
     }
     return table[name]()
+
+
+# warm-start network: layer table (name, Cin, Cout, taps) and seeded initial
+# parameters in the flat order of cdi_unet_set_params
+UNET_LAYERS = (("e0", 2, 16, 27), ("e1", 16, 32, 27), ("e2", 32, 64, 27), ("b", 64, 128, 27),
+               ("d2", 192, 64, 27), ("d1", 96, 32, 27), ("d0", 48, 16, 27), ("head", 16, 1, 1))
+
+
+def unet_initial_params(seed: int = 0) -> np.ndarray:
+    """He-normal weights (std sqrt(2 / (taps Cin))), zero biases; flat vector,
+    per layer the weights [taps][Cout][Cin] then the biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _, ci, co, t in UNET_LAYERS:
+        parts.append((rng.standard_normal((t, co, ci)) * math.sqrt(2.0 / (t * ci))).ravel())
+        parts.append(np.zeros(co))
+    return np.concatenate(parts)
+
+
+def unet_pair(f: np.ndarray, p: np.ndarray, phi: np.ndarray, rho1: float, rho2: float, h: float):
+    """Network input (f / rms(f), rho / max(rho)) and target p / (rms(f) max(rho) h^2)
+    for one pressure solve, channels last."""
+    rms = float(np.sqrt(np.mean(f * f)))
+    rmax = max(rho1, rho2)
+    rho = (rho1 - rho2) * phi + rho2
+    return np.stack([f / rms, rho / rmax], axis=-1), p / (rms * rmax * h * h)

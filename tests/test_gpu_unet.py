@@ -134,15 +134,12 @@ def test_first_adam_step():
 def _pairs(s, wl, nsteps, dt):
     """Normalised (input, target) pairs from the last pressure solve of each step."""
     X, T = [], []
-    rmax = max(wl.rho1, wl.rho2)
     for _ in range(nsteps):
         s.step(dt, 1)
         f, p = s.last_pressure()
-        phi = s.get_fields()[0]
-        rms = np.sqrt(np.mean(f * f))
-        rho = (wl.rho1 - wl.rho2) * phi + wl.rho2
-        X.append(np.stack([f / rms, rho / rmax], axis=-1))
-        T.append(p / (rms * rmax * wl.h ** 2))
+        x, t = inputs.unet_pair(f, p, s.get_fields()[0], wl.rho1, wl.rho2, wl.h)
+        X.append(x)
+        T.append(t)
     return X, T
 
 
@@ -161,7 +158,7 @@ def test_training_and_warm_start_on_3d_drop():
     phi, vel, _ = s.get_fields()
 
     net = cdi.Unet((n, n, n))
-    net.set_params(flat(ref.init_params(0)))
+    net.set_params(inputs.unet_initial_params(0))
     losses = []
     for it in range(1600):
         i = it % len(X)

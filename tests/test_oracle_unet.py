@@ -109,3 +109,17 @@ def test_storage_rounding_is_a_bounded_perturbation():
     y16, _ = unet.forward(P, x, store=unet.bf16_round)
     e = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
     assert 1e-4 < e < 2e-2
+
+
+def test_seeded_initial_parameters_match_the_layer_table():
+    """The input module's initial parameters (the GPU network's seeded input)
+    are the reference network's He-normal initialisation in the flat order."""
+    from paper_2412_16843_gb300 import inputs
+    assert tuple(inputs.UNET_LAYERS) == tuple(unet.LAYERS)
+    P = unet.init_params(5)
+    flat = np.concatenate([np.concatenate([P[n + ".w"].ravel(), P[n + ".b"]]) for n, _, _, _ in unet.LAYERS])
+    assert np.array_equal(inputs.unet_initial_params(5), flat)
+    x, t = inputs.unet_pair(np.array([3.0, -4.0]), np.array([1.0, 2.0]), np.array([1.0, 0.0]), 2.0, 1.0, 0.5)
+    # rms(f) = sqrt(12.5); rho = (2, 1) / 2; p / (rms * 2 * 0.25)
+    assert np.allclose(x, [[3 / 12.5 ** 0.5, 1.0], [-4 / 12.5 ** 0.5, 0.5]])
+    assert np.allclose(t, np.array([1.0, 2.0]) / (12.5 ** 0.5 * 0.5))
