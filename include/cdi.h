@@ -69,9 +69,10 @@ enum { CDI_WALL_LO = 0, CDI_WALL_HI = 1, CDI_WALL_BOTH = 2 };
  * steps extrapolated linearly in time, or the prediction of the network
  * attached with cdi_set_warm_unet (launch-per-kernel execution) */
 enum { CDI_WARM_PREV = 0, CDI_WARM_ZERO = 1, CDI_WARM_EXTRAP = 2, CDI_WARM_UNET = 3 };
-/* how cdi_step runs: one persistent cooperative launch per call (default), or
- * one launch per stencil / multigrid kernel with host-side convergence tests */
-enum { CDI_EXEC_PERSISTENT = 0, CDI_EXEC_KERNELS = 1 };
+/* how cdi_step runs: one persistent cooperative launch per call, one launch
+ * per stencil / multigrid kernel with host-side convergence tests, or
+ * (default) the first for grids up to 2^20 cells and the second above */
+enum { CDI_EXEC_PERSISTENT = 0, CDI_EXEC_KERNELS = 1, CDI_EXEC_AUTO = 2 };
 /* slip models of Sec. 3, Eqs. (Model 1A) .. (Model 4B); 4A is the default */
 enum { CDI_MODEL_1A = 0, CDI_MODEL_1B, CDI_MODEL_2A, CDI_MODEL_2B,
        CDI_MODEL_3A, CDI_MODEL_3B, CDI_MODEL_4A, CDI_MODEL_4B };
@@ -192,11 +193,14 @@ cdi_status cdi_last_stats(cdi_ctx* ctx, int* vcycles, double* resid,
  * persistent mode issues one launch per cdi_step call). */
 cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
 
-/* Execution mode of cdi_step: CDI_EXEC_PERSISTENT (default) runs all steps of
- * the call in one cooperative launch with bounded grid barriers (a barrier
- * that waits longer than 2 s ends the call with CDI_ETIMEOUT);
- * CDI_EXEC_KERNELS launches every stencil and multigrid kernel separately.
- * Both compute the same arithmetic. */
+/* Execution mode of cdi_step: CDI_EXEC_PERSISTENT runs all steps of the call
+ * in one cooperative launch with bounded grid barriers (a barrier that waits
+ * longer than 2 s ends the call with CDI_ETIMEOUT); CDI_EXEC_KERNELS launches
+ * every stencil and multigrid kernel separately; CDI_EXEC_AUTO (default)
+ * takes the persistent launch for grids up to 2^20 cells, where launch
+ * latency dominates, and separate kernels above, where the separate kernels
+ * keep more warps resident for the bandwidth-bound sweeps.  All compute the
+ * same arithmetic. */
 cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
 
 /* Longest wait (nanoseconds, 0 .. 6e10; default 2e9) of a grid barrier in the

@@ -23,7 +23,7 @@ STATUS = {0: "CDI_OK", 1: "CDI_EINVAL", 2: "CDI_ESTATE", 3: "CDI_ECUDA",
 FP64, FP32_MIXED = 0, 1
 WALL_LO, WALL_HI, WALL_BOTH = 0, 1, 2
 WARM_PREV, WARM_ZERO, WARM_EXTRAP, WARM_UNET = 0, 1, 2, 3
-EXEC_PERSISTENT, EXEC_KERNELS = 0, 1
+EXEC_PERSISTENT, EXEC_KERNELS, EXEC_AUTO = 0, 1, 2
 MODELS = {"1A": 0, "1B": 1, "2A": 2, "2B": 3, "3A": 4, "3B": 5, "4A": 6, "4B": 7}
 
 _lib = None

@@ -66,7 +66,7 @@ struct cdi_ctx {
     MG mg{};
     double* host_scal = nullptr;
     // execution of cdi_step: one persistent cooperative launch, or one launch per kernel
-    int exec = CDI_EXEC_PERSISTENT;
+    int exec = CDI_EXEC_AUTO;
     PersistCtl* ctl = nullptr;
     bool persist_ready = false;
     PersistLayout playout{};
@@ -145,11 +145,13 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     for (int l = 0; l < mg.nlev; ++l) {
         MGLevel& L = mg.lv[l];
         const long nl = L.g.N, np = L.g.NP;
-        if (l == 0) {  // FP64 pressure, right-hand side and coefficients of the defect correction
+        if (l == 0) {  // pressure, right-hand side (8 bytes a cell in both forms) and FP64 coefficients
             L.p = (double*)cv.take(nl * sizeof(double));
             L.f = (double*)cv.take(nl * sizeof(double));
+            const bool f64 = c->precision == CDI_FP64;
             for (int a = 0; a < 3; ++a)
-                L.beta[a] = (a < g.D) ? (double*)cv.take((nl + (a == g.W ? np : 0)) * sizeof(double)) : nullptr;
+                L.beta[a] = (f64 && a < g.D) ? (double*)cv.take((nl + (a == g.W ? np : 0)) * sizeof(double))
+                                             : nullptr;
         } else {
             L.p = nullptr;
             L.f = nullptr;
@@ -162,6 +164,7 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     }
     mg.partials = (double*)cv.take(2 * kPartials * sizeof(double));
     mg.scal = (double*)cv.take(S_NSCAL * sizeof(double));
+    mg.scalf = (float*)cv.take(SF_NSCAL * sizeof(float));
     c->ctl = (PersistCtl*)cv.take(sizeof(PersistCtl));
     for (int k = 0; k < 4; ++k)
         for (int j = 0; j < 2; ++j) c->hist[k][j] = (double*)cv.take((size_t)g.N * sizeof(double));
@@ -178,7 +181,10 @@ __global__ void k_from_double(long n, const double* __restrict__ src, T* __restr
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (T)src[i];
 }
-__global__ void k_set_scalar(double* p, double v) { *p = v; }
+__global__ void k_set_gamma(double* p, float* pf, double v) {
+    *p = v;
+    *pf = (float)v;
+}
 template <typename T>
 __global__ void k_zero_wall_planes(long N, long NP, T* __restrict__ w) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -220,6 +226,36 @@ cdi_status download(cdi_ctx* c, double* dst, const void* src, long n) {
     return cuda_check(c, cudaStreamSynchronize(c->stream), "download");
 }
 
+// level-0 pressure, or right-hand side with its mean removed, to host FP64
+// (the FP32-mixed form converts through the staging buffer)
+cdi_status download_level0(cdi_ctx* c, double* dst, bool pressure) {
+    const Geom& g = c->g;
+    const double* src = pressure ? c->mg.lv[0].p : c->mg.lv[0].f;
+    if (c->precision != CDI_FP64) {
+        if (pressure) launch_p_to_double(g, c->mg, c->xfer, c->stream);
+        else launch_f_to_double(g, c->mg, c->xfer, c->stream);
+        src = c->xfer;
+    }
+    cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, src, g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                               "cudaMemcpyAsync(D2H)");
+    if (st) return st;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "download");
+}
+
+// host FP64 pressure or right-hand side into level 0
+cdi_status upload_level0(cdi_ctx* c, const double* src, bool pressure) {
+    const Geom& g = c->g;
+    double* dst = c->precision == CDI_FP64 ? (pressure ? c->mg.lv[0].p : c->mg.lv[0].f) : c->xfer;
+    cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, src, g.N * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                               "cudaMemcpyAsync(H2D)");
+    if (st) return st;
+    if (c->precision != CDI_FP64) {
+        if (pressure) launch_p_from_double(g, c->mg, c->xfer, c->stream);
+        else launch_f_from_double(g, c->mg, c->xfer, c->stream);
+    }
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "upload");
+}
+
 cdi_status read_scalars(cdi_ctx* c) {
     cdi_status st = cuda_check(c, cudaMemcpyAsync(c->host_scal, c->mg.scal, S_NSCAL * sizeof(double),
                                                   cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync(scalars)");
@@ -235,11 +271,12 @@ cdi_status need_bound(cdi_ctx* c) {
 
 // Multigrid solve of div(beta grad p) = f on level 0 (f already mean-free,
 // its norm in S_FNORM, coefficients set); p holds the first guess.
+template <typename T>
 cdi_status mg_solve(cdi_ctx* c) {
     const Geom& g = c->g;
     cudaStream_t s = c->stream;
     MG& mg = c->mg;
-    launch_resid_norm(g, mg, s);
+    launch_resid_norm<T>(g, mg, s);
     cdi_status st = read_scalars(c);
     if (st) return st;
     const double fn = c->host_scal[S_FNORM];
@@ -253,8 +290,8 @@ cdi_status mg_solve(cdi_ctx* c) {
         return CDI_OK;
     }
     while (rn > c->tol * fn && cyc < c->max_vcycles) {
-        launch_vcycle(g, mg, c->npre, c->npost, s);
-        launch_resid_norm(g, mg, s);
+        launch_vcycle<T>(g, mg, c->npre, c->npost, s);
+        launch_resid_norm<T>(g, mg, s);
         st = read_scalars(c);
         if (st) return st;
         rn = c->host_scal[S_RNORM];
@@ -271,7 +308,7 @@ cdi_status mg_solve(cdi_ctx* c) {
                  c->tol);
         return fail(c, CDI_ENOCONV, b);
     }
-    launch_p_mean_remove(g, mg, s);
+    launch_p_mean_remove<T>(g, mg, s);
     return CDI_OK;
 }
 
@@ -281,15 +318,14 @@ cdi_status project(cdi_ctx* c, const T* phi, T* const* u, double cdt) {
     cudaStream_t s = c->stream;
     const T* uc[3] = {u[0], u[1], u[2]};
     launch_div<T>(g, uc, 1.0 / cdt, c->mg, s);
-    launch_sub_mean_and_norm(g, c->mg, s);
+    launch_sub_mean_and_norm<T>(g, c->mg, s);
     launch_mg_coef<T>(g, c->ph, phi, c->mg, s);
     if (c->warm == CDI_WARM_ZERO) cudaMemsetAsync(c->mg.lv[0].p, 0, g.N * sizeof(double), s);
     if (c->warm == CDI_WARM_UNET) {
-        const cudaError_t e = unet_predict_device<T>(c->unet, c->mg.lv[0].f, phi, c->ph.rho1, c->ph.rho2,
-                                                     c->mg.scal + S_FNORM, c->g.h, c->mg.lv[0].p, s);
+        const cudaError_t e = unet_predict_device<T>(c->unet, c->mg, phi, c->ph.rho1, c->ph.rho2, c->g.h, s);
         if (e != cudaSuccess) return cuda_check(c, e, "network first guess");
     }
-    cdi_status st = mg_solve(c);
+    cdi_status st = mg_solve<T>(c);
     if (st) return st;
     launch_project<T>(g, c->ph, phi, u, cdt, c->mg.lv[0].p, s);
     return CDI_OK;
@@ -312,13 +348,14 @@ StageFields<T> stage_fields(cdi_ctx* c, const void* phi, void* const* u) {
     f.wghost = (T*)c->wghost;
     f.wmuw = (T*)c->wmuw;
     f.gamma = c->mg.scal + S_GAMMA;
+    f.gammaf = c->mg.scalf + SF_GAMMA;
     return f;
 }
 
 template <typename T>
 void set_gamma(cdi_ctx* c, const void* const* u, double gamma_arg) {
     if (gamma_arg >= 0.0) {
-        k_set_scalar<<<1, 1, 0, c->stream>>>(c->mg.scal + S_GAMMA, gamma_arg);
+        k_set_gamma<<<1, 1, 0, c->stream>>>(c->mg.scal + S_GAMMA, c->mg.scalf + SF_GAMMA, gamma_arg);
         ++g_launches;
     } else {
         const T* uc[3] = {(const T*)u[0], (const T*)u[1], (const T*)u[2]};
@@ -527,6 +564,7 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
         c->ph.wall[s].beta1 = c->ph.wall[s].beta2 = INFINITY;
         c->ph.wall[s].noslip = 1;
     }
+    finalize_phys(c->ph);
     // multigrid hierarchy: halve every axis while all extents stay even and >= 2
     MG& mg = c->mg;
     mg.nlev = 1;
@@ -606,6 +644,7 @@ cdi_status cdi_set_fluids(cdi_ctx* c, double rho1, double rho2, double mu1, doub
             c->ph.wall[s].beta1 = mu1 / c->wall_slip_length[s];
             c->ph.wall[s].beta2 = mu2 / c->wall_slip_length[s];
         }
+    finalize_phys(c->ph);
     return CDI_OK;
 }
 
@@ -629,10 +668,13 @@ cdi_status cdi_set_wall(cdi_ctx* c, int wall, double theta_eq, double slip_lengt
             w.noslip = 0;
             w.beta1 = c->ph.mu1 / slip_length;
             w.beta2 = c->ph.mu2 / slip_length;
-            if (!(w.beta1 > 0) || !(w.beta2 > 0))
+            if (!(w.beta1 > 0) || !(w.beta2 > 0)) {
+                finalize_phys(c->ph);
                 return fail(c, CDI_EINVAL, "slip length form needs mu1, mu2 > 0 (use cdi_set_wall_beta)");
+            }
         }
     }
+    finalize_phys(c->ph);
     return CDI_OK;
 }
 
@@ -651,6 +693,7 @@ cdi_status cdi_set_wall_beta(cdi_ctx* c, int wall, double beta1, double beta2) {
         w.noslip = inf1 ? 1 : 0;
         c->wall_slip_length[s] = -1.0;
     }
+    finalize_phys(c->ph);
     return CDI_OK;
 }
 
@@ -663,6 +706,7 @@ cdi_status cdi_set_wall_velocity(cdi_ctx* c, int wall, double Ux, double Uy) {
         c->ph.wall[s].U[0] = Ux;
         c->ph.wall[s].U[1] = Uy;
     }
+    finalize_phys(c->ph);
     return CDI_OK;
 }
 
@@ -670,6 +714,7 @@ cdi_status cdi_set_model(cdi_ctx* c, int model) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
     if (model < CDI_MODEL_1A || model > CDI_MODEL_4B) return fail(c, CDI_EINVAL, "unknown slip model");
     c->ph.model = model;
+    finalize_phys(c->ph);
     return CDI_OK;
 }
 
@@ -729,7 +774,9 @@ cdi_status cdi_step(cdi_ctx* c, double dt, int nsteps) {
     if (nsteps == 0) return CDI_OK;
     if (c->warm == CDI_WARM_UNET && !c->unet) return fail(c, CDI_ESTATE, "CDI_WARM_UNET without an attached network");
     const long l0 = g_launches;
-    if (c->exec == CDI_EXEC_PERSISTENT && c->warm != CDI_WARM_UNET) {
+    const bool persistent =
+        c->exec == CDI_EXEC_PERSISTENT || (c->exec == CDI_EXEC_AUTO && c->g.N <= (1L << 20));
+    if (persistent && c->warm != CDI_WARM_UNET) {
         st = (c->precision == CDI_FP64) ? step_persist<double>(c, dt, nsteps) : step_persist<float>(c, dt, nsteps);
         if (st) return st;
     } else {
@@ -758,18 +805,12 @@ cdi_status cdi_set_warm_unet(cdi_ctx* c, cdi_unet* net) {
 cdi_status cdi_last_pressure(cdi_ctx* c, double* f, double* p) {
     cdi_status st = need_bound(c);
     if (st) return st;
-    const long N = c->g.N;
     if (f) {
-        st = cuda_check(c, cudaMemcpyAsync(f, c->mg.lv[0].f, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                        "copy f");
+        st = download_level0(c, f, false);
         if (st) return st;
     }
-    if (p) {
-        st = cuda_check(c, cudaMemcpyAsync(p, c->mg.lv[0].p, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                        "copy p");
-        if (st) return st;
-    }
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "last_pressure");
+    if (p) st = download_level0(c, p, true);
+    return st;
 }
 
 cdi_status cdi_set_barrier_timeout(cdi_ctx* c, long long ns) {
@@ -781,7 +822,8 @@ cdi_status cdi_set_barrier_timeout(cdi_ctx* c, long long ns) {
 
 cdi_status cdi_set_exec(cdi_ctx* c, int mode) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
-    if (mode != CDI_EXEC_PERSISTENT && mode != CDI_EXEC_KERNELS) return fail(c, CDI_EINVAL, "unknown exec mode");
+    if (mode != CDI_EXEC_PERSISTENT && mode != CDI_EXEC_KERNELS && mode != CDI_EXEC_AUTO)
+        return fail(c, CDI_EINVAL, "unknown exec mode");
     c->exec = mode;
     return CDI_OK;
 }
@@ -825,12 +867,7 @@ cdi_status cdi_get_fields(cdi_ctx* c, double* phi, double* u, double* v, double*
         st = download(c, comps[a], c->u_s[a], nface(c->g, a));
         if (st) return st;
     }
-    if (p) {
-        st = cuda_check(c, cudaMemcpyAsync(p, c->mg.lv[0].p, c->g.N * sizeof(double), cudaMemcpyDeviceToHost,
-                                           c->stream), "cudaMemcpyAsync(p)");
-        if (st) return st;
-        st = cuda_check(c, cudaStreamSynchronize(c->stream), "get_fields");
-    }
+    if (p) st = download_level0(c, p, true);
     return st;
 }
 
@@ -879,19 +916,23 @@ cdi_status cdi_solve_pressure(cdi_ctx* c, const double* f, double* p) {
     const Geom& g = c->g;
     MG& mg = c->mg;
     cudaStream_t s = c->stream;
-    st = cuda_check(c, cudaMemcpyAsync(mg.lv[0].f, f, g.N * sizeof(double), cudaMemcpyHostToDevice, s), "copy f");
+    st = upload_level0(c, f, false);
     if (st) return st;
-    st = cuda_check(c, cudaMemcpyAsync(mg.lv[0].p, p, g.N * sizeof(double), cudaMemcpyHostToDevice, s), "copy p");
+    st = upload_level0(c, p, true);
     if (st) return st;
-    launch_sum_f(g, mg, s);
-    launch_sub_mean_and_norm(g, mg, s);
-    if (c->precision == CDI_FP64) launch_mg_coef<double>(g, c->ph, (const double*)c->phi_s, mg, s);
-    else launch_mg_coef<float>(g, c->ph, (const float*)c->phi_s, mg, s);
-    st = mg_solve(c);
+    if (c->precision == CDI_FP64) {
+        launch_sum_f<double>(g, mg, s);
+        launch_sub_mean_and_norm<double>(g, mg, s);
+        launch_mg_coef<double>(g, c->ph, (const double*)c->phi_s, mg, s);
+        st = mg_solve<double>(c);
+    } else {
+        launch_sum_f<float>(g, mg, s);
+        launch_sub_mean_and_norm<float>(g, mg, s);
+        launch_mg_coef<float>(g, c->ph, (const float*)c->phi_s, mg, s);
+        st = mg_solve<float>(c);
+    }
     if (st) return st;
-    st = cuda_check(c, cudaMemcpyAsync(p, mg.lv[0].p, g.N * sizeof(double), cudaMemcpyDeviceToHost, s), "copy p");
-    if (st) return st;
-    return cuda_check(c, cudaStreamSynchronize(s), "solve_pressure");
+    return download_level0(c, p, true);
 }
 
 cdi_status cdi_profile_start(cdi_ctx* c, const char* kernel, int max_launches) {

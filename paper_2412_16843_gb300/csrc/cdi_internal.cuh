@@ -49,8 +49,20 @@ struct Geom {
     long N;       // cells
     long NP;      // cells of one wall plane (= stride of the wall axis)
     double h;
+    double ih, ih2;         // 1/h, 1/h^2
+    float hf, ihf, ih2f;    // FP32 copies (1/h and 1/h^2 rounded from the FP32 h and h^2)
     FastDiv fd0, fd1;  // division by n[0] and by n[1]
 };
+
+// 1/h and 1/h^2 in the arithmetic type of a kernel.  On GB300 an FP64
+// instruction (including a conversion from FP64) issues at a small fraction of
+// the FP32 rate, so FP32 kernels take the FP32 copies made on the host.
+template <typename T> __host__ __device__ __forceinline__ T g_ih(const Geom& g);
+template <> __host__ __device__ __forceinline__ double g_ih<double>(const Geom& g) { return g.ih; }
+template <> __host__ __device__ __forceinline__ float g_ih<float>(const Geom& g) { return g.ihf; }
+template <typename T> __host__ __device__ __forceinline__ T g_ih2(const Geom& g);
+template <> __host__ __device__ __forceinline__ double g_ih2<double>(const Geom& g) { return g.ih2; }
+template <> __host__ __device__ __forceinline__ float g_ih2<float>(const Geom& g) { return g.ih2f; }
 
 inline Geom make_geom(int D, const int n[3], double h) {
     Geom g{};
@@ -60,6 +72,11 @@ inline Geom make_geom(int D, const int n[3], double h) {
     g.N = (long)n[0] * n[1] * n[2];
     g.NP = (D == 2) ? (long)n[0] : (long)n[0] * n[1];
     g.h = h;
+    g.ih = 1.0 / h;
+    g.ih2 = 1.0 / (h * h);
+    g.hf = (float)h;
+    g.ihf = 1.f / (float)h;
+    g.ih2f = 1.f / (float)(h * h);
     g.fd0.init((unsigned)n[0]);
     g.fd1.init((unsigned)n[1]);
     return g;
@@ -75,12 +92,48 @@ struct WallDev {
     int noslip;         // beta infinite
 };
 
+// The parameters in one arithmetic type, with the differences the stencils use.
+template <typename T>
+struct PhysT {
+    T rho1, rho2, mu1, mu2, sigma, eps, delta, tau;
+    T drho, dmu;                       // rho1 - rho2, mu1 - mu2
+    T costh[2], beta2[2], dbeta[2];    // per wall; dbeta = beta1 - beta2
+    T U[2][2];                         // per wall, tangential components
+};
+
 struct PhysDev {
     double rho1, rho2, mu1, mu2, sigma, eps;
     double delta, tau;  // clamp of phi for psi; floor of |grad psi|
     int model;
     WallDev wall[2];
+    PhysT<double> pd;   // copies in FP64 and FP32 (finalize_phys)
+    PhysT<float> pf;
 };
+
+template <typename T>
+inline void fill_phys(const PhysDev& ph, PhysT<T>& o) {
+    o.rho1 = (T)ph.rho1; o.rho2 = (T)ph.rho2; o.mu1 = (T)ph.mu1; o.mu2 = (T)ph.mu2;
+    o.sigma = (T)ph.sigma; o.eps = (T)ph.eps; o.delta = (T)ph.delta; o.tau = (T)ph.tau;
+    o.drho = (T)(ph.rho1 - ph.rho2);
+    o.dmu = (T)(ph.mu1 - ph.mu2);
+    for (int s = 0; s < 2; ++s) {
+        o.costh[s] = (T)ph.wall[s].costh;
+        o.beta2[s] = (T)ph.wall[s].beta2;
+        o.dbeta[s] = ph.wall[s].noslip ? T(0) : (T)(ph.wall[s].beta1 - ph.wall[s].beta2);
+        o.U[s][0] = (T)ph.wall[s].U[0];
+        o.U[s][1] = (T)ph.wall[s].U[1];
+    }
+}
+
+// refresh the typed copies after any change of the FP64 parameters
+inline void finalize_phys(PhysDev& ph) {
+    fill_phys<double>(ph, ph.pd);
+    fill_phys<float>(ph, ph.pf);
+}
+
+template <typename T> __host__ __device__ __forceinline__ const PhysT<T>& phys(const PhysDev& ph);
+template <> __host__ __device__ __forceinline__ const PhysT<double>& phys<double>(const PhysDev& ph) { return ph.pd; }
+template <> __host__ __device__ __forceinline__ const PhysT<float>& phys<float>(const PhysDev& ph) { return ph.pf; }
 
 // Device pointers of one evaluation (stage state in, stage results out).
 template <typename T>
@@ -97,6 +150,7 @@ struct StageFields {
     T* wghost;          // [2][D-1][NP]
     T* wmuw;            // [2][D-1][NP]
     const double* gamma;  // device scalar
+    const float* gammaf;  // its FP32 copy
 };
 
 // ---------------------------------------------------------------------------
@@ -153,14 +207,16 @@ template <typename T>
 void launch_wall_columns(const Geom& g, const PhysDev& ph, const T* phi, T* psi, double* cols,
                          cudaStream_t s);
 
-// Multigrid hierarchy.  The pressure p, its right-hand side f and the level-0
-// face coefficients beta are FP64 (defect correction); every level also holds
-// an FP32 correction e, right-hand side r and coefficients bf for the V-cycle.
+// Multigrid hierarchy.  The pressure p and its right-hand side f live on
+// level 0 in the storage of the precision form (PForm below); the FP64 form
+// also keeps FP64 level-0 face coefficients beta for its residual.  Every
+// level holds an FP32 correction e, right-hand side r and coefficients bf for
+// the V-cycle.
 struct MGLevel {
     Geom g;
-    double* p;         // level 0 only
-    double* f;         // level 0 only
-    double* beta[3];   // level 0 only
+    double* p;         // level 0 only (8 bytes per cell, typed by PForm)
+    double* f;         // level 0 only (8 bytes per cell, typed by PForm)
+    double* beta[3];   // level 0 only, FP64 form
     float* e;
     float* r;
     float* bf[3];
@@ -171,21 +227,49 @@ struct MG {
     MGLevel lv[kMaxLevels];
     double* partials;   // [2 * kPartials]
     double* scal;       // device scalars
+    float* scalf;       // FP32 device scalars
 };
 
 // scalar slots in MG::scal
 enum { S_MEAN = 0, S_FNORM = 1, S_RNORM = 2, S_MASS = 3, S_UMAX = 4, S_GAMMA = 5,
        S_THETA = 6, S_WETTED = 7, S_NSCAL = 16 };
+// slots in MG::scalf: the means of f and p as double-floats (FP32-mixed form) and gamma
+enum { SF_FMEAN_HI = 0, SF_FMEAN_LO = 1, SF_GAMMA = 2, SF_PMEAN_HI = 4, SF_PMEAN_LO = 5, SF_NSCAL = 8 };
+
+// ---------------------------------------------------------------------------
+// Level-0 pressure p and right-hand side f of the two precision forms.
+// FP64 form: p and f FP64, f stored with its mean removed, residual with the
+// FP64 face coefficients.  FP32-mixed form: p is a double-float (hi, lo)
+// pair, about 48 significant bits; f is the FP32 divergence as computed, its
+// mean kept apart as a double-float and removed inside the residual, which
+// uses the FP32 face coefficients of the V-cycles in double-float arithmetic
+// and so issues no FP64 instruction.
+// ---------------------------------------------------------------------------
+template <typename T> struct PForm;
+template <> struct PForm<double> { using P = double; using F = double; };
+template <> struct PForm<float> { using P = float2; using F = float; };
+template <typename T> using PT = typename PForm<T>::P;
+template <typename T> using FT = typename PForm<T>::F;
 
 template <typename T>
 void launch_div(const Geom& g, const T* const* us, double inv_cdt, MG& mg, cudaStream_t s);
+template <typename T>
 void launch_sum_f(const Geom& g, MG& mg, cudaStream_t s);
+template <typename T>
 void launch_sub_mean_and_norm(const Geom& g, MG& mg, cudaStream_t s);
 template <typename T>
 void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cudaStream_t s);
-void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s);   // FP64 residual, its norm, r0 and e0 = 0
+template <typename T>
+void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s);   // residual, its norm, r0 and e0 = 0
+template <typename T>
 void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s);  // FP32 V-cycle, p += e0
+template <typename T>
 void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s);
+// host <-> level-0 p / f conversions of the FP32-mixed form (FP64 staging buffer x)
+void launch_p_to_double(const Geom& g, const MG& mg, double* x, cudaStream_t s);
+void launch_p_from_double(const Geom& g, MG& mg, const double* x, cudaStream_t s);
+void launch_f_to_double(const Geom& g, const MG& mg, double* x, cudaStream_t s);
+void launch_f_from_double(const Geom& g, MG& mg, const double* x, cudaStream_t s);
 template <typename T>
 void launch_project(const Geom& g, const PhysDev& ph, const T* phi, T* const* us, double cdt,
                     const double* p, cudaStream_t s);

@@ -4,15 +4,17 @@
 //
 //   k_div            f = div u* / (c dt)                                   Eq. (NS_incompressibility)
 //   k_sub_mean_sq    remove the mean of f (the walls and periodic sides
-//                    carry no net flux), accumulate |f|^2
-//   k_coef0          face coefficients 1/rho_f (FP64 and FP32), rho_f the  Sec. 2 (rho linear in phi)
-//                    mean of the two adjacent cells, zero on the walls
-//   k_resid64        FP64 residual r = f - A p, |r|^2, FP32 copy of r, e = 0
+//                    carry no net flux), accumulate |f|^2 (FP64 form; the
+//                    FP32-mixed form keeps f and removes the mean in k_resid)
+//   k_coef0          face coefficients 1/rho_f, rho_f the mean of the two  Sec. 2 (rho linear in phi)
+//                    adjacent cells, zero on the walls
+//   k_resid          residual r = f - A p in the form's precision, |r|^2,
+//                    FP32 copy of r, e = 0
 //   k_rbgs           FP32 red-black Gauss-Seidel sweep of A e = r
 //   k_resid_restrict FP32 residual and its restriction (mean of the 2^D children)
 //   k_prolong        FP32 cell-centred (bi/tri)linear prolongation
 //   k_coarse         FP64 dense solve of the coarsest level in one CTA
-//   k_update         p += e (FP64)
+//   k_update         p += e (FP64, or double-float in the FP32-mixed form)
 //   k_project        u = u* - c dt grad p / rho_f on every interior face     Eq. (no-penetration BC)
 //   k_mass, k_umax, k_contact_line: FP64 reductions                          Sec. 2, 3.1, 5.1
 //
@@ -70,6 +72,13 @@ __device__ double block_max(double v) {
     return v;
 }
 
+// out = mean as a double-float, from the FP64 mean (one thread)
+__global__ void k_mean_df(const double* mean, float* out) {
+    const float2 m = ops::dfl::from_double(*mean);
+    out[0] = m.x;
+    out[1] = m.y;
+}
+
 // final pass of a sum: out = scale * sum(partials[0..np))
 __global__ void k_final_sum(const double* part, int np, double scale, double* out, int do_sqrt) {
     double v = 0.0;
@@ -82,22 +91,23 @@ __global__ void k_final_sum(const double* part, int np, double scale, double* ou
 }
 
 template <typename T, int DIM>
-__global__ void k_div(Geom g, const T* u0, const T* u1, const T* u2, double inv_cdt, double* f, double* part) {
+__global__ void k_div(Geom g, const T* u0, const T* u1, const T* u2, T inv_cdt, FT<T>* f, double* part) {
     const T* us[3] = {u0, u1, u2};
-    const double ih = 1.0 / g.h;
-    double acc = 0.0;
+    const T ih = g_ih<T>(g);
+    ops::SumAcc<T> acc;
     const long stride = (long)gridDim.x * blockDim.x;
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N; c += stride) {
-        const double v = ops::div_at<Ld, T, DIM>(g, us, ih, inv_cdt, c);
+        const T v = ops::div_at<Ld, T, DIM>(g, us, ih, inv_cdt, c);
         f[c] = v;
-        acc += v;
+        acc.add(v);
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double a = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
-__global__ void k_sub_mean_sq(long N, double* f, const double* sum, double* part) {
-    const double mean = *sum / (double)N;
+// FP64 form: f -= mean, |f|^2
+__global__ void k_sub_mean_sq(long N, double* f, const double* mean_p, double* part) {
+    const double mean = *mean_p;
     double acc = 0.0;
     const long stride = (long)gridDim.x * blockDim.x;
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += stride) {
@@ -109,13 +119,26 @@ __global__ void k_sub_mean_sq(long N, double* f, const double* sum, double* part
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
+// FP32-mixed form: |f - mean|^2 with the double-float mean, f unchanged
+__global__ void k_fnorm_df(long N, const float* f, const float* mean_df, double* part) {
+    const float mh = mean_df[0], ml = mean_df[1];
+    float acc = 0.f;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += stride) {
+        const float v = (f[c] - mh) - ml;
+        acc += v * v;
+    }
+    const double a = block_sum((double)acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
 template <typename T, int DIM>
-__global__ void k_coef0(Geom g, double rho1, double rho2, const T* phi, double* b0, double* b1, double* b2, float* f0,
-                        float* f1, float* f2) {
+__global__ void k_coef0(Geom g, PhysDev ph, const T* phi, double* b0, double* b1, double* b2, float* f0, float* f1,
+                        float* f2) {
     double* bs[3] = {b0, b1, b2};
     float* bf[3] = {f0, f1, f2};
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < g.N + g.NP) ops::coef0_at<Ld, T, DIM>(g, rho1, rho2, phi, bs, bf, t);
+    if (t < g.N + g.NP) ops::coef0_at<Ld, T, DIM>(g, ph, phi, bs, bf, t);
 }
 
 template <int DIM>
@@ -127,20 +150,21 @@ __global__ void k_coef_restrict(Geom gf, Geom gc, const float* f0, const float* 
     if (t < gc.N + gc.NP) ops::coef_restrict_at<Ld, float, DIM>(gf, gc, fb, cb, t);
 }
 
-template <int DIM>
-__global__ void k_resid64(Geom g, const double* b0, const double* b1, const double* b2, const double* p,
-                          const double* f, float* r32, float* e32, double* part) {
-    const double* beta[3] = {b0, b1, b2};
-    double acc = 0.0;
+template <typename T, int DIM>
+__global__ void k_resid(MGLevel L0, const float* fmean_df, double* part) {
+    const PT<T>* p = ops::pbuf<T>(L0);
+    const FT<T>* f = ops::fbuf<T>(L0);
+    const float2 fmean = fmean_df ? make_float2(fmean_df[0], fmean_df[1]) : make_float2(0.f, 0.f);
+    T acc = T(0);
     const long stride = (long)gridDim.x * blockDim.x;
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < g.N; c += stride) {
-        const double r = ops::resid64_at<Ld, DIM>(g, beta, p, f, c);
-        r32[c] = (float)r;
-        e32[c] = 0.f;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < L0.g.N; c += stride) {
+        const T r = ops::resid_form_at<Ld, DIM>(L0, p, f, fmean, c);
+        L0.r[c] = (float)r;
+        L0.e[c] = 0.f;
         acc += r * r;
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double a = block_sum((double)acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
 template <int DIM>
@@ -176,31 +200,61 @@ __global__ void k_coarse(Geom g, const float* b0, const float* b1, const float* 
     ops::coarse_solve_block<Ld, float, DIM>(g, beta, r, e, A, bb, fct, &piv, &sh);
 }
 
-__global__ void k_update(long N, double* p, const float* e) {
+template <typename T>
+__global__ void k_update(long N, PT<T>* p, const float* e) {
     long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < N) p[c] += (double)e[c];
+    if (c < N) p[c] = ops::p_add(p[c], e[c]);
 }
 
-__global__ void k_partial_sum(long N, const double* x, double* part) {
-    double acc = 0.0;
+template <typename X>
+__global__ void k_partial_sum(long N, const X* x, double* part) {
+    ops::SumAcc<X> acc;
     const long stride = (long)gridDim.x * blockDim.x;
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += stride) acc += x[c];
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += stride) acc.add(x[c]);
+    const double a = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
-__global__ void k_sub_scalar(long N, double* x, const double* sum) {
-    const double mean = *sum / (double)N;
+__global__ void k_partial_sum_df(long N, const float2* x, double* part) {
+    float2 acc = make_float2(0.f, 0.f);
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += stride) acc = ops::dfl::add(acc, x[c]);
+    const double a = block_sum(ops::dfl::to_double(acc));
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
+// p -= mean (mean: the FP64 value, or its double-float copy in the FP32-mixed form)
+template <typename T>
+__global__ void k_sub_mean_p(long N, PT<T>* p, const double* mean, const float* mean_df) {
     long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < N) x[c] -= mean;
+    if (c >= N) return;
+    if constexpr (sizeof(T) == 8) p[c] = p[c] - *mean;
+    else p[c] = ops::dfl::sub(p[c], make_float2(mean_df[0], mean_df[1]));
+}
+
+// host-side conversions of the FP32-mixed level-0 arrays through an FP64 buffer
+__global__ void k_p_to_double(long N, const float2* p, double* x) {
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) x[c] = ops::dfl::to_double(p[c]);
+}
+__global__ void k_p_from_double(long N, float2* p, const double* x) {
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) p[c] = ops::dfl::from_double(x[c]);
+}
+__global__ void k_f_to_double(long N, const float* f, const float* mean_df, double* x) {
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) x[c] = (double)f[c] - ops::dfl::to_double(make_float2(mean_df[0], mean_df[1]));
+}
+__global__ void k_f_from_double(long N, float* f, const double* x) {
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) f[c] = (float)x[c];
 }
 
 template <typename T, int DIM>
-__global__ void k_project(Geom g, double rho1, double rho2, const T* phi, T* u0, T* u1, T* u2, double cdt,
-                          const double* p) {
+__global__ void k_project(Geom g, PhysDev ph, const T* phi, T* u0, T* u1, T* u2, T cdt, const PT<T>* p) {
     T* us[3] = {u0, u1, u2};
     long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < g.N) ops::project_at<Ld, T, DIM>(g, rho1, rho2, phi, us, cdt, p, c);
+    if (c < g.N) ops::project_at<Ld, T, DIM>(g, ph, phi, us, cdt, p, c);
 }
 
 template <typename T>
@@ -214,22 +268,24 @@ __global__ void k_mass_partial(long N, const T* phi, double* part) {
 
 template <typename T>
 __global__ void k_umax_partial(long n0, long n1, long n2, const T* u0, const T* u1, const T* u2, double* part) {
-    double m = 0.0;
+    T m = T(0);
     const long stride = (long)gridDim.x * blockDim.x;
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n0; c += stride) m = fmax(m, fabs((double)u0[c]));
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n1; c += stride) m = fmax(m, fabs((double)u1[c]));
-    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += stride) m = fmax(m, fabs((double)u2[c]));
-    m = block_max(m);
-    if (threadIdx.x == 0) part[blockIdx.x] = m;
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n0; c += stride) m = fmax(m, fabs(u0[c]));
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n1; c += stride) m = fmax(m, fabs(u1[c]));
+    for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < n2; c += stride) m = fmax(m, fabs(u2[c]));
+    const double a = block_max((double)m);
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
-__global__ void k_gamma_final(const double* part, int np, double floor_gamma, double* umax, double* gamma) {
+__global__ void k_gamma_final(const double* part, int np, double floor_gamma, double* umax, double* gamma,
+                              float* gammaf) {
     double v = 0.0;
     for (int t = threadIdx.x; t < np; t += blockDim.x) v = fmax(v, part[t]);
     v = block_max(v);
     if (threadIdx.x == 0) {
         *umax = v;
         *gamma = fmax(2.5 * v, floor_gamma);
+        *gammaf = (float)*gamma;
     }
 }
 
@@ -296,25 +352,36 @@ template <typename T>
 void launch_div(const Geom& g, const T* const* us, double inv_cdt, MG& mg, cudaStream_t s) {
     const unsigned G = red_blocks(g.N);
     const bool on = prof_before(KC_DIV, s);
+    FT<T>* f = ops::fbuf<T>(mg.lv[0]);
     if (g.D == 2)
-        k_div<T, 2><<<G, kThreads, 0, s>>>(g, us[0], us[1], nullptr, inv_cdt, mg.lv[0].f, mg.partials);
+        k_div<T, 2><<<G, kThreads, 0, s>>>(g, us[0], us[1], nullptr, (T)inv_cdt, f, mg.partials);
     else
-        k_div<T, 3><<<G, kThreads, 0, s>>>(g, us[0], us[1], us[2], inv_cdt, mg.lv[0].f, mg.partials);
+        k_div<T, 3><<<G, kThreads, 0, s>>>(g, us[0], us[1], us[2], (T)inv_cdt, f, mg.partials);
     prof_after(on, s);
-    k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0, mg.scal + S_MEAN, 0);
+    k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0 / (double)g.N, mg.scal + S_MEAN, 0);
     g_launches += 2;
 }
 
+template <typename T>
 void launch_sum_f(const Geom& g, MG& mg, cudaStream_t s) {
     const unsigned G = red_blocks(g.N);
-    k_partial_sum<<<G, kThreads, 0, s>>>(g.N, mg.lv[0].f, mg.partials);
-    k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0, mg.scal + S_MEAN, 0);
+    k_partial_sum<FT<T>><<<G, kThreads, 0, s>>>(g.N, ops::fbuf<T>(mg.lv[0]), mg.partials);
+    k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0 / (double)g.N, mg.scal + S_MEAN, 0);
     g_launches += 2;
 }
 
+// S_MEAN holds the mean of f: the FP64 form centres f, the FP32-mixed form
+// keeps a double-float copy of the mean for its residual; then ||f - mean||
+template <typename T>
 void launch_sub_mean_and_norm(const Geom& g, MG& mg, cudaStream_t s) {
     const unsigned G = red_blocks(g.N);
-    k_sub_mean_sq<<<G, kThreads, 0, s>>>(g.N, mg.lv[0].f, mg.scal + S_MEAN, mg.partials);
+    if constexpr (sizeof(T) == 8) {
+        k_sub_mean_sq<<<G, kThreads, 0, s>>>(g.N, mg.lv[0].f, mg.scal + S_MEAN, mg.partials);
+    } else {
+        k_mean_df<<<1, 1, 0, s>>>(mg.scal + S_MEAN, mg.scalf + SF_FMEAN_HI);
+        k_fnorm_df<<<G, kThreads, 0, s>>>(g.N, ops::fbuf<float>(mg.lv[0]), mg.scalf + SF_FMEAN_HI, mg.partials);
+        ++g_launches;
+    }
     k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0, mg.scal + S_FNORM, 1);
     g_launches += 2;
 }
@@ -323,10 +390,10 @@ template <typename T>
 void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cudaStream_t s) {
     MGLevel& L0 = mg.lv[0];
     if (g.D == 2)
-        k_coef0<T, 2><<<blocks_for(g.N + g.NP), kThreads, 0, s>>>(g, ph.rho1, ph.rho2, phi, L0.beta[0], L0.beta[1],
+        k_coef0<T, 2><<<blocks_for(g.N + g.NP), kThreads, 0, s>>>(g, ph, phi, L0.beta[0], L0.beta[1],
                                                                   nullptr, L0.bf[0], L0.bf[1], nullptr);
     else
-        k_coef0<T, 3><<<blocks_for(g.N + g.NP), kThreads, 0, s>>>(g, ph.rho1, ph.rho2, phi, L0.beta[0], L0.beta[1],
+        k_coef0<T, 3><<<blocks_for(g.N + g.NP), kThreads, 0, s>>>(g, ph, phi, L0.beta[0], L0.beta[1],
                                                                   L0.beta[2], L0.bf[0], L0.bf[1], L0.bf[2]);
     ++g_launches;
     for (int l = 1; l < mg.nlev; ++l) {
@@ -374,42 +441,70 @@ static void vcycle_rec(MG& mg, int l, int npre, int npost, cudaStream_t s) {
         }
 }
 
+template <typename T>
 void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s) {
     if (g.D == 2) vcycle_rec<2>(mg, 0, npre, npost, s);
     else vcycle_rec<3>(mg, 0, npre, npost, s);
-    k_update<<<blocks_for(g.N), kThreads, 0, s>>>(g.N, mg.lv[0].p, mg.lv[0].e);
+    k_update<T><<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<T>(mg.lv[0]), mg.lv[0].e);
     ++g_launches;
 }
 
+template <typename T>
 void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s) {
-    MGLevel& L = mg.lv[0];
     const unsigned G = red_blocks(g.N);
+    const float* fm = sizeof(T) == 8 ? nullptr : mg.scalf + SF_FMEAN_HI;
     const bool on = prof_before(KC_RESID, s);
-    if (g.D == 2)
-        k_resid64<2><<<G, kThreads, 0, s>>>(g, L.beta[0], L.beta[1], L.beta[2], L.p, L.f, L.r, L.e, mg.partials);
-    else
-        k_resid64<3><<<G, kThreads, 0, s>>>(g, L.beta[0], L.beta[1], L.beta[2], L.p, L.f, L.r, L.e, mg.partials);
+    if (g.D == 2) k_resid<T, 2><<<G, kThreads, 0, s>>>(mg.lv[0], fm, mg.partials);
+    else k_resid<T, 3><<<G, kThreads, 0, s>>>(mg.lv[0], fm, mg.partials);
     prof_after(on, s);
     k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0, mg.scal + S_RNORM, 1);
     g_launches += 2;
 }
 
+template <typename T>
 void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s) {
     const unsigned G = red_blocks(g.N);
-    k_partial_sum<<<G, kThreads, 0, s>>>(g.N, mg.lv[0].p, mg.partials);
-    k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0, mg.scal + S_MEAN, 0);
-    k_sub_scalar<<<blocks_for(g.N), kThreads, 0, s>>>(g.N, mg.lv[0].p, mg.scal + S_MEAN);
+    if constexpr (sizeof(T) == 8) {
+        k_partial_sum<double><<<G, kThreads, 0, s>>>(g.N, mg.lv[0].p, mg.partials);
+    } else {
+        k_partial_sum_df<<<G, kThreads, 0, s>>>(g.N, ops::pbuf<float>(mg.lv[0]), mg.partials);
+    }
+    k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0 / (double)g.N, mg.scal + S_MEAN, 0);
+    if constexpr (sizeof(T) == 4) {
+        k_mean_df<<<1, 1, 0, s>>>(mg.scal + S_MEAN, mg.scalf + SF_PMEAN_HI);
+        ++g_launches;
+    }
+    k_sub_mean_p<T><<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<T>(mg.lv[0]), mg.scal + S_MEAN,
+                                                        mg.scalf + SF_PMEAN_HI);
     g_launches += 3;
+}
+
+void launch_p_to_double(const Geom& g, const MG& mg, double* x, cudaStream_t s) {
+    k_p_to_double<<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<float>(mg.lv[0]), x);
+    ++g_launches;
+}
+void launch_p_from_double(const Geom& g, MG& mg, const double* x, cudaStream_t s) {
+    k_p_from_double<<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<float>(mg.lv[0]), x);
+    ++g_launches;
+}
+void launch_f_to_double(const Geom& g, const MG& mg, double* x, cudaStream_t s) {
+    k_f_to_double<<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::fbuf<float>(mg.lv[0]), mg.scalf + SF_FMEAN_HI, x);
+    ++g_launches;
+}
+void launch_f_from_double(const Geom& g, MG& mg, const double* x, cudaStream_t s) {
+    k_f_from_double<<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::fbuf<float>(mg.lv[0]), x);
+    ++g_launches;
 }
 
 template <typename T>
 void launch_project(const Geom& g, const PhysDev& ph, const T* phi, T* const* us, double cdt, const double* p,
                     cudaStream_t s) {
     const bool on = prof_before(KC_PROJECT, s);
+    const PT<T>* pp = reinterpret_cast<const PT<T>*>(p);
     if (g.D == 2)
-        k_project<T, 2><<<blocks_for(g.N), kThreads, 0, s>>>(g, ph.rho1, ph.rho2, phi, us[0], us[1], nullptr, cdt, p);
+        k_project<T, 2><<<blocks_for(g.N), kThreads, 0, s>>>(g, ph, phi, us[0], us[1], nullptr, (T)cdt, pp);
     else
-        k_project<T, 3><<<blocks_for(g.N), kThreads, 0, s>>>(g, ph.rho1, ph.rho2, phi, us[0], us[1], us[2], cdt, p);
+        k_project<T, 3><<<blocks_for(g.N), kThreads, 0, s>>>(g, ph, phi, us[0], us[1], us[2], (T)cdt, pp);
     prof_after(on, s);
     ++g_launches;
 }
@@ -429,7 +524,8 @@ void launch_gamma(const Geom& g, const T* const* u, double gamma_param, MG& mg, 
     long n2 = (g.D == 3) ? g.N + g.NP : 0;
     long n1 = (g.D == 2) ? g.N + g.NP : g.N;
     k_umax_partial<T><<<G, kThreads, 0, s>>>(g.N, n1, n2, u[0], u[1], g.D == 3 ? u[2] : u[1], mg.partials);
-    k_gamma_final<<<1, 1024, 0, s>>>(mg.partials, (int)G, -gamma_param, mg.scal + S_UMAX, mg.scal + S_GAMMA);
+    k_gamma_final<<<1, 1024, 0, s>>>(mg.partials, (int)G, -gamma_param, mg.scal + S_UMAX, mg.scal + S_GAMMA,
+                                     mg.scalf + SF_GAMMA);
     g_launches += 2;
 }
 
@@ -440,6 +536,16 @@ void launch_contact_line(const Geom& g, int wall, const double* cols, MG& mg, cu
     ++g_launches;
 }
 
+template void launch_sum_f<double>(const Geom&, MG&, cudaStream_t);
+template void launch_sum_f<float>(const Geom&, MG&, cudaStream_t);
+template void launch_sub_mean_and_norm<double>(const Geom&, MG&, cudaStream_t);
+template void launch_sub_mean_and_norm<float>(const Geom&, MG&, cudaStream_t);
+template void launch_vcycle<double>(const Geom&, MG&, int, int, cudaStream_t);
+template void launch_vcycle<float>(const Geom&, MG&, int, int, cudaStream_t);
+template void launch_resid_norm<double>(const Geom&, MG&, cudaStream_t);
+template void launch_resid_norm<float>(const Geom&, MG&, cudaStream_t);
+template void launch_p_mean_remove<double>(const Geom&, MG&, cudaStream_t);
+template void launch_p_mean_remove<float>(const Geom&, MG&, cudaStream_t);
 template void launch_div<double>(const Geom&, const double* const*, double, MG&, cudaStream_t);
 template void launch_div<float>(const Geom&, const float* const*, double, MG&, cudaStream_t);
 template void launch_mg_coef<double>(const Geom&, const PhysDev&, const double*, MG&, cudaStream_t);

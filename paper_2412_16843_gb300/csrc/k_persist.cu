@@ -267,6 +267,7 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
     if (x.tail_cta()) tail_vcycle<T, DIM>(A, first, sm);
     if (!x.sync()) return false;
     const MGLevel L0 = A.lv[0];
+    PT<T>* P0 = ops::pbuf<T>(L0);
     bool updated = false;
     for (int l = A.lt - 1; l >= 0; --l) {
         const MGLevel L = A.lv[l];
@@ -281,12 +282,12 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
                 for (int k = tid; k < half; k += nth) {
                     const long c = ops::colour_cell(L.g, col, k);
                     ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
-                    if (last) L0.p[c] = L_::ld(L0.p + c) + (double)L.e[c];
+                    if (last) P0[c] = ops::p_add(L_::ld(P0 + c), L.e[c]);
                 }
                 if (last) {  // the other colour is final already
                     for (int k = tid; k < half; k += nth) {
                         const long c = ops::colour_cell(L.g, 0, k);
-                        L0.p[c] = L_::ld(L0.p + c) + (double)L_::ld(L.e + c);
+                        P0[c] = ops::p_add(L_::ld(P0 + c), L_::ld(L.e + c));
                     }
                     updated = true;
                 }
@@ -294,24 +295,26 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
             }
     }
     if (!updated) {
-        for (int c = tid; c < (int)L0.g.N; c += nth) L0.p[c] = L_::ld(L0.p + c) + (double)L_::ld(L0.e + c);
+        for (int c = tid; c < (int)L0.g.N; c += nth) P0[c] = ops::p_add(L_::ld(P0 + c), L_::ld(L0.e + c));
         if (!x.sync()) return false;
     }
     return true;
 }
 
-// FP64 residual of level 0: its squared norm, the FP32 copy r and e = 0
-template <class Ld, int DIM>
-__device__ double resid64_local(const MGLevel& L0, int tid, int nth) {
-    const double* b[3] = {L0.beta[0], L0.beta[1], L0.beta[2]};
-    double acc = 0.0;
+// residual of level 0 in the form's precision: this thread's part of its
+// squared norm; the FP32 copy r and e = 0
+template <class Ld, typename T, int DIM>
+__device__ double resid_local(const MGLevel& L0, float2 fmean, int tid, int nth) {
+    const PT<T>* p = ops::pbuf<T>(L0);
+    const FT<T>* f = ops::fbuf<T>(L0);
+    T acc = T(0);
     for (int c = tid; c < (int)L0.g.N; c += nth) {
-        const double r = ops::resid64_at<Ld, DIM>(L0.g, b, L0.p, L0.f, c);
+        const T r = ops::resid_form_at<Ld, DIM>(L0, p, f, fmean, c);
         L0.r[c] = (float)r;
         L0.e[c] = 0.f;
         acc += r * r;
     }
-    return acc;
+    return (double)acc;
 }
 
 template <class X>
@@ -328,34 +331,42 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
     const Geom& g = A.g;
     const int tid = x.tid(), nth = x.nth();
     const MGLevel L0 = A.lv[0];
-    const double ih = 1.0 / g.h, inv_cdt = 1.0 / cdt;
+    PT<T>* P0 = ops::pbuf<T>(L0);
+    FT<T>* F0 = ops::fbuf<T>(L0);
+    const T ih = g_ih<T>(g), inv_cdt = (T)(1.0 / cdt);
     const T* uc[3] = {u[0], u[1], u[2]};
-    double s = 0.0;
+    ops::SumAcc<T> s;
     for (int c = tid; c < (int)g.N; c += nth) {
-        const double v = ops::div_at<L_, T, DIM>(g, uc, ih, inv_cdt, c);
-        L0.f[c] = v;
-        s += v;
+        const T v = ops::div_at<L_, T, DIM>(g, uc, ih, inv_cdt, c);
+        F0[c] = v;
+        s.add(v);
     }
     double sum;
-    if (!x.template reduce<false>(s, sum)) return false;
+    if (!x.template reduce<false>(s.value(), sum)) return false;
     const double mean = sum / (double)g.N;
-    double s2 = 0.0;
+    // FP64 form: f is centred in place; FP32-mixed form: the residual removes the mean
+    const float2 fmean = ops::dfl::from_double(mean);
+    T s2 = T(0);
     // first guess: zero, the last solve's pressure, or the same RK stage of the
     // last two steps extrapolated linearly in time (2 p_(n-1) - p_(n-2))
     const bool extrap = (A.warm == CDI_WARM_EXTRAP);
-    const double* hnew = extrap ? A.hist[stage][(sg - 1) & 1] : nullptr;
-    const double* hold = extrap ? A.hist[stage][sg & 1] : nullptr;
+    const PT<T>* hnew = extrap ? reinterpret_cast<const PT<T>*>(A.hist[stage][(sg - 1) & 1]) : nullptr;
+    const PT<T>* hold = extrap ? reinterpret_cast<const PT<T>*>(A.hist[stage][sg & 1]) : nullptr;
     for (int c = tid; c < (int)g.N; c += nth) {
-        const double v = L_::ld(L0.f + c) - mean;
-        L0.f[c] = v;
+        T v;
+        if constexpr (sizeof(T) == 8) {
+            v = L_::ld(F0 + c) - mean;
+            F0[c] = v;
+        } else {
+            v = (L_::ld(F0 + c) - fmean.x) - fmean.y;
+        }
         s2 += v * v;
-        if (A.warm == CDI_WARM_ZERO) L0.p[c] = 0.0;
-        else if (extrap && sg >= 2) L0.p[c] = 2.0 * L_::ld(hnew + c) - L_::ld(hold + c);
+        if (A.warm == CDI_WARM_ZERO) P0[c] = ops::p_zero<T>();
+        else if (extrap && sg >= 2) P0[c] = ops::p_extrap(L_::ld(hnew + c), L_::ld(hold + c));
     }
-    for (int t = tid; t < (int)(g.N + g.NP); t += nth)
-        ops::coef0_at<L_, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, L0.beta, L0.bf, t);
+    for (int t = tid; t < (int)(g.N + g.NP); t += nth) ops::coef0_at<L_, T, DIM>(g, A.ph, phi, L0.beta, L0.bf, t);
     double fsq;
-    if (!x.template reduce<false>(s2, fsq)) return false;
+    if (!x.template reduce<false>((double)s2, fsq)) return false;
     const double fn = sqrt(fsq);
     for (int l = 1; l < A.lt; ++l) {
         const MGLevel F = A.lv[l - 1];
@@ -366,18 +377,18 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
         if (!x.sync()) return false;
     }
     double rsq;
-    if (!x.template reduce<false>(resid64_local<L_, DIM>(L0, tid, nth), rsq)) return false;
+    if (!x.template reduce<false>(resid_local<L_, T, DIM>(L0, fmean, tid, nth), rsq)) return false;
     double rn = sqrt(rsq);
     if (!isfinite(fn) || !isfinite(rn)) {
         set_status(x, S, CDI_ENAN);
         return false;
     }
     int cyc = 0;
-    double* hput = extrap ? A.hist[stage][sg & 1] : nullptr;
+    PT<T>* hput = extrap ? reinterpret_cast<PT<T>*>(A.hist[stage][sg & 1]) : nullptr;
     if (fn == 0.0) {
         for (int c = tid; c < (int)g.N; c += nth) {
-            L0.p[c] = 0.0;
-            if (extrap) hput[c] = 0.0;
+            P0[c] = ops::p_zero<T>();
+            if (extrap) hput[c] = ops::p_zero<T>();
         }
         if (!x.sync()) return false;
     } else {
@@ -385,7 +396,7 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
         while (rn > A.tol * fn && cyc < A.max_vcycles) {
             if (!vcycle<T, DIM>(A, x, first, sm)) return false;
             first = false;
-            if (!x.template reduce<false>(resid64_local<L_, DIM>(L0, tid, nth), rsq)) return false;
+            if (!x.template reduce<false>(resid_local<L_, T, DIM>(L0, fmean, tid, nth), rsq)) return false;
             rn = sqrt(rsq);
             ++cyc;
             if (!isfinite(rn)) {
@@ -401,14 +412,22 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
             }
             return false;
         }
-        double ps = 0.0;
-        for (int c = tid; c < (int)g.N; c += nth) ps += L_::ld(L0.p + c);
+        double ps;
+        if constexpr (sizeof(T) == 8) {
+            ps = 0.0;
+            for (int c = tid; c < (int)g.N; c += nth) ps += L_::ld(P0 + c);
+        } else {
+            float2 a = make_float2(0.f, 0.f);
+            for (int c = tid; c < (int)g.N; c += nth) a = ops::dfl::add(a, L_::ld(P0 + c));
+            ps = ops::dfl::to_double(a);
+        }
         double psum;
         if (!x.template reduce<false>(ps, psum)) return false;
         const double pmean = psum / (double)g.N;
+        const float2 pm2 = ops::dfl::from_double(pmean);
         for (int c = tid; c < (int)g.N; c += nth) {
-            const double v = L_::ld(L0.p + c) - pmean;
-            L0.p[c] = v;
+            const PT<T> v = ops::p_sub(L_::ld(P0 + c), pmean, pm2);
+            P0[c] = v;
             if (extrap) hput[c] = v;
         }
         if (!x.sync()) return false;
@@ -419,7 +438,7 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
         S->total_cycles += cyc;
         if (cyc > S->max_cycles) S->max_cycles = cyc;
     }
-    for (int c = tid; c < (int)g.N; c += nth) ops::project_at<L_, T, DIM>(g, A.ph.rho1, A.ph.rho2, phi, u, cdt, L0.p, c);
+    for (int c = tid; c < (int)g.N; c += nth) ops::project_at<L_, T, DIM>(g, A.ph, phi, u, (T)cdt, P0, c);
     return x.sync();
 }
 
@@ -438,13 +457,13 @@ __device__ void run_steps(const InstArgs<T>& A, X& x, int nsteps, InstStats* S, 
     for (int step = 0; step < nsteps; ++step) {
         double gamma = A.gamma_param;
         if (gamma < 0.0) {  // gamma = 2.5 |u|_max, floored (Sec. 5.1)
-            double mx = 0.0;
+            T mx = T(0);
             for (int a = 0; a < DIM; ++a) {
                 const int nf = (int)(g.N + (a == DIM - 1 ? g.NP : 0));
-                for (int c = tid; c < nf; c += nth) mx = fmax(mx, fabs((double)L_::ld(u_s[a] + c)));
+                for (int c = tid; c < nf; c += nth) mx = fmax(mx, fabs(L_::ld(u_s[a] + c)));
             }
             double umax;
-            if (!x.template reduce<true>(mx, umax)) return;
+            if (!x.template reduce<true>((double)mx, umax)) return;
             gamma = fmax(2.5 * umax, -A.gamma_param);
         }
         for (int st = 0; st < 4; ++st) {

@@ -65,10 +65,14 @@ __global__ void k_wall_cols(Geom g, PhysDev ph, const T* phi, const T* psi, doub
     base[2 * g.NP + pidx] = (double)q.dnw;
 }
 
+// gamma of the step in the kernel's type (the FP32 copy in FP32 kernels)
+__device__ __forceinline__ double stage_gamma(const StageFields<double>& f) { return *f.gamma; }
+__device__ __forceinline__ float stage_gamma(const StageFields<float>& f) { return *f.gammaf; }
+
 template <typename T, int DIM>
 __global__ void k_phi_rhs(Geom g, PhysDev ph, StageFields<T> f) {
     long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < g.N) ops::phi_rhs_at<Ld, T, DIM>(g, ph, f, (T)(*f.gamma), c);
+    if (c < g.N) ops::phi_rhs_at<Ld, T, DIM>(g, ph, f, stage_gamma(f), c);
 }
 
 template <typename T, int DIM>

@@ -68,16 +68,16 @@ __device__ __forceinline__ void d12(const Geom& g, const T* s, const IJK& q, lon
 
 template <class L, typename T>
 __device__ __forceinline__ void psi_at(const Geom& g, const PhysDev& ph, const T* phi, T* psi, long c) {
-    const T delta = (T)ph.delta;
-    T pt = clampv(L::ld(phi + c), delta, T(1) - delta);
-    psi[c] = (T)ph.eps * log(pt / (T(1) - pt));
+    const PhysT<T>& P = phys<T>(ph);
+    T pt = clampv(L::ld(phi + c), P.delta, T(1) - P.delta);
+    psi[c] = P.eps * log(pt / (T(1) - pt));
 }
 
 template <class L, typename T, int DIM>
 __device__ __forceinline__ void cell_at(const Geom& g, const PhysDev& ph, const T* phi, const T* psi, T* nh0,
                                         T* nh1, T* nh2, T* muc, long c) {
     const IJK q = decode(g, c);
-    const T ih = T(1) / (T)g.h;
+    const T ih = g_ih<T>(g);
     T gb[3], grad2 = T(0), lap = T(0);
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
@@ -87,11 +87,12 @@ __device__ __forceinline__ void cell_at(const Geom& g, const PhysDev& ph, const 
         grad2 += d1 * d1;
         lap += d2;
     }
-    const T delta = (T)ph.delta, eps = (T)ph.eps;
+    const PhysT<T>& Q = phys<T>(ph);
+    const T delta = Q.delta, eps = Q.eps;
     T pt = clampv(L::ld(phi + c), delta, T(1) - delta);
     T P = pt * (T(1) - pt);
-    muc[c] = T(6) * (T)ph.sigma * (P * (T(1) - T(2) * pt) * (T(1) - grad2) / eps - P * lap);
-    T gm = sqrt(grad2) + (T)ph.tau;
+    muc[c] = T(6) * Q.sigma * (P * (T(1) - T(2) * pt) * (T(1) - grad2) / eps - P * lap);
+    T gm = sqrt(grad2) + Q.tau;
     nh0[c] = gb[0] / gm;
     nh1[c] = gb[1] / gm;
     if (DIM == 3) nh2[c] = gb[2] / gm;
@@ -113,8 +114,8 @@ __device__ ColQ<T> wall_column(const Geom& g, const PhysDev& ph, const T* phi, c
     const int W = DIM - 1, nW = g.n[W];
     const int r0 = s == 0 ? 0 : nW - 1, r1 = s == 0 ? 1 : nW - 2;
     const T sgn = s == 0 ? T(1) : T(-1);  // inward wall normal
-    const T ih = T(1) / (T)g.h;
-    const T delta = (T)ph.delta, eps = (T)ph.eps, tau = (T)ph.tau;
+    const T ih = g_ih<T>(g);
+    const T delta = phys<T>(ph).delta, eps = phys<T>(ph).eps, tau = phys<T>(ph).tau;
     T kp[2], dn[2], dnph[2], gtv[2][2], gtp[2][2], phv[2], psv[2];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
@@ -208,8 +209,9 @@ __device__ void wall_at(const Geom& g, const PhysDev& ph, const T* phi, const T*
     const int j = (DIM == 3) ? (int)(pidx / g.n[0]) : 0;
     const int W = DIM - 1;
     const int r0 = s == 0 ? 0 : g.n[W] - 1;
-    const T ih = T(1) / (T)g.h;
+    const T ih = g_ih<T>(g);
     const WallDev& wp = ph.wall[s];
+    const PhysT<T>& Q = phys<T>(ph);
     const ColQ<T> cR = wall_column<L, T, DIM>(g, ph, phi, psi, s, i, j);
 #pragma unroll
     for (int a = 0; a < DIM - 1; ++a) {
@@ -233,19 +235,19 @@ __device__ void wall_at(const Geom& g, const PhysDev& ph, const T* phi, const T*
             gs += gt * gt;
             gf += gtf * gtf;
         }
-        const T muw = (T)(ph.mu1 - ph.mu2) * pb + (T)ph.mu2;
+        const T muw = Q.dmu * pb + Q.mu2;
         T uY = T(0), lw = T(0);
         if (!wp.noslip) {
-            const T beta = (T)(wp.beta1 - wp.beta2) * pb + (T)wp.beta2;  // beta linear in phi
-            uY = slip_model<T>(ph.model, (T)ph.sigma, (T)ph.eps, beta, (T)wp.costh, P, dnb, dtau, sqrt(gs), dnphi,
-                               dtphi, sqrt(gf), kb, psb);
+            const T beta = Q.dbeta[s] * pb + Q.beta2[s];  // beta linear in phi
+            uY = slip_model<T>(ph.model, Q.sigma, Q.eps, beta, Q.costh[s], P, dnb, dtau, sqrt(gs), dnphi, dtphi,
+                               sqrt(gf), kb, psb);
             lw = muw / beta;
         }
         const long cq = (DIM == 2) ? encode(g, i, r0, 0) : encode(g, i, j, r0);
         const T uf = (a == 0) ? L::ld(u0 + cq) : L::ld(u1 + cq);
         // ghost value: u_w = (u0+ug)/2, d_n u = (u0-ug)/h, u_w - U = l_w d_n u + u^Y
         const T lwh = lw * ih;
-        const T ug = ((T)wp.U[a] + uY - uf * (T(0.5) - lwh)) / (T(0.5) + lwh);
+        const T ug = (Q.U[s][a] + uY - uf * (T(0.5) - lwh)) / (T(0.5) + lwh);
         const long o = ((long)s * (DIM - 1) + a) * g.NP + pidx;
         wuY[o] = uY;
         wghost[o] = ug;
@@ -271,9 +273,10 @@ __device__ __forceinline__ void phi_rhs_at(const Geom& g, const PhysDev& ph, con
                                            long c) {
     const IJK q = decode(g, c);
     const int W = DIM - 1;
-    const T ih = T(1) / (T)g.h;
-    const T eps = (T)ph.eps, delta = (T)ph.delta;
-    const T drho = (T)(ph.rho1 - ph.rho2), rho2 = (T)ph.rho2;
+    const T ih = g_ih<T>(g);
+    const PhysT<T>& Q = phys<T>(ph);
+    const T eps = Q.eps, delta = Q.delta;
+    const T drho = Q.drho, rho2 = Q.rho2;
     T div = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -304,8 +307,8 @@ template <class L, typename T, int DIM>
 __device__ void mom_at(const Geom& g, const PhysDev& ph, const StageFields<T>& f, long c) {
     const IJK q = decode(g, c);
     const int W = DIM - 1, nW = g.n[W];
-    const T ih = T(1) / (T)g.h;
-    const T dmu = (T)(ph.mu1 - ph.mu2), mu2 = (T)ph.mu2;
+    const T ih = g_ih<T>(g);
+    const T dmu = phys<T>(ph).dmu, mu2 = phys<T>(ph).mu2;
     const T* phi = f.phi;
     auto mu = [&](long cc) { return dmu * L::ld(phi + cc) + mu2; };
     const long pidx = (DIM == 2) ? (long)q.i : (long)q.i + (long)g.n[0] * q.j;
@@ -386,7 +389,7 @@ __device__ __forceinline__ void stage_mom_at(const Geom& g, const PhysDev& ph, T
                                              T* const* acc, T* const* uk, long c) {
     const IJK q = decode(g, c);
     const int W = DIM - 1;
-    const T drho = (T)(ph.rho1 - ph.rho2), rho2 = (T)ph.rho2;
+    const T drho = phys<T>(ph).drho, rho2 = phys<T>(ph).rho2;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         if (a == W && coord(q, W) == 0) { uk[a][c] = T(0); acc[a][c] = T(0); continue; }
@@ -405,48 +408,51 @@ __device__ __forceinline__ void stage_mom_at(const Geom& g, const PhysDev& ph, T
 // ---------------------------------------------------------------------------
 // a6..a8: projection and multigrid
 //
-// The pressure solve is FP64 defect correction around an FP32 V-cycle: the
-// residual r = f - A p, its norm and the update p += e are FP64; the V-cycle
-// that computes the correction e ~ A^-1 r runs in FP32 (M = float), except
-// the dense solve of the coarsest level, which is FP64.  The iteration
-// converges to the FP64 tolerance because each V-cycle only has to reduce the
-// error by a fixed factor.
+// The pressure solve is defect correction around an FP32 V-cycle: the
+// residual r = f - A p, its norm and the update p += e are taken in the
+// precision of the form (FP64; or double-float in the FP32-mixed form, see
+// PForm), while the V-cycle that computes the correction e ~ A^-1 r runs in
+// FP32 (M = float), except the dense solve of the coarsest level, which is
+// FP64.  The iteration converges to a tolerance far below FP32 round-off
+// because each V-cycle only has to reduce the error by a fixed factor.
 // ---------------------------------------------------------------------------
 template <class L, typename T, int DIM>
-__device__ __forceinline__ double div_at(const Geom& g, const T* const* us, double ih, double inv_cdt, long c) {
+__device__ __forceinline__ T div_at(const Geom& g, const T* const* us, T ih, T inv_cdt, long c) {
     const IJK q = decode(g, c);
-    double div = 0.0;
+    T div = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         const long hi = (a == DIM - 1) ? c + g.NP : idx(g, shift(g, q, a, 1));
-        div += (double)L::ld(us[a] + hi) - (double)L::ld(us[a] + c);
+        div += L::ld(us[a] + hi) - L::ld(us[a] + c);
     }
     return div * ih * inv_cdt;
 }
 
-// face coefficients 1/rho_f of level 0 in FP64 (bs) and FP32 (bsf); t in
-// [0, N + NP) (the last NP are the high wall faces of the wall-normal component)
+// face coefficients 1/rho_f of level 0: FP32 (bsf) in both forms, and FP64
+// (bs) in the FP64 form, where bsf is the rounded FP64 value; t in [0, N + NP)
+// (the last NP are the high wall faces of the wall-normal component)
 template <class L, typename T, int DIM>
-__device__ __forceinline__ void coef0_at(const Geom& g, double rho1, double rho2, const T* phi, double* const* bs,
+__device__ __forceinline__ void coef0_at(const Geom& g, const PhysDev& ph, const T* phi, double* const* bs,
                                          float* const* bsf, long t) {
+    constexpr bool f64 = sizeof(T) == 8;
     if (t >= g.N) {
-        bs[DIM - 1][t] = 0.0;
+        if (f64) bs[DIM - 1][t] = 0.0;
         bsf[DIM - 1][t] = 0.f;
         return;
     }
     const IJK q = decode(g, t);
-    const double dr = rho1 - rho2;
+    const T dr = phys<T>(ph).drho, rho2 = phys<T>(ph).rho2;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         if (a == DIM - 1 && coord(q, a) == 0) {
-            bs[a][t] = 0.0;
+            if (f64) bs[a][t] = 0.0;
             bsf[a][t] = 0.f;
             continue;
         }
         const long cL = idx(g, shift(g, q, a, -1));
-        const double rf = 0.5 * ((dr * (double)L::ld(phi + cL) + rho2) + (dr * (double)L::ld(phi + t) + rho2));
-        const double b = 1.0 / rf;
-        bs[a][t] = b;
+        const T rf = T(0.5) * ((dr * L::ld(phi + cL) + rho2) + (dr * L::ld(phi + t) + rho2));
+        const T b = T(1) / rf;
+        if (f64) bs[a][t] = (double)b;
         bsf[a][t] = (float)b;
     }
 }
@@ -525,7 +531,7 @@ __device__ __forceinline__ long colour_cell(const Geom& g, int colour, long k) {
 template <class L, typename M, int DIM>
 __device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* p, const M* f, long c) {
     const IJK q = decode(g, c);
-    const M ih2 = M(1) / M(g.h * g.h);
+    const M ih2 = g_ih2<M>(g);
     M diag, off;
     apply_L<L, M, DIM>(g, beta, p, q, c, ih2, diag, off);
     p[c] = (off - L::ld(f + c)) / diag;
@@ -536,17 +542,163 @@ template <class L, int DIM>
 __device__ __forceinline__ double resid64_at(const Geom& g, const double* const* beta, const double* p,
                                              const double* f, long c) {
     const IJK q = decode(g, c);
-    const double ih2 = 1.0 / (g.h * g.h);
+    const double ih2 = g.ih2;
     double diag, off;
     return L::ld(f + c) - apply_L<L, double, DIM>(g, beta, p, q, c, ih2, diag, off);
 }
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic of the FP32-mixed form: a value is hi + lo with
+// |lo| at most half an ulp of hi.  Built from error-free transformations:
+// TwoSum (Knuth, TAOCP vol. 2, sec. 4.2.2: s + e = a + b exactly) and the
+// product error by one FMA (a b - fl(a b) is exact in FP32).  The __f*_rn
+// intrinsics keep the compiler from contracting or reordering them.
+// ---------------------------------------------------------------------------
+namespace dfl {
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// renormalised (hi, lo) of s + e
+__device__ __forceinline__ float2 norm2(float s, float e) {
+    float hi, lo;
+    two_sum(s, e, hi, lo);
+    return make_float2(hi, lo);
+}
+// a + x
+__device__ __forceinline__ float2 add(float2 a, float x) {
+    float s, e;
+    two_sum(a.x, x, s, e);
+    return norm2(s, __fadd_rn(e, a.y));
+}
+// a + b
+__device__ __forceinline__ float2 add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return norm2(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+// a - b
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return add(a, make_float2(-b.x, -b.y)); }
+// the double-float nearest a double (host and device; the device use is per thread, not per cell)
+__host__ __device__ __forceinline__ float2 from_double(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+__host__ __device__ __forceinline__ double to_double(float2 a) { return (double)a.x + (double)a.y; }
+}  // namespace dfl
+
+// Running sum of a form's values, accurate enough that the mean of f it
+// yields leaves no constant component in the residual: FP64, or double-float
+// for FP32 values.
+template <typename T> struct SumAcc;
+template <> struct SumAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct SumAcc<float> {
+    float2 s = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float v) { s = dfl::add(s, v); }
+    __device__ __forceinline__ double value() const { return dfl::to_double(s); }
+};
+
+// S += b (x - y) for double-floats x, y, an FP32 coefficient b and the
+// double-float accumulator (Sh, Sl)
+__device__ __forceinline__ void df_acc_term(float b, float2 x, float2 y, float& Sh, float& Sl) {
+    float d, de;
+    dfl::two_sum(x.x, -y.x, d, de);
+    const float dl = __fadd_rn(de, __fsub_rn(x.y, y.y));
+    float t, te;
+    dfl::two_prod(b, d, t, te);
+    te = __fmaf_rn(b, dl, te);
+    float s2, se;
+    dfl::two_sum(Sh, t, s2, se);
+    Sh = s2;
+    Sl = __fadd_rn(Sl, __fadd_rn(se, te));
+}
+
+// Residual (f - mean) - A p of the FP32-mixed form at cell c, with the FP32
+// face coefficients bf and 1/h^2 of the V-cycles, accumulated in double-float
+// (error about 2^-44 of the largest flux term, far below any tolerance a
+// solve asks for); returned rounded to FP32.  Same stencil as apply_L.
+template <class L, int DIM>
+__device__ __forceinline__ float resid_df_at(const Geom& g, const float* const* bf, const float2* p, const float* f,
+                                             float2 fmean, long c) {
+    const IJK q = decode(g, c);
+    const float2 pc = L::ld(p + c);
+    float Sh = 0.f, Sl = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        long lo, hi;
+        if (a == DIM - 1) {
+            const int r = coord(q, a);
+            lo = r > 0 ? c - g.NP : c;
+            hi = r < g.n[a] - 1 ? c + g.NP : c;
+        } else {
+            lo = idx(g, shift(g, q, a, -1));
+            hi = idx(g, shift(g, q, a, 1));
+        }
+        const long fhi = (a == DIM - 1) ? c + g.NP : hi;
+        const float bm = L::ld(bf[a] + c);
+        const float bp = L::ld(bf[a] + fhi);
+        df_acc_term(bm, L::ld(p + lo), pc, Sh, Sl);
+        df_acc_term(bp, L::ld(p + hi), pc, Sh, Sl);
+    }
+    float ah, al;
+    dfl::two_prod(Sh, g.ih2f, ah, al);
+    al = __fmaf_rn(Sl, g.ih2f, al);
+    float r1, e1, r2, e2;
+    dfl::two_sum(L::ld(f + c), -fmean.x, r1, e1);
+    dfl::two_sum(r1, -ah, r2, e2);
+    return __fadd_rn(r2, __fadd_rn(__fsub_rn(e1, fmean.y), __fsub_rn(e2, al)));
+}
+
+// level-0 residual of either form (fmean: the mean of f, FP32-mixed form only)
+template <class L, int DIM>
+__device__ __forceinline__ double resid_form_at(const MGLevel& L0, const double* p, const double* f, float2, long c) {
+    const double* b[3] = {L0.beta[0], L0.beta[1], L0.beta[2]};
+    return resid64_at<L, DIM>(L0.g, b, p, f, c);
+}
+template <class L, int DIM>
+__device__ __forceinline__ float resid_form_at(const MGLevel& L0, const float2* p, const float* f, float2 fmean,
+                                               long c) {
+    const float* b[3] = {L0.bf[0], L0.bf[1], L0.bf[2]};
+    return resid_df_at<L, DIM>(L0.g, b, p, f, fmean, c);
+}
+
+// typed views of the level-0 pressure and right-hand side
+template <typename T>
+__host__ __device__ __forceinline__ PT<T>* pbuf(const MGLevel& L0) { return reinterpret_cast<PT<T>*>(L0.p); }
+template <typename T>
+__host__ __device__ __forceinline__ FT<T>* fbuf(const MGLevel& L0) { return reinterpret_cast<FT<T>*>(L0.f); }
+
+// pressure updates of either form
+__device__ __forceinline__ double p_add(double p, float e) { return p + (double)e; }
+__device__ __forceinline__ float2 p_add(float2 p, float e) { return dfl::add(p, e); }
+__device__ __forceinline__ double p_sub(double p, double m, float2) { return p - m; }
+__device__ __forceinline__ float2 p_sub(float2 p, double, float2 m) { return dfl::sub(p, m); }
+__device__ __forceinline__ double p_extrap(double pn, double po) { return 2.0 * pn - po; }
+__device__ __forceinline__ float2 p_extrap(float2 pn, float2 po) {
+    return dfl::sub(make_float2(2.f * pn.x, 2.f * pn.y), po);
+}
+template <typename T> __device__ __forceinline__ PT<T> p_zero();
+template <> __device__ __forceinline__ double p_zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float2 p_zero<float>() { return make_float2(0.f, 0.f); }
+// difference of two pressures in the arithmetic type of the form
+__device__ __forceinline__ double p_diff(double a, double b) { return a - b; }
+__device__ __forceinline__ float p_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
 
 // coarse cell t: mean of the 2^D fine residuals; zero coarse correction
 template <class L, typename M, int DIM>
 __device__ __forceinline__ void resid_restrict_at(const Geom& gf, const Geom& gc, const M* const* beta, const M* p,
                                                   const M* f, M* fc, M* pc, long t) {
     const IJK Q = decode(gc, t);
-    const M ih2 = M(1) / M(gf.h * gf.h);
+    const M ih2 = g_ih2<M>(gf);
     const int o2 = (DIM == 3) ? 2 : 1;
     M s = M(0);
     for (int t2 = 0; t2 < o2; ++t2)
@@ -603,18 +755,18 @@ __device__ __forceinline__ void prolong_at(const Geom& gf, const Geom& gc, const
 
 // u = u* - c dt grad p / rho_f on the interior faces of cell c
 template <class L, typename T, int DIM>
-__device__ __forceinline__ void project_at(const Geom& g, double rho1, double rho2, const T* phi, T* const* us,
-                                           double cdt, const double* p, long c) {
+__device__ __forceinline__ void project_at(const Geom& g, const PhysDev& ph, const T* phi, T* const* us, T cdt,
+                                           const PT<T>* p, long c) {
     const IJK q = decode(g, c);
-    const double ih = 1.0 / g.h, dr = rho1 - rho2;
+    const T ih = g_ih<T>(g), dr = phys<T>(ph).drho, rho2 = phys<T>(ph).rho2;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         if (a == DIM - 1 && coord(q, a) == 0) continue;  // wall face stays zero
         const long cL = idx(g, shift(g, q, a, -1));
-        const double rf = 0.5 * ((dr * (double)L::ld(phi + cL) + rho2) + (dr * (double)L::ld(phi + c) + rho2));
-        const double beta = 1.0 / rf;
-        const double dp = (L::ld(p + c) - L::ld(p + cL)) * ih;
-        us[a][c] = (T)((double)L::ld(us[a] + c) - cdt * beta * dp);
+        const T rf = T(0.5) * ((dr * L::ld(phi + cL) + rho2) + (dr * L::ld(phi + c) + rho2));
+        const T beta = T(1) / rf;
+        const T dp = p_diff(L::ld(p + c), L::ld(p + cL)) * ih;
+        us[a][c] = L::ld(us[a] + c) - cdt * beta * dp;
     }
 }
 

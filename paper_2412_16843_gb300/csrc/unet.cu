@@ -14,6 +14,7 @@
 // masks, the mean-squared-error loss and Adam are elementwise kernels.
 // Master weights and Adam moments are FP32; the tensor cores see BF16 copies.
 #include "unet.cuh"
+#include "ops.cuh"
 #include "../../include/cdi.h"
 
 #include <cuda_bf16.h>
@@ -321,26 +322,40 @@ __global__ void k_input_dev(int N, const float* x2, bf16* x) {  // x2: [N][2] on
     x[t] = __float2bfloat16(c < 2 ? x2[(size_t)v * 2 + c] : 0.f);
 }
 
+// scales of one prediction from ||f||_2 (one thread): sd = {1/rms(f), rms(f) max(rho) h^2}
+// in FP64 and sf the same in FP32; a zero right-hand side gives a zero guess
+__global__ void k_solver_scales(const double* fnorm, int N, double rho_h2, double* sd, float* sf) {
+    const double rms = *fnorm / sqrt((double)N);
+    sd[0] = rms > 0.0 ? 1.0 / rms : 0.0;
+    sd[1] = rms * rho_h2;
+    sf[0] = (float)sd[0];
+    sf[1] = (float)sd[1];
+}
+
+// network input from the solver's f (its mean already removed in the FP64
+// form; removed here with the double-float mean in the FP32-mixed form) and phi
 template <typename T>
-__global__ void k_input_solver(int N, const double* f, const T* phi, double rho1, double rho2, const double* fnorm,
-                               bf16* x) {
+__global__ void k_input_solver(int N, const FT<T>* f, const float* fmean_df, const T* phi, float drho, float rho2,
+                               float inv_rmax, const double* sd, const float* sf, bf16* x) {
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long)N * 16) return;
     const int c = (int)(t % 16), v = (int)(t / 16);
     float val = 0.f;
     if (c == 0) {
-        const double fr = *fnorm / sqrt((double)N);
-        val = fr > 0.0 ? (float)(f[v] / fr) : 0.f;
+        if constexpr (sizeof(T) == 8) val = (float)(f[v] * sd[0]);
+        else val = ((f[v] - fmean_df[0]) - fmean_df[1]) * sf[0];
     } else if (c == 1) {
-        val = (float)(((rho1 - rho2) * (double)phi[v] + rho2) / fmax(rho1, rho2));
+        val = (drho * (float)phi[v] + rho2) * inv_rmax;
     }
     x[t] = __float2bfloat16(val);
 }
 
-__global__ void k_output_solver(int N, const float* y, const double* fnorm, double scale, double* p) {
+template <typename T>
+__global__ void k_output_solver(int N, const float* y, const double* sd, const float* sf, PT<T>* p) {
     const long v = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= N) return;
-    p[v] = (double)y[v] * (*fnorm / sqrt((double)N)) * scale;
+    if constexpr (sizeof(T) == 8) p[v] = (double)y[v] * sd[1];
+    else p[v] = make_float2(y[v] * sf[1], 0.f);
 }
 
 unsigned blocks(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -366,6 +381,8 @@ struct cdi_unet {
     bf16 *gy, *gd0, *gc0, *gd1, *gc1, *gd2, *gc2, *gb, *gp2, *ge2, *gp1, *ge1, *gp0, *ge0;
     float *y, *t, *part;
     double* x2;  // host-input staging [N][2]
+    double* sd;  // prediction scales (FP64 and FP32 copies)
+    float* sf;
     long adam_t = 0;
     bool weights_ready = false;
     std::string err;
@@ -443,6 +460,8 @@ void unet_carve(cdi_unet* u, char* base, size_t* total) {
     u->y = (float*)cv.take((size_t)N0 * 4);
     u->t = (float*)cv.take((size_t)N0 * 4);
     u->part = (float*)cv.take(256);
+    u->sd = (double*)cv.take(4 * sizeof(double));
+    u->sf = (float*)cv.take(4 * sizeof(float));
     u->x2 = (double*)cv.take((size_t)N0 * 2 * 8);
     *total = cv.off + 256;
 }
@@ -633,16 +652,20 @@ cdi_status upload_x(cdi_unet* u, const double* x_host) {
 namespace cdi {
 
 template <typename T>
-cudaError_t unet_predict_device(cdi_unet* u, const double* f_dev, const T* phi_dev, double rho1, double rho2,
-                                const double* fnorm_dev, double h, double* p_dev, cudaStream_t s) {
+cudaError_t unet_predict_device(cdi_unet* u, const MG& mg, const T* phi_dev, double rho1, double rho2, double h,
+                                cudaStream_t s) {
     cudaStream_t keep = u->stream;
     u->stream = s;
     if (!u->weights_ready) refresh_weights(u);
     const long N = u->g[0].N;
-    k_input_solver<T><<<blocks(N * 16), 256, 0, s>>>((int)N, f_dev, phi_dev, rho1, rho2, fnorm_dev, u->x);
+    const double rmax = fmax(rho1, rho2);
+    k_solver_scales<<<1, 1, 0, s>>>(mg.scal + S_FNORM, (int)N, rmax * h * h, u->sd, u->sf);
+    k_input_solver<T><<<blocks(N * 16), 256, 0, s>>>((int)N, ops::fbuf<T>(mg.lv[0]), mg.scalf + SF_FMEAN_HI,
+                                                     phi_dev, (float)(rho1 - rho2), (float)rho2, (float)(1.0 / rmax),
+                                                     u->sd, u->sf, u->x);
     forward(u);
-    k_output_solver<<<blocks(N), 256, 0, s>>>((int)N, u->y, fnorm_dev, fmax(rho1, rho2) * h * h, p_dev);
-    g_launches += 2;
+    k_output_solver<T><<<blocks(N), 256, 0, s>>>((int)N, u->y, u->sd, u->sf, ops::pbuf<T>(mg.lv[0]));
+    g_launches += 3;
     u->stream = keep;
     return cudaGetLastError();
 }
@@ -653,10 +676,10 @@ void unet_extents(const cdi_unet* u, int* n) {
     n[2] = u->n[2];
 }
 
-template cudaError_t unet_predict_device<double>(cdi_unet*, const double*, const double*, double, double,
-                                                 const double*, double, double*, cudaStream_t);
-template cudaError_t unet_predict_device<float>(cdi_unet*, const double*, const float*, double, double, const double*,
-                                                double, double*, cudaStream_t);
+template cudaError_t unet_predict_device<double>(cdi_unet*, const MG&, const double*, double, double, double,
+                                                 cudaStream_t);
+template cudaError_t unet_predict_device<float>(cdi_unet*, const MG&, const float*, double, double, double,
+                                                cudaStream_t);
 
 }  // namespace cdi
 
