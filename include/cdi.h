@@ -64,10 +64,10 @@ typedef enum {
 
 enum { CDI_FP64 = 0, CDI_FP32_MIXED = 1 };
 enum { CDI_WALL_LO = 0, CDI_WALL_HI = 1, CDI_WALL_BOTH = 2 };
-/* first guess of each pressure solve: the last solve's pressure, zero,
- * (persistent and batched execution) the same RK stage of the two previous
- * steps extrapolated linearly in time, or the prediction of the network
- * attached with cdi_set_warm_unet (launch-per-kernel execution) */
+/* first guess of each pressure solve: the last solve's pressure, zero, the
+ * same RK stage of the two previous steps extrapolated linearly in time, or
+ * the prediction of the network attached with cdi_set_warm_unet
+ * (launch-per-kernel execution) */
 enum { CDI_WARM_PREV = 0, CDI_WARM_ZERO = 1, CDI_WARM_EXTRAP = 2, CDI_WARM_UNET = 3 };
 /* how cdi_step runs: one persistent cooperative launch per call, one launch
  * per stencil / multigrid kernel with host-side convergence tests, or
@@ -137,10 +137,9 @@ cdi_status cdi_set_velocity(cdi_ctx* ctx, const double* u, const double* v,
 
 /* Pressure solve controls: relative residual tolerance ||f - A p||_2 <=
  * tol ||f||_2, cap on V-cycles per solve, and the first guess
- * (CDI_WARM_PREV, CDI_WARM_ZERO or CDI_WARM_EXTRAP; the launch-per-kernel
- * execution treats CDI_WARM_EXTRAP as CDI_WARM_PREV).  Setting the state
- * (cdi_set_phi, cdi_set_velocity) or the solver restarts the extrapolation
- * history. */
+ * (CDI_WARM_PREV, CDI_WARM_ZERO, CDI_WARM_EXTRAP or CDI_WARM_UNET).  Setting
+ * the state (cdi_set_phi, cdi_set_velocity) or the solver restarts the
+ * extrapolation history. */
 cdi_status cdi_set_solver(cdi_ctx* ctx, double tol, int max_vcycles, int warm);
 
 /* Advance nsteps RK4 steps of size dt (Sec. 4): each stage evaluates the phi

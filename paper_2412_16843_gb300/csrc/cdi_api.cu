@@ -69,6 +69,8 @@ struct cdi_ctx {
     int exec = CDI_EXEC_AUTO;
     PersistCtl* ctl = nullptr;
     bool persist_ready = false;
+    void* tail_dev = nullptr;  // launch-per-kernel path: descriptor of the V-cycle's shared-memory tail
+    bool tail_ready = false;
     PersistLayout playout{};
     int persist_lt = 0;
     size_t persist_smem = 0;
@@ -152,9 +154,11 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
             for (int a = 0; a < 3; ++a)
                 L.beta[a] = (f64 && a < g.D) ? (double*)cv.take((nl + (a == g.W ? np : 0)) * sizeof(double))
                                              : nullptr;
+            L.rho0 = (float*)cv.take(nl * sizeof(float));
         } else {
             L.p = nullptr;
             L.f = nullptr;
+            L.rho0 = nullptr;
             for (int a = 0; a < 3; ++a) L.beta[a] = nullptr;
         }
         L.e = (float*)cv.take(nl * sizeof(float));
@@ -166,6 +170,7 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     mg.scal = (double*)cv.take(S_NSCAL * sizeof(double));
     mg.scalf = (float*)cv.take(SF_NSCAL * sizeof(float));
     c->ctl = (PersistCtl*)cv.take(sizeof(PersistCtl));
+    c->tail_dev = cv.take(sizeof(InstArgs<float>));
     for (int k = 0; k < 4; ++k)
         for (int j = 0; j < 2; ++j) c->hist[k][j] = (double*)cv.take((size_t)g.N * sizeof(double));
     *total = cv.off + 256;
@@ -271,11 +276,53 @@ cdi_status need_bound(cdi_ctx* c) {
 
 // Multigrid solve of div(beta grad p) = f on level 0 (f already mean-free,
 // its norm in S_FNORM, coefficients set); p holds the first guess.
+size_t pick_tail(const cdi_ctx* c, size_t budget, int* lt_out, PersistLayout* L);
+cdi_status smem_optin(cdi_ctx* c, size_t* bytes);
+
+// Launch-per-kernel path: the coarse levels of every V-cycle that fit in one
+// CTA's shared memory run as a single launch (k_tail) instead of one launch
+// per sweep; set up once per bound workspace.
+cdi_status kernels_tail_setup(cdi_ctx* c) {
+    if (c->tail_ready) return CDI_OK;
+    size_t optin = 0;
+    cdi_status st = smem_optin(c, &optin);
+    if (st) return st;
+    const size_t budget = optin > 8192 ? optin - 4096 : 0;
+    int lt = 0;
+    PersistLayout lay{};
+    const size_t sm = pick_tail(c, budget, &lt, &lay);
+    c->mg.tail_args = nullptr;
+    if (sm <= budget) {
+        InstArgs<float> A{};
+        static_cast<PersistLayout&>(A) = lay;
+        A.g = c->g;
+        for (int l = 0; l < kMaxLevels; ++l) A.lv[l] = c->mg.lv[l];
+        A.nlev = c->mg.nlev;
+        A.lt = lt;
+        A.npre = c->npre;
+        A.npost = c->npost;
+        st = cuda_check(c, cudaMemcpyAsync(c->tail_dev, &A, sizeof A, cudaMemcpyHostToDevice, c->stream),
+                        "cudaMemcpyAsync(tail)");
+        if (st) return st;
+        st = cuda_check(c, cudaStreamSynchronize(c->stream), "tail setup");
+        if (st) return st;
+        st = cuda_check(c, tail_prepare(c->g.D, sm), "tail kernel setup");
+        if (st) return st;
+        c->mg.tail_args = c->tail_dev;
+        c->mg.tail_lt = lt;
+        c->mg.tail_smem = sm;
+    }
+    c->tail_ready = true;
+    return CDI_OK;
+}
+
 template <typename T>
 cdi_status mg_solve(cdi_ctx* c) {
     const Geom& g = c->g;
     cudaStream_t s = c->stream;
     MG& mg = c->mg;
+    cdi_status st0 = kernels_tail_setup(c);
+    if (st0) return st0;
     launch_resid_norm<T>(g, mg, s);
     cdi_status st = read_scalars(c);
     if (st) return st;
@@ -313,20 +360,30 @@ cdi_status mg_solve(cdi_ctx* c) {
 }
 
 template <typename T>
-cdi_status project(cdi_ctx* c, const T* phi, T* const* u, double cdt) {
+cdi_status project(cdi_ctx* c, const T* phi, T* const* u, double cdt, int stage) {
     const Geom& g = c->g;
     cudaStream_t s = c->stream;
     const T* uc[3] = {u[0], u[1], u[2]};
     launch_div<T>(g, uc, 1.0 / cdt, c->mg, s);
     launch_sub_mean_and_norm<T>(g, c->mg, s);
     launch_mg_coef<T>(g, c->ph, phi, c->mg, s);
+    // first guess: zero, the last solve's pressure, the same RK stage of the
+    // last two steps extrapolated linearly in time, or the network's prediction
+    const bool extrap = c->warm == CDI_WARM_EXTRAP;
+    const long sg = c->hist_steps;
     if (c->warm == CDI_WARM_ZERO) cudaMemsetAsync(c->mg.lv[0].p, 0, g.N * sizeof(double), s);
+    if (extrap && sg >= 2) launch_p_extrap<T>(g, c->mg, c->hist[stage][(sg - 1) & 1], c->hist[stage][sg & 1], s);
     if (c->warm == CDI_WARM_UNET) {
         const cudaError_t e = unet_predict_device<T>(c->unet, c->mg, phi, c->ph.rho1, c->ph.rho2, c->g.h, s);
         if (e != cudaSuccess) return cuda_check(c, e, "network first guess");
     }
     cdi_status st = mg_solve<T>(c);
     if (st) return st;
+    if (extrap) {
+        st = cuda_check(c, cudaMemcpyAsync(c->hist[stage][sg & 1], c->mg.lv[0].p, g.N * sizeof(double),
+                                           cudaMemcpyDeviceToDevice, s), "cudaMemcpyAsync(history)");
+        if (st) return st;
+    }
     launch_project<T>(g, c->ph, phi, u, cdt, c->mg.lv[0].p, s);
     return CDI_OK;
 }
@@ -381,9 +438,10 @@ cdi_status step_once(cdi_ctx* c, double dt) {
         launch_stage_update<T>(g, c->ph, st, dt, (const T*)c->phi_s, u0, (const T*)c->rphi, rmc, (T*)c->acc_phi, accm,
                                (T*)c->phi_k, uk, s);
         const double cdt = (st == 3 ? 1.0 : ck[st + 1]) * dt;
-        cdi_status stt = project<T>(c, (const T*)c->phi_k, uk, cdt);
+        cdi_status stt = project<T>(c, (const T*)c->phi_k, uk, cdt, st);
         if (stt) return stt;
     }
+    ++c->hist_steps;
     std::swap(c->phi_s, c->phi_k);
     for (int a = 0; a < 3; ++a) std::swap(c->u_s[a], c->u_k[a]);
     return cuda_check(c, cudaGetLastError(), "kernel launch");
@@ -613,6 +671,8 @@ cdi_status cdi_bind_workspace(cdi_ctx* c, void* dev_ptr, size_t bytes, void* str
     c->stream = (cudaStream_t)stream;
     size_t total = 0;
     carve(c, c->ws, &total);
+    c->mg.tail_args = nullptr;
+    c->tail_ready = false;
     if (!c->host_scal) {
         cdi_status st = cuda_check(c, cudaMallocHost((void**)&c->host_scal, S_NSCAL * sizeof(double)),
                                    "cudaMallocHost");

@@ -217,6 +217,7 @@ struct MGLevel {
     double* p;         // level 0 only (8 bytes per cell, typed by PForm)
     double* f;         // level 0 only (8 bytes per cell, typed by PForm)
     double* beta[3];   // level 0 only, FP64 form
+    float* rho0;       // level 0 only: FP32 cell densities (the level-0 smoother's coefficients)
     float* e;
     float* r;
     float* bf[3];
@@ -228,6 +229,12 @@ struct MG {
     double* partials;   // [2 * kPartials]
     double* scal;       // device scalars
     float* scalf;       // FP32 device scalars
+    // launch-per-kernel path: levels tail_lt .. nlev-1 of a V-cycle run as one
+    // single-CTA launch in shared memory (tail_args: its descriptor in device
+    // memory, an InstArgs<float>; null: every level as separate kernels)
+    const void* tail_args;
+    int tail_lt;
+    size_t tail_smem;
 };
 
 // scalar slots in MG::scal
@@ -265,6 +272,12 @@ template <typename T>
 void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s);  // FP32 V-cycle, p += e0
 template <typename T>
 void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s);
+// p = 2 hnew - hold (extrapolated first guess; history arrays in the form's p storage)
+template <typename T>
+void launch_p_extrap(const Geom& g, MG& mg, const double* hnew, const double* hold, cudaStream_t s);
+// the single-CTA shared-memory tail of a V-cycle as its own launch (k_persist.cu)
+cudaError_t tail_prepare(int dim, size_t smem);
+cudaError_t launch_tail(const void* inst_args, int dim, size_t smem, cudaStream_t s);
 // host <-> level-0 p / f conversions of the FP32-mixed form (FP64 staging buffer x)
 void launch_p_to_double(const Geom& g, const MG& mg, double* x, cudaStream_t s);
 void launch_p_from_double(const Geom& g, MG& mg, const double* x, cudaStream_t s);

@@ -24,6 +24,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <unordered_map>
 
 namespace cdi {
 
@@ -32,8 +34,31 @@ namespace {
 constexpr int kThreads = 256;
 using Ld = ops::LdPlain;
 inline unsigned blocks_for(long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
-inline unsigned red_blocks(long n) {
-    return (unsigned)std::max(1L, std::min((long)kPartials, (n + kThreads - 1) / kThreads));
+// Grid of a grid-stride reduction kernel: at most kPartials blocks, at most one
+// cell per thread, and no more blocks than the device holds at once (a second,
+// partial wave would leave most SMs idle while it runs).  The grid depends only
+// on the kernel and the device, so every sum keeps its fixed order.
+unsigned red_blocks(const void* kernel, long n) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, long> resident;
+    long res;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = resident.find(kernel);
+        if (it == resident.end()) {
+            int dev = 0, nsm = 0, per = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, 0) != cudaSuccess) {
+                cudaGetLastError();
+                nsm = 1;
+                per = kPartials;
+            }
+            it = resident.emplace(kernel, std::max(1L, (long)nsm * per)).first;
+        }
+        res = it->second;
+    }
+    return (unsigned)std::max(1L, std::min({(long)kPartials, res, (n + kThreads - 1) / kThreads}));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -134,11 +159,11 @@ __global__ void k_fnorm_df(long N, const float* f, const float* mean_df, double*
 
 template <typename T, int DIM>
 __global__ void k_coef0(Geom g, PhysDev ph, const T* phi, double* b0, double* b1, double* b2, float* f0, float* f1,
-                        float* f2) {
+                        float* f2, float* rho0) {
     double* bs[3] = {b0, b1, b2};
     float* bf[3] = {f0, f1, f2};
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < g.N + g.NP) ops::coef0_at<Ld, T, DIM>(g, ph, phi, bs, bf, t);
+    if (t < g.N + g.NP) ops::coef0_at<Ld, T, DIM>(g, ph, phi, bs, bf, rho0, t);
 }
 
 template <int DIM>
@@ -173,6 +198,71 @@ __global__ void k_rbgs(Geom g, const float* b0, const float* b1, const float* b2
     const float* beta[3] = {b0, b1, b2};
     long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < g.N / 2) ops::rbgs_at<Ld, float, DIM>(g, beta, e, r, ops::colour_cell(g, colour, k));
+}
+
+// Level-0 red-black sweep of one colour on a (x/2, y, z) thread grid: thread
+// (ix, j, k) updates cell i = 2 ix + ((colour + j + k) & 1) of row (j, k), so
+// no index is recovered by division.  Coefficients 2 / (rho_c + rho_nb) from
+// the FP32 cell densities, zero through the walls (the last axis); the update
+// e_c = (sum b e_nb - r h^2) / sum b is the Gauss-Seidel step of apply_L_rho.
+constexpr int kSweepX = 64, kSweepY = 4;
+template <int DIM>
+__global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float* __restrict__ rho,
+                                                             float* __restrict__ e, const float* __restrict__ r,
+                                                             int colour, float h2) {
+    const int nx = g.n[0], ny = g.n[1];
+    const int ix = blockIdx.x * kSweepX + threadIdx.x;
+    const int j = blockIdx.y * kSweepY + threadIdx.y;
+    const int k = (DIM == 3) ? (int)blockIdx.z : 0;
+    if (2 * ix >= nx || j >= ny) return;
+    const int i = 2 * ix + ((colour + j + k) & 1);
+    const long row = (long)nx * ((long)j + (long)ny * k);
+    const long c = row + i;
+    const float rc = rho[c];
+    const long xm = row + (i == 0 ? nx - 1 : i - 1), xp = row + (i == nx - 1 ? 0 : i + 1);
+    float bsum, off;
+    {
+        const float b0 = __fdividef(2.f, rc + rho[xm]), b1 = __fdividef(2.f, rc + rho[xp]);
+        bsum = b0 + b1;
+        off = b0 * e[xm] + b1 * e[xp];
+    }
+    if (DIM == 2) {  // y is the wall axis
+        if (j > 0) {
+            const float b = __fdividef(2.f, rc + rho[c - nx]);
+            bsum += b;
+            off += b * e[c - nx];
+        }
+        if (j < ny - 1) {
+            const float b = __fdividef(2.f, rc + rho[c + nx]);
+            bsum += b;
+            off += b * e[c + nx];
+        }
+    } else {
+        const long ym = (j == 0) ? c + (long)(ny - 1) * nx : c - nx;
+        const long yp = (j == ny - 1) ? c - (long)(ny - 1) * nx : c + nx;
+        const float b2 = __fdividef(2.f, rc + rho[ym]), b3 = __fdividef(2.f, rc + rho[yp]);
+        bsum += b2 + b3;
+        off += b2 * e[ym] + b3 * e[yp];
+        const long np = g.NP;
+        if (k > 0) {
+            const float b = __fdividef(2.f, rc + rho[c - np]);
+            bsum += b;
+            off += b * e[c - np];
+        }
+        if (k < g.n[2] - 1) {
+            const float b = __fdividef(2.f, rc + rho[c + np]);
+            bsum += b;
+            off += b * e[c + np];
+        }
+    }
+    e[c] = __fdividef(off - r[c] * h2, bsum);
+}
+
+template <int DIM>
+__global__ void k_resid_restrict0(Geom gf, Geom gc, const float* rho0, const float* e, const float* r, float* rc,
+                                  float* ec) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < gc.N) ops::resid_restrict_rho_at<Ld, DIM>(gf, gc, rho0, e, r, rc, ec, t);
 }
 
 template <int DIM>
@@ -230,6 +320,12 @@ __global__ void k_sub_mean_p(long N, PT<T>* p, const double* mean, const float* 
     if (c >= N) return;
     if constexpr (sizeof(T) == 8) p[c] = p[c] - *mean;
     else p[c] = ops::dfl::sub(p[c], make_float2(mean_df[0], mean_df[1]));
+}
+
+template <typename T>
+__global__ void k_p_extrap(long N, PT<T>* p, const PT<T>* hnew, const PT<T>* hold) {
+    long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < N) p[c] = ops::p_extrap(hnew[c], hold[c]);
 }
 
 // host-side conversions of the FP32-mixed level-0 arrays through an FP64 buffer
@@ -350,7 +446,7 @@ __global__ void k_contact_line(int D, int nx, int nlines, double h, const double
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_div(const Geom& g, const T* const* us, double inv_cdt, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.N);
+    const unsigned G = red_blocks(g.D == 2 ? (const void*)k_div<T, 2> : (const void*)k_div<T, 3>, g.N);
     const bool on = prof_before(KC_DIV, s);
     FT<T>* f = ops::fbuf<T>(mg.lv[0]);
     if (g.D == 2)
@@ -364,7 +460,7 @@ void launch_div(const Geom& g, const T* const* us, double inv_cdt, MG& mg, cudaS
 
 template <typename T>
 void launch_sum_f(const Geom& g, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.N);
+    const unsigned G = red_blocks((const void*)k_partial_sum<FT<T>>, g.N);
     k_partial_sum<FT<T>><<<G, kThreads, 0, s>>>(g.N, ops::fbuf<T>(mg.lv[0]), mg.partials);
     k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0 / (double)g.N, mg.scal + S_MEAN, 0);
     g_launches += 2;
@@ -374,7 +470,8 @@ void launch_sum_f(const Geom& g, MG& mg, cudaStream_t s) {
 // keeps a double-float copy of the mean for its residual; then ||f - mean||
 template <typename T>
 void launch_sub_mean_and_norm(const Geom& g, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.N);
+    const unsigned G =
+        red_blocks(sizeof(T) == 8 ? (const void*)k_sub_mean_sq : (const void*)k_fnorm_df, g.N);
     if constexpr (sizeof(T) == 8) {
         k_sub_mean_sq<<<G, kThreads, 0, s>>>(g.N, mg.lv[0].f, mg.scal + S_MEAN, mg.partials);
     } else {
@@ -391,10 +488,10 @@ void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cuda
     MGLevel& L0 = mg.lv[0];
     if (g.D == 2)
         k_coef0<T, 2><<<blocks_for(g.N + g.NP), kThreads, 0, s>>>(g, ph, phi, L0.beta[0], L0.beta[1],
-                                                                  nullptr, L0.bf[0], L0.bf[1], nullptr);
+                                                                  nullptr, L0.bf[0], L0.bf[1], nullptr, L0.rho0);
     else
         k_coef0<T, 3><<<blocks_for(g.N + g.NP), kThreads, 0, s>>>(g, ph, phi, L0.beta[0], L0.beta[1],
-                                                                  L0.beta[2], L0.bf[0], L0.bf[1], L0.bf[2]);
+                                                                  L0.beta[2], L0.bf[0], L0.bf[1], L0.bf[2], L0.rho0);
     ++g_launches;
     for (int l = 1; l < mg.nlev; ++l) {
         const MGLevel& F = mg.lv[l - 1];
@@ -411,6 +508,11 @@ void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cuda
 template <int DIM>
 static void vcycle_rec(MG& mg, int l, int npre, int npost, cudaStream_t s) {
     MGLevel& L = mg.lv[l];
+    if (mg.tail_args && l == mg.tail_lt) {
+        CDI_PROF(KC_COARSE, s, launch_tail(mg.tail_args, DIM, mg.tail_smem, s));
+        ++g_launches;
+        return;
+    }
     if (l == mg.nlev - 1) {
         CDI_PROF(KC_COARSE, s, (k_coarse<DIM><<<1, 64, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.r, L.e)));
         ++g_launches;
@@ -419,26 +521,35 @@ static void vcycle_rec(MG& mg, int l, int npre, int npost, cudaStream_t s) {
     const unsigned nb = blocks_for(L.g.N);
     const unsigned nbh = blocks_for(L.g.N / 2);
     const int kc_rbgs = (l == 0) ? KC_RBGS0 : KC_RBGS;
-    for (int it = 0; it < npre; ++it)
-        for (int col = 0; col < 2; ++col) {
+    // one red-black sweep; level 0 forms its coefficients from the cell densities
+    const dim3 sweep_grid((unsigned)((L.g.n[0] / 2 + kSweepX - 1) / kSweepX),
+                          (unsigned)((L.g.n[1] + kSweepY - 1) / kSweepY), (unsigned)(DIM == 3 ? L.g.n[2] : 1));
+    const float h2 = (float)(L.g.h * L.g.h);
+    auto sweep = [&](int col) {
+        if (l == 0)
+            CDI_PROF(kc_rbgs, s,
+                     (k_rbgs0<DIM><<<sweep_grid, dim3(kSweepX, kSweepY), 0, s>>>(L.g, L.rho0, L.e, L.r, col, h2)));
+        else
             CDI_PROF(kc_rbgs, s,
                      (k_rbgs<DIM><<<nbh, kThreads, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r, col)));
-            ++g_launches;
-        }
+        ++g_launches;
+    };
+    for (int it = 0; it < npre; ++it)
+        for (int col = 0; col < 2; ++col) sweep(col);
     MGLevel& C = mg.lv[l + 1];
-    CDI_PROF(l == 0 ? KC_RESTRICT0 : -1, s,
-             (k_resid_restrict<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.bf[0], L.bf[1], L.bf[2], L.e,
-                                                                           L.r, C.r, C.e)));
+    if (l == 0)
+        CDI_PROF(KC_RESTRICT0, s,
+                 (k_resid_restrict0<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.rho0, L.e, L.r, C.r,
+                                                                                C.e)));
+    else
+        k_resid_restrict<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r,
+                                                                     C.r, C.e);
     ++g_launches;
     vcycle_rec<DIM>(mg, l + 1, npre, npost, s);
     CDI_PROF(l == 0 ? KC_PROLONG0 : -1, s, (k_prolong<DIM><<<nb, kThreads, 0, s>>>(L.g, C.g, C.e, L.e)));
     ++g_launches;
     for (int it = 0; it < npost; ++it)
-        for (int col = 0; col < 2; ++col) {
-            CDI_PROF(kc_rbgs, s,
-                     (k_rbgs<DIM><<<nbh, kThreads, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r, col)));
-            ++g_launches;
-        }
+        for (int col = 0; col < 2; ++col) sweep(col);
 }
 
 template <typename T>
@@ -451,7 +562,7 @@ void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s) {
 
 template <typename T>
 void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.N);
+    const unsigned G = red_blocks(g.D == 2 ? (const void*)k_resid<T, 2> : (const void*)k_resid<T, 3>, g.N);
     const float* fm = sizeof(T) == 8 ? nullptr : mg.scalf + SF_FMEAN_HI;
     const bool on = prof_before(KC_RESID, s);
     if (g.D == 2) k_resid<T, 2><<<G, kThreads, 0, s>>>(mg.lv[0], fm, mg.partials);
@@ -463,7 +574,8 @@ void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s) {
 
 template <typename T>
 void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.N);
+    const unsigned G =
+        red_blocks(sizeof(T) == 8 ? (const void*)k_partial_sum<double> : (const void*)k_partial_sum_df, g.N);
     if constexpr (sizeof(T) == 8) {
         k_partial_sum<double><<<G, kThreads, 0, s>>>(g.N, mg.lv[0].p, mg.partials);
     } else {
@@ -478,6 +590,16 @@ void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s) {
                                                         mg.scalf + SF_PMEAN_HI);
     g_launches += 3;
 }
+
+template <typename T>
+void launch_p_extrap(const Geom& g, MG& mg, const double* hnew, const double* hold, cudaStream_t s) {
+    k_p_extrap<T><<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<T>(mg.lv[0]),
+                                                      reinterpret_cast<const PT<T>*>(hnew),
+                                                      reinterpret_cast<const PT<T>*>(hold));
+    ++g_launches;
+}
+template void launch_p_extrap<double>(const Geom&, MG&, const double*, const double*, cudaStream_t);
+template void launch_p_extrap<float>(const Geom&, MG&, const double*, const double*, cudaStream_t);
 
 void launch_p_to_double(const Geom& g, const MG& mg, double* x, cudaStream_t s) {
     k_p_to_double<<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<float>(mg.lv[0]), x);
@@ -511,7 +633,7 @@ void launch_project(const Geom& g, const PhysDev& ph, const T* phi, T* const* us
 
 template <typename T>
 void launch_mass(const Geom& g, const T* phi, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.N);
+    const unsigned G = red_blocks((const void*)k_mass_partial<T>, g.N);
     k_mass_partial<T><<<G, kThreads, 0, s>>>(g.N, phi, mg.partials);
     double dv = (g.D == 2) ? g.h * g.h : g.h * g.h * g.h;
     k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, dv, mg.scal + S_MASS, 0);
@@ -520,7 +642,7 @@ void launch_mass(const Geom& g, const T* phi, MG& mg, cudaStream_t s) {
 
 template <typename T>
 void launch_gamma(const Geom& g, const T* const* u, double gamma_param, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.N + g.NP);
+    const unsigned G = red_blocks((const void*)k_umax_partial<T>, g.N + g.NP);
     long n2 = (g.D == 3) ? g.N + g.NP : 0;
     long n1 = (g.D == 2) ? g.N + g.NP : g.N;
     k_umax_partial<T><<<G, kThreads, 0, s>>>(g.N, n1, n2, u[0], u[1], g.D == 3 ? u[2] : u[1], mg.partials);

@@ -256,12 +256,17 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
         const int half = (int)(L.g.N / 2);
         for (int it = 0; it < A.npre; ++it)
             for (int col = 0; col < 2; ++col) {
-                for (int k = tid; k < half; k += nth)
-                    ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
+                for (int k = tid; k < half; k += nth) {
+                    const long c = ops::colour_cell(L.g, col, k);
+                    if (l == 0) ops::rbgs_rho_at<L_, DIM>(L.g, L.rho0, L.e, L.r, c);
+                    else ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
+                }
                 if (!x.sync()) return false;
             }
-        for (int t = tid; t < (int)C.g.N; t += nth)
-            ops::resid_restrict_at<L_, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
+        for (int t = tid; t < (int)C.g.N; t += nth) {
+            if (l == 0) ops::resid_restrict_rho_at<L_, DIM>(L.g, C.g, L.rho0, L.e, L.r, C.r, C.e, t);
+            else ops::resid_restrict_at<L_, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
+        }
         if (!x.sync()) return false;
     }
     if (x.tail_cta()) tail_vcycle<T, DIM>(A, first, sm);
@@ -281,7 +286,8 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
                 const bool last = (l == 0 && it == A.npost - 1 && col == 1);
                 for (int k = tid; k < half; k += nth) {
                     const long c = ops::colour_cell(L.g, col, k);
-                    ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
+                    if (l == 0) ops::rbgs_rho_at<L_, DIM>(L.g, L.rho0, L.e, L.r, c);
+                    else ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
                     if (last) P0[c] = ops::p_add(L_::ld(P0 + c), L.e[c]);
                 }
                 if (last) {  // the other colour is final already
@@ -364,7 +370,8 @@ __device__ bool project(const InstArgs<T>& A, X& x, InstStats* S, const T* phi, 
         if (A.warm == CDI_WARM_ZERO) P0[c] = ops::p_zero<T>();
         else if (extrap && sg >= 2) P0[c] = ops::p_extrap(L_::ld(hnew + c), L_::ld(hold + c));
     }
-    for (int t = tid; t < (int)(g.N + g.NP); t += nth) ops::coef0_at<L_, T, DIM>(g, A.ph, phi, L0.beta, L0.bf, t);
+    for (int t = tid; t < (int)(g.N + g.NP); t += nth)
+        ops::coef0_at<L_, T, DIM>(g, A.ph, phi, L0.beta, L0.bf, L0.rho0, t);
     double fsq;
     if (!x.template reduce<false>((double)s2, fsq)) return false;
     const double fn = sqrt(fsq);
@@ -576,6 +583,27 @@ size_t persist_tail_layout(const Geom& g, const MG& mg, int lt, PersistLayout& L
     L.sm_fct = d;
     d += kMaxCoarse;
     return (size_t)off * sizeof(float) + (size_t)d * sizeof(double);
+}
+
+// One V-cycle's shared-memory tail as its own single-CTA launch (the
+// launch-per-kernel path): levels lt .. nlev-1 of the descriptor, the tail
+// coefficients restricted afresh each launch (shared memory does not outlive it)
+template <int DIM>
+__global__ void __launch_bounds__(kPersistThreads, 1) k_tail(const InstArgs<float>* A) {
+    extern __shared__ double smd[];
+    tail_vcycle<float, DIM>(*A, true, reinterpret_cast<float*>(smd));
+}
+
+cudaError_t tail_prepare(int dim, size_t smem) {
+    const void* fn = (dim == 2) ? (const void*)k_tail<2> : (const void*)k_tail<3>;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_tail(const void* inst_args, int dim, size_t smem, cudaStream_t s) {
+    const InstArgs<float>* A = static_cast<const InstArgs<float>*>(inst_args);
+    if (dim == 2) k_tail<2><<<1, kPersistThreads, smem, s>>>(A);
+    else k_tail<3><<<1, kPersistThreads, smem, s>>>(A);
+    return cudaGetLastError();
 }
 
 template <typename T>

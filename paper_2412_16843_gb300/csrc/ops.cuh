@@ -433,7 +433,7 @@ __device__ __forceinline__ T div_at(const Geom& g, const T* const* us, T ih, T i
 // (the last NP are the high wall faces of the wall-normal component)
 template <class L, typename T, int DIM>
 __device__ __forceinline__ void coef0_at(const Geom& g, const PhysDev& ph, const T* phi, double* const* bs,
-                                         float* const* bsf, long t) {
+                                         float* const* bsf, float* rho0, long t) {
     constexpr bool f64 = sizeof(T) == 8;
     if (t >= g.N) {
         if (f64) bs[DIM - 1][t] = 0.0;
@@ -442,6 +442,7 @@ __device__ __forceinline__ void coef0_at(const Geom& g, const PhysDev& ph, const
     }
     const IJK q = decode(g, t);
     const T dr = phys<T>(ph).drho, rho2 = phys<T>(ph).rho2;
+    rho0[t] = (float)(dr * L::ld(phi + t) + rho2);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         if (a == DIM - 1 && coord(q, a) == 0) {
@@ -517,6 +518,41 @@ __device__ __forceinline__ M apply_L(const Geom& g, const M* const* beta, const 
     return off - diag * L::ld(p + c);
 }
 
+// apply_L on level 0 with the face coefficients formed from the FP32 cell
+// densities, beta = 2 / (rho_L + rho_R) (coef0_at's 1 / mean density, by the
+// fast FP32 division): one array read instead of D coefficient arrays.  Used
+// by the level-0 smoother and residual restriction only; the defect-correction
+// residual keeps the stored coefficients.  Walls carry a zero coefficient.
+template <class L, int DIM>
+__device__ __forceinline__ float apply_L_rho(const Geom& g, const float* rho, const float* p, const IJK& q, long c,
+                                             float ih2, float& diag, float& off) {
+    diag = 0.f;
+    off = 0.f;
+    const float rc = L::ld(rho + c);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        long lo, hi;
+        float mlo = 1.f, mhi = 1.f;
+        if (a == DIM - 1) {
+            const int r = coord(q, a);
+            lo = r > 0 ? c - g.NP : c;
+            hi = r < g.n[a] - 1 ? c + g.NP : c;
+            mlo = r > 0 ? 1.f : 0.f;
+            mhi = r < g.n[a] - 1 ? 1.f : 0.f;
+        } else {
+            lo = idx(g, shift(g, q, a, -1));
+            hi = idx(g, shift(g, q, a, 1));
+        }
+        const float bm = mlo * __fdividef(2.f, rc + L::ld(rho + lo));
+        const float bp = mhi * __fdividef(2.f, rc + L::ld(rho + hi));
+        const float pm = L::ld(p + lo);
+        const float pp = L::ld(p + hi);
+        diag += (bm + bp) * ih2;
+        off += (bm * pm + bp * pp) * ih2;
+    }
+    return off - diag * L::ld(p + c);
+}
+
 // k-th cell of one colour ((i+j+k) even or odd); every extent of a smoothed level is even
 __device__ __forceinline__ long colour_cell(const Geom& g, int colour, long k) {
     const unsigned half = (unsigned)g.n[0] >> 1;
@@ -534,6 +570,15 @@ __device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* 
     const M ih2 = g_ih2<M>(g);
     M diag, off;
     apply_L<L, M, DIM>(g, beta, p, q, c, ih2, diag, off);
+    p[c] = (off - L::ld(f + c)) / diag;
+}
+
+// level-0 smoothing step with density-formed coefficients (apply_L_rho)
+template <class L, int DIM>
+__device__ __forceinline__ void rbgs_rho_at(const Geom& g, const float* rho, float* p, const float* f, long c) {
+    const IJK q = decode(g, c);
+    float diag, off;
+    apply_L_rho<L, DIM>(g, rho, p, q, c, g.ih2f, diag, off);
     p[c] = (off - L::ld(f + c)) / diag;
 }
 
@@ -715,6 +760,29 @@ __device__ __forceinline__ void resid_restrict_at(const Geom& gf, const Geom& gc
             }
     fc[t] = s * (M(1) / M(4 * o2));
     pc[t] = M(0);
+}
+
+// resid_restrict_at on level 0 with density-formed coefficients (apply_L_rho)
+template <class L, int DIM>
+__device__ __forceinline__ void resid_restrict_rho_at(const Geom& gf, const Geom& gc, const float* rho, const float* p,
+                                                      const float* f, float* fc, float* pc, long t) {
+    const IJK Q = decode(gc, t);
+    const int o2 = (DIM == 3) ? 2 : 1;
+    float s = 0.f;
+    for (int t2 = 0; t2 < o2; ++t2)
+        for (int t1 = 0; t1 < 2; ++t1)
+            for (int t0 = 0; t0 < 2; ++t0) {
+                IJK q;
+                q.i = 2 * Q.i + t0;
+                q.j = 2 * Q.j + t1;
+                q.k = (DIM == 3) ? 2 * Q.k + t2 : 0;
+                const long c = idx(gf, q);
+                float diag, off;
+                const float Lp = apply_L_rho<L, DIM>(gf, rho, p, q, c, gf.ih2f, diag, off);
+                s += L::ld(f + c) - Lp;
+            }
+    fc[t] = s * (1.f / (float)(4 * o2));
+    pc[t] = 0.f;
 }
 
 // cell-centred (bi/tri)linear prolongation, weights 3/4 and 1/4 per axis;

@@ -285,7 +285,7 @@ def test_adaptive_gamma_parity_both_modes():
             assert rel(vel_g[a], vel_o[a]) < 1e-10
 
 
-@pytest.mark.parametrize("exec_mode", [cdi.EXEC_PERSISTENT], ids=["persistent"])
+@pytest.mark.parametrize("exec_mode", [cdi.EXEC_PERSISTENT, cdi.EXEC_KERNELS], ids=["persistent", "kernels"])
 def test_extrapolated_warm_start_parity_and_fewer_cycles(exec_mode):
     """First guess by linear extrapolation in time of each RK stage's pressure:
     same solution as the oracle (whose first guess is the last solve's
