@@ -169,6 +169,7 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     mg.partials = (double*)cv.take(2 * kPartials * sizeof(double));
     mg.scal = (double*)cv.take(S_NSCAL * sizeof(double));
     mg.scalf = (float*)cv.take(SF_NSCAL * sizeof(float));
+    mg.ainv = (float*)cv.take((size_t)kMaxCoarse * kMaxCoarse * sizeof(float));
     c->ctl = (PersistCtl*)cv.take(sizeof(PersistCtl));
     c->tail_dev = cv.take(sizeof(InstArgs<float>));
     for (int k = 0; k < 4; ++k)
@@ -301,6 +302,7 @@ cdi_status kernels_tail_setup(cdi_ctx* c) {
         A.lt = lt;
         A.npre = c->npre;
         A.npost = c->npost;
+        A.ainv = c->mg.ainv;
         st = cuda_check(c, cudaMemcpyAsync(c->tail_dev, &A, sizeof A, cudaMemcpyHostToDevice, c->stream),
                         "cudaMemcpyAsync(tail)");
         if (st) return st;
@@ -523,6 +525,7 @@ void fill_inst(const cdi_ctx* c, InstArgs<T>& A, int lt, const PersistLayout& la
     for (int k = 0; k < 4; ++k)
         for (int j = 0; j < 2; ++j) A.hist[k][j] = c->hist[k][j];
     A.hist_step0 = c->hist_steps;
+    A.ainv = nullptr;  // the shared-memory tail inverts the coarsest level itself
 }
 
 // record one launch's outcome on the context; the kernel swapped the state

@@ -229,6 +229,7 @@ struct MG {
     double* partials;   // [2 * kPartials]
     double* scal;       // device scalars
     float* scalf;       // FP32 device scalars
+    float* ainv;        // launch-per-kernel path: inverse of the coarsest level [kMaxCoarse^2]
     // launch-per-kernel path: levels tail_lt .. nlev-1 of a V-cycle run as one
     // single-CTA launch in shared memory (tail_args: its descriptor in device
     // memory, an InstArgs<float>; null: every level as separate kernels)
@@ -341,6 +342,8 @@ struct __align__(16) InstArgs : PersistLayout {
     // RK stage k of the last two steps, hist[k][s & 1] written at step s
     double* hist[4][2];
     long hist_step0;   // steps stored before this launch
+    const float* ainv; // coarsest-level inverse in global memory (launch-per-kernel tail), or null:
+                       // the tail inverts in shared memory at the first V-cycle of each solve
 };
 
 template <typename T>

@@ -279,15 +279,21 @@ __global__ void k_prolong(Geom gf, Geom gc, const float* ec, float* e) {
     if (c < gf.N) ops::prolong_at<Ld, float, DIM>(gf, gc, ec, e, c);
 }
 
+// inverse of the coarsest level's shifted matrix, once per solve (one block)
 template <int DIM>
-__global__ void k_coarse(Geom g, const float* b0, const float* b1, const float* b2, const float* r, float* e) {
+__global__ void k_coarse_invert(Geom g, const float* b0, const float* b1, const float* b2, float* ainv) {
     const float* beta[3] = {b0, b1, b2};
-    __shared__ double A[kMaxCoarse * kMaxCoarse];
-    __shared__ double bb[2 * kMaxCoarse];
-    __shared__ double fct[kMaxCoarse];
-    __shared__ int piv;
-    __shared__ double sh;
-    ops::coarse_solve_block<Ld, float, DIM>(g, beta, r, e, A, bb, fct, &piv, &sh);
+    __shared__ float A[kMaxCoarse * kMaxCoarse];
+    __shared__ float fct[kMaxCoarse];
+    __shared__ float sh;
+    ops::coarse_invert_block<Ld, float, DIM>(g, beta, A, fct, &sh);
+    const int n = (int)g.N;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) ainv[t] = A[t];
+}
+
+// coarsest-level correction e = Ainv r (every V-cycle)
+__global__ void k_coarse(int n, const float* ainv, const float* r, float* e) {
+    ops::coarse_apply_block<Ld, float>(n, ainv, r, e);
 }
 
 template <typename T>
@@ -503,6 +509,10 @@ void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cuda
             k_coef_restrict<3><<<nb, kThreads, 0, s>>>(F.g, C.g, F.bf[0], F.bf[1], F.bf[2], C.bf[0], C.bf[1], C.bf[2]);
         ++g_launches;
     }
+    const MGLevel& Lc = mg.lv[mg.nlev - 1];
+    if (g.D == 2) k_coarse_invert<2><<<1, 256, 0, s>>>(Lc.g, Lc.bf[0], Lc.bf[1], nullptr, mg.ainv);
+    else k_coarse_invert<3><<<1, 256, 0, s>>>(Lc.g, Lc.bf[0], Lc.bf[1], Lc.bf[2], mg.ainv);
+    ++g_launches;
 }
 
 template <int DIM>
@@ -514,7 +524,7 @@ static void vcycle_rec(MG& mg, int l, int npre, int npost, cudaStream_t s) {
         return;
     }
     if (l == mg.nlev - 1) {
-        CDI_PROF(KC_COARSE, s, (k_coarse<DIM><<<1, 64, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.r, L.e)));
+        CDI_PROF(KC_COARSE, s, (k_coarse<<<1, 64, 0, s>>>((int)L.g.N, mg.ainv, L.r, L.e)));
         ++g_launches;
         return;
     }

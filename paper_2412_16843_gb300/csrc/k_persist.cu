@@ -218,10 +218,12 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
     {
         const SmLevel C = sm_level<T, DIM>(A, sm, nl - 1);
         const float* bc[3] = {C.b[0], C.b[1], C.b[2]};
-        __shared__ int piv;
-        __shared__ double shv;
-        ops::coarse_solve_block<LP, float, DIM>(C.g, bc, C.r, C.e, sd + A.sm_A, sd + A.sm_bb, sd + A.sm_fct, &piv,
-                                                &shv);
+        float* Asm = reinterpret_cast<float*>(sd + A.sm_A);
+        if (!A.ainv && first) {
+            __shared__ float shv;
+            ops::coarse_invert_block<LP, float, DIM>(C.g, bc, Asm, reinterpret_cast<float*>(sd + A.sm_fct), &shv);
+        }
+        ops::coarse_apply_block<LP, float>((int)C.g.N, A.ainv ? A.ainv : Asm, C.r, C.e);
     }
     for (int l = nl - 2; l >= lt; --l) {  // up
         const SmLevel L = sm_level<T, DIM>(A, sm, l), C = sm_level<T, DIM>(A, sm, l + 1);

@@ -839,80 +839,70 @@ __device__ __forceinline__ void project_at(const Geom& g, const PhysDev& ph, con
 }
 
 // ---------------------------------------------------------------------------
-// Dense FP64 solve of (A + c 1 1^T) e = r on a level of at most kMaxCoarse
-// cells by one thread block (Gaussian elimination with partial pivoting).
-// A, bb, fct: FP64 scratch of kMaxCoarse^2, kMaxCoarse and kMaxCoarse values.
-// The rank-one term c 1 1^T (c = mean diagonal / n) removes the constant null
-// space of the periodic + Neumann operator; the right-hand side sums to zero.
+// Coarsest level (at most kMaxCoarse cells), solved by one thread block.
+// The matrix A of the level plus the rank-one term c 1 1^T (c = -(mean
+// diagonal magnitude) / n) is negative definite: A is negative semidefinite
+// with the constants as its null space, and the rank-one term is negative on
+// them.  Its coefficients are fixed during a pressure solve, so the block
+// inverts it once per solve (coarse_invert_block: in-place Gauss-Jordan
+// elimination, which needs no pivoting for a definite matrix) and every
+// V-cycle applies the inverse (coarse_apply_block).  With a right-hand side
+// summing to zero, e = (A + c 1 1^T)^-1 r solves A e = r with sum(e) = 0.
+// FP32 suffices: the result is the coarse correction of an FP32 V-cycle.
 // ---------------------------------------------------------------------------
 template <class L, typename M, int DIM>
-__device__ void coarse_solve_block(const Geom& g, const M* const* beta, const M* f, M* p, double* A, double* bb,
-                                   double* fct, int* piv_s, double* shift_s) {
+__device__ void coarse_invert_block(const Geom& g, const M* const* beta, float* A, float* fct, float* shift_s) {
     const int n = (int)g.N;
-    const double ih2 = 1.0 / (g.h * g.h);
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = 0.0;
+    const float ih2 = g.ih2f;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] = 0.f;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double dsum = 0.0;
-        for (int c = 0; c < n; ++c) {
-            const IJK q = decode(g, c);
-            for (int a = 0; a < DIM; ++a) {
-                const long hi = (a == DIM - 1) ? c + g.NP : idx(g, shift(g, q, a, 1));
-                const double bm = (double)L::ld(beta[a] + c), bp = (double)L::ld(beta[a] + hi);
-                A[c * n + c] -= (bm + bp) * ih2;
-                if (bm != 0.0) A[c * n + idx(g, shift(g, q, a, -1))] += bm * ih2;
-                if (bp != 0.0) A[c * n + hi] += bp * ih2;
-            }
-            dsum += -A[c * n + c];
-            bb[c] = (double)L::ld(f + c);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {  // row c of A
+        const IJK q = decode(g, c);
+        float diag = 0.f;
+        for (int a = 0; a < DIM; ++a) {
+            const long hi = (a == DIM - 1) ? c + g.NP : idx(g, shift(g, q, a, 1));
+            const float bm = (float)L::ld(beta[a] + c), bp = (float)L::ld(beta[a] + hi);
+            diag -= (bm + bp) * ih2;
+            if (bm != 0.f) A[c * n + idx(g, shift(g, q, a, -1))] += bm * ih2;
+            if (bp != 0.f) A[c * n + hi] += bp * ih2;
         }
-        *shift_s = -dsum / ((double)n * (double)n);
+        A[c * n + c] += diag;
+        fct[c] = -diag;
     }
     __syncthreads();
-    const double sh = *shift_s;
+    if (threadIdx.x == 0) {
+        float dsum = 0.f;
+        for (int c = 0; c < n; ++c) dsum += fct[c];
+        *shift_s = -dsum / ((float)n * (float)n);
+    }
+    __syncthreads();
+    const float sh = *shift_s;
     for (int t = threadIdx.x; t < n * n; t += blockDim.x) A[t] += sh;
     __syncthreads();
-    for (int col = 0; col < n; ++col) {
-        if (threadIdx.x == 0) {
-            int pv = col;
-            for (int r = col + 1; r < n; ++r)
-                if (fabs(A[r * n + col]) > fabs(A[pv * n + col])) pv = r;
-            *piv_s = pv;
-        }
+    for (int k = 0; k < n; ++k) {
+        const float piv = A[k * n + k];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) fct[i] = A[i * n + k];
         __syncthreads();
-        const int pv = *piv_s;
-        if (pv != col) {
-            for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                double tmp = A[col * n + t];
-                A[col * n + t] = A[pv * n + t];
-                A[pv * n + t] = tmp;
-            }
-            if (threadIdx.x == 0) {
-                double tmp = bb[col];
-                bb[col] = bb[pv];
-                bb[pv] = tmp;
-            }
-        }
+        for (int jj = threadIdx.x; jj < n; jj += blockDim.x) A[k * n + jj] = (jj == k ? 1.f : A[k * n + jj]) / piv;
         __syncthreads();
-        for (int r = col + 1 + threadIdx.x; r < n; r += blockDim.x) fct[r] = A[r * n + col] / A[col * n + col];
-        __syncthreads();
-        for (int r = col + 1 + threadIdx.x; r < n; r += blockDim.x) {
-            const double fr = fct[r];
-            if (fr == 0.0) continue;
-            for (int t = col; t < n; ++t) A[r * n + t] -= fr * A[col * n + t];
-            bb[r] -= fr * bb[col];
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int i = t / n, jj = t - i * n;
+            if (i == k) continue;
+            A[t] = (jj == k ? 0.f : A[t]) - fct[i] * A[k * n + jj];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        for (int r = n - 1; r >= 0; --r) {
-            double s = bb[r];
-            for (int t = r + 1; t < n; ++t) s -= A[r * n + t] * bb[n + t];
-            bb[n + r] = s / A[r * n + r];
-        }
+}
+
+// e = Ainv r on the coarsest level (Ainv symmetric up to rounding; thread c
+// reads column c, so neighbouring threads read neighbouring words)
+template <class L, typename M>
+__device__ void coarse_apply_block(int n, const float* Ainv, const M* r, M* e) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        float s = 0.f;
+        for (int t = 0; t < n; ++t) s += L::ld(Ainv + t * n + c) * (float)L::ld(r + t);
+        e[c] = (M)s;
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < n; c += blockDim.x) p[c] = (M)bb[n + c];
     __syncthreads();
 }
 
