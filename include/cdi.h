@@ -324,6 +324,12 @@ cdi_status cdi_unet_forward_device(cdi_unet* net, const float* x, float* y);
 cdi_status cdi_unet_train_step(cdi_unet* net, const double* x, const double* target,
                                double lr, double* loss, double* grads);
 
+/* Kernel of the 3x3x3 convolutions (forward and data gradient): 1 (default)
+ * the tcgen05 implicit GEMM (M = 128 voxels, accumulator in tensor memory,
+ * input tile with halo staged once in shared memory for all 27 taps); 0 the
+ * warp-level mma.sync implicit GEMM.  Both compute the same sums in FP32. */
+cdi_status cdi_unet_set_conv_kernel(cdi_unet* net, int tensor_core);
+
 /* Last error of the network (NULL: of the last failed cdi_unet_create). */
 const char* cdi_unet_last_error(const cdi_unet* net);
 

@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "cdi_unet_get_params": [P, DP, S],
         "cdi_unet_forward": [P, DP, DP],
         "cdi_unet_forward_device": [P, P, P],
+        "cdi_unet_set_conv_kernel": [P, I],
         "cdi_unet_train_step": [P, DP, DP, D, DP, DP],
         "cdi_set_warm_unet": [P, P],
         "cdi_last_pressure": [P, DP, DP],
@@ -433,6 +434,10 @@ class Unet:
         y = np.empty(self.shape)
         self._check(self.lib.cdi_unet_forward(self.h, _dp(xa), _dp(y)))
         return y
+
+    def set_conv_kernel(self, tensor_core: bool):
+        """3x3x3 convolutions on tcgen05 (True, default) or mma.sync (False)."""
+        self._check(self.lib.cdi_unet_set_conv_kernel(self.h, 1 if tensor_core else 0))
 
     def forward_device(self, x, y):
         """Device forward pass: torch float32 tensors x (..., 2) and y (...) on

@@ -19,6 +19,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -360,6 +361,245 @@ __global__ void k_output_solver(int N, const float* y, const double* sd, const f
 
 unsigned blocks(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution on the 5th-generation tensor cores (tcgen05).
+//
+// One CTA of 128 threads computes an output tile of M = 128 voxels (8 along
+// x, 16 along y, one z plane) for all N output channels; the FP32 accumulator
+// D[128][N] lives in tensor memory (TMEM lane m = voxel m, column n = channel
+// n).  For each block of 16 input channels the CTA stages the input tile with
+// a one-voxel halo (10 x 18 x 3 voxels) in shared memory once, and all 27 taps
+// read their A operand from it: tap (dz, dy, dx) is the same tile shifted by
+// whole 16-byte rows, so it only changes the start address of the shared-
+// memory matrix descriptor.  Weights are staged nine taps at a time into two
+// alternating buffers.  One thread issues the MMAs
+// (tcgen05.mma.cta_group::1.kind::f16: BF16 A and B, FP32 D, M = 128, K = 16)
+// and commits them to an mbarrier; the buffers are rewritten only after the
+// MMAs that read them have completed.  Operands use the canonical K-major
+// layout without swizzling: a core matrix is 8 rows of 16 bytes (8 channels),
+// stored contiguously; the descriptor's leading offset steps to the next 8
+// channels, its stride offset to the next 8 rows.
+// ---------------------------------------------------------------------------
+constexpr int kTcThreads = 128;
+constexpr int kTileX = 8, kTileY = 16;
+constexpr int kHX = kTileX + 2, kHY = kTileY + 2, kHZ = 3, kKC = 2;  // halo tile; 16 channels = 2 chunks of 8
+constexpr int kHaloUnits = kHZ * kHY * kKC * kHX;                   // 16-byte units
+constexpr int kHaloBytes = kHaloUnits * 16;
+constexpr int kGuardBytes = 4096;
+constexpr int kTapsPerIter = 9;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long tc_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait (at most about one second) for the phase of the given parity to complete
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = tc_globaltimer();
+    while (!mbar_try_wait(bar, parity))
+        if (tc_globaltimer() - t0 > 1000000000ull) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: start address, leading byte offset (next 8
+// channels), stride byte offset (next 8 rows), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tcgen05 convolution: out[v][co] = act(bias[co] + sum_t sum_ci in[v + off(t)][ci] w[t][co][ci]) for
+// co < cout (BF16 out, row stride out_stride); cin and N multiples of 16, N <= 256; ncols: TMEM
+// columns (a power of two >= max(32, N)).  On a wait that runs out, *err is set and the CTA stops.
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __restrict__ in, int cin,
+                                                        const bf16* __restrict__ w, int N,
+                                                        const float* __restrict__ bias, int cout, bf16* out,
+                                                        int out_stride, int relu, int ncols, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    uint4* halo = reinterpret_cast<uint4*>(smem);
+    uint4* bbuf = reinterpret_cast<uint4*>(smem + kHaloBytes + kGuardBytes);
+    const int bunits = kTapsPerIter * 2 * N;  // 16-byte units of one weight buffer
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = idesc_bf16(128, N);
+    const uint32_t halo_addr = smem_u32(halo);
+    const uint32_t b_addr = smem_u32(bbuf);
+
+    const int tiles_x = (g.nx + kTileX - 1) / kTileX, tiles_y = (g.ny + kTileY - 1) / kTileY;
+    const long ntiles = (long)tiles_x * tiles_y * g.nz;
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    int buf = 0;
+
+    // every thread waits for the MMAs that read buffer b before anyone rewrites it; a wait that
+    // runs out sets s_abort, which the whole CTA reads after its next barrier
+    auto wait_buf = [&](int b) {
+        if (pending[b]) {
+            if (!mbar_wait_bounded(&mbar[b], phase[b])) {
+                s_abort = 1;
+                atomicExch(err, 1);
+            }
+            phase[b] ^= 1u;
+            pending[b] = false;
+        }
+    };
+
+    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int z = (int)(tile / ((long)tiles_x * tiles_y));
+        const int rem = (int)(tile - (long)z * tiles_x * tiles_y);
+        const int y0 = (rem / tiles_x) * kTileY, x0 = (rem % tiles_x) * kTileX;
+        bool first = true;
+        for (int cb = 0; cb < cin; cb += 16) {
+            wait_buf(0);
+            wait_buf(1);
+            __syncthreads();
+            if (s_abort) break;
+            // input tile with halo: unit ((hz * kHY + hy) * kKC + kc) * kHX + hx
+            for (int u = tid; u < kHaloUnits; u += kTcThreads) {
+                const int hx = u % kHX, r1 = u / kHX, kc = r1 % kKC, r2 = r1 / kKC, hy = r2 % kHY, hz = r2 / kHY;
+                const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz)
+                    v = *reinterpret_cast<const uint4*>(in + ((size_t)((long)gz * g.ny + gy) * g.nx + gx) * cin + cb +
+                                                        kc * 8);
+                halo[u] = v;
+            }
+            for (int t0 = 0; t0 < 27; t0 += kTapsPerIter) {
+                const int b = buf;
+                wait_buf(b);
+                // weights of taps t0 .. t0+8, channels cb .. cb+15: unit (t * 2N) + (n/8 * 2 + kc) * 8 + n%8
+                uint4* bb = bbuf + (size_t)b * bunits;
+                for (int u = tid; u < bunits; u += kTcThreads) {
+                    const int t = u / (2 * N), r = u - t * 2 * N;
+                    const int ng = r >> 4, kc = (r >> 3) & 1, n = ng * 8 + (r & 7);
+                    bb[u] = *reinterpret_cast<const uint4*>(w + ((size_t)(t0 + t) * N + n) * cin + cb + kc * 8);
+                }
+                fence_proxy_async();
+                __syncthreads();
+                if (s_abort) break;
+                if (tid == 0) {
+                    tc_fence_after();
+#pragma unroll 1
+                    for (int t = 0; t < kTapsPerIter; ++t) {
+                        const int tap = t0 + t;
+                        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                        const int u0 = ((1 + dz) * kHY + (1 + dy)) * kKC * kHX + (1 + dx);
+                        const uint64_t ad = smem_desc(halo_addr + (uint32_t)u0 * 16u, kHX * 16, kKC * kHX * 16);
+                        const uint64_t bd =
+                            smem_desc(b_addr + (uint32_t)(b * bunits + t * 2 * N) * 16u, 8 * 16, kKC * 8 * 16);
+                        tc_mma(tmem, ad, bd, idesc, first ? 0u : 1u);
+                        first = false;
+                    }
+                    tc_commit(&mbar[b]);
+                }
+                first = false;
+                pending[b] = true;
+                buf ^= 1;
+            }
+            if (s_abort) break;
+        }
+        wait_buf(0);
+        wait_buf(1);
+        __syncthreads();
+        if (s_abort) break;
+        tc_fence_after();
+        // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (voxels), 8 channels at a time
+        const int m = warp * 32 + lane;
+        const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
+        const bool inside = gx < g.nx && gy < g.ny;
+        bf16* orow = out + ((size_t)((long)z * g.ny + (inside ? gy : 0)) * g.nx + (inside ? gx : 0)) * out_stride;
+        for (int c0 = 0; c0 < N; c0 += 8) {
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (inside && c0 + 8 <= cout) {
+                __align__(16) bf16 o[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float a = v[e] + (bias ? bias[c0 + e] : 0.f);
+                    if (relu) a = fmaxf(a, 0.f);
+                    o[e] = __float2bfloat16(a);
+                }
+                *reinterpret_cast<uint4*>(orow + c0) = *reinterpret_cast<const uint4*>(o);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    // a CTA that gave up waits (bounded) for its MMAs in flight before releasing TMEM
+    for (int b = 0; b < 2; ++b)
+        if (pending[b]) mbar_wait_bounded(&mbar[b], phase[b]);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
 }  // namespace
 }  // namespace cdi
 
@@ -383,6 +623,8 @@ struct cdi_unet {
     double* x2;  // host-input staging [N][2]
     double* sd;  // prediction scales (FP64 and FP32 copies)
     float* sf;
+    int* tc_err;          // set by a tcgen05 convolution whose bounded wait ran out
+    bool use_tc = true;   // 3x3x3 convolutions on tcgen05 (else mma.sync)
     long adam_t = 0;
     bool weights_ready = false;
     std::string err;
@@ -462,13 +704,44 @@ void unet_carve(cdi_unet* u, char* base, size_t* total) {
     u->part = (float*)cv.take(256);
     u->sd = (double*)cv.take(4 * sizeof(double));
     u->sf = (float*)cv.take(4 * sizeof(float));
+    u->tc_err = (int*)cv.take(sizeof(int));
     u->x2 = (double*)cv.take((size_t)N0 * 2 * 8);
     *total = cv.off + 256;
+}
+
+// tcgen05 convolution launch: a persistent grid of as many CTAs as fit at once (shared memory
+// bounds the CTAs per SM below what the TMEM columns allow, so no TMEM allocation ever waits)
+void conv_tc(cdi_unet* u, const CG& gl, const bf16* in, int cin, const bf16* w, int N, const float* bias, int cout,
+             bf16* out, int out_stride, bool relu) {
+    static int nsm = 0, smem_sm = 0;
+    static bool attr = false;
+    const int ncols = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+    const size_t smem = (size_t)kHaloBytes + kGuardBytes + 2 * (size_t)kTapsPerIter * 2 * N * 16;
+    if (!attr) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        attr = true;
+    }
+    // CTAs per SM: shared memory (1 KB reserved per CTA, plus the static 1 KB), threads, TMEM columns
+    int per = (int)((size_t)smem_sm / (smem + 2048));
+    per = std::max(1, std::min({per, 2048 / kTcThreads, 512 / ncols}));
+    const long tiles = (long)((gl.nx + kTileX - 1) / kTileX) * ((gl.ny + kTileY - 1) / kTileY) * gl.nz;
+    const unsigned grid = (unsigned)std::max(1L, std::min(tiles, (long)nsm * per));
+    k_conv_tc<<<grid, kTcThreads, smem, u->stream>>>(gl, in, cin, w, N, bias, cout, out, out_stride, relu ? 1 : 0,
+                                                     ncols, u->tc_err);
 }
 
 // y = conv(in) for layer l on level grid gl into out (stride, offset)
 template <bool OUTF32>
 void conv_fwd(cdi_unet* u, int l, const CG& gl, const bf16* in, void* out, int stride, int off, bool relu) {
+    if (!OUTF32 && kTaps[l] == 27 && u->use_tc && off == 0 && stride == u->co_pad[l]) {
+        conv_tc(u, gl, in, u->ci_pad[l], u->Wb[l], u->co_pad[l], u->B[l], u->co_pad[l], (bf16*)out, stride, relu);
+        return;
+    }
     const unsigned gb = (unsigned)((gl.N + 63) / 64);
     const int nf = u->co_pad[l] / 8;
     const int cin = u->ci_pad[l], cop = u->co_pad[l];
@@ -490,6 +763,10 @@ void conv_fwd(cdi_unet* u, int l, const CG& gl, const bf16* in, void* out, int s
 
 // dx (BF16 [N][ci_pad]) = adjoint of layer l applied to dy (BF16 [N][co_pad])
 void conv_dgrad(cdi_unet* u, int l, const CG& gl, const bf16* dy, bf16* dx) {
+    if (kTaps[l] == 27 && u->use_tc) {
+        conv_tc(u, gl, dy, u->co_pad[l], u->Wt[l], u->ci_pad[l], nullptr, u->ci_pad[l], dx, u->ci_pad[l], false);
+        return;
+    }
     const unsigned gb = (unsigned)((gl.N + 63) / 64);
     const int nf = u->ci_pad[l] / 8;
     cudaStream_t s = u->stream;
@@ -637,6 +914,18 @@ size_t param_count() {
     size_t n = 0;
     for (int l = 0; l < kLayers; ++l) n += (size_t)kTaps[l] * kCout[l] * kCin[l] + kCout[l];
     return n;
+}
+
+// after a synchronisation: did a tcgen05 convolution give up on a wait?
+cdi_status check_tc(cdi_unet* u) {
+    int e = 0;
+    if (cudaMemcpy(&e, u->tc_err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ufail(u, CDI_ECUDA, "error flag read failed");
+    if (e) {
+        cudaMemset(u->tc_err, 0, sizeof(int));
+        return ufail(u, CDI_ETIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+    }
+    return CDI_OK;
 }
 
 cdi_status upload_x(cdi_unet* u, const double* x_host) {
@@ -792,7 +1081,7 @@ cdi_status cdi_unet_forward(cdi_unet* u, const double* x_host, double* y_host) {
         cudaStreamSynchronize(u->stream) != cudaSuccess)
         return ufail(u, CDI_ECUDA, std::string("forward: ") + cudaGetErrorString(cudaGetLastError()));
     for (long i = 0; i < N; ++i) y_host[i] = y[i];
-    return CDI_OK;
+    return check_tc(u);
 }
 
 // forward pass on device arrays (FP32 [N][2] -> FP32 [N]), stream-ordered, no host copies
@@ -845,6 +1134,13 @@ cdi_status cdi_unet_train_step(cdi_unet* u, const double* x_host, const double* 
     if (cudaStreamSynchronize(u->stream) != cudaSuccess)
         return ufail(u, CDI_ECUDA, std::string("train step: ") + cudaGetErrorString(cudaGetLastError()));
     if (loss) *loss = (double)part / (double)N;
+    return check_tc(u);
+}
+
+cdi_status cdi_unet_set_conv_kernel(cdi_unet* u, int tensor_core) {
+    if (!u) return ufail(nullptr, CDI_EINVAL, "null network");
+    if (tensor_core != 0 && tensor_core != 1) return ufail(u, CDI_EINVAL, "tensor_core must be 0 or 1");
+    u->use_tc = tensor_core == 1;
     return CDI_OK;
 }
 

@@ -200,3 +200,24 @@ def test_warm_unet_needs_a_network():
     with pytest.raises(cdi.CdiError) as e:
         s.step(1e-5, 1)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("n", [(8, 8, 8), (24, 40, 16)], ids=["8^3", "24x40x16"])
+def test_tensor_core_and_warp_mma_convolutions_agree(n):
+    """The tcgen05 convolution (default) and the mma.sync one compute the same
+    FP32 sums over the same BF16 operands: forward outputs and gradients agree
+    to accumulation-order round-off (relative 1e-3; ReLU masks can flip where a
+    BF16 rounding tie breaks differently)."""
+    shape = (n[2], n[1], n[0])
+    P, x, t = random_case(shape, 21)
+    nets = []
+    for tc in (True, False):
+        net = cdi.Unet(n)
+        net.set_conv_kernel(tc)
+        net.set_params(flat(P))
+        nets.append(net)
+    y_tc, y_mma = nets[0].forward(x), nets[1].forward(x)
+    assert relnorm(y_tc, y_mma) < 1e-3
+    _, g_tc = nets[0].train_step(x, t[..., 0], lr=0.0, want_grads=True)
+    _, g_mma = nets[1].train_step(x, t[..., 0], lr=0.0, want_grads=True)
+    assert relnorm(g_tc, g_mma) < 1e-2
