@@ -198,20 +198,28 @@ __global__ void k_bias_grad(int N, const bf16* dy, int stride, int C, float* db)
     if (threadIdx.x == 0) atomicAdd(&db[c], sh[0]);
 }
 
-// 2x2x2 mean of the fine grid gf into the coarse grid
+// 2x2x2 mean of the fine grid gf into the coarse grid; 8 channels (16 bytes) per thread
 __global__ void k_pool(CG gf, const bf16* in, int C, bf16* out) {
-    const int Nc = gf.N / 8;
+    const int Nc = gf.N / 8, C8 = C / 8;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)Nc * C) return;
-    const int c = (int)(t % C), V = (int)(t / C);
+    if (t >= (long)Nc * C8) return;
+    const int g8 = (int)(t % C8), V = (int)(t / C8);
     const int cx = gf.nx / 2, cy = gf.ny / 2;
     const int X = V % cx, Y = (V / cx) % cy, Z = V / (cx * cy);
-    float s = 0.f;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < 2; ++k)
         for (int j = 0; j < 2; ++j)
-            for (int i = 0; i < 2; ++i)
-                s += __bfloat162float(in[(size_t)((2 * X + i) + gf.nx * ((2 * Y + j) + gf.ny * (2 * Z + k))) * C + c]);
-    out[t] = __float2bfloat16(0.125f * s);
+            for (int i = 0; i < 2; ++i) {
+                const size_t v = (size_t)((2 * X + i) + gf.nx * ((2 * Y + j) + gf.ny * (2 * Z + k)));
+                const uint4 q = *reinterpret_cast<const uint4*>(in + v * C + 8 * g8);
+                const bf16* h = reinterpret_cast<const bf16*>(&q);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) s[e] += __bfloat162float(h[e]);
+            }
+    __align__(16) bf16 o[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) o[e] = __float2bfloat16(0.125f * s[e]);
+    *reinterpret_cast<uint4*>(out + (size_t)V * C + 8 * g8) = *reinterpret_cast<const uint4*>(o);
 }
 
 // din[v][off+c] += dout[parent(v)][c] / 8 on the fine grid gf
@@ -225,14 +233,16 @@ __global__ void k_pool_bwd_add(CG gf, const bf16* dout, int C, bf16* din, int st
     din[o] = __float2bfloat16(__bfloat162float(din[o]) + 0.125f * __bfloat162float(dout[(size_t)P * C + c]));
 }
 
-// nearest upsampling of the coarse input into channels [off, off+C) of the fine output
+// nearest upsampling of the coarse input into channels [off, off+C) of the fine output; 8 channels per thread
 __global__ void k_up(CG gf, const bf16* in, int C, bf16* out, int stride, int off) {
+    const int C8 = C / 8;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)gf.N * C) return;
-    const int c = (int)(t % C), v = (int)(t / C);
+    if (t >= (long)gf.N * C8) return;
+    const int g8 = (int)(t % C8), v = (int)(t / C8);
     const int x = v % gf.nx, y = (v / gf.nx) % gf.ny, z = v / (gf.nx * gf.ny);
     const int P = (x / 2) + (gf.nx / 2) * ((y / 2) + (gf.ny / 2) * (z / 2));
-    out[(size_t)v * stride + off + c] = in[(size_t)P * C + c];
+    *reinterpret_cast<uint4*>(out + (size_t)v * stride + off + 8 * g8) =
+        *reinterpret_cast<const uint4*>(in + (size_t)P * C + 8 * g8);
 }
 
 // adjoint of k_up: din[V][c] = sum of the 8 children dout[child][off+c]
@@ -252,11 +262,14 @@ __global__ void k_up_bwd(CG gf, const bf16* dout, int stride, int off, int C, bf
     din[t] = __float2bfloat16(s);
 }
 
+// channel block copy, 8 channels (16 bytes) per thread; strides, offsets and C multiples of 8
 __global__ void k_copy_ch(int N, const bf16* src, int sstride, int soff, bf16* dst, int dstride, int doff, int C) {
+    const int C8 = C / 8;
     const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long)N * C) return;
-    const int c = (int)(t % C), v = (int)(t / C);
-    dst[(size_t)v * dstride + doff + c] = src[(size_t)v * sstride + soff + c];
+    if (t >= (long)N * C8) return;
+    const int g8 = (int)(t % C8), v = (int)(t / C8);
+    *reinterpret_cast<uint4*>(dst + (size_t)v * dstride + doff + 8 * g8) =
+        *reinterpret_cast<const uint4*>(src + (size_t)v * sstride + soff + 8 * g8);
 }
 
 // g *= (y > 0) (ReLU backward), both [N][C] contiguous
@@ -364,26 +377,29 @@ unsigned blocks(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 // ---------------------------------------------------------------------------
 // 3x3x3 convolution on the 5th-generation tensor cores (tcgen05).
 //
-// One CTA of 128 threads computes an output tile of M = 128 voxels (8 along
-// x, 16 along y, one z plane) for all N output channels; the FP32 accumulator
-// D[128][N] lives in tensor memory (TMEM lane m = voxel m, column n = channel
-// n).  For each block of 16 input channels the CTA stages the input tile with
-// a one-voxel halo (10 x 18 x 3 voxels) in shared memory once, and all 27 taps
-// read their A operand from it: tap (dz, dy, dx) is the same tile shifted by
-// whole 16-byte rows, so it only changes the start address of the shared-
-// memory matrix descriptor.  Weights are staged nine taps at a time into two
-// alternating buffers.  One thread issues the MMAs
-// (tcgen05.mma.cta_group::1.kind::f16: BF16 A and B, FP32 D, M = 128, K = 16)
-// and commits them to an mbarrier; the buffers are rewritten only after the
-// MMAs that read them have completed.  Operands use the canonical K-major
-// layout without swizzling: a core matrix is 8 rows of 16 bytes (8 channels),
-// stored contiguously; the descriptor's leading offset steps to the next 8
-// channels, its stride offset to the next 8 rows.
+// One CTA of 128 threads computes output tiles of 8 (x) x 16 (y) x 2 (z)
+// voxels for all N output channels: two M = 128 GEMMs (one per z plane) whose
+// FP32 accumulators D[128][N] live side by side in tensor memory (TMEM lane m
+// = voxel m of the plane, column zp N + n = channel n).  The work of a tile is
+// a sequence of steps (16-input-channel block cb, nine taps t0 .. t0+8).  For
+// each channel block the CTA stages the input tile with a one-voxel halo
+// (10 x 18 x 4 voxels) in shared memory once, and every tap of both planes
+// reads its A operand from it: tap (dz, dy, dx) is the tile shifted by whole
+// 16-byte rows, so it only changes the start address of the shared-memory
+// matrix descriptor.  Halo tiles and weight blocks are double-buffered and
+// filled with cp.async while the tensor core works on the previous step; one
+// thread issues the MMAs (tcgen05.mma.cta_group::1.kind::f16: BF16 A and B,
+// FP32 D, M = 128, K = 16) and commits them to the step's mbarrier, and a
+// buffer is refilled only after the MMAs that read it have completed.
+// Operands use the canonical K-major layout without swizzling: a core matrix
+// is 8 rows of 16 bytes (8 channels) stored contiguously; the descriptor's
+// leading offset steps to the next 8 channels, its stride offset to the next
+// 8 rows.
 // ---------------------------------------------------------------------------
 constexpr int kTcThreads = 128;
-constexpr int kTileX = 8, kTileY = 16;
-constexpr int kHX = kTileX + 2, kHY = kTileY + 2, kHZ = 3, kKC = 2;  // halo tile; 16 channels = 2 chunks of 8
-constexpr int kHaloUnits = kHZ * kHY * kKC * kHX;                   // 16-byte units
+constexpr int kTileX = 8, kTileY = 16, kTileZ = 2;
+constexpr int kHX = kTileX + 2, kHY = kTileY + 2, kHZ = kTileZ + 2, kKC = 2;  // halo; 16 channels = 2 x 8
+constexpr int kHaloUnits = kHZ * kHY * kKC * kHX;                            // 16-byte units
 constexpr int kHaloBytes = kHaloUnits * 16;
 constexpr int kGuardBytes = 4096;
 constexpr int kTapsPerIter = 9;
@@ -455,10 +471,21 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // tcgen05 convolution: out[v][co] = act(bias[co] + sum_t sum_ci in[v + off(t)][ci] w[t][co][ci]) for
 // co < cout (BF16 out, row stride out_stride); cin and N multiples of 16, N <= 256; ncols: TMEM
-// columns (a power of two >= max(32, N)).  On a wait that runs out, *err is set and the CTA stops.
+// columns (a power of two >= max(32, 2N)).  With up != NULL the input is the concatenation
+// [nearest upsampling of up (cup channels, on the grid of half the extents), in (cin - cup channels)],
+// gathered while staging instead of being stored.  On a wait that runs out, *err is set and the CTA
+// stops.
 __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __restrict__ in, int cin,
+                                                        const bf16* __restrict__ up, int cup,
                                                         const bf16* __restrict__ w, int N,
                                                         const float* __restrict__ bias, int cout, bf16* out,
                                                         int out_stride, int relu, int ncols, int* err) {
@@ -466,9 +493,9 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __rest
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
-    uint4* halo = reinterpret_cast<uint4*>(smem);
-    uint4* bbuf = reinterpret_cast<uint4*>(smem + kHaloBytes + kGuardBytes);
     const int bunits = kTapsPerIter * 2 * N;  // 16-byte units of one weight buffer
+    const uint32_t halo_addr = smem_u32(smem);                                   // 2 halo buffers
+    const uint32_t b_addr = smem_u32(smem + 2 * kHaloBytes + kGuardBytes);       // 2 weight buffers
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
@@ -488,18 +515,28 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __rest
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = idesc_bf16(128, N);
-    const uint32_t halo_addr = smem_u32(halo);
-    const uint32_t b_addr = smem_u32(bbuf);
 
     const int tiles_x = (g.nx + kTileX - 1) / kTileX, tiles_y = (g.ny + kTileY - 1) / kTileY;
-    const long ntiles = (long)tiles_x * tiles_y * g.nz;
+    const int tiles_z = (g.nz + kTileZ - 1) / kTileZ;
+    const long ntiles = (long)tiles_x * tiles_y * tiles_z;
+    const int ncb = cin / 16, steps_per_cb = 27 / kTapsPerIter;
+    const int steps_per_tile = ncb * steps_per_cb;
+    // this CTA's tiles: blockIdx.x, blockIdx.x + gridDim.x, ...; its steps are numbered 0, 1, ...
+    const long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long nsteps = my_tiles * steps_per_tile;
     uint32_t phase[2] = {0u, 0u};
     bool pending[2] = {false, false};
-    int buf = 0;
 
-    // every thread waits for the MMAs that read buffer b before anyone rewrites it; a wait that
-    // runs out sets s_abort, which the whole CTA reads after its next barrier
-    auto wait_buf = [&](int b) {
+    auto tile_origin = [&](long k, int& x0, int& y0, int& z0) {
+        const long tile = blockIdx.x + k * gridDim.x;
+        const long tz = tile / ((long)tiles_x * tiles_y);
+        const int rem = (int)(tile - tz * tiles_x * tiles_y);
+        z0 = (int)tz * kTileZ;
+        y0 = (rem / tiles_x) * kTileY;
+        x0 = (rem % tiles_x) * kTileX;
+    };
+    // wait for the MMAs committed to mbarrier b (every thread; a wait that runs out sets s_abort)
+    auto wait_mma = [&](int b) {
         if (pending[b]) {
             if (!mbar_wait_bounded(&mbar[b], phase[b])) {
                 s_abort = 1;
@@ -509,91 +546,108 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __rest
             pending[b] = false;
         }
     };
-
-    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int z = (int)(tile / ((long)tiles_x * tiles_y));
-        const int rem = (int)(tile - (long)z * tiles_x * tiles_y);
-        const int y0 = (rem / tiles_x) * kTileY, x0 = (rem % tiles_x) * kTileX;
-        bool first = true;
-        for (int cb = 0; cb < cin; cb += 16) {
-            wait_buf(0);
-            wait_buf(1);
-            __syncthreads();
-            if (s_abort) break;
-            // input tile with halo: unit ((hz * kHY + hy) * kKC + kc) * kHX + hx
+    // issue the cp.async loads of step s: the halo tile when s starts a channel block, and the weights
+    auto load_step = [&](long s) {
+        const long k = s / steps_per_tile;
+        const int r = (int)(s - k * steps_per_tile), cbi = r / steps_per_cb, t0 = (r % steps_per_cb) * kTapsPerIter;
+        const int cb = cbi * 16;
+        if (t0 == 0) {
+            int x0, y0, z0;
+            tile_origin(k, x0, y0, z0);
+            const uint32_t hbase = halo_addr + (uint32_t)(((k * ncb + cbi) & 1) * kHaloBytes);
             for (int u = tid; u < kHaloUnits; u += kTcThreads) {
                 const int hx = u % kHX, r1 = u / kHX, kc = r1 % kKC, r2 = r1 / kKC, hy = r2 % kHY, hz = r2 / kHY;
-                const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z + hz - 1;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz)
-                    v = *reinterpret_cast<const uint4*>(in + ((size_t)((long)gz * g.ny + gy) * g.nx + gx) * cin + cb +
-                                                        kc * 8);
-                halo[u] = v;
-            }
-            for (int t0 = 0; t0 < 27; t0 += kTapsPerIter) {
-                const int b = buf;
-                wait_buf(b);
-                // weights of taps t0 .. t0+8, channels cb .. cb+15: unit (t * 2N) + (n/8 * 2 + kc) * 8 + n%8
-                uint4* bb = bbuf + (size_t)b * bunits;
-                for (int u = tid; u < bunits; u += kTcThreads) {
-                    const int t = u / (2 * N), r = u - t * 2 * N;
-                    const int ng = r >> 4, kc = (r >> 3) & 1, n = ng * 8 + (r & 7);
-                    bb[u] = *reinterpret_cast<const uint4*>(w + ((size_t)(t0 + t) * N + n) * cin + cb + kc * 8);
+                const int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
+                const bool ok = gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny && gz >= 0 && gz < g.nz;
+                const int c = cb + kc * 8;
+                const bf16* src = in;
+                if (ok) {
+                    if (c < cup)
+                        src = up + ((size_t)((long)(gz >> 1) * (g.ny >> 1) + (gy >> 1)) * (g.nx >> 1) + (gx >> 1)) * cup +
+                              c;
+                    else
+                        src = in + ((size_t)((long)gz * g.ny + gy) * g.nx + gx) * (cin - cup) + (c - cup);
                 }
-                fence_proxy_async();
-                __syncthreads();
-                if (s_abort) break;
-                if (tid == 0) {
-                    tc_fence_after();
-#pragma unroll 1
-                    for (int t = 0; t < kTapsPerIter; ++t) {
-                        const int tap = t0 + t;
-                        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-                        const int u0 = ((1 + dz) * kHY + (1 + dy)) * kKC * kHX + (1 + dx);
-                        const uint64_t ad = smem_desc(halo_addr + (uint32_t)u0 * 16u, kHX * 16, kKC * kHX * 16);
-                        const uint64_t bd =
-                            smem_desc(b_addr + (uint32_t)(b * bunits + t * 2 * N) * 16u, 8 * 16, kKC * 8 * 16);
-                        tc_mma(tmem, ad, bd, idesc, first ? 0u : 1u);
-                        first = false;
-                    }
-                    tc_commit(&mbar[b]);
-                }
-                first = false;
-                pending[b] = true;
-                buf ^= 1;
+                cp_async16(hbase + (uint32_t)u * 16u, src, ok);
             }
-            if (s_abort) break;
         }
-        wait_buf(0);
-        wait_buf(1);
+        const uint32_t bbase = b_addr + (uint32_t)((s & 1) * bunits * 16);
+        for (int u = tid; u < bunits; u += kTcThreads) {
+            const int t = u / (2 * N), rr = u - t * 2 * N;
+            const int ng = rr >> 4, kc = (rr >> 3) & 1, n = ng * 8 + (rr & 7);
+            cp_async16(bbase + (uint32_t)u * 16u, w + ((size_t)(t0 + t) * N + n) * cin + cb + kc * 8, true);
+        }
+        cp_async_commit();
+    };
+
+    if (nsteps > 0) load_step(0);
+    for (long s = 0; s < nsteps; ++s) {
+        const long k = s / steps_per_tile;
+        const int r = (int)(s - k * steps_per_tile), cbi = r / steps_per_cb, t0 = (r % steps_per_cb) * kTapsPerIter;
+        // operands of step s are in shared memory
+        cp_async_wait_all();
+        fence_proxy_async();
         __syncthreads();
         if (s_abort) break;
-        tc_fence_after();
-        // epilogue: warp w reads TMEM lanes 32w .. 32w+31 (voxels), 8 channels at a time
-        const int m = warp * 32 + lane;
-        const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
-        const bool inside = gx < g.nx && gy < g.ny;
-        bf16* orow = out + ((size_t)((long)z * g.ny + (inside ? gy : 0)) * g.nx + (inside ? gx : 0)) * out_stride;
-        for (int c0 = 0; c0 < N; c0 += 8) {
-            float v[8];
-            tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (inside && c0 + 8 <= cout) {
-                __align__(16) bf16 o[8];
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t hbase = halo_addr + (uint32_t)(((k * ncb + cbi) & 1) * kHaloBytes);
+            const uint32_t bbase = b_addr + (uint32_t)((s & 1) * bunits * 16);
+#pragma unroll 1
+            for (int t = 0; t < kTapsPerIter; ++t) {
+                const int tap = t0 + t;
+                const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+                const uint64_t bd = smem_desc(bbase + (uint32_t)(t * 2 * N) * 16u, 8 * 16, kKC * 8 * 16);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    float a = v[e] + (bias ? bias[c0 + e] : 0.f);
-                    if (relu) a = fmaxf(a, 0.f);
-                    o[e] = __float2bfloat16(a);
+                for (int zp = 0; zp < kTileZ; ++zp) {
+                    const int u0 = ((zp + 1 + dz) * kHY + (1 + dy)) * kKC * kHX + (1 + dx);
+                    const uint64_t ad = smem_desc(hbase + (uint32_t)u0 * 16u, kHX * 16, kKC * kHX * 16);
+                    tc_mma(tmem + (uint32_t)(zp * N), ad, bd, idesc, (r == 0 && t == 0) ? 0u : 1u);
                 }
-                *reinterpret_cast<uint4*>(orow + c0) = *reinterpret_cast<const uint4*>(o);
             }
+            tc_commit(&mbar[s & 1]);
         }
-        tc_fence_before();
-        __syncthreads();
+        pending[s & 1] = true;
+        // the buffers of step s+1 were last read by step s-1: wait for it, then prefetch step s+1
+        wait_mma((int)((s + 1) & 1));
+        if (s + 1 < nsteps) load_step(s + 1);
+        if (r == steps_per_tile - 1) {
+            // last step of the tile: accumulators complete once step s's MMAs are
+            wait_mma((int)(s & 1));
+            __syncthreads();
+            if (s_abort) break;
+            tc_fence_after();
+            int x0, y0, z0;
+            tile_origin(k, x0, y0, z0);
+            const int m = warp * 32 + lane;
+            const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
+            for (int zp = 0; zp < kTileZ; ++zp) {
+                const int gz = z0 + zp;
+                const bool inside = gx < g.nx && gy < g.ny && gz < g.nz;
+                bf16* orow =
+                    out + ((size_t)((long)(inside ? gz : 0) * g.ny + (inside ? gy : 0)) * g.nx + (inside ? gx : 0)) *
+                              out_stride;
+                for (int c0 = 0; c0 < N; c0 += 8) {
+                    float v[8];
+                    tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zp * N + c0), v);
+                    if (inside && c0 + 8 <= cout) {
+                        __align__(16) bf16 o[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            float a = v[e] + (bias ? bias[c0 + e] : 0.f);
+                            if (relu) a = fmaxf(a, 0.f);
+                            o[e] = __float2bfloat16(a);
+                        }
+                        *reinterpret_cast<uint4*>(orow + c0) = *reinterpret_cast<const uint4*>(o);
+                    }
+                }
+            }
+            tc_fence_before();
+        }
     }
-    // a CTA that gave up waits (bounded) for its MMAs in flight before releasing TMEM
-    for (int b = 0; b < 2; ++b)
-        if (pending[b]) mbar_wait_bounded(&mbar[b], phase[b]);
+    // outstanding copies and MMAs (bounded) before TMEM is released
+    cp_async_wait_all();
+    for (int b = 0; b < 2; ++b) wait_mma(b);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
@@ -712,11 +766,11 @@ void unet_carve(cdi_unet* u, char* base, size_t* total) {
 // tcgen05 convolution launch: a persistent grid of as many CTAs as fit at once (shared memory
 // bounds the CTAs per SM below what the TMEM columns allow, so no TMEM allocation ever waits)
 void conv_tc(cdi_unet* u, const CG& gl, const bf16* in, int cin, const bf16* w, int N, const float* bias, int cout,
-             bf16* out, int out_stride, bool relu) {
+             bf16* out, int out_stride, bool relu, const bf16* up = nullptr, int cup = 0) {
     static int nsm = 0, smem_sm = 0;
     static bool attr = false;
-    const int ncols = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
-    const size_t smem = (size_t)kHaloBytes + kGuardBytes + 2 * (size_t)kTapsPerIter * 2 * N * 16;
+    const int ncols = 2 * N <= 32 ? 32 : 2 * N <= 64 ? 64 : 2 * N <= 128 ? 128 : 2 * N <= 256 ? 256 : 512;
+    const size_t smem = 2 * (size_t)kHaloBytes + kGuardBytes + 2 * (size_t)kTapsPerIter * 2 * N * 16;
     if (!attr) {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -729,10 +783,11 @@ void conv_tc(cdi_unet* u, const CG& gl, const bf16* in, int cin, const bf16* w, 
     // CTAs per SM: shared memory (1 KB reserved per CTA, plus the static 1 KB), threads, TMEM columns
     int per = (int)((size_t)smem_sm / (smem + 2048));
     per = std::max(1, std::min({per, 2048 / kTcThreads, 512 / ncols}));
-    const long tiles = (long)((gl.nx + kTileX - 1) / kTileX) * ((gl.ny + kTileY - 1) / kTileY) * gl.nz;
+    const long tiles = (long)((gl.nx + kTileX - 1) / kTileX) * ((gl.ny + kTileY - 1) / kTileY) *
+                       ((gl.nz + kTileZ - 1) / kTileZ);
     const unsigned grid = (unsigned)std::max(1L, std::min(tiles, (long)nsm * per));
-    k_conv_tc<<<grid, kTcThreads, smem, u->stream>>>(gl, in, cin, w, N, bias, cout, out, out_stride, relu ? 1 : 0,
-                                                     ncols, u->tc_err);
+    k_conv_tc<<<grid, kTcThreads, smem, u->stream>>>(gl, in, cin, up, cup, w, N, bias, cout, out, out_stride,
+                                                     relu ? 1 : 0, ncols, u->tc_err);
 }
 
 // y = conv(in) for layer l on level grid gl into out (stride, offset)
@@ -819,28 +874,40 @@ void refresh_weights(cdi_unet* u) {
     u->weights_ready = true;
 }
 
-// forward pass from u->x to u->y (FP32)
-void forward(cdi_unet* u) {
-    const CG *g = u->g;
+// forward pass from u->x to u->y (FP32).  With keep_concat the decoder inputs
+// [up(coarser), skip] are stored (the weight gradients read them); otherwise the
+// tcgen05 convolution gathers them while staging its input tiles.
+void forward(cdi_unet* u, bool keep_concat = true) {
+    const CG* g = u->g;
     cudaStream_t s = u->stream;
+    const bool fuse = !keep_concat && u->use_tc;
     conv_fwd<false>(u, 0, g[0], u->x, u->e0, 16, 0, true);
-    k_pool<<<blocks(g[1].N * 16L), 256, 0, s>>>(g[0], u->e0, 16, u->p0);
+    k_pool<<<blocks(g[1].N * 2L), 256, 0, s>>>(g[0], u->e0, 16, u->p0);
     conv_fwd<false>(u, 1, g[1], u->p0, u->e1, 32, 0, true);
-    k_pool<<<blocks(g[2].N * 32L), 256, 0, s>>>(g[1], u->e1, 32, u->p1);
+    k_pool<<<blocks(g[2].N * 4L), 256, 0, s>>>(g[1], u->e1, 32, u->p1);
     conv_fwd<false>(u, 2, g[2], u->p1, u->e2, 64, 0, true);
-    k_pool<<<blocks(g[3].N * 64L), 256, 0, s>>>(g[2], u->e2, 64, u->p2);
+    k_pool<<<blocks(g[3].N * 8L), 256, 0, s>>>(g[2], u->e2, 64, u->p2);
     conv_fwd<false>(u, 3, g[3], u->p2, u->b, 128, 0, true);
-    k_up<<<blocks(g[2].N * 128L), 256, 0, s>>>(g[2], u->b, 128, u->c2, 192, 0);
-    k_copy_ch<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2].N, u->e2, 64, 0, u->c2, 192, 128, 64);
-    conv_fwd<false>(u, 4, g[2], u->c2, u->d2, 64, 0, true);
-    k_up<<<blocks(g[1].N * 64L), 256, 0, s>>>(g[1], u->d2, 64, u->c1, 96, 0);
-    k_copy_ch<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1].N, u->e1, 32, 0, u->c1, 96, 64, 32);
-    conv_fwd<false>(u, 5, g[1], u->c1, u->d1, 32, 0, true);
-    k_up<<<blocks(g[0].N * 32L), 256, 0, s>>>(g[0], u->d1, 32, u->c0, 48, 0);
-    k_copy_ch<<<blocks(g[0].N * 16L), 256, 0, s>>>(g[0].N, u->e0, 16, 0, u->c0, 48, 32, 16);
-    conv_fwd<false>(u, 6, g[0], u->c0, u->d0, 16, 0, true);
+    g_launches += 7;
+    if (fuse) {
+        conv_tc(u, g[2], u->e2, 192, u->Wb[4], 64, u->B[4], 64, u->d2, 64, true, u->b, 128);
+        conv_tc(u, g[1], u->e1, 96, u->Wb[5], 32, u->B[5], 32, u->d1, 32, true, u->d2, 64);
+        conv_tc(u, g[0], u->e0, 48, u->Wb[6], 16, u->B[6], 16, u->d0, 16, true, u->d1, 32);
+        g_launches += 3;
+    } else {
+        k_up<<<blocks(g[2].N * 16L), 256, 0, s>>>(g[2], u->b, 128, u->c2, 192, 0);
+        k_copy_ch<<<blocks(g[2].N * 8L), 256, 0, s>>>(g[2].N, u->e2, 64, 0, u->c2, 192, 128, 64);
+        conv_fwd<false>(u, 4, g[2], u->c2, u->d2, 64, 0, true);
+        k_up<<<blocks(g[1].N * 8L), 256, 0, s>>>(g[1], u->d2, 64, u->c1, 96, 0);
+        k_copy_ch<<<blocks(g[1].N * 4L), 256, 0, s>>>(g[1].N, u->e1, 32, 0, u->c1, 96, 64, 32);
+        conv_fwd<false>(u, 5, g[1], u->c1, u->d1, 32, 0, true);
+        k_up<<<blocks(g[0].N * 4L), 256, 0, s>>>(g[0], u->d1, 32, u->c0, 48, 0);
+        k_copy_ch<<<blocks(g[0].N * 2L), 256, 0, s>>>(g[0].N, u->e0, 16, 0, u->c0, 48, 32, 16);
+        conv_fwd<false>(u, 6, g[0], u->c0, u->d0, 16, 0, true);
+        g_launches += 9;
+    }
     conv_fwd<true>(u, 7, g[0], u->d0, u->y, 1, 0, false);
-    g_launches += 22;
+    g_launches += 1;
 }
 
 // gradients of the mean squared error (u->y against u->t) into gW, gB
@@ -862,19 +929,19 @@ void backward(cdi_unet* u) {
     conv_dgrad(u, 6, g[0], u->gd0, u->gc0);
     k_up_bwd<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[0], u->gc0, 48, 0, 32, u->gd1);
     k_relu_mask<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1].N * 32L, u->gd1, u->d1);
-    k_copy_ch<<<blocks(g[0].N * 16L), 256, 0, s>>>(g[0].N, u->gc0, 48, 32, u->ge0, 16, 0, 16);
+    k_copy_ch<<<blocks(g[0].N * 2L), 256, 0, s>>>(g[0].N, u->gc0, 48, 32, u->ge0, 16, 0, 16);
     // d1
     conv_wgrad(u, 5, g[1], u->c1, u->gd1);
     conv_dgrad(u, 5, g[1], u->gd1, u->gc1);
     k_up_bwd<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[1], u->gc1, 96, 0, 64, u->gd2);
     k_relu_mask<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2].N * 64L, u->gd2, u->d2);
-    k_copy_ch<<<blocks(g[1].N * 32L), 256, 0, s>>>(g[1].N, u->gc1, 96, 64, u->ge1, 32, 0, 32);
+    k_copy_ch<<<blocks(g[1].N * 4L), 256, 0, s>>>(g[1].N, u->gc1, 96, 64, u->ge1, 32, 0, 32);
     // d2
     conv_wgrad(u, 4, g[2], u->c2, u->gd2);
     conv_dgrad(u, 4, g[2], u->gd2, u->gc2);
     k_up_bwd<<<blocks(g[3].N * 128L), 256, 0, s>>>(g[2], u->gc2, 192, 0, 128, u->gb);
     k_relu_mask<<<blocks(g[3].N * 128L), 256, 0, s>>>(g[3].N * 128L, u->gb, u->b);
-    k_copy_ch<<<blocks(g[2].N * 64L), 256, 0, s>>>(g[2].N, u->gc2, 192, 128, u->ge2, 64, 0, 64);
+    k_copy_ch<<<blocks(g[2].N * 8L), 256, 0, s>>>(g[2].N, u->gc2, 192, 128, u->ge2, 64, 0, 64);
     // bottleneck
     conv_wgrad(u, 3, g[3], u->p2, u->gb);
     conv_dgrad(u, 3, g[3], u->gb, u->gp2);
@@ -952,7 +1019,7 @@ cudaError_t unet_predict_device(cdi_unet* u, const MG& mg, const T* phi_dev, dou
     k_input_solver<T><<<blocks(N * 16), 256, 0, s>>>((int)N, ops::fbuf<T>(mg.lv[0]), mg.scalf + SF_FMEAN_HI,
                                                      phi_dev, (float)(rho1 - rho2), (float)rho2, (float)(1.0 / rmax),
                                                      u->sd, u->sf, u->x);
-    forward(u);
+    forward(u, false);
     k_output_solver<T><<<blocks(N), 256, 0, s>>>((int)N, u->y, u->sd, u->sf, ops::pbuf<T>(mg.lv[0]));
     g_launches += 3;
     u->stream = keep;
@@ -1074,7 +1141,7 @@ cdi_status cdi_unet_forward(cdi_unet* u, const double* x_host, double* y_host) {
     if (!u->weights_ready) refresh_weights(u);
     cdi_status st = upload_x(u, x_host);
     if (st) return st;
-    forward(u);
+    forward(u, false);
     const long N = u->g[0].N;
     std::vector<float> y(N);
     if (cudaMemcpyAsync(y.data(), u->y, (size_t)N * 4, cudaMemcpyDeviceToHost, u->stream) != cudaSuccess ||
@@ -1091,7 +1158,7 @@ cdi_status cdi_unet_forward_device(cdi_unet* u, const float* x_dev, float* y_dev
     if (!u->weights_ready) refresh_weights(u);
     const long N = u->g[0].N;
     k_input_dev<<<blocks(N * 16), 256, 0, u->stream>>>((int)N, x_dev, u->x);
-    forward(u);
+    forward(u, false);
     g_launches += 1;
     if (cudaMemcpyAsync(y_dev, u->y, (size_t)N * 4, cudaMemcpyDeviceToDevice, u->stream) != cudaSuccess)
         return ufail(u, CDI_ECUDA, "output copy failed");

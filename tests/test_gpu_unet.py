@@ -221,3 +221,24 @@ def test_tensor_core_and_warp_mma_convolutions_agree(n):
     _, g_tc = nets[0].train_step(x, t[..., 0], lr=0.0, want_grads=True)
     _, g_mma = nets[1].train_step(x, t[..., 0], lr=0.0, want_grads=True)
     assert relnorm(g_tc, g_mma) < 1e-2
+
+
+def test_fused_decoder_inputs_match_stored_ones():
+    """Inference gathers the decoder inputs [up(coarser), skip] while staging
+    the convolution tiles; training stores them.  Both feed the same BF16
+    values to the same MMAs, so the outputs are identical."""
+    torch = pytest.importorskip("torch")
+    n = (16, 24, 16)
+    shape = (n[2], n[1], n[0])
+    P, x, t = random_case(shape, 31)
+    net = cdi.Unet(n)
+    net.set_params(flat(P))
+    y_host = net.forward(x)                       # fused gather
+    xd = torch.tensor(x.reshape(-1), dtype=torch.float32, device="cuda")
+    yd = torch.empty(x.size // 2, dtype=torch.float32, device="cuda")
+    net.forward_device(xd, yd)                    # fused gather, FP32 input
+    torch.cuda.synchronize()
+    y_ref, _ = ref.forward(as_stored(P), x, store=ref.bf16_round)
+    assert relnorm(yd.cpu().numpy().reshape(shape), y_ref[..., 0]) < 2e-3
+    loss, _ = net.train_step(x, t[..., 0], lr=0.0, want_grads=True)   # stored concatenations
+    assert abs(loss - float(np.mean((y_host - t[..., 0]) ** 2))) <= 1e-6 * loss
