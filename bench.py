@@ -56,34 +56,25 @@ def workload():
 # algorithmic bytes per launch of the kernels the roofline can name
 # (unique words each launch must read or write at least once)
 # ---------------------------------------------------------------------------
-def vcycle_bytes(D):
-    """Bytes per finest-level cell of one V-cycle plus its convergence test.
-    The cycle itself runs in FP32 (error e, residual r, D face coefficients):
-    2+2 red-black sweeps each read e, r and the coefficients and write e; the
-    residual-restriction pass reads e, r, the coefficients and writes the
-    coarse r and e; the prolongation reads the coarse e and updates e; all
-    levels together weigh 1/(1 - 2^-D) of the finest one.  The FP64 defect
-    correction adds p += e (read p and e, write p) and the residual of the
-    test (read p, f and the D FP64 coefficients, write the FP32 r)."""
-    fine = 4 * (3 + D) + (2 + D) + 3.0 / 2 ** D + 2
-    return 4 * fine / (1 - 2.0 ** -D) + (8 + 4 + 8) + (8 * (2 + D) + 4)
-
-
-def solve_fixed_bytes(D, word):
-    """Bytes per cell of one pressure solve outside its V-cycles: divergence
-    (read D face velocities, write the FP64 f), coefficients (read phi, write
-    D FP32 and D FP64 face values) and projection (read p, phi and the D
-    velocities, write the D velocities)."""
-    return (D * word + 8) + (word + 12 * D) + (8 + word * (1 + 2 * D))
+def vcycle_words(D):
+    """Words per finest-level cell of one V-cycle (the per-unit figure of the
+    measurement contract): on the finest level 4 smoothing sweeps x 4 words (p
+    read and write, f, phi), the residual 4, the restriction 1 + 2^-D, the
+    prolongation and correction 2 + 2^-D; the whole hierarchy weighs
+    1/(1 - 2^-D) of the finest level (about 31 words in 2D, 27 in 3D)."""
+    fine = 4 * 4 + 4 + (1 + 2.0 ** -D) + (2 + 2.0 ** -D)
+    return fine / (1 - 2.0 ** -D)
 
 
 def step_bytes(D, N, word, vcycles_per_step):
-    """Algorithmic bytes of one full step: per RK stage the fused stencil
-    minimum (read the stage state and y^n, read+write the accumulator, write
-    the next stage: 5(1+D) words of the state precision), four pressure solves
-    and the V-cycles of the step."""
-    stencil = 4 * 5 * (1 + D) * word
-    return N * (stencil + 4 * solve_fixed_bytes(D, word) + vcycles_per_step * vcycle_bytes(D))
+    """Algorithmic bytes of one full step, B = W [4 * 5(1+D) + 4 (3 + (2D+1) +
+    N_V V_D)] per cell: per RK stage the fused stencil minimum (read the stage
+    state and y^n, read+write the accumulator, write the next stage: 5(1+D)
+    words), per pressure solve the divergence (3 words), the projection
+    (2D+1) and N_V V-cycles of V_D words; W is the state word size."""
+    nv_per_solve = vcycles_per_step / 4.0
+    words = 4 * 5 * (1 + D) + 4 * (3 + (2 * D + 1) + nv_per_solve * vcycle_words(D))
+    return N * word * words
 
 
 def algorithmic_bytes(kernel, dim, N, NP, word):

@@ -71,6 +71,11 @@ struct cdi_ctx {
     bool persist_ready = false;
     void* tail_dev = nullptr;  // launch-per-kernel path: descriptor of the V-cycle's shared-memory tail
     bool tail_ready = false;
+    // launch-per-kernel path: one V-cycle plus its residual norm as a CUDA graph per form
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
+    long vc_nodes[2] = {0, 0};
+    bool vc_graph_failed = false;
     PersistLayout playout{};
     int persist_lt = 0;
     size_t persist_smem = 0;
@@ -318,6 +323,47 @@ cdi_status kernels_tail_setup(cdi_ctx* c) {
     return CDI_OK;
 }
 
+// One V-cycle and the residual norm after it.  Outside the event profiler the
+// sequence (about 50 launches, most of them on small coarse levels) is
+// captured once into a CUDA graph on a private stream and replayed on the
+// context's stream, which removes the per-launch latency.
+template <typename T>
+void vcycle_and_residual(cdi_ctx* c) {
+    const Geom& g = c->g;
+    MG& mg = c->mg;
+    const int k = sizeof(T) == 8 ? 0 : 1;
+    if (g_prof.target < 0 && !c->vc_graph_failed) {
+        if (!c->vc_exec[k]) {
+            bool ok = c->cap_stream || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+            cudaGraph_t gr = nullptr;
+            const long l0 = g_launches;
+            if (ok) ok = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                launch_vcycle<T>(g, mg, c->npre, c->npost, c->cap_stream);
+                launch_resid_norm<T>(g, mg, c->cap_stream);
+                ok = cudaStreamEndCapture(c->cap_stream, &gr) == cudaSuccess && gr;
+            }
+            c->vc_nodes[k] = g_launches - l0;
+            g_launches = l0;
+            if (ok) ok = cudaGraphInstantiate(&c->vc_exec[k], gr, 0) == cudaSuccess;
+            if (gr) cudaGraphDestroy(gr);
+            if (!ok) {
+                cudaGetLastError();
+                c->vc_exec[k] = nullptr;
+                c->vc_graph_failed = true;
+            }
+        }
+        if (c->vc_exec[k] && cudaGraphLaunch(c->vc_exec[k], c->stream) == cudaSuccess) {
+            g_launches += c->vc_nodes[k];
+            return;
+        }
+        cudaGetLastError();
+        c->vc_graph_failed = true;
+    }
+    launch_vcycle<T>(g, mg, c->npre, c->npost, c->stream);
+    launch_resid_norm<T>(g, mg, c->stream);
+}
+
 template <typename T>
 cdi_status mg_solve(cdi_ctx* c) {
     const Geom& g = c->g;
@@ -339,8 +385,7 @@ cdi_status mg_solve(cdi_ctx* c) {
         return CDI_OK;
     }
     while (rn > c->tol * fn && cyc < c->max_vcycles) {
-        launch_vcycle<T>(g, mg, c->npre, c->npost, s);
-        launch_resid_norm<T>(g, mg, s);
+        vcycle_and_residual<T>(c);
         st = read_scalars(c);
         if (st) return st;
         rn = c->host_scal[S_RNORM];
@@ -676,6 +721,11 @@ cdi_status cdi_bind_workspace(cdi_ctx* c, void* dev_ptr, size_t bytes, void* str
     carve(c, c->ws, &total);
     c->mg.tail_args = nullptr;
     c->tail_ready = false;
+    for (int k = 0; k < 2; ++k)
+        if (c->vc_exec[k]) {
+            cudaGraphExecDestroy(c->vc_exec[k]);
+            c->vc_exec[k] = nullptr;
+        }
     if (!c->host_scal) {
         cdi_status st = cuda_check(c, cudaMallocHost((void**)&c->host_scal, S_NSCAL * sizeof(double)),
                                    "cudaMallocHost");
@@ -1074,6 +1124,9 @@ const char* cdi_last_error(const cdi_ctx* c) {
 
 void cdi_destroy(cdi_ctx* c) {
     if (!c) return;
+    for (int k = 0; k < 2; ++k)
+        if (c->vc_exec[k]) cudaGraphExecDestroy(c->vc_exec[k]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->host_scal) cudaFreeHost(c->host_scal);
     delete c;
 }
