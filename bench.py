@@ -425,6 +425,31 @@ def unet_form(flush, n_train=64, pairs=40, iters=800, n_infer=256):
     params = net.get_params()
     del net
     torch.cuda.empty_cache()
+    # the wide 3D drop (512 x 256 x 256, density ratio 20): V-cycles per solve and time per step
+    # from zero, from the previous pressure and from the network trained above (it is fully
+    # convolutional); warm-up steps first, then timed steps, each mode from the same initial state
+    wl5 = inputs.drop_3d_wide(512)
+    c5 = {"grid": list(wl5.n), "warmup_steps": 10, "timed_steps": 10, "dt": wl5.dt, "precision": "fp32_mixed",
+          "exec": "kernels", "pressure_tol": PRESSURE_TOL}
+    for name, warm in (("zero", cdi.WARM_ZERO), ("previous", cdi.WARM_PREV), ("network", cdi.WARM_UNET)):
+        r = cdi.from_workload(wl5, precision=cdi.FP32_MIXED, tol=PRESSURE_TOL)
+        r.set_exec(cdi.EXEC_KERNELS)
+        r.set_solver(PRESSURE_TOL, 100, warm)
+        big = None
+        if warm == cdi.WARM_UNET:
+            big = cdi.Unet(wl5.n)
+            big.set_params(params)
+            r.set_warm_unet(big)
+        r.step(wl5.dt, 10)
+        cyc, ms = 0, 0.0
+        for _ in range(10):
+            ms += _timed_steps(lambda: r.step(wl5.dt, 1), 1, flush)
+            cyc += r.last_stats()["total_cycles_call"]
+        c5["vcycles_per_solve_" + name] = cyc / 40.0
+        c5["ms_per_step_" + name] = ms / 10
+        del r, big
+        torch.cuda.empty_cache()
+    res["drop3d_512x256x256"] = c5
     big = cdi.Unet((n_infer,) * 3)
     big.set_params(params)
     N = n_infer ** 3

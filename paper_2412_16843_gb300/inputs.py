@@ -182,6 +182,23 @@ def drop_3d(n: int = 256, theta_eq_deg: float = 60.0, seed: int = 12345,
                     math.radians(theta_eq_deg), h, 0.0, 0.0, 3.5e-5, 5000, phi)
 
 
+def drop_3d_wide(nx: int = 512, seed: int = 12345, noise: float = 1e-3) -> Workload:
+    """Wide 3D drop: nx x nx/2 x nx/2 on [0,2]x[0,1]x[0,1], walls z, a 90 deg
+    cap R = 0.25 at (1, 0.5, 0) relaxing on a 45 deg wall; density ratio 20
+    (rho 1 / 0.05), viscosity ratio 10 (mu 0.05 / 0.005), sigma = 1, eps = dx,
+    gamma = 1, slip length dx; dt = 3.0e-5 (the RK4 viscous limit of the
+    lighter fluid, nu = 0.1, is 0.23 dx^2 / nu = 3.6e-5 at dx = 1/256);
+    seeded uniform noise clamped to [0,1]."""
+    ny = nx // 2
+    h = 2.0 / nx
+    phi = cap_phi_3d(nx, ny, ny, h, 0.25, math.pi / 2, 1.0, 0.5, h)
+    if noise > 0:
+        phi = add_noise(phi, noise, seed)
+    return Workload("drop3d_%dx%dx%d" % (nx, ny, ny), 3, (nx, ny, ny), (2.0, 1.0, 1.0),
+                    1.0, 0.05, 0.05, 0.005, 1.0, h, 1.0,
+                    math.radians(45.0), h, 0.0, 0.0, 3.0e-5, 300, phi)
+
+
 SWEEP_SIZES = (64, 96, 128, 192, 256, 384, 512)
 
 
