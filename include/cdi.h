@@ -202,6 +202,15 @@ cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
  * same arithmetic. */
 cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
 
+/* Red-black Gauss-Seidel sweeps before and after the coarse-grid correction
+ * on every multigrid level (each in [1, 4]; default 1 and 1 in 2D, 2 and 2 in
+ * 3D: measured fastest per step of a single 2D or 3D grid; in batched
+ * execution, where an instance's barriers are CTA barriers, 2 and 2 measured
+ * faster on the 2D sweep).  The solve
+ * still iterates to its tolerance; the counts trade work per V-cycle against
+ * V-cycles per solve. */
+cdi_status cdi_set_smoothing(cdi_ctx* ctx, int npre, int npost);
+
 /* Longest wait (nanoseconds, 0 .. 6e10; default 2e9) of a grid barrier in the
  * persistent step kernel before the call ends with CDI_ETIMEOUT.  A timed-out
  * call leaves the state undefined but the context and the device usable. */

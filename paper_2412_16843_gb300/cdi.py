@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "cdi_last_stats": [P, IP, DP, IP, IP],
         "cdi_set_exec": [P, I],
         "cdi_set_barrier_timeout": [P, ctypes.c_longlong],
+        "cdi_set_smoothing": [P, I, I],
         "cdi_launches_per_step": [P, ctypes.POINTER(ctypes.c_long)],
         "cdi_profile_start": [P, ctypes.c_char_p, I],
         "cdi_profile_stop": [P, DP, ctypes.POINTER(ctypes.c_long)],
@@ -284,6 +285,9 @@ class Solver:
 
     def set_exec(self, mode: int):
         self._check(self.lib.cdi_set_exec(self.h, mode))
+
+    def set_smoothing(self, npre: int, npost: int):
+        self._check(self.lib.cdi_set_smoothing(self.h, npre, npost))
 
     def set_barrier_timeout(self, ns: int):
         self._check(self.lib.cdi_set_barrier_timeout(self.h, int(ns)))

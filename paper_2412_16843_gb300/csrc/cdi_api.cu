@@ -662,6 +662,8 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     c->g = make_geom(dim, n, h);
     for (int a = 0; a < 3; ++a) c->L[a] = L[a];
     c->precision = precision;
+    // V(1,1) in 2D, where the small grids are bound by the barriers of each sweep; V(2,2) in 3D
+    c->npre = c->npost = (dim == 2) ? 1 : 2;
     c->ph.delta = precision == CDI_FP64 ? 1e-12 : 1e-6;
     c->ph.tau = precision == CDI_FP64 ? 1e-12 : 1e-6;
     c->ph.model = M4A;
@@ -924,6 +926,22 @@ cdi_status cdi_last_pressure(cdi_ctx* c, double* f, double* p) {
     }
     if (p) st = download_level0(c, p, true);
     return st;
+}
+
+cdi_status cdi_set_smoothing(cdi_ctx* c, int npre, int npost) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (npre < 1 || npre > 4 || npost < 1 || npost > 4) return fail(c, CDI_EINVAL, "sweeps must lie in [1, 4]");
+    c->npre = npre;
+    c->npost = npost;
+    // the launch-per-kernel tail descriptor and V-cycle graphs hold the sweep counts
+    c->tail_ready = false;
+    c->mg.tail_args = nullptr;
+    for (int k = 0; k < 2; ++k)
+        if (c->vc_exec[k]) {
+            cudaGraphExecDestroy(c->vc_exec[k]);
+            c->vc_exec[k] = nullptr;
+        }
+    return CDI_OK;
 }
 
 cdi_status cdi_set_barrier_timeout(cdi_ctx* c, long long ns) {
