@@ -188,8 +188,8 @@ cdi_status cdi_solve_pressure(cdi_ctx* ctx, const double* f, double* p);
 cdi_status cdi_last_stats(cdi_ctx* ctx, int* vcycles, double* resid,
                           int* max_vcycles_step, int* total_vcycles_call);
 
-/* Number of kernel launches the last cdi_step issued per time step (the
- * persistent mode issues one launch per cdi_step call). */
+/* Number of kernel launches the last cdi_step issued per time step, rounded
+ * up (the persistent mode issues one launch per cdi_step call and reports 1). */
 cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
 
 /* Execution mode of cdi_step: CDI_EXEC_PERSISTENT runs all steps of the call

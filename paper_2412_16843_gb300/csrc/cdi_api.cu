@@ -900,7 +900,7 @@ cdi_status cdi_step(cdi_ctx* c, double dt, int nsteps) {
             if (st) return st;
         }
     }
-    c->launches_per_step = (g_launches - l0) / nsteps;
+    c->launches_per_step = (g_launches - l0 + nsteps - 1) / nsteps;   // rounded up: 1 for a persistent call
     return cuda_check(c, cudaStreamSynchronize(c->stream), "cdi_step");
 }
 

@@ -312,3 +312,31 @@ def test_extrapolated_warm_start_parity_and_fewer_cycles(exec_mode):
     for a in range(2):
         assert rel(vel_g[a], vel_o[a]) < 1e-10
     assert cyc_ext < cyc_prev, (cyc_ext, cyc_prev)
+
+
+@EXEC_MODES
+def test_smoothing_counts_change_cycles_not_the_solution(exec_mode):
+    """The red-black sweeps before and after each coarse-grid correction
+    (cdi_set_smoothing) change only how the solve gets to its tolerance: after
+    20 steps V(1,1), V(2,2) and V(3,1) all match the oracle within the FP64
+    bar; more sweeps need no more V-cycles.  Counts outside [1, 4] are
+    rejected."""
+    wl = inputs.couette_2d(128, 32, 1.0)
+    o = oracle.from_workload(wl, tol=1e-12)
+    o.step(wl.dt, 20)
+    phi_o, vel_o, _ = o.get_state()
+    cycles = {}
+    for npre, npost in ((1, 1), (2, 2), (3, 1)):
+        g = cdi.from_workload(wl, tol=1e-12)
+        g.set_exec(exec_mode)
+        g.set_smoothing(npre, npost)
+        g.step(wl.dt, 20)
+        cycles[(npre, npost)] = g.last_stats()["total_cycles_call"]
+        phi_g, vel_g, _ = g.get_fields()
+        assert rel(phi_g, phi_o) < 1e-11
+        for a in range(2):
+            assert rel(vel_g[a], vel_o[a]) < 1e-10
+    assert cycles[(2, 2)] <= cycles[(1, 1)], cycles
+    for bad in ((0, 1), (1, 5)):
+        with pytest.raises(cdi.CdiError):
+            g.set_smoothing(*bad)
