@@ -311,10 +311,12 @@ struct InstStats {
 
 // control block of the single-grid persistent kernel in the workspace
 struct PersistCtl {
-    unsigned bar_count;
-    unsigned bar_gen;
+    // grid-barrier arrivals since the launch (zeroed by the host before it);
+    // kBarError added when a CTA gives up waiting
+    unsigned long long bar;
     InstStats st;
 };
+constexpr unsigned long long kBarError = 1ull << 62;
 
 // offsets (in floats) of the FP32 multigrid tail levels in dynamic shared
 // memory, and of the FP64 scratch of the coarsest dense solve (in doubles,

@@ -9,12 +9,13 @@
 //   k_coef0          face coefficients 1/rho_f, rho_f the mean of the two  Sec. 2 (rho linear in phi)
 //                    adjacent cells, zero on the walls
 //   k_resid          residual r = f - A p in the form's precision, |r|^2,
-//                    FP32 copy of r, e = 0
+//                    FP32 copy of r
 //   k_rbgs           FP32 red-black Gauss-Seidel sweep of A e = r
 //   k_resid_restrict FP32 residual and its restriction (mean of the 2^D children)
 //   k_prolong        FP32 cell-centred (bi/tri)linear prolongation
 //   k_coarse         FP64 dense solve of the coarsest level in one CTA
-//   k_update         p += e (FP64, or double-float in the FP32-mixed form)
+//   k_update         p += e (FP64, or double-float in the FP32-mixed form) where
+//                    the V-cycle's last level-0 sweep does not add it
 //   k_project        u = u* - c dt grad p / rho_f on every interior face     Eq. (no-penetration BC)
 //   k_mass, k_umax, k_contact_line: FP64 reductions                          Sec. 2, 3.1, 5.1
 //
@@ -185,7 +186,6 @@ __global__ void k_resid(MGLevel L0, const float* fmean_df, double* part) {
     for (long c = (long)blockIdx.x * blockDim.x + threadIdx.x; c < L0.g.N; c += stride) {
         const T r = ops::resid_form_at<Ld, DIM>(L0, p, f, fmean, c);
         L0.r[c] = (float)r;
-        L0.e[c] = 0.f;
         acc += r * r;
     }
     const double a = block_sum((double)acc);
@@ -205,11 +205,16 @@ __global__ void k_rbgs(Geom g, const float* b0, const float* b1, const float* b2
 // no index is recovered by division.  Coefficients 2 / (rho_c + rho_nb) from
 // the FP32 cell densities, zero through the walls (the last axis); the update
 // e_c = (sum b e_nb - r h^2) / sum b is the Gauss-Seidel step of apply_L_rho.
+// kSweepFromZero: the first red pass of a V-cycle, whose neighbours are all
+// zero (e is not cleared beforehand: every cell of e is written before it is
+// read).  kSweepUpdate: the last black pass, which also adds the now final
+// correction of both cells of the thread's pair (2 ix, 2 ix + 1) to p.
 constexpr int kSweepX = 64, kSweepY = 4;
-template <int DIM>
+enum SweepMode { kSweepPlain = 0, kSweepFromZero = 1, kSweepUpdate = 2 };
+template <typename T, int DIM, int MODE>
 __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float* __restrict__ rho,
                                                              float* __restrict__ e, const float* __restrict__ r,
-                                                             int colour, float h2) {
+                                                             int colour, float h2, PT<T>* __restrict__ p) {
     const int nx = g.n[0], ny = g.n[1];
     const int ix = blockIdx.x * kSweepX + threadIdx.x;
     const int j = blockIdx.y * kSweepY + threadIdx.y;
@@ -219,43 +224,51 @@ __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float
     const long row = (long)nx * ((long)j + (long)ny * k);
     const long c = row + i;
     const float rc = rho[c];
+    // e of a neighbour (zero in the first pass: the loads are not issued)
+    auto en = [&](long n) { return MODE == kSweepFromZero ? 0.f : e[n]; };
     const long xm = row + (i == 0 ? nx - 1 : i - 1), xp = row + (i == nx - 1 ? 0 : i + 1);
     float bsum, off;
     {
         const float b0 = __fdividef(2.f, rc + rho[xm]), b1 = __fdividef(2.f, rc + rho[xp]);
         bsum = b0 + b1;
-        off = b0 * e[xm] + b1 * e[xp];
+        off = b0 * en(xm) + b1 * en(xp);
     }
     if (DIM == 2) {  // y is the wall axis
         if (j > 0) {
             const float b = __fdividef(2.f, rc + rho[c - nx]);
             bsum += b;
-            off += b * e[c - nx];
+            off += b * en(c - nx);
         }
         if (j < ny - 1) {
             const float b = __fdividef(2.f, rc + rho[c + nx]);
             bsum += b;
-            off += b * e[c + nx];
+            off += b * en(c + nx);
         }
     } else {
         const long ym = (j == 0) ? c + (long)(ny - 1) * nx : c - nx;
         const long yp = (j == ny - 1) ? c - (long)(ny - 1) * nx : c + nx;
         const float b2 = __fdividef(2.f, rc + rho[ym]), b3 = __fdividef(2.f, rc + rho[yp]);
         bsum += b2 + b3;
-        off += b2 * e[ym] + b3 * e[yp];
+        off += b2 * en(ym) + b3 * en(yp);
         const long np = g.NP;
         if (k > 0) {
             const float b = __fdividef(2.f, rc + rho[c - np]);
             bsum += b;
-            off += b * e[c - np];
+            off += b * en(c - np);
         }
         if (k < g.n[2] - 1) {
             const float b = __fdividef(2.f, rc + rho[c + np]);
             bsum += b;
-            off += b * e[c + np];
+            off += b * en(c + np);
         }
     }
-    e[c] = __fdividef(off - r[c] * h2, bsum);
+    const float ec = __fdividef(off - r[c] * h2, bsum);
+    e[c] = ec;
+    if (MODE == kSweepUpdate) {
+        const long co = c ^ 1;  // the pair's other cell (row starts are even: nx is even)
+        p[c] = ops::p_add(p[c], ec);
+        p[co] = ops::p_add(p[co], e[co]);
+    }
 }
 
 template <int DIM>
@@ -515,18 +528,21 @@ void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cuda
     ++g_launches;
 }
 
-template <int DIM>
-static void vcycle_rec(MG& mg, int l, int npre, int npost, cudaStream_t s) {
+// One V-cycle from level l.  On level 0 (when the single-CTA tail does not
+// take it) the first sweep starts from e = 0 and the last one adds e to p;
+// returns whether p has been updated.
+template <typename T, int DIM>
+static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_t s) {
     MGLevel& L = mg.lv[l];
     if (mg.tail_args && l == mg.tail_lt) {
         CDI_PROF(KC_COARSE, s, launch_tail(mg.tail_args, DIM, mg.tail_smem, s));
         ++g_launches;
-        return;
+        return false;
     }
     if (l == mg.nlev - 1) {
         CDI_PROF(KC_COARSE, s, (k_coarse<<<1, 64, 0, s>>>((int)L.g.N, mg.ainv, L.r, L.e)));
         ++g_launches;
-        return;
+        return false;
     }
     const unsigned nb = blocks_for(L.g.N);
     const unsigned nbh = blocks_for(L.g.N / 2);
@@ -534,18 +550,31 @@ static void vcycle_rec(MG& mg, int l, int npre, int npost, cudaStream_t s) {
     // one red-black sweep; level 0 forms its coefficients from the cell densities
     const dim3 sweep_grid((unsigned)((L.g.n[0] / 2 + kSweepX - 1) / kSweepX),
                           (unsigned)((L.g.n[1] + kSweepY - 1) / kSweepY), (unsigned)(DIM == 3 ? L.g.n[2] : 1));
+    const dim3 sweep_block(kSweepX, kSweepY);
     const float h2 = (float)(L.g.h * L.g.h);
-    auto sweep = [&](int col) {
-        if (l == 0)
-            CDI_PROF(kc_rbgs, s,
-                     (k_rbgs0<DIM><<<sweep_grid, dim3(kSweepX, kSweepY), 0, s>>>(L.g, L.rho0, L.e, L.r, col, h2)));
-        else
+    auto sweep = [&](int col, int mode) {
+        if (l == 0) {
+            if (mode == kSweepFromZero)
+                CDI_PROF(kc_rbgs, s,
+                         (k_rbgs0<T, DIM, kSweepFromZero><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
+                                                                                              col, h2, p)));
+            else if (mode == kSweepUpdate)
+                CDI_PROF(kc_rbgs, s,
+                         (k_rbgs0<T, DIM, kSweepUpdate><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
+                                                                                            col, h2, p)));
+            else
+                CDI_PROF(kc_rbgs, s,
+                         (k_rbgs0<T, DIM, kSweepPlain><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
+                                                                                           col, h2, p)));
+        } else {
             CDI_PROF(kc_rbgs, s,
                      (k_rbgs<DIM><<<nbh, kThreads, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r, col)));
+        }
         ++g_launches;
     };
     for (int it = 0; it < npre; ++it)
-        for (int col = 0; col < 2; ++col) sweep(col);
+        for (int col = 0; col < 2; ++col)
+            sweep(col, (l == 0 && it == 0 && col == 0) ? kSweepFromZero : kSweepPlain);
     MGLevel& C = mg.lv[l + 1];
     if (l == 0)
         CDI_PROF(KC_RESTRICT0, s,
@@ -555,19 +584,25 @@ static void vcycle_rec(MG& mg, int l, int npre, int npost, cudaStream_t s) {
         k_resid_restrict<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r,
                                                                      C.r, C.e);
     ++g_launches;
-    vcycle_rec<DIM>(mg, l + 1, npre, npost, s);
+    vcycle_rec<T, DIM>(mg, p, l + 1, npre, npost, s);
     CDI_PROF(l == 0 ? KC_PROLONG0 : -1, s, (k_prolong<DIM><<<nb, kThreads, 0, s>>>(L.g, C.g, C.e, L.e)));
     ++g_launches;
     for (int it = 0; it < npost; ++it)
-        for (int col = 0; col < 2; ++col) sweep(col);
+        for (int col = 0; col < 2; ++col)
+            sweep(col, (l == 0 && it == npost - 1 && col == 1) ? kSweepUpdate : kSweepPlain);
+    return l == 0;
 }
 
+// one V-cycle on A e = r and p += e (npre, npost >= 1)
 template <typename T>
 void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s) {
-    if (g.D == 2) vcycle_rec<2>(mg, 0, npre, npost, s);
-    else vcycle_rec<3>(mg, 0, npre, npost, s);
-    k_update<T><<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<T>(mg.lv[0]), mg.lv[0].e);
-    ++g_launches;
+    PT<T>* p = ops::pbuf<T>(mg.lv[0]);
+    const bool updated = (g.D == 2) ? vcycle_rec<T, 2>(mg, p, 0, npre, npost, s)
+                                    : vcycle_rec<T, 3>(mg, p, 0, npre, npost, s);
+    if (!updated) {
+        k_update<T><<<blocks_for(g.N), kThreads, 0, s>>>(g.N, p, mg.lv[0].e);
+        ++g_launches;
+    }
 }
 
 template <typename T>

@@ -67,43 +67,56 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // ---------------------------------------------------------------------------
 // executors
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* a, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(a), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* a) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(a) : "memory");
+    return v;
+}
+
 struct GridX {
     PersistCtl* ctl;
     double* partials;  // 2 * kPartials
     long limit;        // barrier timeout, ns
     int red;
+    unsigned long long epoch;  // barriers passed by this CTA
     using Ld = LG;
     __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ int nth() const { return gridDim.x * blockDim.x; }
     __device__ bool tail_cta() const { return blockIdx.x == 0; }
     __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
-    // grid barrier; false when the launch is ending (timeout or error)
+    // Grid barrier on one arrival counter that only grows: barrier number m
+    // is passed once the counter reaches m x gridDim.x.  Thread 0 arrives with
+    // one acquire-release atomic (publishing the CTA's writes, ordered before
+    // it by __syncthreads) and polls with acquire loads.  A wait longer than
+    // `limit` ns (or 2^31 polls) sets CDI_ETIMEOUT and adds kBarError to the
+    // counter, which releases every waiter of this and every later barrier
+    // with false.  Returns false when the launch is ending.
     __device__ bool sync() {
         __shared__ int ok;
         __syncthreads();  // the CTA's writes of this phase are done
+        ++epoch;
         if (threadIdx.x == 0) {
-            volatile unsigned* genp = &ctl->bar_gen;
-            const unsigned gen = *genp;
-            __threadfence();
-            const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(&ctl->bar_count, 0u);
-                __threadfence();
-                atomicAdd(&ctl->bar_gen, 1u);
-            } else {
-                // bounded wait: give up after `limit` ns (or 2^31 polls)
+            const unsigned long long target = epoch * gridDim.x;
+            unsigned long long v = atom_add_acq_rel(&ctl->bar, 1ull) + 1ull;
+            if (v < target) {
                 const unsigned long long t0 = globaltimer();
                 long it = 0;
-                while (*genp == gen) {
-                    if (++it > (1L << 31) || globaltimer() - t0 > (unsigned long long)limit) {
+                do {
+                    __nanosleep(20);
+                    v = ld_acquire(&ctl->bar);
+                    if (v < target && (++it > (1L << 31) || globaltimer() - t0 > (unsigned long long)limit)) {
                         atomicCAS(&ctl->st.status, 0, (int)CDI_ETIMEOUT);
-                        break;
+                        atom_add_acq_rel(&ctl->bar, kBarError);
+                        v = kBarError;
                     }
-                    __nanosleep(32);
-                }
+                } while (v < target);
             }
-            __threadfence();
-            ok = (*(volatile int*)&ctl->st.status == 0);
+            ok = v < kBarError;
         }
         __syncthreads();
         return ok != 0;
@@ -533,7 +546,7 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kPersistThreads, 1) k_step_persist(PersistArgs<T> P) {
     extern __shared__ double smd[];
     float* sm = reinterpret_cast<float*>(smd);
-    GridX x{P.ctl, P.partials, P.spin_limit, 0};
+    GridX x{P.ctl, P.partials, P.spin_limit, 0, 0ull};
     run_steps<T, DIM>(P.I, x, P.nsteps, &P.ctl->st, sm);
 }
 
