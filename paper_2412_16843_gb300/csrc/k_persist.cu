@@ -205,27 +205,46 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
             __syncthreads();
         }
     }
+    // As in the grid-wide levels, a smoothed level starts with its red cells at
+    // their first step from zero, written with its r (here on copying it in,
+    // below by the restriction).  (The coarsest level is solved directly.)
     {
         const SmLevel top = sm_level<T, DIM>(A, sm, lt);
+        const float* bt[3] = {top.b[0], top.b[1], top.b[2]};
         const float* src = A.lv[lt].r;
-        for (int c = t0; c < (int)top.g.N; c += nt) {
-            top.r[c] = __ldcg(src + c);
-            top.e[c] = 0.f;
+        const bool seed = lt < nl - 1;
+        const int n = (int)top.g.N;
+        constexpr int U = 8;  // loads in flight per thread before the first store
+        for (int c0 = t0; c0 < n; c0 += U * nt) {
+            float rv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) rv[u] = (c0 + u * nt < n) ? __ldcg(src + c0 + u * nt) : 0.f;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int c = c0 + u * nt;
+                if (c < n) {
+                    top.r[c] = rv[u];
+                    if (seed) ops::coarse_start<LP, float, DIM>(top.g, bt, decode(top.g, c), c, rv[u], top.e);
+                }
+            }
         }
         __syncthreads();
     }
     for (int l = lt; l < nl - 1; ++l) {  // down
         const SmLevel L = sm_level<T, DIM>(A, sm, l), C = sm_level<T, DIM>(A, sm, l + 1);
         const float* bl[3] = {L.b[0], L.b[1], L.b[2]};
+        const float* bc[3] = {C.b[0], C.b[1], C.b[2]};
         const int half = (int)(L.g.N / 2);
         for (int it = 0; it < A.npre; ++it)
             for (int col = 0; col < 2; ++col) {
+                if (it == 0 && col == 0) continue;
                 for (int k = t0; k < half; k += nt)
                     ops::rbgs_at<LP, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
                 __syncthreads();
             }
+        const float* const* cbp = (l + 1 < nl - 1) ? bc : nullptr;
         for (int t = t0; t < (int)C.g.N; t += nt)
-            ops::resid_restrict_at<LP, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
+            ops::resid_restrict_at<LP, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t, cbp);
         __syncthreads();
     }
     {
@@ -238,7 +257,9 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
         }
         ops::coarse_apply_block<LP, float>((int)C.g.N, A.ainv ? A.ainv : Asm, C.r, C.e);
     }
-    for (int l = nl - 2; l >= lt; --l) {  // up
+    // up: in shared memory a separate prolongation pass is cheaper than
+    // prolonging the neighbours of every red cell on the fly
+    for (int l = nl - 2; l >= lt; --l) {
         const SmLevel L = sm_level<T, DIM>(A, sm, l), C = sm_level<T, DIM>(A, sm, l + 1);
         const float* bl[3] = {L.b[0], L.b[1], L.b[2]};
         const int half = (int)(L.g.N / 2);
@@ -258,8 +279,14 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
     }
 }
 
-// one FP32 V-cycle on the correction equation A e = r from level 0 (levels
-// 0 .. lt-1 by the executor's threads, the tail by one CTA), ending with p += e
+// One FP32 V-cycle on the correction equation A e = r from level 0 (levels
+// 0 .. lt-1 by the executor's threads, the tail by one CTA), ending with
+// p += e.  Every grid-wide level starts with its red cells already at their
+// first smoothing step from zero (written with r: by resid_local on level 0,
+// by the restriction above), and the first smoothing step after the
+// coarse-grid correction reads the black neighbours with the prolongation
+// added on the fly, so neither e = 0 nor the prolonged e is ever stored: two
+// grid barriers fewer per level.
 template <typename T, int DIM, class X>
 __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
     using L_ = typename X::Ld;
@@ -271,6 +298,7 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
         const int half = (int)(L.g.N / 2);
         for (int it = 0; it < A.npre; ++it)
             for (int col = 0; col < 2; ++col) {
+                if (it == 0 && col == 0) continue;  // written with this level's r
                 for (int k = tid; k < half; k += nth) {
                     const long c = ops::colour_cell(L.g, col, k);
                     if (l == 0) ops::rbgs_rho_at<L_, DIM>(L.g, L.rho0, L.e, L.r, c);
@@ -278,9 +306,12 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
                 }
                 if (!x.sync()) return false;
             }
+        // the tail starts its top level from zero itself
+        const float* cb[3] = {C.bf[0], C.bf[1], C.bf[2]};
+        const float* const* cbp = (l + 1 < A.lt) ? cb : nullptr;
         for (int t = tid; t < (int)C.g.N; t += nth) {
-            if (l == 0) ops::resid_restrict_rho_at<L_, DIM>(L.g, C.g, L.rho0, L.e, L.r, C.r, C.e, t);
-            else ops::resid_restrict_at<L_, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t);
+            if (l == 0) ops::resid_restrict_rho_at<L_, DIM>(L.g, C.g, L.rho0, L.e, L.r, C.r, C.e, t, cbp);
+            else ops::resid_restrict_at<L_, float, DIM>(L.g, C.g, bl, L.e, L.r, C.r, C.e, t, cbp);
         }
         if (!x.sync()) return false;
     }
@@ -294,15 +325,21 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
         const MGLevel C = A.lv[l + 1];
         const float* bl[3] = {L.bf[0], L.bf[1], L.bf[2]};
         const int half = (int)(L.g.N / 2);
-        for (int c = tid; c < (int)L.g.N; c += nth) ops::prolong_at<L_, float, DIM>(L.g, C.g, C.e, L.e, c);
-        if (!x.sync()) return false;
         for (int it = 0; it < A.npost; ++it)
             for (int col = 0; col < 2; ++col) {
                 const bool last = (l == 0 && it == A.npost - 1 && col == 1);
+                const bool pro = (it == 0 && col == 0);
                 for (int k = tid; k < half; k += nth) {
                     const long c = ops::colour_cell(L.g, col, k);
-                    if (l == 0) ops::rbgs_rho_at<L_, DIM>(L.g, L.rho0, L.e, L.r, c);
-                    else ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
+                    if (pro) {
+                        if (l == 0)
+                            ops::rbgs_rho_at<L_, DIM, ops::kNbProlong>(L.g, L.rho0, L.e, L.r, c, &C.g, C.e);
+                        else
+                            ops::rbgs_at<L_, float, DIM, ops::kNbProlong>(L.g, bl, L.e, L.r, c, &C.g, C.e);
+                    } else {
+                        if (l == 0) ops::rbgs_rho_at<L_, DIM>(L.g, L.rho0, L.e, L.r, c);
+                        else ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
+                    }
                     if (last) P0[c] = ops::p_add(L_::ld(P0 + c), L.e[c]);
                 }
                 if (last) {  // the other colour is final already
@@ -323,7 +360,8 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
 }
 
 // residual of level 0 in the form's precision: this thread's part of its
-// squared norm; the FP32 copy r and e = 0
+// squared norm, the FP32 copy r, and on the red cells the first smoothing
+// step of the next V-cycle from zero (rbgs_rho_at with kNbZero)
 template <class Ld, typename T, int DIM>
 __device__ double resid_local(const MGLevel& L0, float2 fmean, int tid, int nth) {
     const PT<T>* p = ops::pbuf<T>(L0);
@@ -331,8 +369,14 @@ __device__ double resid_local(const MGLevel& L0, float2 fmean, int tid, int nth)
     T acc = T(0);
     for (int c = tid; c < (int)L0.g.N; c += nth) {
         const T r = ops::resid_form_at<Ld, DIM>(L0, p, f, fmean, c);
-        L0.r[c] = (float)r;
-        L0.e[c] = 0.f;
+        const float rf = (float)r;
+        L0.r[c] = rf;
+        const IJK q = decode(L0.g, c);
+        if (((q.i + q.j + q.k) & 1) == 0) {
+            float diag, off;
+            ops::stencil_L_rho<Ld, DIM>(L0.g, L0.rho0, q, c, L0.g.ih2f, [](long) { return 0.f; }, diag, off);
+            L0.e[c] = (off - rf) / diag;
+        }
         acc += r * r;
     }
     return (double)acc;

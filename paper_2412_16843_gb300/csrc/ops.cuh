@@ -486,23 +486,24 @@ __device__ __forceinline__ void coef_restrict_at(const Geom& gf, const Geom& gc,
     }
 }
 
-// (A p)_c pieces: diag = sum (beta- + beta+)/h^2, off = sum (beta- p- + beta+ p+)/h^2;
-// zero coefficients on the walls (Neumann); returns off - diag p_c
-template <class L, typename M, int DIM>
-__device__ __forceinline__ M apply_L(const Geom& g, const M* const* beta, const M* p, const IJK& q, long c, M ih2,
-                                     M& diag, M& off) {
+// (A p)_c pieces: diag = sum (beta- + beta+)/h^2, off = sum (beta- p- + beta+ p+)/h^2,
+// the neighbour values p+- given by nv(index); zero coefficients on the walls
+// (Neumann), where no neighbour value is taken (it may not exist yet)
+template <class L, typename M, int DIM, class NV>
+__device__ __forceinline__ void stencil_L(const Geom& g, const M* const* beta, const IJK& q, long c, M ih2, NV nv,
+                                          M& diag, M& off) {
     diag = M(0);
     off = M(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        // neighbour indices; beyond a wall the index is clamped to c itself and
-        // the zero wall coefficient cancels the term, so every load is issued
-        // at once (no load waits on the coefficient)
         long lo, hi;
+        bool wlo = false, whi = false;
         if (a == DIM - 1) {
             const int r = coord(q, a);
-            lo = r > 0 ? c - g.NP : c;
-            hi = r < g.n[a] - 1 ? c + g.NP : c;
+            wlo = r == 0;
+            whi = r == g.n[a] - 1;
+            lo = wlo ? c : c - g.NP;
+            hi = whi ? c : c + g.NP;
         } else {
             lo = idx(g, shift(g, q, a, -1));
             hi = idx(g, shift(g, q, a, 1));
@@ -510,46 +511,59 @@ __device__ __forceinline__ M apply_L(const Geom& g, const M* const* beta, const 
         const long fhi = (a == DIM - 1) ? c + g.NP : hi;
         const M bm = L::ld(beta[a] + c);
         const M bp = L::ld(beta[a] + fhi);
-        const M pm = L::ld(p + lo);
-        const M pp = L::ld(p + hi);
+        const M pm = wlo ? M(0) : nv(lo);
+        const M pp = whi ? M(0) : nv(hi);
         diag += (bm + bp) * ih2;
         off += (bm * pm + bp * pp) * ih2;
     }
+}
+
+// (A p)_c with the stored neighbour values; returns off - diag p_c
+template <class L, typename M, int DIM>
+__device__ __forceinline__ M apply_L(const Geom& g, const M* const* beta, const M* p, const IJK& q, long c, M ih2,
+                                     M& diag, M& off) {
+    stencil_L<L, M, DIM>(g, beta, q, c, ih2, [&](long n) { return L::ld(p + n); }, diag, off);
     return off - diag * L::ld(p + c);
 }
 
-// apply_L on level 0 with the face coefficients formed from the FP32 cell
+// stencil_L on level 0 with the face coefficients formed from the FP32 cell
 // densities, beta = 2 / (rho_L + rho_R) (coef0_at's 1 / mean density, by the
 // fast FP32 division): one array read instead of D coefficient arrays.  Used
 // by the level-0 smoother and residual restriction only; the defect-correction
 // residual keeps the stored coefficients.  Walls carry a zero coefficient.
-template <class L, int DIM>
-__device__ __forceinline__ float apply_L_rho(const Geom& g, const float* rho, const float* p, const IJK& q, long c,
-                                             float ih2, float& diag, float& off) {
+template <class L, int DIM, class NV>
+__device__ __forceinline__ void stencil_L_rho(const Geom& g, const float* rho, const IJK& q, long c, float ih2, NV nv,
+                                              float& diag, float& off) {
     diag = 0.f;
     off = 0.f;
     const float rc = L::ld(rho + c);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         long lo, hi;
-        float mlo = 1.f, mhi = 1.f;
+        bool wlo = false, whi = false;
         if (a == DIM - 1) {
             const int r = coord(q, a);
-            lo = r > 0 ? c - g.NP : c;
-            hi = r < g.n[a] - 1 ? c + g.NP : c;
-            mlo = r > 0 ? 1.f : 0.f;
-            mhi = r < g.n[a] - 1 ? 1.f : 0.f;
+            wlo = r == 0;
+            whi = r == g.n[a] - 1;
+            lo = wlo ? c : c - g.NP;
+            hi = whi ? c : c + g.NP;
         } else {
             lo = idx(g, shift(g, q, a, -1));
             hi = idx(g, shift(g, q, a, 1));
         }
-        const float bm = mlo * __fdividef(2.f, rc + L::ld(rho + lo));
-        const float bp = mhi * __fdividef(2.f, rc + L::ld(rho + hi));
-        const float pm = L::ld(p + lo);
-        const float pp = L::ld(p + hi);
+        const float bm = (wlo ? 0.f : 1.f) * __fdividef(2.f, rc + L::ld(rho + lo));
+        const float bp = (whi ? 0.f : 1.f) * __fdividef(2.f, rc + L::ld(rho + hi));
+        const float pm = wlo ? 0.f : nv(lo);
+        const float pp = whi ? 0.f : nv(hi);
         diag += (bm + bp) * ih2;
         off += (bm * pm + bp * pp) * ih2;
     }
+}
+
+template <class L, int DIM>
+__device__ __forceinline__ float apply_L_rho(const Geom& g, const float* rho, const float* p, const IJK& q, long c,
+                                             float ih2, float& diag, float& off) {
+    stencil_L_rho<L, DIM>(g, rho, q, c, ih2, [&](long n) { return L::ld(p + n); }, diag, off);
     return off - diag * L::ld(p + c);
 }
 
@@ -564,21 +578,47 @@ __device__ __forceinline__ long colour_cell(const Geom& g, int colour, long k) {
     return (long)(i + (unsigned)g.n[0] * line);
 }
 
+// Gauss-Seidel step p_c = (off - f_c) / diag of cell c; the variants take the
+// neighbour values as zero (the first step of a V-cycle's smoothing, whose
+// correction starts from zero) or as stored plus the prolongation of the
+// coarse correction pc (the first step after the coarse-grid correction, which
+// is then never stored: a Gauss-Seidel step does not read its own cell)
+enum StepNb { kNbStored = 0, kNbZero = 1, kNbProlong = 2 };
+
 template <class L, typename M, int DIM>
-__device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* p, const M* f, long c) {
+__device__ __forceinline__ M prolong_val(const Geom& gf, const Geom& gc, const M* pc, long c);
+
+template <class L, typename M, int DIM, int NB = kNbStored>
+__device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* p, const M* f, long c,
+                                        const Geom* gc = nullptr, const M* pc = nullptr) {
     const IJK q = decode(g, c);
     const M ih2 = g_ih2<M>(g);
     M diag, off;
-    apply_L<L, M, DIM>(g, beta, p, q, c, ih2, diag, off);
+    stencil_L<L, M, DIM>(
+        g, beta, q, c, ih2,
+        [&](long n) -> M {
+            if (NB == kNbZero) return M(0);
+            if (NB == kNbProlong) return L::ld(p + n) + prolong_val<L, M, DIM>(g, *gc, pc, n);
+            return L::ld(p + n);
+        },
+        diag, off);
     p[c] = (off - L::ld(f + c)) / diag;
 }
 
-// level-0 smoothing step with density-formed coefficients (apply_L_rho)
-template <class L, int DIM>
-__device__ __forceinline__ void rbgs_rho_at(const Geom& g, const float* rho, float* p, const float* f, long c) {
+// level-0 smoothing step with density-formed coefficients (stencil_L_rho)
+template <class L, int DIM, int NB = kNbStored>
+__device__ __forceinline__ void rbgs_rho_at(const Geom& g, const float* rho, float* p, const float* f, long c,
+                                            const Geom* gc = nullptr, const float* pc = nullptr) {
     const IJK q = decode(g, c);
     float diag, off;
-    apply_L_rho<L, DIM>(g, rho, p, q, c, g.ih2f, diag, off);
+    stencil_L_rho<L, DIM>(
+        g, rho, q, c, g.ih2f,
+        [&](long n) -> float {
+            if (NB == kNbZero) return 0.f;
+            if (NB == kNbProlong) return L::ld(p + n) + prolong_val<L, float, DIM>(g, *gc, pc, n);
+            return L::ld(p + n);
+        },
+        diag, off);
     p[c] = (off - L::ld(f + c)) / diag;
 }
 
@@ -738,10 +778,27 @@ template <> __device__ __forceinline__ float2 p_zero<float>() { return make_floa
 __device__ __forceinline__ double p_diff(double a, double b) { return a - b; }
 __device__ __forceinline__ float p_diff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
 
-// coarse cell t: mean of the 2^D fine residuals; zero coarse correction
+// Coarse correction at coarse cell t after its right-hand side fc_t is known:
+// zero (cb null: the level starts from zero elsewhere), or, on a red cell
+// ((i + j + k) even: the colour smoothed first), the first Gauss-Seidel step
+// from zero, -fc_t / diag (rbgs_at with kNbZero); black cells are left for the
+// black half-sweep, which overwrites them without reading them.
+template <class L, typename M, int DIM>
+__device__ __forceinline__ void coarse_start(const Geom& gc, const M* const* cb, const IJK& Q, long t, M fct, M* pc) {
+    if (!cb) {
+        pc[t] = M(0);
+        return;
+    }
+    if (((Q.i + Q.j + Q.k) & 1) != 0) return;
+    M diag, off;
+    stencil_L<L, M, DIM>(gc, cb, Q, t, g_ih2<M>(gc), [](long) { return M(0); }, diag, off);
+    pc[t] = (off - fct) / diag;
+}
+
+// coarse cell t: mean of the 2^D fine residuals, then coarse_start
 template <class L, typename M, int DIM>
 __device__ __forceinline__ void resid_restrict_at(const Geom& gf, const Geom& gc, const M* const* beta, const M* p,
-                                                  const M* f, M* fc, M* pc, long t) {
+                                                  const M* f, M* fc, M* pc, long t, const M* const* cb = nullptr) {
     const IJK Q = decode(gc, t);
     const M ih2 = g_ih2<M>(gf);
     const int o2 = (DIM == 3) ? 2 : 1;
@@ -758,14 +815,16 @@ __device__ __forceinline__ void resid_restrict_at(const Geom& gf, const Geom& gc
                 const M Lp = apply_L<L, M, DIM>(gf, beta, p, q, c, ih2, diag, off);
                 s += L::ld(f + c) - Lp;
             }
-    fc[t] = s * (M(1) / M(4 * o2));
-    pc[t] = M(0);
+    const M v = s * (M(1) / M(4 * o2));
+    fc[t] = v;
+    coarse_start<L, M, DIM>(gc, cb, Q, t, v, pc);
 }
 
 // resid_restrict_at on level 0 with density-formed coefficients (apply_L_rho)
 template <class L, int DIM>
 __device__ __forceinline__ void resid_restrict_rho_at(const Geom& gf, const Geom& gc, const float* rho, const float* p,
-                                                      const float* f, float* fc, float* pc, long t) {
+                                                      const float* f, float* fc, float* pc, long t,
+                                                      const float* const* cb = nullptr) {
     const IJK Q = decode(gc, t);
     const int o2 = (DIM == 3) ? 2 : 1;
     float s = 0.f;
@@ -781,8 +840,9 @@ __device__ __forceinline__ void resid_restrict_rho_at(const Geom& gf, const Geom
                 const float Lp = apply_L_rho<L, DIM>(gf, rho, p, q, c, gf.ih2f, diag, off);
                 s += L::ld(f + c) - Lp;
             }
-    fc[t] = s * (1.f / (float)(4 * o2));
-    pc[t] = 0.f;
+    const float v = s * (1.f / (float)(4 * o2));
+    fc[t] = v;
+    coarse_start<L, float, DIM>(gc, cb, Q, t, v, pc);
 }
 
 // cell-centred (bi/tri)linear prolongation, weights 3/4 and 1/4 per axis;
