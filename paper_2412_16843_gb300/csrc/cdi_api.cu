@@ -61,6 +61,7 @@ struct cdi_ctx {
     void* wuY = nullptr;
     void* wghost = nullptr;
     void* wmuw = nullptr;
+    void* colq = nullptr;  // persistent mode: extrapolated wall-column quantities (9 values a column)
     double* cols = nullptr;
     double* xfer = nullptr;  // FP64 staging of one face field for host copies
     MG mg{};
@@ -146,6 +147,7 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     c->wuY = cv.take(nw * es);
     c->wghost = cv.take(nw * es);
     c->wmuw = cv.take(nw * es);
+    c->colq = cv.take((size_t)2 * g.NP * 9 * es);
     c->cols = (double*)cv.take((size_t)2 * 3 * g.NP * sizeof(double));
     c->xfer = (double*)cv.take((size_t)(g.N + g.NP) * sizeof(double));
     MG& mg = c->mg;
@@ -549,6 +551,7 @@ void fill_inst(const cdi_ctx* c, InstArgs<T>& A, int lt, const PersistLayout& la
     A.wuY = (T*)c->wuY;
     A.wghost = (T*)c->wghost;
     A.wmuw = (T*)c->wmuw;
+    A.colq = c->colq;
     for (int a = 0; a < 3; ++a) {
         A.u_s[a] = (T*)c->u_s[a];
         A.u_k[a] = (T*)c->u_k[a];

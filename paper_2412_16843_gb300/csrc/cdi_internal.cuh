@@ -346,6 +346,7 @@ struct __align__(16) InstArgs : PersistLayout {
     long hist_step0;   // steps stored before this launch
     const float* ainv; // coarsest-level inverse in global memory (launch-per-kernel tail), or null:
                        // the tail inverts in shared memory at the first V-cycle of each solve
+    void* colq;        // extrapolated wall-column quantities, [2 NP] (ops::ColQ<T>)
 };
 
 template <typename T>

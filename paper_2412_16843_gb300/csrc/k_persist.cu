@@ -87,6 +87,9 @@ struct GridX {
     using Ld = LG;
     __device__ int tid() const { return blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ int nth() const { return gridDim.x * blockDim.x; }
+    // the thread's first index of a loop with stride nth() whose consecutive
+    // indices go to consecutive CTAs
+    __device__ int spread() const { return threadIdx.x * gridDim.x + blockIdx.x; }
     __device__ bool tail_cta() const { return blockIdx.x == 0; }
     __device__ bool leader() const { return blockIdx.x == 0 && threadIdx.x == 0; }
     // Grid barrier on one arrival counter that only grows: barrier number m
@@ -139,6 +142,7 @@ struct BlockX {
     using Ld = LP;  // one CTA owns the instance: its own writes are visible after __syncthreads
     __device__ int tid() const { return threadIdx.x; }
     __device__ int nth() const { return blockDim.x; }
+    __device__ int spread() const { return threadIdx.x; }
     __device__ bool tail_cta() const { return true; }
     __device__ bool leader() const { return threadIdx.x == 0; }
     __device__ bool sync() {
@@ -375,7 +379,7 @@ __device__ double resid_local(const MGLevel& L0, float2 fmean, int tid, int nth)
         if (((q.i + q.j + q.k) & 1) == 0) {
             float diag, off;
             ops::stencil_L_rho<Ld, DIM>(L0.g, L0.rho0, q, c, L0.g.ih2f, [](long) { return 0.f; }, diag, off);
-            L0.e[c] = (off - rf) / diag;
+            L0.e[c] = ops::step_div(off - rf, diag);
         }
         acc += r * r;
     }
@@ -551,12 +555,20 @@ __device__ void run_steps(const InstArgs<T>& A, X& x, int nsteps, InstStats* S, 
             f.wmuw = A.wmuw;
             for (int c = tid; c < (int)g.N; c += nth) ops::psi_at<L_>(g, A.ph, phi, A.psi, c);
             if (!x.sync()) return;
+            // Wall columns are spread over the CTAs (column w on CTA w mod CTAs: each
+            // is FP64-heavy, and a grid-stride loop would give them all to the first
+            // CTAs); their extrapolated quantities are formed once per column here,
+            // and the slip and ghost values, which two adjacent columns combine into,
+            // in the next phase (phi_rhs does not read them).
+            ops::ColQ<T>* colq = reinterpret_cast<ops::ColQ<T>*>(A.colq);
             for (int c = tid; c < (int)g.N; c += nth)
                 ops::cell_at<L_, T, DIM>(g, A.ph, phi, A.psi, A.nh[0], A.nh[1], A.nh[2], A.muc, c);
-            for (int t = tid; t < (int)(2 * g.NP); t += nth)
-                ops::wall_at<L_, T, DIM>(g, A.ph, phi, A.psi, u[0], u[1], A.wuY, A.wghost, A.wmuw, t);
+            for (int t = x.spread(); t < (int)(2 * g.NP); t += nth)
+                ops::wall_colq_at<L_, T, DIM>(g, A.ph, phi, A.psi, colq, t);
             if (!x.sync()) return;
             for (int c = tid; c < (int)g.N; c += nth) ops::phi_rhs_at<L_, T, DIM>(g, A.ph, f, (T)gamma, c);
+            for (int t = x.spread(); t < (int)(2 * g.NP); t += nth)
+                ops::wall_from_colq_at<L_, T, DIM>(g, A.ph, colq, u[0], u[1], A.wuY, A.wghost, A.wmuw, t);
             if (!x.sync()) return;
             for (int c = tid; c < (int)g.N; c += nth) ops::mom_at<L_, T, DIM>(g, A.ph, f, c);
             if (!x.sync()) return;

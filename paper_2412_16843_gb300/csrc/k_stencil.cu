@@ -102,6 +102,10 @@ __global__ void k_stage_mom(Geom g, PhysDev ph, T b, T cdt, T dt, int first, int
 
 }  // namespace
 
+// wall columns are FP64-heavy and few: small blocks spread them over the SMs
+constexpr int kWallThreads = 64;
+inline unsigned wall_blocks(const Geom& g) { return (unsigned)((2 * g.NP + kWallThreads - 1) / kWallThreads); }
+
 template <typename T>
 void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaStream_t s) {
     const unsigned nb = blocks_for(g.N);
@@ -109,14 +113,14 @@ void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaS
     if (g.D == 2) {
         CDI_PROF(KC_CELL, s,
                  (k_cell<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi, f.nh[0], f.nh[1], nullptr, f.muc)));
-        CDI_PROF(KC_WALL, s, (k_wall<T, 2><<<blocks_for(2 * g.NP), kThreads, 0, s>>>(
+        CDI_PROF(KC_WALL, s, (k_wall<T, 2><<<wall_blocks(g), kWallThreads, 0, s>>>(
                                  g, ph, f.phi, f.psi, f.u[0], nullptr, f.wuY, f.wghost, f.wmuw)));
         CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f)));
         CDI_PROF(KC_MOM, s, (k_mom<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f)));
     } else {
         CDI_PROF(KC_CELL, s,
                  (k_cell<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi, f.nh[0], f.nh[1], f.nh[2], f.muc)));
-        CDI_PROF(KC_WALL, s, (k_wall<T, 3><<<blocks_for(2 * g.NP), kThreads, 0, s>>>(
+        CDI_PROF(KC_WALL, s, (k_wall<T, 3><<<wall_blocks(g), kWallThreads, 0, s>>>(
                                  g, ph, f.phi, f.psi, f.u[0], f.u[1], f.wuY, f.wghost, f.wmuw)));
         CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));
         CDI_PROF(KC_MOM, s, (k_mom<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));

@@ -92,10 +92,10 @@ __device__ __forceinline__ void cell_at(const Geom& g, const PhysDev& ph, const 
     T pt = clampv(L::ld(phi + c), delta, T(1) - delta);
     T P = pt * (T(1) - pt);
     muc[c] = T(6) * Q.sigma * (P * (T(1) - T(2) * pt) * (T(1) - grad2) / eps - P * lap);
-    T gm = sqrt(grad2) + Q.tau;
-    nh0[c] = gb[0] / gm;
-    nh1[c] = gb[1] / gm;
-    if (DIM == 3) nh2[c] = gb[2] / gm;
+    const T igm = T(1) / (sqrt(grad2) + Q.tau);  // one division (FP64 is scarce on this part)
+    nh0[c] = gb[0] * igm;
+    nh1[c] = gb[1] * igm;
+    if (DIM == 3) nh2[c] = gb[2] * igm;
 }
 
 // ---------------------------------------------------------------------------
@@ -198,60 +198,126 @@ __device__ __forceinline__ T slip_model(int model, T sigma, T eps, T beta, T cos
     return -(T(6) * sigma / beta) * (A + B * costh) * Tt;
 }
 
-// thread t in [0, 2 NP): wall s = t / NP, wall-plane position t % NP; slip
-// velocity, ghost value and wall viscosity of every tangential component
+// slip velocity, ghost value and wall viscosity of tangential component a at
+// position pidx = (i, j) of wall s, from the extrapolated quantities of the
+// column (cR) and of its low neighbour along a (cL)
 template <class L, typename T, int DIM>
-__device__ void wall_at(const Geom& g, const PhysDev& ph, const T* phi, const T* psi, const T* u0, const T* u1,
-                        T* wuY, T* wghost, T* wmuw, long t) {
-    const int s = (int)(t / g.NP);
-    const long pidx = t - s * g.NP;
-    const int i = (int)(pidx % g.n[0]);
-    const int j = (DIM == 3) ? (int)(pidx / g.n[0]) : 0;
+__device__ __forceinline__ void wall_finish(const Geom& g, const PhysDev& ph, const ColQ<T>& cR, const ColQ<T>& cL,
+                                            int a, int s, long pidx, int i, int j, const T* u0, const T* u1, T* wuY,
+                                            T* wghost, T* wmuw) {
     const int W = DIM - 1;
     const int r0 = s == 0 ? 0 : g.n[W] - 1;
     const T ih = g_ih<T>(g);
     const WallDev& wp = ph.wall[s];
     const PhysT<T>& Q = phys<T>(ph);
-    const ColQ<T> cR = wall_column<L, T, DIM>(g, ph, phi, psi, s, i, j);
+    const T pb = T(0.5) * (cL.phiw + cR.phiw);
+    const T P = pb * (T(1) - pb);
+    const T psb = T(0.5) * (cL.psiw + cR.psiw);
+    const T dnb = T(0.5) * (cL.dnw + cR.dnw);
+    const T kb = T(0.5) * (cL.kpw + cR.kpw);
+    const T dtau = (cR.psiw - cL.psiw) * ih;
+    const T dnphi = T(0.5) * (cL.dnphiw + cR.dnphiw);
+    const T dtphi = (cR.phiw - cL.phiw) * ih;
+    T gs = dnb * dnb, gf = dnphi * dnphi;
+#pragma unroll
+    for (int tt = 0; tt < DIM - 1; ++tt) {
+        T gt = (tt == a) ? dtau : T(0.5) * (cL.gt[tt] + cR.gt[tt]);
+        T gtf = (tt == a) ? dtphi : T(0.5) * (cL.gtphi[tt] + cR.gtphi[tt]);
+        gs += gt * gt;
+        gf += gtf * gtf;
+    }
+    const T muw = Q.dmu * pb + Q.mu2;
+    T uY = T(0), lw = T(0);
+    if (!wp.noslip) {
+        const T beta = Q.dbeta[s] * pb + Q.beta2[s];  // beta linear in phi
+        uY = slip_model<T>(ph.model, Q.sigma, Q.eps, beta, Q.costh[s], P, dnb, dtau, sqrt(gs), dnphi, dtphi, sqrt(gf),
+                           kb, psb);
+        lw = muw / beta;
+    }
+    const long cq = (DIM == 2) ? encode(g, i, r0, 0) : encode(g, i, j, r0);
+    const T uf = (a == 0) ? L::ld(u0 + cq) : L::ld(u1 + cq);
+    // ghost value: u_w = (u0+ug)/2, d_n u = (u0-ug)/h, u_w - U = l_w d_n u + u^Y
+    const T lwh = lw * ih;
+    const T ug = (Q.U[s][a] + uY - uf * (T(0.5) - lwh)) / (T(0.5) + lwh);
+    const long o = ((long)s * (DIM - 1) + a) * g.NP + pidx;
+    wuY[o] = uY;
+    wghost[o] = ug;
+    wmuw[o] = muw;
+}
+
+// wall s = t / NP and wall-plane position t % NP of a thread index t in [0, 2 NP)
+struct WallPos {
+    int s, i, j;
+    long pidx;
+};
+__device__ __forceinline__ WallPos wall_pos(const Geom& g, int dim, long t) {
+    WallPos w;
+    w.s = (int)(t / g.NP);
+    w.pidx = t - w.s * g.NP;
+    w.i = (int)(w.pidx % g.n[0]);
+    w.j = (dim == 3) ? (int)(w.pidx / g.n[0]) : 0;
+    return w;
+}
+// position of the low neighbour along tangential axis a (periodic)
+__device__ __forceinline__ void wall_low(const Geom& g, int a, int i, int j, int& iL, int& jL) {
+    iL = i;
+    jL = j;
+    if (a == 0) iL = (i == 0) ? g.n[0] - 1 : i - 1;
+    else jL = (j == 0) ? g.n[1] - 1 : j - 1;
+}
+
+// thread t in [0, 2 NP): slip velocity, ghost value and wall viscosity of
+// every tangential component, the column quantities formed here
+template <class L, typename T, int DIM>
+__device__ void wall_at(const Geom& g, const PhysDev& ph, const T* phi, const T* psi, const T* u0, const T* u1,
+                        T* wuY, T* wghost, T* wmuw, long t) {
+    const WallPos w = wall_pos(g, DIM, t);
+    const ColQ<T> cR = wall_column<L, T, DIM>(g, ph, phi, psi, w.s, w.i, w.j);
 #pragma unroll
     for (int a = 0; a < DIM - 1; ++a) {
-        int iL = i, jL = j;
-        if (a == 0) iL = (i == 0) ? g.n[0] - 1 : i - 1;
-        else jL = (j == 0) ? g.n[1] - 1 : j - 1;
-        const ColQ<T> cL = wall_column<L, T, DIM>(g, ph, phi, psi, s, iL, jL);
-        const T pb = T(0.5) * (cL.phiw + cR.phiw);
-        const T P = pb * (T(1) - pb);
-        const T psb = T(0.5) * (cL.psiw + cR.psiw);
-        const T dnb = T(0.5) * (cL.dnw + cR.dnw);
-        const T kb = T(0.5) * (cL.kpw + cR.kpw);
-        const T dtau = (cR.psiw - cL.psiw) * ih;
-        const T dnphi = T(0.5) * (cL.dnphiw + cR.dnphiw);
-        const T dtphi = (cR.phiw - cL.phiw) * ih;
-        T gs = dnb * dnb, gf = dnphi * dnphi;
+        int iL, jL;
+        wall_low(g, a, w.i, w.j, iL, jL);
+        const ColQ<T> cL = wall_column<L, T, DIM>(g, ph, phi, psi, w.s, iL, jL);
+        wall_finish<L, T, DIM>(g, ph, cR, cL, a, w.s, w.pidx, w.i, w.j, u0, u1, wuY, wghost, wmuw);
+    }
+}
+
+// the column quantities of wall position t, once per column (stored in cq[t])
+template <class L, typename T, int DIM>
+__device__ __forceinline__ void wall_colq_at(const Geom& g, const PhysDev& ph, const T* phi, const T* psi, ColQ<T>* cq,
+                                             long t) {
+    const WallPos w = wall_pos(g, DIM, t);
+    cq[t] = wall_column<L, T, DIM>(g, ph, phi, psi, w.s, w.i, w.j);
+}
+
+template <class L, typename T>
+__device__ __forceinline__ ColQ<T> load_colq(const ColQ<T>* p) {
+    ColQ<T> q;
+    q.phiw = L::ld(&p->phiw);
+    q.psiw = L::ld(&p->psiw);
+    q.dnw = L::ld(&p->dnw);
+    q.kpw = L::ld(&p->kpw);
+    q.dnphiw = L::ld(&p->dnphiw);
+    for (int k = 0; k < 2; ++k) {
+        q.gt[k] = L::ld(&p->gt[k]);
+        q.gtphi[k] = L::ld(&p->gtphi[k]);
+    }
+    return q;
+}
+
+// wall_at from the stored column quantities (wall_colq_at)
+template <class L, typename T, int DIM>
+__device__ void wall_from_colq_at(const Geom& g, const PhysDev& ph, const ColQ<T>* cq, const T* u0, const T* u1,
+                                  T* wuY, T* wghost, T* wmuw, long t) {
+    const WallPos w = wall_pos(g, DIM, t);
+    const ColQ<T> cR = load_colq<L>(cq + t);
 #pragma unroll
-        for (int tt = 0; tt < DIM - 1; ++tt) {
-            T gt = (tt == a) ? dtau : T(0.5) * (cL.gt[tt] + cR.gt[tt]);
-            T gtf = (tt == a) ? dtphi : T(0.5) * (cL.gtphi[tt] + cR.gtphi[tt]);
-            gs += gt * gt;
-            gf += gtf * gtf;
-        }
-        const T muw = Q.dmu * pb + Q.mu2;
-        T uY = T(0), lw = T(0);
-        if (!wp.noslip) {
-            const T beta = Q.dbeta[s] * pb + Q.beta2[s];  // beta linear in phi
-            uY = slip_model<T>(ph.model, Q.sigma, Q.eps, beta, Q.costh[s], P, dnb, dtau, sqrt(gs), dnphi, dtphi,
-                               sqrt(gf), kb, psb);
-            lw = muw / beta;
-        }
-        const long cq = (DIM == 2) ? encode(g, i, r0, 0) : encode(g, i, j, r0);
-        const T uf = (a == 0) ? L::ld(u0 + cq) : L::ld(u1 + cq);
-        // ghost value: u_w = (u0+ug)/2, d_n u = (u0-ug)/h, u_w - U = l_w d_n u + u^Y
-        const T lwh = lw * ih;
-        const T ug = (Q.U[s][a] + uY - uf * (T(0.5) - lwh)) / (T(0.5) + lwh);
-        const long o = ((long)s * (DIM - 1) + a) * g.NP + pidx;
-        wuY[o] = uY;
-        wghost[o] = ug;
-        wmuw[o] = muw;
+    for (int a = 0; a < DIM - 1; ++a) {
+        int iL, jL;
+        wall_low(g, a, w.i, w.j, iL, jL);
+        const long tL = (long)w.s * g.NP + (DIM == 2 ? (long)iL : (long)iL + (long)g.n[0] * jL);
+        const ColQ<T> cL = load_colq<L>(cq + tL);
+        wall_finish<L, T, DIM>(g, ph, cR, cL, a, w.s, w.pidx, w.i, w.j, u0, u1, wuY, wghost, wmuw);
     }
 }
 
@@ -585,6 +651,11 @@ __device__ __forceinline__ long colour_cell(const Geom& g, int colour, long k) {
 // is then never stored: a Gauss-Seidel step does not read its own cell)
 enum StepNb { kNbStored = 0, kNbZero = 1, kNbProlong = 2 };
 
+// quotient of a smoothing step: the fast FP32 division (a preconditioner's
+// arithmetic; the defect correction iterates to the tolerance regardless)
+__device__ __forceinline__ float step_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double step_div(double a, double b) { return a / b; }
+
 template <class L, typename M, int DIM>
 __device__ __forceinline__ M prolong_val(const Geom& gf, const Geom& gc, const M* pc, long c);
 
@@ -602,7 +673,7 @@ __device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* 
             return L::ld(p + n);
         },
         diag, off);
-    p[c] = (off - L::ld(f + c)) / diag;
+    p[c] = step_div(off - L::ld(f + c), diag);
 }
 
 // level-0 smoothing step with density-formed coefficients (stencil_L_rho)
@@ -619,7 +690,7 @@ __device__ __forceinline__ void rbgs_rho_at(const Geom& g, const float* rho, flo
             return L::ld(p + n);
         },
         diag, off);
-    p[c] = (off - L::ld(f + c)) / diag;
+    p[c] = step_div(off - L::ld(f + c), diag);
 }
 
 // FP64 residual f - A p of level 0
@@ -792,7 +863,7 @@ __device__ __forceinline__ void coarse_start(const Geom& gc, const M* const* cb,
     if (((Q.i + Q.j + Q.k) & 1) != 0) return;
     M diag, off;
     stencil_L<L, M, DIM>(gc, cb, Q, t, g_ih2<M>(gc), [](long) { return M(0); }, diag, off);
-    pc[t] = (off - fct) / diag;
+    pc[t] = step_div(off - fct, diag);
 }
 
 // coarse cell t: mean of the 2^D fine residuals, then coarse_start
