@@ -196,6 +196,18 @@ def oracle_rate(wl, steps, budget_s=None):
         done, wl.n[0], wl.n[1])
 
 
+def job_rate(units_per_rank, local_seconds, world, device):
+    """Whole-job rate of `world` replicas: the units all ranks processed over
+    the slowest rank's time (max over ranks, an all-reduce where world > 1).
+    Returns (rate in units per second, slowest seconds)."""
+    import torch
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    slowest = float(t.item())
+    return units_per_rank * world / slowest, slowest
+
+
 def reference_arm(args, rank, world):
     from paper_2412_16843_gb300 import inputs
     if rank != 0:
@@ -284,11 +296,9 @@ def gpu_arm(args, rank, world, local_rank):
     kern_ms, kern_n = s.profile_stop()
     clk = clocks.stop()
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = wl.cells * args.steps * world / (ms_max / 1e3) / 1e6
+    rate, slowest_s = job_rate(wl.cells * args.steps, ms / 1e3, world, "cuda")
+    ms_max = slowest_s * 1e3
+    value = rate / 1e6
 
     # end to end through the public API with host buffers
     ne = args.e2e_steps or max(5, min(args.steps, 30))
@@ -309,10 +319,7 @@ def gpu_arm(args, rank, world, local_rank):
         s.get_fields((phi_h, vel_h, p_h))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_value = wl.cells * ne * world / float(te.item()) / 1e6
+    e2e_value = job_rate(wl.cells * ne, e2e_s, world, "cuda")[0] / 1e6
 
     if rank != 0:
         return
