@@ -180,6 +180,19 @@ __device__ __forceinline__ SmLevel sm_level(const InstArgs<T>& A, float* sm, int
     return s;
 }
 
+// one colour of a smoothing pass of a shared-memory level of the tail
+template <int DIM>
+__device__ __forceinline__ void tail_pass(const SmLevel& L, const float* const* bl, int col, int t0, int nt,
+                                          int half) {
+    ops::colour_pass(
+        t0, half, nt,
+        [&](int k, long& c) {
+            c = ops::colour_cell(L.g, col, k);
+            return ops::rbgs_val<LP, float, DIM>(L.g, bl, L.e, L.r, c);
+        },
+        [&](long c, float v) { L.e[c] = v; });
+}
+
 template <typename T, int DIM>
 __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
     const int lt = A.lt, nl = A.nlev;
@@ -242,8 +255,7 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
         for (int it = 0; it < A.npre; ++it)
             for (int col = 0; col < 2; ++col) {
                 if (it == 0 && col == 0) continue;
-                for (int k = t0; k < half; k += nt)
-                    ops::rbgs_at<LP, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
+                tail_pass<DIM>(L, bl, col, t0, nt, half);
                 __syncthreads();
             }
         const float* const* cbp = (l + 1 < nl - 1) ? bc : nullptr;
@@ -271,8 +283,7 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
         __syncthreads();
         for (int it = 0; it < A.npost; ++it)
             for (int col = 0; col < 2; ++col) {
-                for (int k = t0; k < half; k += nt)
-                    ops::rbgs_at<LP, float, DIM>(L.g, bl, L.e, L.r, ops::colour_cell(L.g, col, k));
+                tail_pass<DIM>(L, bl, col, t0, nt, half);
                 __syncthreads();
             }
     }
@@ -303,11 +314,14 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
         for (int it = 0; it < A.npre; ++it)
             for (int col = 0; col < 2; ++col) {
                 if (it == 0 && col == 0) continue;  // written with this level's r
-                for (int k = tid; k < half; k += nth) {
-                    const long c = ops::colour_cell(L.g, col, k);
-                    if (l == 0) ops::rbgs_rho_at<L_, DIM>(L.g, L.rho0, L.e, L.r, c);
-                    else ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
-                }
+                ops::colour_pass(
+                    tid, half, nth,
+                    [&](int k, long& c) {
+                        c = ops::colour_cell(L.g, col, k);
+                        return l == 0 ? ops::rbgs_rho_val<L_, DIM>(L.g, L.rho0, L.e, L.r, c)
+                                      : ops::rbgs_val<L_, float, DIM>(L.g, bl, L.e, L.r, c);
+                    },
+                    [&](long c, float v) { L.e[c] = v; });
                 if (!x.sync()) return false;
             }
         // the tail starts its top level from zero itself
@@ -333,19 +347,22 @@ __device__ bool vcycle(const InstArgs<T>& A, X& x, bool first, float* sm) {
             for (int col = 0; col < 2; ++col) {
                 const bool last = (l == 0 && it == A.npost - 1 && col == 1);
                 const bool pro = (it == 0 && col == 0);
-                for (int k = tid; k < half; k += nth) {
-                    const long c = ops::colour_cell(L.g, col, k);
-                    if (pro) {
-                        if (l == 0)
-                            ops::rbgs_rho_at<L_, DIM, ops::kNbProlong>(L.g, L.rho0, L.e, L.r, c, &C.g, C.e);
-                        else
-                            ops::rbgs_at<L_, float, DIM, ops::kNbProlong>(L.g, bl, L.e, L.r, c, &C.g, C.e);
-                    } else {
-                        if (l == 0) ops::rbgs_rho_at<L_, DIM>(L.g, L.rho0, L.e, L.r, c);
-                        else ops::rbgs_at<L_, float, DIM>(L.g, bl, L.e, L.r, c);
-                    }
-                    if (last) P0[c] = ops::p_add(L_::ld(P0 + c), L.e[c]);
-                }
+                ops::colour_pass(
+                    tid, half, nth,
+                    [&](int k, long& c) {
+                        c = ops::colour_cell(L.g, col, k);
+                        if (pro)
+                            return l == 0 ? ops::rbgs_rho_val<L_, DIM, ops::kNbProlong>(L.g, L.rho0, L.e, L.r, c,
+                                                                                      &C.g, C.e)
+                                          : ops::rbgs_val<L_, float, DIM, ops::kNbProlong>(L.g, bl, L.e, L.r, c,
+                                                                                         &C.g, C.e);
+                        return l == 0 ? ops::rbgs_rho_val<L_, DIM>(L.g, L.rho0, L.e, L.r, c)
+                                      : ops::rbgs_val<L_, float, DIM>(L.g, bl, L.e, L.r, c);
+                    },
+                    [&](long c, float v) {
+                        L.e[c] = v;
+                        if (last) P0[c] = ops::p_add(L_::ld(P0 + c), v);
+                    });
                 if (last) {  // the other colour is final already
                     for (int k = tid; k < half; k += nth) {
                         const long c = ops::colour_cell(L.g, 0, k);

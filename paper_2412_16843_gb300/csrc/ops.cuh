@@ -659,9 +659,10 @@ __device__ __forceinline__ double step_div(double a, double b) { return a / b; }
 template <class L, typename M, int DIM>
 __device__ __forceinline__ M prolong_val(const Geom& gf, const Geom& gc, const M* pc, long c);
 
+// the new value of cell c (rbgs_at without the store)
 template <class L, typename M, int DIM, int NB = kNbStored>
-__device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* p, const M* f, long c,
-                                        const Geom* gc = nullptr, const M* pc = nullptr) {
+__device__ __forceinline__ M rbgs_val(const Geom& g, const M* const* beta, const M* p, const M* f, long c,
+                                      const Geom* gc = nullptr, const M* pc = nullptr) {
     const IJK q = decode(g, c);
     const M ih2 = g_ih2<M>(g);
     M diag, off;
@@ -673,13 +674,19 @@ __device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* 
             return L::ld(p + n);
         },
         diag, off);
-    p[c] = step_div(off - L::ld(f + c), diag);
+    return step_div(off - L::ld(f + c), diag);
 }
 
-// level-0 smoothing step with density-formed coefficients (stencil_L_rho)
+template <class L, typename M, int DIM, int NB = kNbStored>
+__device__ __forceinline__ void rbgs_at(const Geom& g, const M* const* beta, M* p, const M* f, long c,
+                                        const Geom* gc = nullptr, const M* pc = nullptr) {
+    p[c] = rbgs_val<L, M, DIM, NB>(g, beta, p, f, c, gc, pc);
+}
+
+// level-0 smoothing value with density-formed coefficients (stencil_L_rho)
 template <class L, int DIM, int NB = kNbStored>
-__device__ __forceinline__ void rbgs_rho_at(const Geom& g, const float* rho, float* p, const float* f, long c,
-                                            const Geom* gc = nullptr, const float* pc = nullptr) {
+__device__ __forceinline__ float rbgs_rho_val(const Geom& g, const float* rho, const float* p, const float* f, long c,
+                                              const Geom* gc = nullptr, const float* pc = nullptr) {
     const IJK q = decode(g, c);
     float diag, off;
     stencil_L_rho<L, DIM>(
@@ -690,7 +697,34 @@ __device__ __forceinline__ void rbgs_rho_at(const Geom& g, const float* rho, flo
             return L::ld(p + n);
         },
         diag, off);
-    p[c] = step_div(off - L::ld(f + c), diag);
+    return step_div(off - L::ld(f + c), diag);
+}
+
+template <class L, int DIM, int NB = kNbStored>
+__device__ __forceinline__ void rbgs_rho_at(const Geom& g, const float* rho, float* p, const float* f, long c,
+                                            const Geom* gc = nullptr, const float* pc = nullptr) {
+    p[c] = rbgs_rho_val<L, DIM, NB>(g, rho, p, f, c, gc, pc);
+}
+
+// One colour of a red-black pass over the cells k0, k0 + stride, ... < half
+// of that colour: two cells an iteration, both values formed (val(k, c))
+// before either is stored (put(c, v)), so their loads overlap; cells of one
+// colour do not depend on each other, so the result is the same.
+template <class VAL, class PUT>
+__device__ __forceinline__ void colour_pass(int k0, int half, int stride, VAL val, PUT put) {
+    int k = k0;
+    for (; k + stride < half; k += 2 * stride) {
+        long c0, c1;
+        const auto v0 = val(k, c0);
+        const auto v1 = val(k + stride, c1);
+        put(c0, v0);
+        put(c1, v1);
+    }
+    if (k < half) {
+        long c0;
+        const auto v0 = val(k, c0);
+        put(c0, v0);
+    }
 }
 
 // FP64 residual f - A p of level 0
