@@ -67,20 +67,21 @@ def vcycle_words(D):
 
 
 def step_bytes(D, N, word, vcycles_per_step):
-    """Algorithmic bytes of one full step, B = W [4 * 5(1+D) + 4 (3 + (2D+1) +
-    N_V V_D)] per cell: per RK stage the fused stencil minimum (read the stage
+    """Algorithmic bytes of one full step, B = W [4 * 5(1+D) + 4 ((D+1) + (2D+1)
+    + N_V V_D)] per cell: per RK stage the fused stencil minimum (read the stage
     state and y^n, read+write the accumulator, write the next stage: 5(1+D)
-    words), per pressure solve the divergence (3 words), the projection
-    (2D+1) and N_V V-cycles of V_D words; W is the state word size."""
+    words), per pressure solve the divergence (D velocity components read, f
+    written: D+1 words), the projection (2D+1) and N_V V-cycles of V_D words;
+    W is the state word size."""
     nv_per_solve = vcycles_per_step / 4.0
-    words = 4 * 5 * (1 + D) + 4 * (3 + (2 * D + 1) + nv_per_solve * vcycle_words(D))
+    words = 4 * 5 * (1 + D) + 4 * ((D + 1) + (2 * D + 1) + nv_per_solve * vcycle_words(D))
     return N * word * words
 
 
 def algorithmic_bytes(kernel, dim, N, NP, word):
     D = dim
     words = {
-        "rbgs0": 0.5 * N + 0.5 * N + 0.5 * N + D * N + NP,  # e read/write of one colour, r, face coefficients
+        "rbgs0": 2.5 * N,  # one colour: rho, the other colour's e, own r, own e written
         "mom": (3 * D + 2) * N + NP,                           # u, m, phi, mu_c in; rhs of every component out
         "phi_rhs": (3 * D + 2) * N + NP,                       # phi, u, n in; rhs_phi, m out
         "cell": (3 + D) * N,                                   # phi, psi in; n, mu_c out
