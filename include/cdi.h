@@ -198,8 +198,10 @@ cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
  * every stencil and multigrid kernel separately; CDI_EXEC_AUTO (default)
  * takes the persistent launch for grids up to 2^20 cells, where launch
  * latency dominates, and separate kernels above, where the separate kernels
- * keep more warps resident for the bandwidth-bound sweeps.  All compute the
- * same arithmetic. */
+ * keep more warps resident for the bandwidth-bound sweeps.  All take the same
+ * discretisation and solver; they order some FP32 operations of the V-cycle
+ * differently, so their results agree to the pressure tolerance, not bit for
+ * bit. */
 cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
 
 /* Red-black Gauss-Seidel sweeps before and after the coarse-grid correction
@@ -218,8 +220,9 @@ cdi_status cdi_set_barrier_timeout(cdi_ctx* ctx, long long ns);
 
 /* Launch profiler (diagnostics): from now on record a CUDA event pair on the
  * launching stream around each of the next max_launches launches of one
- * kernel class ("rbgs0" = red-black sweep on the finest level, "mom",
- * "phi_rhs", "wall", "cell", "psi", "stage_phi", "stage_mom", "div",
+ * kernel class ("step" = the persistent step kernel, one launch per cdi_step
+ * call; separate kernels: "rbgs0" = red-black sweep on the finest level,
+ * "mom", "phi_rhs", "wall", "cell", "psi", "stage_phi", "stage_mom", "div",
  * "rbgs", "resid_restrict0", "prolong0", "coarse", "resid", "project").
  * Creates events (host objects); allocates no device memory. */
 cdi_status cdi_profile_start(cdi_ctx* ctx, const char* kernel, int max_launches);
