@@ -71,6 +71,7 @@ def _load():
                                        ctypes.POINTER(ctypes.c_long)]
         lib.orc_eval_psi.argtypes = [P, DP] + [DP] * 10
         lib.orc_eval_wall.argtypes = [P, DP, DP, DP]
+        lib.orc_eval_wall_columns.argtypes = [P, DP, DP]
         lib.orc_eval_rhs.argtypes = [P, D, DP, DP, DP, DP]
         lib.orc_poisson.argtypes = [P, DP, DP, ctypes.POINTER(I), DP]
         lib.orc_poisson_direct.argtypes = [P, DP, DP]
@@ -225,6 +226,16 @@ class Oracle:
         self.lib.orc_eval_wall(self.handle, _ptr(uY), _ptr(g), _ptr(pw))
         sh = (2, t) + self.plane
         return uY.reshape(sh), g.reshape(sh), pw.reshape((2,) + self.plane)
+
+    def wall_columns(self):
+        """Extrapolated psi_w and in-plane curvature kappa_p of every wall
+        column, shape (2,) + wall plane (low wall first)."""
+        np_ = int(np.prod(self.plane))
+        psiw = np.zeros((2, np_))
+        kpw = np.zeros((2, np_))
+        self.lib.orc_eval_wall_columns(self.handle, _ptr(psiw), _ptr(kpw))
+        sh = (2,) + self.plane
+        return psiw.reshape(sh), kpw.reshape(sh)
 
     def eval_rhs(self, gamma=-1.0):
         rphi = np.zeros(self.cell_shape)

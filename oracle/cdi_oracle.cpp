@@ -1079,6 +1079,24 @@ int orc_eval_wall(void* h, double* uY, double* ghost, double* phiw) {
     return ORC_OK;
 }
 
+// wall-column quantities of the current state, per wall and column of the wall
+// plane: the extrapolated psi_w and in-plane curvature kappa_p (read-only view
+// of eval_wall's intermediate values, for the closed-form pins)
+int orc_eval_wall_columns(void* h, double* psiw, double* kpw) {
+    auto* S = (Solver*)h;
+    const Grid& g = S->g;
+    PsiOut ps;
+    WallOut w;
+    eval_psi(*S, S->phi, ps);
+    eval_wall(*S, S->phi, S->u, ps, w);
+    long NP = (g.D == 2) ? g.n[0] : (long)g.n[0] * g.n[1];
+    for (int s = 0; s < 2; ++s) {
+        if (psiw) std::memcpy(psiw + s * NP, w.psiw[s].data(), sizeof(double) * NP);
+        if (kpw) std::memcpy(kpw + s * NP, w.kpw[s].data(), sizeof(double) * NP);
+    }
+    return ORC_OK;
+}
+
 // a1..a4 on the current state with the given gamma (gamma < 0: the step's rule)
 int orc_eval_rhs(void* h, double gamma, double* rphi, double* ru, double* rv, double* rw) {
     auto* S = (Solver*)h;

@@ -488,3 +488,33 @@ def test_3d_step_reproduces_2d_step_for_y_invariant_data():
     assert np.abs(v3[0] - v2[0][:, None, :]).max() < 1e-10 * np.abs(v2[0]).max()
     assert np.abs(v3[2] - v2[1][:, None, :]).max() < 1e-10 * np.abs(v2[0]).max()
     assert np.abs(v3[1]).max() < 1e-14
+
+
+@pytest.mark.parametrize("theta_deg", [60, 90, 120])
+def test_in_plane_curvature_on_spherical_cap_3d(theta_deg):
+    """3D in-plane curvature kappa_p of the wall columns (R13): on a spherical
+    cap with psi = R - r exactly (the tanh profile), the phase-field curvature
+    is 2/r and the normal curvature along the contact-line tangent 1/r, so
+    kappa_p = 1/r at every cell and, extrapolated to the wall, 1/r_w with
+    r_w = R - psi_w.  Near the contact line (|psi_w| < eps) the oracle's
+    kappa_p converges to it under refinement with eps ~ h (first order: the
+    (1 - |grad psi|^2)/eps term is O(h^2)/eps); dropping the tangential
+    correction (2/r), flipping its sign (3/r) or the mixed derivative's would
+    leave an O(1) error."""
+    th = math.radians(theta_deg)
+    R = 0.3
+    errs = []
+    for n in (32, 64):
+        h = 1.0 / n
+        dims = (n, n, n // 2)
+        eps = 1.3 * h
+        phi = inputs.cap_phi_3d(*dims, h, R, th, 0.5, 0.5, eps)
+        o = oracle.Oracle(3, dims, tuple(x * h for x in dims))
+        o.set_fluids(1.0, 1.0, 0.1, 0.1, 1.0, eps, 0.0)
+        o.set_state(phi)
+        psiw, kpw = o.wall_columns()
+        near = np.abs(psiw[0]) < eps
+        assert near.sum() > 100
+        errs.append(np.abs(kpw[0][near] * (R - psiw[0][near]) - 1.0).max())
+    assert errs[0] < 0.06 and errs[1] < 0.025
+    assert errs[1] < errs[0] / 1.7
