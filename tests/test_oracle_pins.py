@@ -518,3 +518,28 @@ def test_in_plane_curvature_on_spherical_cap_3d(theta_deg):
         errs.append(np.abs(kpw[0][near] * (R - psiw[0][near]) - 1.0).max())
     assert errs[0] < 0.06 and errs[1] < 0.025
     assert errs[1] < errs[0] / 1.7
+
+
+def test_adaptive_gamma_is_the_printed_factor_times_the_largest_velocity(golden):
+    """Sec. 5.1 (and 5.2): gamma = 2.5 |u|_max, the factor the paper prints.
+    With gamma < 0 the oracle takes that rule, floored at -gamma (reading
+    R11): its phi right-hand side equals the one evaluated with the explicit
+    gamma, 2.5 x the largest face speed, or the floor when that is smaller; a
+    factor of 2 would differ."""
+    factor = golden["equilibrium_drop"]["gamma_factor"]
+    wl = inputs.drop_2d(64, 32)
+    o = oracle.from_workload(wl, tol=1e-12)
+    o.set_fluids(wl.rho1, wl.rho2, wl.mu1, wl.mu2, wl.sigma, wl.eps, -0.05)
+    rng = np.random.default_rng(17)
+    for umax, expected in ((0.4, factor * 0.4), (0.01, 0.05)):
+        vel = [umax * rng.uniform(-0.9, 0.9, o.face_shape(a)) for a in range(2)]
+        vel[1][0] = 0.0
+        vel[1][-1] = 0.0
+        vel[0][10, 20] = -umax
+        o.set_state(wl.phi0, vel)
+        r_rule, _ = o.eval_rhs(gamma=-1.0)
+        r_expl, _ = o.eval_rhs(gamma=expected)
+        assert np.array_equal(r_rule, r_expl), umax
+        if umax == 0.4:
+            r_two, _ = o.eval_rhs(gamma=2.0 * umax)
+            assert not np.allclose(r_rule, r_two)
