@@ -4,6 +4,8 @@
     python -m paper_2412_16843_gb300.profile_cases unet 128     # network forward passes at 128^3
     python -m paper_2412_16843_gb300.profile_cases batch 64     # 64-instance FP32-mixed sweep, 3 steps
     python -m paper_2412_16843_gb300.profile_cases drop3d 256   # 3D drop, FP32-mixed, separate kernels, 2 steps
+    python -m paper_2412_16843_gb300.profile_cases wide 512 1   # 512x256x256 drop, FP32-mixed, previous-pressure
+                                                                # first guess, separate kernels, 1 step
 """
 import sys
 
@@ -49,6 +51,16 @@ def main(argv):
         s.step(wl.dt, 2)
         torch.cuda.synchronize()
         print('drop3d ok', s.last_stats())
+    elif mode == 'wide':
+        n = int(argv[2]) if len(argv) > 2 else 512
+        steps = int(argv[3]) if len(argv) > 3 else 1
+        wl = inputs.drop_3d_wide(n)
+        s = cdi.from_workload(wl, precision=cdi.FP32_MIXED, tol=1e-8)
+        s.set_exec(cdi.EXEC_KERNELS)
+        s.set_solver(1e-8, 100, cdi.WARM_PREV)
+        s.step(wl.dt, steps)
+        torch.cuda.synchronize()
+        print('wide ok', s.last_stats())
 
 
 if __name__ == "__main__":
