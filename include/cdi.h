@@ -213,6 +213,19 @@ cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
  * V-cycles per solve. */
 cdi_status cdi_set_smoothing(cdi_ctx* ctx, int npre, int npost);
 
+/* Smoother kernel of the finest multigrid level of 3D grids on the
+ * launch-per-kernel path (the pressure solve of Eq. NS_incompressibility;
+ * the solver is this library's choice): CDI_SWEEP_ONEPASS runs each
+ * red-black Gauss-Seidel sweep as one launch that marches along z over
+ * 64 x 16 tiles with planes staged in shared memory, reading the correction
+ * from one buffer and writing it to another (both colours in one pass over
+ * memory; needs nx a multiple of 64 and ny of 16); CDI_SWEEP_COLOUR runs
+ * one launch per colour; CDI_SWEEP_AUTO (default) takes the one-pass sweep
+ * where the grid has enough tiles to fill the GPU.  Both compute the same
+ * red-then-black update (each cell's terms in the same order). */
+enum { CDI_SWEEP_AUTO = 0, CDI_SWEEP_ONEPASS = 1, CDI_SWEEP_COLOUR = 2 };
+cdi_status cdi_set_level0_sweep(cdi_ctx* ctx, int mode);
+
 /* Longest wait (nanoseconds, 0 .. 6e10; default 2e9) of a grid barrier in the
  * persistent step kernel before the call ends with CDI_ETIMEOUT.  A timed-out
  * call leaves the state undefined but the context and the device usable. */
@@ -371,7 +384,9 @@ cdi_status cdi_last_pressure(cdi_ctx* ctx, double* f, double* p);
  * library until the process exits.  Hence n must lie in [1, 33554432];
  * other n returns CDI_EINVAL.  The first call on a device looks up the
  * scratch address on that device (make that first call before any stream
- * capture).  Every call on a device shares the scratch and leaves its partial
+ * capture) and keeps it for the life of the process: a device reset while
+ * the library is loaded is not supported.  A CUDA error already pending
+ * from earlier work is reported as such (CDI_ECUDA) before any launch.  Every call on a device shares the scratch and leaves its partial
  * sums there; calls whose kernels overlap on the GPU race with each other.
  * Blocks sum fixed chunks in a fixed order, so the result is deterministic.
  * On failure a one-line message is copied into err (err_len bytes, may be

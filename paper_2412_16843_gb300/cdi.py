@@ -24,6 +24,7 @@ FP64, FP32_MIXED = 0, 1
 WALL_LO, WALL_HI, WALL_BOTH = 0, 1, 2
 WARM_PREV, WARM_ZERO, WARM_EXTRAP, WARM_UNET = 0, 1, 2, 3
 EXEC_PERSISTENT, EXEC_KERNELS, EXEC_AUTO = 0, 1, 2
+SWEEP_AUTO, SWEEP_ONEPASS, SWEEP_COLOUR = 0, 1, 2
 MODELS = {"1A": 0, "1B": 1, "2A": 2, "2B": 3, "3A": 4, "3B": 5, "4A": 6, "4B": 7}
 
 _lib = None
@@ -79,6 +80,7 @@ def load(path: str = LIB_PATH):
         "cdi_set_exec": [P, I],
         "cdi_set_barrier_timeout": [P, ctypes.c_longlong],
         "cdi_set_smoothing": [P, I, I],
+        "cdi_set_level0_sweep": [P, I],
         "cdi_launches_per_step": [P, ctypes.POINTER(ctypes.c_long)],
         "cdi_profile_start": [P, ctypes.c_char_p, I],
         "cdi_profile_stop": [P, DP, ctypes.POINTER(ctypes.c_long)],
@@ -288,6 +290,9 @@ class Solver:
 
     def set_smoothing(self, npre: int, npost: int):
         self._check(self.lib.cdi_set_smoothing(self.h, npre, npost))
+
+    def set_level0_sweep(self, mode: int):
+        self._check(self.lib.cdi_set_level0_sweep(self.h, mode))
 
     def set_barrier_timeout(self, ns: int):
         self._check(self.lib.cdi_set_barrier_timeout(self.h, int(ns)))

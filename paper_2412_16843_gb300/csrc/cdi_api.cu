@@ -162,10 +162,12 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
                 L.beta[a] = (f64 && a < g.D) ? (double*)cv.take((nl + (a == g.W ? np : 0)) * sizeof(double))
                                              : nullptr;
             L.rho0 = (float*)cv.take(nl * sizeof(float));
+            L.e2 = sweep0_supported(g) ? (float*)cv.take(nl * sizeof(float)) : nullptr;
         } else {
             L.p = nullptr;
             L.f = nullptr;
             L.rho0 = nullptr;
+            L.e2 = nullptr;
             for (int a = 0; a < 3; ++a) L.beta[a] = nullptr;
         }
         L.e = (float*)cv.take(nl * sizeof(float));
@@ -176,7 +178,7 @@ void carve(cdi_ctx* c, char* base, size_t* total) {
     mg.partials = (double*)cv.take(2 * kPartials * sizeof(double));
     mg.scal = (double*)cv.take(S_NSCAL * sizeof(double));
     mg.scalf = (float*)cv.take(SF_NSCAL * sizeof(float));
-    mg.ainv = (float*)cv.take((size_t)kMaxCoarse * kMaxCoarse * sizeof(float));
+    mg.ainv = (float*)cv.take(((size_t)kMaxCoarse * kMaxCoarse + 1) * sizeof(float));  // inverse, then the shift
     c->ctl = (PersistCtl*)cv.take(sizeof(PersistCtl));
     c->tail_dev = cv.take(sizeof(InstArgs<float>));
     for (int k = 0; k < 4; ++k)
@@ -295,6 +297,10 @@ cdi_status kernels_tail_setup(cdi_ctx* c) {
     size_t optin = 0;
     cdi_status st = smem_optin(c, &optin);
     if (st) return st;
+    if (c->mg.lv[0].e2) {
+        st = cuda_check(c, sweep0_prepare(), "one-pass sweep setup");
+        if (st) return st;
+    }
     const size_t budget = optin > 8192 ? optin - 4096 : 0;
     int lt = 0;
     PersistLayout lay{};
@@ -939,6 +945,20 @@ cdi_status cdi_set_smoothing(cdi_ctx* c, int npre, int npost) {
     // the launch-per-kernel tail descriptor and V-cycle graphs hold the sweep counts
     c->tail_ready = false;
     c->mg.tail_args = nullptr;
+    for (int k = 0; k < 2; ++k)
+        if (c->vc_exec[k]) {
+            cudaGraphExecDestroy(c->vc_exec[k]);
+            c->vc_exec[k] = nullptr;
+        }
+    return CDI_OK;
+}
+
+cdi_status cdi_set_level0_sweep(cdi_ctx* c, int mode) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (mode != CDI_SWEEP_AUTO && mode != CDI_SWEEP_ONEPASS && mode != CDI_SWEEP_COLOUR)
+        return fail(c, CDI_EINVAL, "sweep mode must be CDI_SWEEP_AUTO, CDI_SWEEP_ONEPASS or CDI_SWEEP_COLOUR");
+    c->mg.sweep_mode = mode;
+    // the V-cycle graphs hold the launches of the previous choice
     for (int k = 0; k < 2; ++k)
         if (c->vc_exec[k]) {
             cudaGraphExecDestroy(c->vc_exec[k]);

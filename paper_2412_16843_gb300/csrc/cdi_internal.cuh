@@ -218,6 +218,7 @@ struct MGLevel {
     double* f;         // level 0 only (8 bytes per cell, typed by PForm)
     double* beta[3];   // level 0 only, FP64 form
     float* rho0;       // level 0 only: FP32 cell densities (the level-0 smoother's coefficients)
+    float* e2;         // level 0 only: the second correction buffer of the one-pass 3D sweep
     float* e;
     float* r;
     float* bf[3];
@@ -229,13 +230,16 @@ struct MG {
     double* partials;   // [2 * kPartials]
     double* scal;       // device scalars
     float* scalf;       // FP32 device scalars
-    float* ainv;        // launch-per-kernel path: inverse of the coarsest level [kMaxCoarse^2]
+    float* ainv;        // launch-per-kernel path: FP32 inverse of the coarsest level [n^2] and its shift
     // launch-per-kernel path: levels tail_lt .. nlev-1 of a V-cycle run as one
     // single-CTA launch in shared memory (tail_args: its descriptor in device
     // memory, an InstArgs<float>; null: every level as separate kernels)
     const void* tail_args;
     int tail_lt;
     size_t tail_smem;
+    // launch-per-kernel path, 3D level 0: 0 one-pass sweeps where the grid
+    // fills the GPU, 1 one-pass sweeps wherever the tile shape fits, 2 colour passes
+    int sweep_mode;
 };
 
 // scalar slots in MG::scal
@@ -276,6 +280,17 @@ void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s);
 // p = 2 hnew - hold (extrapolated first guess; history arrays in the form's p storage)
 template <typename T>
 void launch_p_extrap(const Geom& g, MG& mg, const double* hnew, const double* hold, cudaStream_t s);
+// level-0 smoothing modes: plain; the first sweep of a V-cycle, whose old
+// correction is zero (not read); the last, which also adds the correction to p
+enum SweepMode { kSweepPlain = 0, kSweepFromZero = 1, kSweepUpdate = 2 };
+// one-pass red-black sweep of the 3D level 0 (k_sweep.cu): ein -> eout in one
+// launch (ein unused from zero; the update mode also adds eout to p)
+bool sweep0_supported(const Geom& g);  // the tile shape fits the grid
+bool sweep0_auto(const Geom& g);       // it fits and the grid fills the GPU
+cudaError_t sweep0_prepare();
+template <typename T>
+void launch_sweep0(const Geom& g, const float* rho, const float* ein, float* eout, const float* r, int mode,
+                   PT<T>* p, cudaStream_t s);
 // the single-CTA shared-memory tail of a V-cycle as its own launch (k_persist.cu)
 cudaError_t tail_prepare(int dim, size_t smem);
 cudaError_t launch_tail(const void* inst_args, int dim, size_t smem, cudaStream_t s);
@@ -312,7 +327,7 @@ struct InstStats {
 // control block of the single-grid persistent kernel in the workspace
 struct PersistCtl {
     // grid-barrier arrivals since the launch (zeroed by the host before it);
-    // kBarError added when a CTA gives up waiting
+    // bit kBarError set (atomic OR) when a CTA gives up waiting
     unsigned long long bar;
     InstStats st;
 };

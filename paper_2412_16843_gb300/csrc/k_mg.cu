@@ -210,7 +210,6 @@ __global__ void k_rbgs(Geom g, const float* b0, const float* b1, const float* b2
 // read).  kSweepUpdate: the last black pass, which also adds the now final
 // correction of both cells of the thread's pair (2 ix, 2 ix + 1) to p.
 constexpr int kSweepX = 64, kSweepY = 4;
-enum SweepMode { kSweepPlain = 0, kSweepFromZero = 1, kSweepUpdate = 2 };
 template <typename T, int DIM, int MODE>
 __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float* __restrict__ rho,
                                                              float* __restrict__ e, const float* __restrict__ r,
@@ -296,17 +295,21 @@ __global__ void k_prolong(Geom gf, Geom gc, const float* ec, float* e) {
 template <int DIM>
 __global__ void k_coarse_invert(Geom g, const float* b0, const float* b1, const float* b2, float* ainv) {
     const float* beta[3] = {b0, b1, b2};
-    __shared__ float A[kMaxCoarse * kMaxCoarse];
+    __shared__ float A[kMaxCoarse * kMaxCoarse + 1];
     __shared__ float fct[kMaxCoarse];
     __shared__ float sh;
     ops::coarse_invert_block<Ld, float, DIM>(g, beta, A, fct, &sh);
     const int n = (int)g.N;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) ainv[t] = A[t];
+    for (int t = threadIdx.x; t <= n * n; t += blockDim.x) ainv[t] = A[t];  // inverse and shift
 }
 
-// coarsest-level correction e = Ainv r (every V-cycle)
-__global__ void k_coarse(int n, const float* ainv, const float* r, float* e) {
-    ops::coarse_apply_block<Ld, float>(n, ainv, r, e);
+// coarsest-level correction: the FP64 solve of A e = r (every V-cycle)
+template <int DIM>
+__global__ void k_coarse(Geom g, const float* b0, const float* b1, const float* b2, const float* ainv,
+                         const float* r, float* e) {
+    const float* beta[3] = {b0, b1, b2};
+    __shared__ double rd[kMaxCoarse], ed[kMaxCoarse], rr[kMaxCoarse];
+    ops::coarse_apply_block<Ld, float, DIM>(g, beta, ainv, r, e, rd, ed, rr);
 }
 
 template <typename T>
@@ -540,13 +543,44 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
         return false;
     }
     if (l == mg.nlev - 1) {
-        CDI_PROF(KC_COARSE, s, (k_coarse<<<1, 64, 0, s>>>((int)L.g.N, mg.ainv, L.r, L.e)));
+        CDI_PROF(KC_COARSE, s, (k_coarse<DIM><<<1, 64, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], mg.ainv, L.r, L.e)));
         ++g_launches;
         return false;
     }
     const unsigned nb = blocks_for(L.g.N);
     const unsigned nbh = blocks_for(L.g.N / 2);
     const int kc_rbgs = (l == 0) ? KC_RBGS0 : KC_RBGS;
+    if (DIM == 3 && l == 0 && L.e2 && (mg.sweep_mode == 1 || (mg.sweep_mode == 0 && sweep0_auto(L.g)))) {
+        // one-pass sweeps (k_sweep.cu), alternating between the two correction
+        // buffers: the first starts from e = 0, the last adds e to p
+        float* buf[2] = {L.e, L.e2};
+        int cur = -1;
+        for (int it = 0; it < npre; ++it) {
+            const int out = cur == 0 ? 1 : 0;
+            CDI_PROF(KC_RBGS0, s,
+                     launch_sweep0<T>(L.g, L.rho0, cur < 0 ? nullptr : buf[cur], buf[out], L.r,
+                                      cur < 0 ? kSweepFromZero : kSweepPlain, p, s));
+            ++g_launches;
+            cur = out;
+        }
+        MGLevel& C = mg.lv[1];
+        CDI_PROF(KC_RESTRICT0, s,
+                 (k_resid_restrict0<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.rho0, buf[cur], L.r, C.r,
+                                                                                C.e)));
+        ++g_launches;
+        vcycle_rec<T, DIM>(mg, p, 1, npre, npost, s);
+        CDI_PROF(KC_PROLONG0, s, (k_prolong<DIM><<<nb, kThreads, 0, s>>>(L.g, C.g, C.e, buf[cur])));
+        ++g_launches;
+        for (int it = 0; it < npost; ++it) {
+            const int out = 1 - cur;
+            CDI_PROF(KC_RBGS0, s,
+                     launch_sweep0<T>(L.g, L.rho0, buf[cur], buf[out], L.r,
+                                      it == npost - 1 ? kSweepUpdate : kSweepPlain, p, s));
+            ++g_launches;
+            cur = out;
+        }
+        return true;
+    }
     // one red-black sweep; level 0 forms its coefficients from the cell densities
     const dim3 sweep_grid((unsigned)((L.g.n[0] / 2 + kSweepX - 1) / kSweepX),
                           (unsigned)((L.g.n[1] + kSweepY - 1) / kSweepY), (unsigned)(DIM == 3 ? L.g.n[2] : 1));

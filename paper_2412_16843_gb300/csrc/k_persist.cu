@@ -96,8 +96,10 @@ struct GridX {
     // is passed once the counter reaches m x gridDim.x.  Thread 0 arrives with
     // one acquire-release atomic (publishing the CTA's writes, ordered before
     // it by __syncthreads) and polls with acquire loads.  A wait longer than
-    // `limit` ns (or 2^31 polls) sets CDI_ETIMEOUT and adds kBarError to the
-    // counter, which releases every waiter of this and every later barrier
+    // `limit` ns (or 2^31 polls) sets CDI_ETIMEOUT and sets the bit kBarError
+    // of the counter with an atomic OR (idempotent, so CTAs that give up at
+    // the same time cannot carry it out of the word; arrivals never reach
+    // that bit), which releases every waiter of this and every later barrier
     // with false.  Returns false when the launch is ending.
     __device__ bool sync() {
         __shared__ int ok;
@@ -114,7 +116,7 @@ struct GridX {
                     v = ld_acquire(&ctl->bar);
                     if (v < target && (++it > (1L << 31) || globaltimer() - t0 > (unsigned long long)limit)) {
                         atomicCAS(&ctl->st.status, 0, (int)CDI_ETIMEOUT);
-                        atom_add_acq_rel(&ctl->bar, kBarError);
+                        atomicOr(&ctl->bar, kBarError);
                         v = kBarError;
                     }
                 } while (v < target);
@@ -271,7 +273,9 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
             __shared__ float shv;
             ops::coarse_invert_block<LP, float, DIM>(C.g, bc, Asm, reinterpret_cast<float*>(sd + A.sm_fct), &shv);
         }
-        ops::coarse_apply_block<LP, float>((int)C.g.N, A.ainv ? A.ainv : Asm, C.r, C.e);
+        double* cs = sd + A.sm_bb;  // FP64 scratch of the solve: 3 x kMaxCoarse doubles (sm_bb, then sm_fct)
+        ops::coarse_apply_block<LP, float, DIM>(C.g, bc, A.ainv ? A.ainv : Asm, C.r, C.e, cs, cs + kMaxCoarse,
+                                                sd + A.sm_fct);
     }
     // up: in shared memory a separate prolongation pass is cheaper than
     // prolonging the neighbours of every red cell on the fly

@@ -103,7 +103,9 @@ extern "C" cdi_status cdi_mass_noalloc(const double* phi_dev, long long n, doubl
     double* scratch = nullptr;
     {
         // once per device, with that device current: the device address of the
-        // scratch array (in host code its name is only a host-side stand-in)
+        // scratch array (in host code its name is only a host-side stand-in).
+        // The address is kept for the life of the process, so a device reset
+        // (cudaDeviceReset) while the library is loaded is not supported.
         std::lock_guard<std::mutex> lock(g_setup_mu);
         if (!g_scratch[dev]) {
             void* ptr = nullptr;
@@ -117,6 +119,15 @@ extern "C" cdi_status cdi_mass_noalloc(const double* phi_dev, long long n, doubl
             g_scratch[dev] = (double*)ptr;
         }
         scratch = g_scratch[dev];
+    }
+    // an error left by earlier work would otherwise be reported as this call's launch failure
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        char b[160];
+        std::snprintf(b, sizeof b, "cdi_mass_noalloc: a CUDA error from earlier work is pending: %s",
+                      cudaGetErrorString(e));
+        put_err(err, err_len, b);
+        return CDI_ECUDA;
     }
     const int nparts = (int)((n + kChunk - 1) / kChunk);
     cudaStream_t s = (cudaStream_t)cuda_stream;

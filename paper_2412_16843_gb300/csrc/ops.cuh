@@ -1009,11 +1009,17 @@ __device__ __forceinline__ void project_at(const Geom& g, const PhysDev& ph, con
 // diagonal magnitude) / n) is negative definite: A is negative semidefinite
 // with the constants as its null space, and the rank-one term is negative on
 // them.  Its coefficients are fixed during a pressure solve, so the block
-// inverts it once per solve (coarse_invert_block: in-place Gauss-Jordan
-// elimination, which needs no pivoting for a definite matrix) and every
-// V-cycle applies the inverse (coarse_apply_block).  With a right-hand side
-// summing to zero, e = (A + c 1 1^T)^-1 r solves A e = r with sum(e) = 0.
-// FP32 suffices: the result is the coarse correction of an FP32 V-cycle.
+// inverts it once per solve in FP32 (coarse_invert_block: in-place
+// Gauss-Jordan elimination, which needs no pivoting for a definite matrix;
+// the shift c is stored after the n x n inverse) and every V-cycle solves
+// (A + c 1 1^T) e = r in FP64 (coarse_apply_block): e = Ainv r, then two
+// steps of iterative refinement whose residuals r - (A + c 1 1^T) e are
+// formed in FP64 from the level's coefficients, each corrected with the FP32
+// inverse.  The FP32 inverse has a relative error of about 1e-7 cond(A), so
+// two steps bring e to FP64 round-off for the condition numbers of these
+// small levels; an FP64 inverse would cost n^3 FP64 operations on one SM per
+// solve.  With a right-hand side summing to zero, the solution also solves
+// A e = r with sum(e) = 0.
 // ---------------------------------------------------------------------------
 template <class L, typename M, int DIM>
 __device__ void coarse_invert_block(const Geom& g, const M* const* beta, float* A, float* fct, float* shift_s) {
@@ -1057,17 +1063,51 @@ __device__ void coarse_invert_block(const Geom& g, const M* const* beta, float* 
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0) A[n * n] = sh;  // the shift, read by coarse_apply_block
+    __syncthreads();
 }
 
-// e = Ainv r on the coarsest level (Ainv symmetric up to rounding; thread c
-// reads column c, so neighbouring threads read neighbouring words)
-template <class L, typename M>
-__device__ void coarse_apply_block(int n, const float* Ainv, const M* r, M* e) {
+// x[c] += Ainv y on the coarsest level (Ainv symmetric up to rounding; thread
+// c reads column c, so neighbouring threads read neighbouring words)
+__device__ __forceinline__ void coarse_ainv_add(int n, const float* Ainv, const double* y, double* x, bool add) {
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
         float s = 0.f;
-        for (int t = 0; t < n; ++t) s += L::ld(Ainv + t * n + c) * (float)L::ld(r + t);
-        e[c] = (M)s;
+        for (int t = 0; t < n; ++t) s += Ainv[t * n + c] * (float)y[t];
+        x[c] = add ? x[c] + (double)s : (double)s;
     }
+}
+
+// e = (A + c 1 1^T)^-1 r in FP64 (see above); rd, ed, rr: 3 x n doubles of
+// block-shared scratch; beta: the level's face coefficients
+template <class L, typename M, int DIM>
+__device__ void coarse_apply_block(const Geom& g, const M* const* beta, const float* Ainv, const M* r, M* e,
+                                   double* rd, double* ed, double* rr) {
+    const int n = (int)g.N;
+    const double ih2 = g.ih2;
+    const double sh = (double)Ainv[n * n];
+    for (int c = threadIdx.x; c < n; c += blockDim.x) rd[c] = (double)L::ld(r + c);
+    __syncthreads();
+    coarse_ainv_add(n, Ainv, rd, ed, false);
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            double esum = 0.0;
+            for (int t = 0; t < n; ++t) esum += ed[t];
+            const IJK q = decode(g, c);
+            double Ae = 0.0;
+            for (int a = 0; a < DIM; ++a) {
+                const long hi = (a == DIM - 1) ? c + g.NP : idx(g, shift(g, q, a, 1));
+                const double bm = (double)L::ld(beta[a] + c), bp = (double)L::ld(beta[a] + hi);
+                if (bm != 0.0) Ae += bm * (ed[idx(g, shift(g, q, a, -1))] - ed[c]);
+                if (bp != 0.0) Ae += bp * (ed[hi] - ed[c]);
+            }
+            rr[c] = rd[c] - (Ae * ih2 + sh * esum);
+        }
+        __syncthreads();
+        coarse_ainv_add(n, Ainv, rr, ed, true);
+        __syncthreads();
+    }
+    for (int c = threadIdx.x; c < n; c += blockDim.x) e[c] = (M)ed[c];
     __syncthreads();
 }
 

@@ -424,11 +424,25 @@ __device__ __forceinline__ unsigned long long tc_globaltimer() {
     return t;
 }
 // wait (at most about one second) for the phase of the given parity to complete
+// Wait for phase `parity` of an mbarrier.  It gives up only after 1 s of
+// wall time AND 2^20 polls: a context switched out by time slicing does not
+// poll, so a long preemption alone cannot end the wait.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
     const unsigned long long t0 = tc_globaltimer();
+    long polls = 0;
     while (!mbar_try_wait(bar, parity))
-        if (tc_globaltimer() - t0 > 1000000000ull) return false;
+        if (++polls > (1L << 20) && tc_globaltimer() - t0 > 1000000000ull) return false;
     return true;
+}
+// A second wait for a phase whose first wait gave up, bounded by polls only
+// (2^22 polls with a 1 us back-off, about 4 s of running time); true once
+// the phase completed.
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity) {
+    for (long it = 0; it < (1L << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(1000);
+    }
+    return false;
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -482,8 +496,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // co < cout (BF16 out, row stride out_stride); cin and N multiples of 16, N <= 256; ncols: TMEM
 // columns (a power of two >= max(32, 2N)).  With up != NULL the input is the concatenation
 // [nearest upsampling of up (cup channels, on the grid of half the extents), in (cin - cup channels)],
-// gathered while staging instead of being stored.  On a wait that runs out, *err is set and the CTA
-// stops.
+// gathered while staging instead of being stored.  On a wait that runs out, *err is set to 1 and
+// the CTA stops.  Tensor memory is released only once every MMA the CTA committed has been seen
+// complete: a barrier whose wait gave up is waited for again (poll-bounded) before the dealloc;
+// if an MMA is still unconfirmed then, *err is set to 2 (the CTA must still release its columns
+// before it exits, so their contents are not to be trusted by any later kernel of the context).
 __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __restrict__ in, int cin,
                                                         const bf16* __restrict__ up, int cup,
                                                         const bf16* __restrict__ w, int N,
@@ -526,6 +543,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __rest
     const long nsteps = my_tiles * steps_per_tile;
     uint32_t phase[2] = {0u, 0u};
     bool pending[2] = {false, false};
+    bool unconfirmed[2] = {false, false};   // a wait on this barrier gave up (phase uphase[b])
+    uint32_t uphase[2] = {0u, 0u};
 
     auto tile_origin = [&](long k, int& x0, int& y0, int& z0) {
         const long tile = blockIdx.x + k * gridDim.x;
@@ -541,6 +560,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __rest
             if (!mbar_wait_bounded(&mbar[b], phase[b])) {
                 s_abort = 1;
                 atomicExch(err, 1);
+                unconfirmed[b] = true;
+                uphase[b] = phase[b];
             }
             phase[b] ^= 1u;
             pending[b] = false;
@@ -645,9 +666,12 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __rest
             tc_fence_before();
         }
     }
-    // outstanding copies and MMAs (bounded) before TMEM is released
+    // outstanding copies and MMAs (bounded) before TMEM is released; a phase
+    // whose wait gave up must be seen complete before the dealloc
     cp_async_wait_all();
     for (int b = 0; b < 2; ++b) wait_mma(b);
+    for (int b = 0; b < 2; ++b)
+        if (unconfirmed[b] && !mbar_drain(&mbar[b], uphase[b])) atomicMax(err, 2);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
@@ -990,7 +1014,10 @@ cdi_status check_tc(cdi_unet* u) {
         return ufail(u, CDI_ECUDA, "error flag read failed");
     if (e) {
         cudaMemset(u->tc_err, 0, sizeof(int));
-        return ufail(u, CDI_ETIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+        return ufail(u, CDI_ETIMEOUT,
+                     e == 1 ? "a tensor-core convolution timed out waiting for its MMAs"
+                            : "a tensor-core convolution released tensor memory with an MMA still unconfirmed "
+                              "after its waits ran out: treat the device state as unknown");
     }
     return CDI_OK;
 }

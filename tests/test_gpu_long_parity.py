@@ -1,0 +1,118 @@
+"""Long-horizon parity of the CUDA path with the FP64 oracle, and the stated
+error of the FP32-mixed form on a 3D cut of the 256^3 drop workload.
+
+The oracle's states come from tests/golden/oracle_*.npz, written by
+tests/golden/make_oracle_fixtures.py, which calls only the oracle and the
+seeded input generators (the oracle needs about 1.4 s a step at 32^3).  Both
+sides start from the same seeded initial state and use the pressure
+tolerance 1e-13 (parity mode) unless stated otherwise.
+
+FP64 bar: every field within 1e-10 relative of the oracle after 1000 steps
+(max-norm difference over the field's max norm, p zero-mean).
+FP32-mixed: the error bounds stated in each test.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2412_16843_gb300 import cdi, inputs
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+EXEC_MODES = pytest.mark.parametrize("exec_mode", [cdi.EXEC_PERSISTENT, cdi.EXEC_KERNELS],
+                                     ids=["persistent", "kernels"])
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2412_16843_gb300 import build
+    build.build()
+    cdi.load()
+
+
+def fixture(name):
+    return np.load(os.path.join(GOLDEN, "oracle_%s.npz" % name))
+
+
+def workload(name):
+    if name.startswith("drop3d_32_noise"):
+        return inputs.drop_3d(32)
+    if name == "drop3d_32_smooth":
+        return inputs.drop_3d(32, noise=0.0)
+    if name == "couette_128x32":
+        return inputs.couette_2d(128, 32, 1.0)
+    raise KeyError(name)
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def errors(g, ref, step, dim):
+    phi, vel, p = g.get_fields()
+    out = {"phi": np.abs(phi - ref["phi_%d" % step]).max()}
+    for a in range(dim):
+        out["u%d" % a] = rel(vel[a], ref["u%d_%d" % (a, step)])
+    po = ref["p_%d" % step]
+    out["p"] = rel(p - p.mean(), po - po.mean())
+    return out
+
+
+def run_gpu(name, precision, tol, exec_mode, steps):
+    wl = workload(name)
+    ref = fixture(name)
+    g = cdi.from_workload(wl, precision=precision, tol=tol)
+    g.set_exec(exec_mode)
+    m0 = g.mass()
+    # the same initial phase volume (the FP32 form stores phi rounded to FP32)
+    assert abs(m0 - float(ref["mass0"])) <= (1e-13 if precision == cdi.FP64 else 1e-6) * abs(m0)
+    g.step(float(ref["dt"]), steps)
+    return g, wl, ref, m0
+
+
+@EXEC_MODES
+@pytest.mark.parametrize("name", ["couette_128x32", "drop3d_32_smooth", "drop3d_32_noise"])
+def test_fp64_parity_1000_steps(name, exec_mode):
+    """1000 FP64 steps: the 128x32 cut of the two-phase Couette workload
+    (moving walls, slip length dx) and the 32^3 cut of the 3D drop workload
+    (density and viscosity ratio 10), with and without its seeded noise:
+    every field within 1e-10 relative of the oracle, mass conserved to
+    round-off."""
+    g, wl, ref, m0 = run_gpu(name, cdi.FP64, 1e-13, exec_mode, 1000)
+    e = errors(g, ref, 1000, wl.dim)
+    print(name, exec_mode, {k: "%.2e" % v for k, v in e.items()})
+    for k, v in e.items():
+        assert v < 1e-10, (k, v)
+    assert abs(g.mass() - float(ref["mass_1000"])) <= 1e-12 * abs(m0)
+    assert abs(g.mass() - m0) <= 1e-12 * abs(m0)
+
+
+# Stated error of the FP32-mixed form (FP32 state and stencils, FP64
+# reductions, double-float defect correction to 1e-10, FP64 coarsest solve)
+# after 200 steps of the 32^3 drop cut, against the FP64 oracle:
+#   phi:             max |phi_32 - phi_64|                 (absolute; phi in [0, 1])
+#   u, v, w, p:      max |q_32 - q_64| / max |q_64|
+# Bounds (the measured values times about 3):
+FP32_BOUNDS = {
+    # noise-free field: FP32 arithmetic alone
+    "drop3d_32_smooth": {"phi": 3e-5, "u0": 3e-3, "u1": 3e-3, "u2": 3e-3, "p": 3e-3},
+    # noisy field, oracle with the FP32 form's clamp (phi in [1e-6, 1-1e-6],
+    # |grad psi| floored at 1e-6): FP32 arithmetic on the noisy field
+    "drop3d_32_noise_d6": {"phi": 3e-5, "u0": 3e-3, "u1": 3e-3, "u2": 3e-3, "p": 3e-3},
+    # noisy field, oracle with the FP64 clamp 1e-12: arithmetic plus the
+    # difference between the two clamps in the cells the noise drives to 0 or 1
+    "drop3d_32_noise": {"phi": 3e-5, "u0": 3e-3, "u1": 3e-3, "u2": 3e-3, "p": 3e-3},
+}
+
+
+@pytest.mark.parametrize("name", list(FP32_BOUNDS))
+def test_fp32_mixed_error_3d_drop_cut(name):
+    g, wl, ref, m0 = run_gpu(name, cdi.FP32_MIXED, 1e-10, cdi.EXEC_KERNELS, 200)
+    e = errors(g, ref, 200, 3)
+    print(name, "fp32-mixed vs fp64 oracle after 200 steps:", {k: "%.2e" % v for k, v in e.items()})
+    for k, bound in FP32_BOUNDS[name].items():
+        assert e[k] < bound, (k, e[k], bound)
+    assert abs(g.mass() - m0) / m0 < 1e-6

@@ -195,6 +195,43 @@ def test_step_parity_3d_drop(exec_mode):
         assert rel(vel_g[a], vel_o[a]) < 1e-10, a
 
 
+@pytest.mark.parametrize("sweep", [cdi.SWEEP_ONEPASS, cdi.SWEEP_COLOUR], ids=["onepass", "colour"])
+@pytest.mark.parametrize("precision", [cdi.FP64, cdi.FP32_MIXED], ids=["fp64", "fp32_mixed"])
+def test_step_parity_3d_level0_sweeps(precision, sweep):
+    """64x16x16 3D drop (density ratio 10, noise) on the launch-per-kernel path
+    with each level-0 smoother: one-pass red-black sweeps over 64 x 16 tiles
+    marching along z (forced: on a grid this small the automatic choice takes
+    the colour passes), and one launch per colour; 10 steps: FP64 within the
+    FP64 bar of the oracle, FP32-mixed within its FP32-level bounds."""
+    n = (64, 16, 16)
+    h = 1.0 / 16
+    L = tuple(x * h for x in n)
+    phi = inputs.add_noise(inputs.cap_phi_3d(*n, h, 0.3, math.pi / 2, 2.0, 0.5, h), 1e-3, 99)
+    g = cdi.Solver(3, n, L, precision=precision)
+    o = oracle.Oracle(3, n, L)
+    for s in (g, o):
+        s.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, 1.0)
+        s.set_solver(1e-12, 100)
+    g.set_wall(cdi.WALL_BOTH, math.radians(60), h, 0.0)
+    g.set_exec(cdi.EXEC_KERNELS)
+    g.set_level0_sweep(sweep)
+    o.set_wall_slip_length(2, math.radians(60), h, 0.0)
+    if precision == cdi.FP32_MIXED:
+        o.set_regularisation(1e-6, 1e-6)   # the FP32 form's clamp of phi and floor of |grad psi|
+    g.set_state(phi)
+    o.set_state(phi)
+    g.step(5e-5, 10)
+    o.step(5e-5, 10)
+    assert g.last_stats()["resid"] <= 1e-12
+    phi_g, vel_g, p_g = g.get_fields()
+    phi_o, vel_o, p_o = o.get_state()
+    tol_phi, tol_u = (1e-11, 1e-10) if precision == cdi.FP64 else (1e-5, 1e-3)
+    assert rel(phi_g, phi_o) < tol_phi
+    for a in range(3):
+        assert rel(vel_g[a], vel_o[a]) < tol_u, a
+    assert rel(p_g - p_g.mean(), p_o - p_o.mean()) < tol_u
+
+
 @EXEC_MODES
 def test_couette_full_size_512x128_parity(exec_mode):
     """The full 512x128 Couette workload in the launch configuration the bench

@@ -64,6 +64,20 @@ def test_noalloc_mass_matches_cdi_mass_on_two_calls(lib):
     assert abs(got1 - got3) > 1e-3  # the two calls really saw different inputs
 
 
+@pytest.mark.parametrize("n", [5 * 8192 + 1234, 33554432])
+def test_noalloc_mass_ragged_and_largest_sizes(lib, n):
+    """Several blocks with a partial last chunk, and the largest accepted size
+    (every one of the 4096 scratch partials in use, 268 MB of FP64 input),
+    against a float64 sum of the same values on the host."""
+    import torch
+    rng = np.random.default_rng(n)
+    x = rng.uniform(0.0, 1.0, n)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    got = _noalloc_mass(lib, torch.from_numpy(x).cuda(), 0.5, out, torch.cuda.current_stream())
+    ref = 0.5 * math.fsum(x.tolist()) if n < 100000 else 0.5 * float(np.sum(x, dtype=np.float64))
+    assert abs(got - ref) <= TOL * abs(ref)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     import torch
     x = torch.zeros(8, dtype=torch.float64, device="cuda")
