@@ -586,7 +586,7 @@ def forms_report(steps=30):
         solvers.append(sv)
     b = cdi.Batch(solvers)
     dts = np.array([w.dt for w in wls])
-    best, tune_ms = b.autotune(dts, 1)
+    best, tail, tune_ms = b.autotune(dts, 1)
     b.step(dts, 2)
     kb = max(2, min(steps, 5))
     ms_b = _timed_steps(lambda: b.step(dts, 1), kb, flush)
@@ -595,8 +595,9 @@ def forms_report(steps=30):
     out["batched_sweep_512_fp32"] = {
         "value": cells * kb / (ms_b / 1e3) / 1e6, "unit": UNIT, "instances": len(wls), "cells": cells,
         "ms_per_step": ms_b / kb, "looped_single_grid_value": cells / (loop_ms / 1e3) / 1e6,
-        "speedup_vs_looped": (loop_ms) / (ms_b / kb), "autotuned_threads": best,
-        "autotune_ms": [float(x) for x in tune_ms], "mean_vcycles_per_step": float(np.mean(cyc)),
+        "speedup_vs_looped": (loop_ms) / (ms_b / kb), "autotuned_threads": best, "autotuned_tail_bytes": tail,
+        "autotune_ms_budget_by_threads": [[float(x) for x in row] for row in tune_ms],
+        "mean_vcycles_per_step": float(np.mean(cyc)),
         "pressure_tol": PRESSURE_TOL}
     del b, solvers
     torch.cuda.empty_cache()

@@ -282,11 +282,20 @@ cdi_status cdi_batch_step(cdi_batch* b, const double* dt, int nsteps);
 /* Threads per CTA of the batched kernel: 256, 512 (default) or 1024. */
 cdi_status cdi_batch_set_threads(cdi_batch* b, int threads);
 
-/* Autotuner: time trial_steps steps of the whole batch with each CTA size
- * (256, 512, 1024) and keep the fastest; ms_out (3 entries, may be NULL)
- * receives the times.  The trial steps advance the instances. */
+/* Shared-memory budget (bytes, 8 KiB .. the device's opt-in limit - 4 KiB;
+ * default 100 KiB) of one CTA's multigrid tail: every instance's coarse
+ * levels that fit run in shared memory inside the CTA; the larger the budget,
+ * the more levels run there and the fewer CTAs fit on an SM. */
+cdi_status cdi_batch_set_tail_budget(cdi_batch* b, size_t bytes);
+
+/* Autotuner: time trial_steps steps of the whole batch for every pair of CTA
+ * size (256, 512, 1024 threads) and tail budget (32 KiB, 64 KiB, 100 KiB and
+ * the device's opt-in limit less 4 KiB) that launches, and keep the fastest;
+ * ms_out (12 entries, [budget][CTA size], -1 where the pair does not
+ * launch; may be NULL) receives the times.  The trial steps advance the
+ * instances. */
 cdi_status cdi_batch_autotune(cdi_batch* b, const double* dt, int trial_steps,
-                              int* threads_out, double* ms_out);
+                              int* threads_out, size_t* tail_bytes_out, double* ms_out);
 
 /* Outcome of instance i in the last cdi_batch_step: status, largest V-cycle
  * count of one solve, total V-cycles; and the launch's device time (ms). */

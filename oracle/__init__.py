@@ -159,7 +159,7 @@ class Oracle:
     def set_solver(self, tol=1e-10, maxcyc=200, warm=True):
         self.lib.orc_set_solver(self.handle, tol, maxcyc, 1 if warm else 0)
 
-    def set_regularisation(self, delta=1e-12, tau=1e-12):
+    def set_regularisation(self, delta=1e-6, tau=1e-6):
         self.lib.orc_set_regularisation(self.handle, delta, tau)
 
     def project_final_only(self, flag=True):

@@ -34,7 +34,8 @@
 // means of the two adjacent cells; the normal on a face is the mean of the two
 // cell-centre normals; the velocity slip condition is imposed through a ghost
 // value below the wall; every stage value of RK4 and the final value are
-// projected; psi uses phi clamped to [delta, 1-delta].
+// projected; psi uses phi clamped to [delta, 1-delta] (delta = 1e-6, a clamp
+// that FP32 arithmetic also represents, so both precisions share it).
 //
 // In 3D (an extension: the paper is 2D) the in-plane curvature kappa_p is the
 // EB curvature minus the normal curvature along the contact-line direction
@@ -104,7 +105,7 @@ struct Solver {
     double rho1 = 1, rho2 = 1, mu1 = 1, mu2 = 1, sigma = 0, eps = 1, gamma = 0;
     WallParams wall[2];
     int model = M4A;
-    double delta = 1e-12, tau = 1e-12;
+    double delta = 1e-6, tau = 1e-6;  // clamp of phi for psi and phi(1-phi); floor of |grad psi|
     double tol = 1e-10;
     int maxcyc = 200;
     int warm = 1;           // 1: previous pressure as the first guess, 0: zero

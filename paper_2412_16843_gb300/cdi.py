@@ -91,7 +91,8 @@ def load(path: str = LIB_PATH):
         "cdi_batch_bind_workspace": [P, P, S, P],
         "cdi_batch_step": [P, DP, I],
         "cdi_batch_set_threads": [P, I],
-        "cdi_batch_autotune": [P, DP, I, IP, DP],
+        "cdi_batch_autotune": [P, DP, I, IP, ctypes.POINTER(S), DP],
+        "cdi_batch_set_tail_budget": [P, S],
         "cdi_batch_stats": [P, I, IP, IP, IP, ctypes.POINTER(ctypes.c_float)],
         "cdi_unet_create": [ctypes.POINTER(P), I, I, I],
         "cdi_unet_workspace_bytes": [P, ctypes.POINTER(S)],
@@ -368,12 +369,19 @@ class Batch:
     def set_threads(self, threads):
         self._check(self.lib.cdi_batch_set_threads(self.h, threads))
 
+    def set_tail_budget(self, nbytes):
+        self._check(self.lib.cdi_batch_set_tail_budget(self.h, int(nbytes)))
+
     def autotune(self, dts, trial_steps=1):
+        """Returns (threads, tail budget in bytes, times in ms [budget][threads],
+        -1 where a pair does not launch)."""
         d = np.ascontiguousarray(dts, dtype=np.float64)
         best = ctypes.c_int()
-        ms = np.zeros(3)
-        self._check(self.lib.cdi_batch_autotune(self.h, _dp(d), trial_steps, ctypes.byref(best), _dp(ms)))
-        return best.value, ms
+        tail = ctypes.c_size_t()
+        ms = np.zeros(12)
+        self._check(self.lib.cdi_batch_autotune(self.h, _dp(d), trial_steps, ctypes.byref(best), ctypes.byref(tail),
+                                                _dp(ms)))
+        return best.value, tail.value, ms.reshape(4, 3)
 
     def stats(self, i):
         st, mx, tot, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()

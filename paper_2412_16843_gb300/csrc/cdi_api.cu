@@ -673,8 +673,11 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     c->precision = precision;
     // V(1,1) in 2D, where the small grids are bound by the barriers of each sweep; V(2,2) in 3D
     c->npre = c->npost = (dim == 2) ? 1 : 2;
-    c->ph.delta = precision == CDI_FP64 ? 1e-12 : 1e-6;
-    c->ph.tau = precision == CDI_FP64 ? 1e-12 : 1e-6;
+    // one clamp rule for both precisions, representable in FP32 (1 - delta
+    // must differ from 1): phi in [1e-6, 1 - 1e-6] for psi and every phi(1-phi)
+    // factor, |grad psi| floored at 1e-6
+    c->ph.delta = 1e-6;
+    c->ph.tau = 1e-6;
     c->ph.model = M4A;
     for (int s = 0; s < 2; ++s) {
         c->ph.wall[s].costh = 0.0;
@@ -1186,6 +1189,7 @@ struct cdi_batch {
     std::vector<int> lt;           // per instance: first level solved in shared memory
     std::vector<PersistLayout> lay;
     size_t smem = 0;               // dynamic shared memory of the launch
+    size_t tail_budget = 0;        // shared-memory budget of one CTA's multigrid tail
     int threads = 512;
     int grid = 0;
     bool prepared = false;
@@ -1281,6 +1285,18 @@ cdi_status batch_launch(cdi_batch* b, const double* dt, int nsteps, float* ms) {
 
 extern "C" {
 
+// levels of every instance solved in one CTA's shared memory under a budget
+// (bytes a CTA); the launch takes the largest instance's need
+void batch_tail_layout(cdi_batch* b, size_t budget) {
+    b->tail_budget = budget;
+    b->smem = 0;
+    for (int i = 0; i < b->n; ++i) {
+        const size_t sm = pick_tail(b->inst[i], budget, &b->lt[i], &b->lay[i]);
+        b->smem = std::max(b->smem, sm);
+    }
+    b->prepared = false;
+}
+
 cdi_status cdi_batch_create(cdi_batch** out, int n, cdi_ctx* const* instances) {
     if (!out) return bfail(nullptr, CDI_EINVAL, "out is NULL");
     *out = nullptr;
@@ -1320,14 +1336,10 @@ cdi_status cdi_batch_create(cdi_batch** out, int n, cdi_ctx* const* instances) {
         delete b;
         return bfail(nullptr, st, "cannot query the device");
     }
-    const size_t budget = std::min<size_t>(optin > 8192 ? optin - 4096 : 0, 100 * 1024);
     b->lt.resize(n);
     b->lay.resize(n);
     b->stats.assign(n, InstStats{});
-    for (int i = 0; i < n; ++i) {
-        const size_t sm = pick_tail(b->inst[i], budget, &b->lt[i], &b->lay[i]);
-        b->smem = std::max(b->smem, sm);
-    }
+    batch_tail_layout(b, std::min<size_t>(optin > 8192 ? optin - 4096 : 0, 100 * 1024));
     size_t total = 0;
     batch_carve(b, nullptr, &total);
     b->ws_bytes = total;
@@ -1375,34 +1387,57 @@ cdi_status cdi_batch_step(cdi_batch* b, const double* dt, int nsteps) {
                                     : batch_launch<float>(b, dt, nsteps, &b->last_ms);
 }
 
-cdi_status cdi_batch_autotune(cdi_batch* b, const double* dt, int trial_steps, int* threads_out, double* ms_out) {
+cdi_status cdi_batch_set_tail_budget(cdi_batch* b, size_t bytes) {
+    if (!b) return bfail(nullptr, CDI_EINVAL, "null batch");
+    size_t optin = 0;
+    cdi_status st = smem_optin(b->inst[0], &optin);
+    if (st) return bfail(b, st, "cannot query the device");
+    if (bytes < 8192 || bytes + 4096 > optin) return bfail(b, CDI_EINVAL, "tail budget outside [8 KiB, opt-in limit - 4 KiB]");
+    batch_tail_layout(b, bytes);
+    return CDI_OK;
+}
+
+cdi_status cdi_batch_autotune(cdi_batch* b, const double* dt, int trial_steps, int* threads_out,
+                              size_t* tail_bytes_out, double* ms_out) {
     if (!b) return bfail(nullptr, CDI_EINVAL, "null batch");
     if (trial_steps < 1) return bfail(b, CDI_EINVAL, "trial_steps must be >= 1");
+    size_t optin = 0;
+    cdi_status st = smem_optin(b->inst[0], &optin);
+    if (st) return bfail(b, st, "cannot query the device");
     const int cand[3] = {256, 512, 1024};
+    const size_t budgets[4] = {32 * 1024, 64 * 1024, 100 * 1024, optin > 8192 ? optin - 4096 : 0};
     int best = b->threads;
+    size_t best_budget = b->tail_budget;
     float best_ms = 1e30f;
-    for (int k = 0; k < 3; ++k) {
-        cdi_status st = cdi_batch_set_threads(b, cand[k]);
-        if (st) return st;
-        {  // the candidate must fit one CTA per SM with the batch's shared memory
-            int grid = 0;
-            cudaError_t e = b->precision == CDI_FP64 ? batch_prepare<double>(b->dim, cand[k], b->smem, &grid)
-                                                     : batch_prepare<float>(b->dim, cand[k], b->smem, &grid);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                continue;
+    for (int u = 0; u < 4; ++u) {
+        batch_tail_layout(b, budgets[u]);
+        for (int k = 0; k < 3; ++k) {
+            if (ms_out) ms_out[u * 3 + k] = -1.0;
+            st = cdi_batch_set_threads(b, cand[k]);
+            if (st) return st;
+            {  // the candidate must fit one CTA per SM with this shared memory
+                int grid = 0;
+                cudaError_t e = b->precision == CDI_FP64 ? batch_prepare<double>(b->dim, cand[k], b->smem, &grid)
+                                                         : batch_prepare<float>(b->dim, cand[k], b->smem, &grid);
+                if (e != cudaSuccess || grid < 1) {
+                    cudaGetLastError();
+                    continue;
+                }
+            }
+            st = cdi_batch_step(b, dt, trial_steps);
+            if (st) return st;
+            if (ms_out) ms_out[u * 3 + k] = b->last_ms;
+            if (b->last_ms < best_ms) {
+                best_ms = b->last_ms;
+                best = cand[k];
+                best_budget = budgets[u];
             }
         }
-        st = cdi_batch_step(b, dt, trial_steps);
-        if (st) return st;
-        if (ms_out) ms_out[k] = b->last_ms;
-        if (b->last_ms < best_ms) {
-            best_ms = b->last_ms;
-            best = cand[k];
-        }
     }
+    batch_tail_layout(b, best_budget);
     cdi_batch_set_threads(b, best);
     if (threads_out) *threads_out = best;
+    if (tail_bytes_out) *tail_bytes_out = best_budget;
     return CDI_OK;
 }
 

@@ -81,6 +81,75 @@ __global__ void k_mom(Geom g, PhysDev ph, StageFields<T> f) {
     if (c < g.N) ops::mom_at<Ld, T, DIM>(g, ph, f, c);
 }
 
+// 3D cell-centre quantities with the arithmetic of ops::cell_at (the same
+// terms in the same order: derivatives along x, y, z; central inside, the
+// second-order one-sided wall-normal stencils in the first and last rows,
+// Sec. 4): one thread per (x, y) column marching over kCellZ planes, the
+// in-plane neighbour offsets (periodic wraps) formed once.  Blocks of 32 x 8
+// columns; nx a multiple of 32 and ny of 8.
+constexpr int kCellZ = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) k_cell3(Geom g, PhysDev ph, const T* __restrict__ phi,
+                                               const T* __restrict__ psi, T* __restrict__ nh0, T* __restrict__ nh1,
+                                               T* __restrict__ nh2, T* __restrict__ muc) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long NP = g.NP;
+    const long dxm = i == 0 ? nx - 1 : -1, dxp = i == nx - 1 ? -(long)(nx - 1) : 1;
+    const long dym = j == 0 ? (long)(ny - 1) * nx : -(long)nx, dyp = j == ny - 1 ? -(long)(ny - 1) * nx : (long)nx;
+    const T ih = g_ih<T>(g);
+    const T half_ih = T(0.5) * ih, ih2 = ih * ih;
+    const PhysT<T>& Q = phys<T>(ph);
+    const T delta = Q.delta, eps = Q.eps;
+    const long pidx = (long)i + (long)nx * j;
+    const int k0 = blockIdx.z * kCellZ, k1 = min(k0 + kCellZ, nz);
+    for (int k = k0; k < k1; ++k) {
+        const long c = pidx + (long)k * NP;
+        const T s0 = __ldg(psi + c);
+        T gb[3], grad2 = T(0), lap = T(0);
+        {  // x
+            const T sm = __ldg(psi + c + dxm), sp = __ldg(psi + c + dxp);
+            const T d1 = (sp - sm) * half_ih, d2 = (sp - T(2) * s0 + sm) * ih2;
+            gb[0] = d1;
+            grad2 += d1 * d1;
+            lap += d2;
+        }
+        {  // y
+            const T sm = __ldg(psi + c + dym), sp = __ldg(psi + c + dyp);
+            const T d1 = (sp - sm) * half_ih, d2 = (sp - T(2) * s0 + sm) * ih2;
+            gb[1] = d1;
+            grad2 += d1 * d1;
+            lap += d2;
+        }
+        {  // z: the wall axis
+            T d1, d2;
+            if (k == 0) {
+                const T s1 = __ldg(psi + c + NP), s2 = __ldg(psi + c + 2 * NP), s3 = __ldg(psi + c + 3 * NP);
+                d1 = (T(-3) * s0 + T(4) * s1 - s2) * half_ih;
+                d2 = (T(2) * s0 - T(5) * s1 + T(4) * s2 - s3) * ih2;
+            } else if (k == nz - 1) {
+                const T s1 = __ldg(psi + c - NP), s2 = __ldg(psi + c - 2 * NP), s3 = __ldg(psi + c - 3 * NP);
+                d1 = (T(3) * s0 - T(4) * s1 + s2) * half_ih;
+                d2 = (T(2) * s0 - T(5) * s1 + T(4) * s2 - s3) * ih2;
+            } else {
+                const T sm = __ldg(psi + c - NP), sp = __ldg(psi + c + NP);
+                d1 = (sp - sm) * half_ih;
+                d2 = (sp - T(2) * s0 + sm) * ih2;
+            }
+            gb[2] = d1;
+            grad2 += d1 * d1;
+            lap += d2;
+        }
+        T pt = clampv(__ldg(phi + c), delta, T(1) - delta);
+        T P = pt * (T(1) - pt);
+        muc[c] = T(6) * Q.sigma * (P * (T(1) - T(2) * pt) * (T(1) - grad2) / eps - P * lap);
+        const T igm = T(1) / (sqrt(grad2) + Q.tau);
+        nh0[c] = gb[0] * igm;
+        nh1[c] = gb[1] * igm;
+        nh2[c] = gb[2] * igm;
+    }
+}
+
 // 3D momentum right-hand side with the arithmetic of ops::mom_at (the same
 // terms in the same order), one thread per (x, y) column marching over kMomZ
 // planes: the neighbour offsets (periodic wraps in x and y) are formed once
@@ -201,8 +270,14 @@ void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaS
         CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f)));
         CDI_PROF(KC_MOM, s, (k_mom<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f)));
     } else {
-        CDI_PROF(KC_CELL, s,
-                 (k_cell<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi, f.nh[0], f.nh[1], f.nh[2], f.muc)));
+        if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
+            const dim3 grid((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kCellZ - 1) / kCellZ));
+            CDI_PROF(KC_CELL, s,
+                     (k_cell3<T><<<grid, dim3(32, 8), 0, s>>>(g, ph, f.phi, f.psi, f.nh[0], f.nh[1], f.nh[2], f.muc)));
+        } else {
+            CDI_PROF(KC_CELL, s,
+                     (k_cell<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi, f.nh[0], f.nh[1], f.nh[2], f.muc)));
+        }
         CDI_PROF(KC_WALL, s, (k_wall<T, 3><<<wall_blocks(g), kWallThreads, 0, s>>>(
                                  g, ph, f.phi, f.psi, f.u[0], f.u[1], f.wuY, f.wghost, f.wmuw)));
         CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));

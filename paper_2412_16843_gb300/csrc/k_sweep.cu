@@ -23,9 +23,13 @@
 // terms, are those of k_rbgs0 (x-, x+, y-, y+, z-, z+), so the result equals
 // a red pass followed by a black pass.
 //
-// Threads: warps 0..17 cover rows -1..16 of the tile (lane = cell pair (2p,
-// 2p+1), p = 0..31; each pair holds one red and one black cell of a plane);
-// warp 18 updates the red ring cell of each row left or right of the tile.
+// Threads: a thread owns a cell pair (2p, 2p+1) of one tile row (each pair
+// holds one red and one black cell of a plane).  A warp covers 16 pairs of
+// two adjacent rows: the colour of the pair's red cell flips from one row to
+// the next and a staged row is 72 words long, so the two half-warps read
+// even and odd banks, free of conflicts.  Warps 0..15 cover tile rows 0..15
+// (red and black updates), warps 16..17 the ring rows -1 and 16 (red only),
+// warp 18 the red ring cell of each row left or right of the tile.
 #include "ops.cuh"
 
 #include <cmath>
@@ -165,17 +169,26 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
     issue(z0 - 1, -1);
     for (int m = 0; m < kPD; ++m) issue(z0 + m, z0 - 1 + m);
 
-    // this thread's red cell: staged row and pair (the colour within the pair
-    // alternates with the plane); the ring warp's row and side
-    int red_row = -1, red_pc = 0;
-    if (warp < kTY + 2) {
-        red_row = warp;       // tile row warp - 1
-        red_pc = lane + 2;
-    } else if (lane < kTY + 2) {
+    // this thread's pair: red update on rows -1..kTY (warps 0..kTY+1), black
+    // update on rows 0..kTY-1 (warps 2..kTY+1); warp kTY+2: the ring cells
+    const int half = lane >> 4, sub = lane & 15;
+    int red_row = -1, pc = 0;   // staged r row (tile row + 1) and staged pair (tile pair + 2)
+    if (warp < kTY) {           // tile rows 0..kTY-1: red and black updates
+        red_row = 2 * (warp >> 1) + half + 1;
+        pc = 16 * (warp & 1) + sub + 2;
+    } else if (warp < kTY + 2) {  // ring rows -1 and kTY (opposite colours: conflict-free too)
+        red_row = half ? kTY + 1 : 0;
+        pc = 16 * (warp & 1) + sub + 2;
+    } else if (lane < kTY + 2) {  // ring columns
         red_row = lane;
     }
-    // slots of planes k-1, k, k+1 (e / rho) at the current step
+    const bool black_thread = warp < kTY;
+    const int jrel = red_row - 1;  // tile row of the pair
+    // slots of planes k-1, k, k+1 (e / rho) and of r planes k, k+1 at the
+    // current step, and the slots the step's loads fill (e / rho plane k+4, r
+    // plane k+3); global offsets of those planes
     int sm1 = eslot(z0 - 3 + kESlots), s0 = eslot(z0 - 2), sp1 = eslot(z0 - 1);
+    int r0 = rslot(z0 - 2 + kRSlots), rp1 = rslot(z0 - 1);
     for (int k = z0 - 2; k < z1; ++k) {
         cp_async_wait<kPD - 1>();
         __syncthreads();  // e / rho planes <= k+2 and r planes <= k+1 are staged
@@ -187,20 +200,19 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
         const int kr = k + 1;
         if (kr >= 0 && kr < nz && red_row >= 0) {
             const int y = y0 + red_row - 1;
-            int pc, t;
+            int pcr = pc, t;
             if (warp < kTY + 2) {
-                pc = red_pc;
                 t = (y + kr) & 1;
             } else {
                 // the red one of cells x0-1 (pair -1, second cell) and x0+kTX (pair kTP, first cell)
                 const bool left = ((y + kr) & 1) != 0;
-                pc = left ? 1 : kTP + 2;
+                pcr = left ? 1 : kTP + 2;
                 t = left ? 1 : 0;
             }
-            const int fi = (red_row + 1) * kRowF + 2 * pc + t;
+            const int fi = (red_row + 1) * kRowF + 2 * pcr + t;
             const float* E = Es + sp1 * kEPlane;
             const float* H = Rh + sp1 * kEPlane;
-            const float rcen = Rs[rslot(kr) * kRPlane + red_row * kRowF + 2 * pc + t];
+            const float rcen = Rs[rp1 * kRPlane + red_row * kRowF + 2 * pcr + t];
             const float v = cell_update(E, H, kr > 0 ? Es + s0 * kEPlane : nullptr, Rh + s0 * kEPlane,
                                         kr < nz - 1 ? Es + sp2 * kEPlane : nullptr, Rh + sp2 * kEPlane, fi, rcen,
                                         h2);
@@ -208,25 +220,26 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
         }
         __syncthreads();  // the red values of plane k+1 are visible
         // black cells of plane k on the tile, written out with their red partners
-        if (k >= z0 && warp >= 1 && warp <= kTY) {
-            const int jrel = warp - 1;
+        if (k >= z0 && black_thread) {
             const int t = (y0 + jrel + k + 1) & 1;
-            const int fb = (jrel + 2) * kRowF + 2 * (lane + 2);
+            const int fb = (jrel + 2) * kRowF + 2 * pc;
             const float* E = Es + s0 * kEPlane;
             const float* H = Rh + s0 * kEPlane;
-            const float rcen = Rs[rslot(k) * kRPlane + (jrel + 1) * kRowF + 2 * (lane + 2) + t];
+            const float rcen = Rs[r0 * kRPlane + (jrel + 1) * kRowF + 2 * pc + t];
             const float v = cell_update(E, H, k > 0 ? Es + sm1 * kEPlane : nullptr, Rh + sm1 * kEPlane,
                                         k < nz - 1 ? Es + sp1 * kEPlane : nullptr, Rh + sp1 * kEPlane, fb + t, rcen,
                                         h2);
             const float red = E[fb + 1 - t];  // the pair's red value is in place
             const float2 out = t == 0 ? make_float2(v, red) : make_float2(red, v);
-            const long c = (long)k * NP + (long)(x0 + 2 * lane) + (long)nx * (y0 + jrel);
+            const long c = (long)k * NP + (long)(x0 + 2 * (pc - 2)) + (long)nx * (y0 + jrel);
             reinterpret_cast<float2*>(eout)[c >> 1] = out;
             if (MODE == kSweepUpdate) p_add_pair(p + c, out);
         }
         sm1 = s0;
         s0 = sp1;
         sp1 = sp2;
+        r0 = rp1;
+        rp1 = next_slot(rp1, kRSlots);
     }
     cp_async_wait<0>();
 }

@@ -17,9 +17,6 @@ Cases:
   drop3d_32_smooth  the same without the noise; steps 200 and 1000
   couette_128x32    the two-phase Couette workload cut to 128x32 (walls at
                     -/+0.1, slip length dx, Ca 0.05); steps 1000
-  drop3d_32_noise_d6  drop3d_32_noise with phi clamped to [1e-6, 1 - 1e-6]
-                    for psi and |grad psi| floored at 1e-6 (the FP32 form's
-                    clamp); step 200
 """
 from __future__ import annotations
 
@@ -43,7 +40,6 @@ def cases():
         "drop3d_32_noise": (d_noise, inputs.stable_dt(d_noise), (200, 1000), None),
         "drop3d_32_smooth": (d_smooth, inputs.stable_dt(d_smooth), (200, 1000), None),
         "couette_128x32": (c, c.dt, (1000,), None),
-        "drop3d_32_noise_d6": (d_noise, inputs.stable_dt(d_noise), (200,), (1e-6, 1e-6)),
     }
 
 

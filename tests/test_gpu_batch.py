@@ -64,10 +64,65 @@ def test_batch_matches_oracle_fp64():
 
 
 def test_batch_autotune_picks_a_candidate():
+    """The autotuner times every (CTA size, tail budget) pair that launches and
+    keeps the fastest; the tail budget changes the work split between shared
+    memory and global memory but not the arithmetic: a batch stepped with
+    each budget ends where its instances stepped alone end."""
     wls = small_sweep(4, seed=3)
     batched = [cdi.from_workload(w, precision=cdi.FP32_MIXED, tol=1e-8) for w in wls]
     b = cdi.Batch(batched)
-    best, ms = b.autotune(np.array([w.dt for w in wls]), 1)
+    best, tail, ms = b.autotune(np.array([w.dt for w in wls]), 1)
     assert best in (256, 512, 1024)
-    assert np.all(ms[ms > 0] > 0)
+    assert tail >= 32 * 1024
+    assert (ms > 0).sum() >= 6
+    assert ms.min(initial=1e30, where=ms > 0) == pytest.approx(ms[ms > 0].min())
     b.step(np.array([w.dt for w in wls]), 2)
+
+
+@pytest.mark.parametrize("budget", [32 * 1024, 100 * 1024])
+def test_batch_tail_budget_keeps_the_arithmetic(budget):
+    wls = small_sweep(4, seed=5)
+    alone = [cdi.from_workload(w, precision=cdi.FP64, tol=1e-12) for w in wls]
+    batched = [cdi.from_workload(w, precision=cdi.FP64, tol=1e-12) for w in wls]
+    b = cdi.Batch(batched)
+    b.set_tail_budget(budget)
+    b.step(np.array([w.dt for w in wls]), 4)
+    for w, s_a, s_b in zip(wls, alone, batched):
+        s_a.step(w.dt, 4)
+        assert rel(s_b.get_fields()[0], s_a.get_fields()[0]) < 1e-11, w.name
+
+
+def test_timed_sweep_fp32_instances_vs_oracle():
+    """A few instances of the 512-instance sweep that the bench times (FP32-mixed,
+    batched, autotuned launch), 20 steps, against the FP64 oracle: the
+    smallest drop and Couette instances and the largest-density-ratio one
+    within 1e-5 in phi and 1e-3 relative in velocity (the FP32-level bounds
+    of the 2D FP32-mixed form)."""
+    wls = inputs.sweep_2d()
+    pick = sorted(range(len(wls)), key=lambda i: wls[i].cells)
+    drops = [i for i in pick if "drop" in wls[i].name][:2]
+    couettes = [i for i in pick if "couette" in wls[i].name][:2]
+    small = [i for i in pick if wls[i].cells <= 4096]
+    heavy = max(small, key=lambda i: wls[i].rho1 / wls[i].rho2)
+    chosen = sorted(set(drops + couettes + [heavy]))
+    solvers = []
+    for w in wls:
+        sv = cdi.from_workload(w, precision=cdi.FP32_MIXED, tol=1e-10)
+        sv.set_solver(1e-10, 100, cdi.WARM_EXTRAP)
+        sv.set_smoothing(2, 2)
+        solvers.append(sv)
+    b = cdi.Batch(solvers)
+    dts = np.array([w.dt for w in wls])
+    b.autotune(dts, 1)
+    for sv, w in zip(solvers, wls):  # back to the initial state after the autotuner's trial steps
+        sv.set_state(w.phi0)
+    b.step(dts, 20)
+    for i in chosen:
+        w = wls[i]
+        o = oracle.from_workload(w, tol=1e-10)
+        o.step(w.dt, 20)
+        pg, vg, _ = solvers[i].get_fields()
+        po, vo, _ = o.get_state()
+        assert np.abs(pg - po).max() < 1e-5, w.name
+        for a in range(2):
+            assert rel(vg[a], vo[a]) < 1e-3, (w.name, a)

@@ -38,7 +38,7 @@ def fixture(name):
 
 
 def workload(name):
-    if name.startswith("drop3d_32_noise"):
+    if name == "drop3d_32_noise":
         return inputs.drop_3d(32)
     if name == "drop3d_32_smooth":
         return inputs.drop_3d(32, noise=0.0)
@@ -92,19 +92,18 @@ def test_fp64_parity_1000_steps(name, exec_mode):
 
 # Stated error of the FP32-mixed form (FP32 state and stencils, FP64
 # reductions, double-float defect correction to 1e-10, FP64 coarsest solve)
-# after 200 steps of the 32^3 drop cut, against the FP64 oracle:
+# after 200 steps of the 32^3 drop cut, against the FP64 oracle (both with the
+# one clamp rule of phi, [1e-6, 1 - 1e-6]):
 #   phi:             max |phi_32 - phi_64|                 (absolute; phi in [0, 1])
 #   u, v, w, p:      max |q_32 - q_64| / max |q_64|
-# Bounds (the measured values times about 3):
+# Measured on GB300: phi 4.6e-7 / 3.4e-7, velocities 3.5e-6 / 3.6e-6, p 2.2e-6
+# / 1.5e-6 (smooth / noisy field).  Bounds: about 5 x those.  (With the FP64
+# form's earlier clamp 1e-12 against FP32's 1e-6, the noisy field's cells at 0
+# or 1 alone gave phi 3.4e-5 and velocities 6e-3: the clamp, not the FP32
+# arithmetic, set the error, hence the one rule.)
 FP32_BOUNDS = {
-    # noise-free field: FP32 arithmetic alone
-    "drop3d_32_smooth": {"phi": 3e-5, "u0": 3e-3, "u1": 3e-3, "u2": 3e-3, "p": 3e-3},
-    # noisy field, oracle with the FP32 form's clamp (phi in [1e-6, 1-1e-6],
-    # |grad psi| floored at 1e-6): FP32 arithmetic on the noisy field
-    "drop3d_32_noise_d6": {"phi": 3e-5, "u0": 3e-3, "u1": 3e-3, "u2": 3e-3, "p": 3e-3},
-    # noisy field, oracle with the FP64 clamp 1e-12: arithmetic plus the
-    # difference between the two clamps in the cells the noise drives to 0 or 1
-    "drop3d_32_noise": {"phi": 3e-5, "u0": 3e-3, "u1": 3e-3, "u2": 3e-3, "p": 3e-3},
+    "drop3d_32_smooth": {"phi": 2.5e-6, "u0": 2e-5, "u1": 2e-5, "u2": 2e-5, "p": 1.5e-5},
+    "drop3d_32_noise": {"phi": 2.5e-6, "u0": 2e-5, "u1": 2e-5, "u2": 2e-5, "p": 1.5e-5},
 }
 
 

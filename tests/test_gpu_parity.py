@@ -216,8 +216,6 @@ def test_step_parity_3d_level0_sweeps(precision, sweep):
     g.set_exec(cdi.EXEC_KERNELS)
     g.set_level0_sweep(sweep)
     o.set_wall_slip_length(2, math.radians(60), h, 0.0)
-    if precision == cdi.FP32_MIXED:
-        o.set_regularisation(1e-6, 1e-6)   # the FP32 form's clamp of phi and floor of |grad psi|
     g.set_state(phi)
     o.set_state(phi)
     g.step(5e-5, 10)

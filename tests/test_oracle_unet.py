@@ -123,3 +123,38 @@ def test_seeded_initial_parameters_match_the_layer_table():
     # rms(f) = sqrt(12.5); rho = (2, 1) / 2; p / (rms * 2 * 0.25)
     assert np.allclose(x, [[3 / 12.5 ** 0.5, 1.0], [-4 / 12.5 ** 0.5, 0.5]])
     assert np.allclose(t, np.array([1.0, 2.0]) / (12.5 ** 0.5 * 0.5))
+
+
+def test_parity_bounds_catch_a_wrong_tap_or_channel():
+    """The bounds the GPU network tests use (forward 2e-3 relative L2, 1e-2
+    per voxel; gradients 5e-2 relative L2, 1e-1 per entry, per layer) are
+    below what a plausible indexing mistake does to the FP64 network: a
+    mirrored tap (x+1 read as x-1) or two swapped input channels in one layer
+    move the output by more than 10x the forward bound (18x to 600x here),
+    and that layer's weight gradient by more than 1.5x the gradient bound."""
+    rng = np.random.default_rng(5)
+    shape = (8, 8, 8)
+    P = unet.init_params(3)
+    for k in P:
+        if k.endswith(".b"):
+            P[k] = 0.1 * rng.standard_normal(P[k].shape)
+    x = rng.standard_normal(shape + (2,))
+    t = rng.standard_normal(shape + (1,))
+    y, c = unet.forward(P, x)
+    G = unet.backward(P, c, y, t)
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+    tp, tm = 1 * 9 + 1 * 3 + 2, 1 * 9 + 1 * 3 + 0      # taps (0, 0, +1) and (0, 0, -1)
+    for layer, kind in (("e1", "tap"), ("d0", "tap"), ("e0", "channel"), ("d1", "channel")):
+        Pm = {k: v.copy() for k, v in P.items()}
+        w = Pm[layer + ".w"]
+        if kind == "tap":
+            w[[tp, tm]] = w[[tm, tp]]
+        else:
+            w[:, :, [0, 1]] = w[:, :, [1, 0]]
+        ym, cm = unet.forward(Pm, x)
+        Gm = unet.backward(Pm, cm, ym, t)
+        assert rel(ym, y) > 10 * 2e-3, (layer, kind, rel(ym, y))
+        assert rel(Gm[layer + ".w"], G[layer + ".w"]) > 1.5 * 5e-2, (layer, kind)
