@@ -126,12 +126,15 @@ cdi_status cdi_set_wall_velocity(cdi_ctx* ctx, int wall, double Ux, double Uy);
 /* Slip model of Sec. 3 (CDI_MODEL_*); Model 4A (Eq. u_slip_Y) by default. */
 cdi_status cdi_set_model(cdi_ctx* ctx, int model);
 
-/* Copy the phase field from host memory (cell layout above). */
+/* Copy the phase field from host memory (cell layout above).  A value that is
+ * not finite returns CDI_ENAN (checked on the device after the copy; the
+ * field is then undefined). */
 cdi_status cdi_set_phi(cdi_ctx* ctx, const double* phi_host);
 
 /* Copy the face velocities from host memory (face layouts above); w is
  * ignored in 2D.  The wall planes of the wall-normal component are forced to
- * zero (Eq. no-penetration BC). */
+ * zero (Eq. no-penetration BC).  A value that is not finite returns CDI_ENAN
+ * (checked on the device; the velocity is then undefined). */
 cdi_status cdi_set_velocity(cdi_ctx* ctx, const double* u, const double* v,
                             const double* w);
 

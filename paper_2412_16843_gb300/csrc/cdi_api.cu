@@ -191,10 +191,20 @@ __global__ void k_to_double(long n, const T* __restrict__ src, double* __restric
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (double)src[i];
 }
+// dst = src in the field's type; *bad = 1 where a value is not finite (every
+// writer stores the same value)
 template <typename T>
-__global__ void k_from_double(long n, const double* __restrict__ src, T* __restrict__ dst) {
+__global__ void k_from_double(long n, const double* __restrict__ src, T* __restrict__ dst, double* bad) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = (T)src[i];
+    if (i < n) {
+        const double v = src[i];
+        if (!isfinite(v)) *bad = 1.0;
+        dst[i] = (T)v;
+    }
+}
+__global__ void k_check_finite(long n, const double* __restrict__ x, double* bad) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(x[i])) *bad = 1.0;
 }
 __global__ void k_set_gamma(double* p, float* pf, double v) {
     *p = v;
@@ -211,19 +221,31 @@ __global__ void k_zero_wall_planes(long N, long NP, T* __restrict__ w) {
 
 unsigned nblk(long n) { return (unsigned)((n + 255) / 256); }
 
-// copy a host double array into a device field of the context's precision
-cdi_status upload(cdi_ctx* c, void* dst, const double* src, long n) {
+// copy a host double array into a device field of the context's precision;
+// a value that is not finite (found on the device while converting or by a
+// check of the copy) returns CDI_ENAN, leaving the field undefined
+cdi_status upload(cdi_ctx* c, void* dst, const double* src, long n, const char* what) {
+    double* bad = c->mg.scal + S_BADIN;
+    cdi_status st = cuda_check(c, cudaMemsetAsync(bad, 0, sizeof(double), c->stream), "cudaMemsetAsync");
+    if (st) return st;
     if (c->precision == CDI_FP64) {
-        cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream),
-                                   "cudaMemcpyAsync(H2D)");
+        st = cuda_check(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                        "cudaMemcpyAsync(H2D)");
         if (st) return st;
+        k_check_finite<<<nblk(n), 256, 0, c->stream>>>(n, (const double*)dst, bad);
     } else {
-        cdi_status st = cuda_check(c, cudaMemcpyAsync(c->xfer, src, n * sizeof(double), cudaMemcpyHostToDevice,
-                                                      c->stream), "cudaMemcpyAsync(H2D)");
+        st = cuda_check(c, cudaMemcpyAsync(c->xfer, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                        "cudaMemcpyAsync(H2D)");
         if (st) return st;
-        k_from_double<float><<<nblk(n), 256, 0, c->stream>>>(n, c->xfer, (float*)dst);
+        k_from_double<float><<<nblk(n), 256, 0, c->stream>>>(n, c->xfer, (float*)dst, bad);
     }
-    return cuda_check(c, cudaStreamSynchronize(c->stream), "upload");
+    st = cuda_check(c, cudaMemcpyAsync(c->host_scal + S_BADIN, bad, sizeof(double), cudaMemcpyDeviceToHost,
+                                       c->stream), "cudaMemcpyAsync(D2H)");
+    if (st) return st;
+    st = cuda_check(c, cudaStreamSynchronize(c->stream), "upload");
+    if (st) return st;
+    if (c->host_scal[S_BADIN] != 0.0) return fail(c, CDI_ENAN, std::string(what) + " holds a non-finite value");
+    return CDI_OK;
 }
 
 cdi_status download(cdi_ctx* c, double* dst, const void* src, long n) {
@@ -849,10 +871,8 @@ cdi_status cdi_set_phi(cdi_ctx* c, const double* phi) {
     cdi_status st = need_bound(c);
     if (st) return st;
     if (!phi) return fail(c, CDI_EINVAL, "phi is NULL");
-    for (long i = 0; i < c->g.N; ++i)
-        if (!std::isfinite(phi[i])) return fail(c, CDI_ENAN, "phi holds a non-finite value");
     c->hist_steps = 0;
-    return upload(c, c->phi_s, phi, c->g.N);
+    return upload(c, c->phi_s, phi, c->g.N, "phi");
 }
 
 cdi_status cdi_set_velocity(cdi_ctx* c, const double* u, const double* v, const double* w) {
@@ -861,10 +881,7 @@ cdi_status cdi_set_velocity(cdi_ctx* c, const double* u, const double* v, const 
     const double* comps[3] = {u, v, w};
     for (int a = 0; a < c->g.D; ++a) {
         if (!comps[a]) return fail(c, CDI_EINVAL, "velocity component is NULL");
-        const long n = nface(c->g, a);
-        for (long i = 0; i < n; ++i)
-            if (!std::isfinite(comps[a][i])) return fail(c, CDI_ENAN, "velocity holds a non-finite value");
-        st = upload(c, c->u_s[a], comps[a], n);
+        st = upload(c, c->u_s[a], comps[a], nface(c->g, a), "velocity");
         if (st) return st;
     }
     c->hist_steps = 0;

@@ -244,7 +244,7 @@ struct MG {
 
 // scalar slots in MG::scal
 enum { S_MEAN = 0, S_FNORM = 1, S_RNORM = 2, S_MASS = 3, S_UMAX = 4, S_GAMMA = 5,
-       S_THETA = 6, S_WETTED = 7, S_NSCAL = 16 };
+       S_THETA = 6, S_WETTED = 7, S_BADIN = 8 /* nonzero: an uploaded value was not finite */, S_NSCAL = 16 };
 // slots in MG::scalf: the means of f and p as double-floats (FP32-mixed form) and gamma
 enum { SF_FMEAN_HI = 0, SF_FMEAN_LO = 1, SF_GAMMA = 2, SF_PMEAN_HI = 4, SF_PMEAN_LO = 5, SF_NSCAL = 8 };
 

@@ -277,6 +277,117 @@ __global__ void k_resid_restrict0(Geom gf, Geom gc, const float* rho0, const flo
     if (t < gc.N) ops::resid_restrict_rho_at<Ld, DIM>(gf, gc, rho0, e, r, rc, ec, t);
 }
 
+// Level-0 -> level-1 restriction of the residual of 3D grids with the
+// arithmetic of ops::resid_restrict_rho_at (children in the order z, y, x;
+// each child's stencil x, y, z with its coefficients 2 / (rho_c + rho_nb)):
+// one thread per coarse (x, y) column marching over a z chunk, the fine
+// neighbour offsets formed once.  r_c = mean of the children's f - A e,
+// e_c = 0.  Coarse blocks of 32 x 8 columns.
+constexpr int kRestrictZ = 4;
+__global__ void __launch_bounds__(256) k_restrict0_3(Geom gf, Geom gc, const float* __restrict__ rho,
+                                                     const float* __restrict__ e, const float* __restrict__ r,
+                                                     float* __restrict__ rc, float* __restrict__ ec) {
+    const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y;
+    const int nx = gf.n[0], ny = gf.n[1], nz = gf.n[2];
+    const long NP = gf.NP;
+    const float ih2 = gf.ih2f;
+    // offsets of the x and y neighbours of the children 2I + t0, 2J + t1
+    long xm[2], xp[2], ym[2], yp[2];
+    xm[0] = 2 * I == 0 ? nx - 1 : -1;
+    xp[0] = 1;
+    xm[1] = -1;
+    xp[1] = 2 * I + 1 == nx - 1 ? -(long)(nx - 1) : 1;
+    ym[0] = 2 * J == 0 ? (long)(ny - 1) * nx : -(long)nx;
+    yp[0] = nx;
+    ym[1] = -(long)nx;
+    yp[1] = 2 * J + 1 == ny - 1 ? -(long)(ny - 1) * nx : (long)nx;
+    const long cbase = 2L * I + (long)nx * (2L * J);
+    const long tbase = (long)I + (long)gc.n[0] * J;
+    const int K0 = blockIdx.z * kRestrictZ, K1 = min(K0 + kRestrictZ, gc.n[2]);
+    for (int K = K0; K < K1; ++K) {
+        float s = 0.f;
+#pragma unroll
+        for (int t2 = 0; t2 < 2; ++t2)
+#pragma unroll
+            for (int t1 = 0; t1 < 2; ++t1)
+#pragma unroll
+                for (int t0 = 0; t0 < 2; ++t0) {
+                    const int k = 2 * K + t2;
+                    const long c = cbase + t0 + (long)nx * t1 + (long)k * NP;
+                    const float rcen = __ldg(rho + c);
+                    float diag = 0.f, off = 0.f;
+                    {
+                        const long lo = c + xm[t0], hi = c + xp[t0];
+                        const float bm = 1.f * __fdividef(2.f, rcen + __ldg(rho + lo));
+                        const float bp = 1.f * __fdividef(2.f, rcen + __ldg(rho + hi));
+                        diag += (bm + bp) * ih2;
+                        off += (bm * __ldg(e + lo) + bp * __ldg(e + hi)) * ih2;
+                    }
+                    {
+                        const long lo = c + ym[t1], hi = c + yp[t1];
+                        const float bm = 1.f * __fdividef(2.f, rcen + __ldg(rho + lo));
+                        const float bp = 1.f * __fdividef(2.f, rcen + __ldg(rho + hi));
+                        diag += (bm + bp) * ih2;
+                        off += (bm * __ldg(e + lo) + bp * __ldg(e + hi)) * ih2;
+                    }
+                    {
+                        const bool wlo = k == 0, whi = k == nz - 1;
+                        const long lo = wlo ? c : c - NP, hi = whi ? c : c + NP;
+                        const float bm = (wlo ? 0.f : 1.f) * __fdividef(2.f, rcen + __ldg(rho + lo));
+                        const float bp = (whi ? 0.f : 1.f) * __fdividef(2.f, rcen + __ldg(rho + hi));
+                        const float pm = wlo ? 0.f : __ldg(e + lo);
+                        const float pp = whi ? 0.f : __ldg(e + hi);
+                        diag += (bm + bp) * ih2;
+                        off += (bm * pm + bp * pp) * ih2;
+                    }
+                    const float Lp = off - diag * __ldg(e + c);
+                    s += __ldg(r + c) - Lp;
+                }
+        const long t = tbase + (long)K * gc.NP;
+        rc[t] = s * (1.f / 8.f);
+        ec[t] = 0.f;
+    }
+}
+
+// Level-1 -> level-0 prolongation of 3D grids with the arithmetic of
+// ops::prolong_val (trilinear weights 3/4, 1/4; coarse neighbours in the order
+// z, y, x), one thread per fine (x, y) column marching over a z chunk, the
+// coarse column indices formed once: e += P e_c.  Fine blocks of 32 x 8.
+constexpr int kProlongZ = 8;
+__global__ void __launch_bounds__(256) k_prolong0_3(Geom gf, Geom gc, const float* __restrict__ ecoarse,
+                                                    float* __restrict__ e) {
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int ncx = gc.n[0], ncy = gc.n[1], ncz = gc.n[2];
+    int Ix[2], Iy[2];
+    Ix[0] = i >> 1;
+    Ix[1] = (i & 1) ? Ix[0] + 1 : Ix[0] - 1;
+    if (Ix[1] < 0) Ix[1] += ncx;
+    else if (Ix[1] >= ncx) Ix[1] -= ncx;
+    Iy[0] = j >> 1;
+    Iy[1] = (j & 1) ? Iy[0] + 1 : Iy[0] - 1;
+    if (Iy[1] < 0) Iy[1] += ncy;
+    else if (Iy[1] >= ncy) Iy[1] -= ncy;
+    const float w[2] = {0.75f, 0.25f};
+    const long cbase = (long)i + (long)gf.n[0] * j;
+    const int k0 = blockIdx.z * kProlongZ, k1 = min(k0 + kProlongZ, gf.n[2]);
+    for (int k = k0; k < k1; ++k) {
+        int Iz[2];
+        Iz[0] = k >> 1;
+        Iz[1] = min(max((k & 1) ? Iz[0] + 1 : Iz[0] - 1, 0), ncz - 1);
+        float s = 0.f;
+#pragma unroll
+        for (int t2 = 0; t2 < 2; ++t2)
+#pragma unroll
+            for (int t1 = 0; t1 < 2; ++t1)
+#pragma unroll
+                for (int t0 = 0; t0 < 2; ++t0)
+                    s += w[t0] * w[t1] * w[t2] *
+                         __ldg(ecoarse + (long)Ix[t0] + (long)ncx * (Iy[t1] + (long)ncy * Iz[t2]));
+        const long c = cbase + (long)k * gf.NP;
+        e[c] = e[c] + s;
+    }
+}
+
 template <int DIM>
 __global__ void k_resid_restrict(Geom gf, Geom gc, const float* b0, const float* b1, const float* b2, const float* e,
                                  const float* r, float* rc, float* ec) {
@@ -373,6 +484,37 @@ __global__ void k_project(Geom g, PhysDev ph, const T* phi, T* u0, T* u1, T* u2,
     T* us[3] = {u0, u1, u2};
     long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c < g.N) ops::project_at<Ld, T, DIM>(g, ph, phi, us, cdt, p, c);
+}
+
+// 3D projection with the arithmetic of ops::project_at (faces of x, y, z in
+// that order; the wall face of z stays zero): one thread per (x, y) column
+// marching over kProjectZ planes, neighbour offsets formed once.
+constexpr int kProjectZ = 8;
+template <typename T>
+__global__ void __launch_bounds__(256) k_project3(Geom g, PhysDev ph, const T* __restrict__ phi, T* u0, T* u1,
+                                                  T* u2, T cdt, const PT<T>* __restrict__ p) {
+    T* us[3] = {u0, u1, u2};
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long NP = g.NP;
+    const long dm[3] = {i == 0 ? nx - 1 : -1, j == 0 ? (long)(ny - 1) * nx : -(long)nx, -NP};
+    const T ih = g_ih<T>(g), dr = phys<T>(ph).drho, rho2 = phys<T>(ph).rho2;
+    const long pidx = (long)i + (long)nx * j;
+    const int k0 = blockIdx.z * kProjectZ, k1 = min(k0 + kProjectZ, nz);
+    for (int k = k0; k < k1; ++k) {
+        const long c = pidx + (long)k * NP;
+        const T phic = __ldg(phi + c);
+        const PT<T> pc = __ldg(p + c);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a == 2 && k == 0) continue;  // wall face stays zero
+            const long cL = c + dm[a];
+            const T rf = T(0.5) * ((dr * __ldg(phi + cL) + rho2) + (dr * phic + rho2));
+            const T beta = T(1) / rf;
+            const T dpv = ops::p_diff(pc, __ldg(p + cL)) * ih;
+            us[a][c] = us[a][c] - cdt * beta * dpv;
+        }
+    }
 }
 
 template <typename T>
@@ -531,6 +673,32 @@ void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cuda
     ++g_launches;
 }
 
+// level-0 restriction and prolongation: the column-marching 3D kernels where
+// the block shape fits, else one thread per cell
+template <int DIM>
+static void launch_restrict0(const MGLevel& L, MGLevel& C, const float* e, cudaStream_t s) {
+    if (DIM == 3 && C.g.n[0] % 32 == 0 && C.g.n[1] % 8 == 0) {
+        const dim3 grid((unsigned)(C.g.n[0] / 32), (unsigned)(C.g.n[1] / 8),
+                        (unsigned)((C.g.n[2] + kRestrictZ - 1) / kRestrictZ));
+        CDI_PROF(KC_RESTRICT0, s, (k_restrict0_3<<<grid, dim3(32, 8), 0, s>>>(L.g, C.g, L.rho0, e, L.r, C.r, C.e)));
+    } else {
+        CDI_PROF(KC_RESTRICT0, s,
+                 (k_resid_restrict0<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.rho0, e, L.r, C.r, C.e)));
+    }
+    ++g_launches;
+}
+template <int DIM>
+static void launch_prolong0(const MGLevel& L, const MGLevel& C, float* e, cudaStream_t s) {
+    if (DIM == 3 && L.g.n[0] % 32 == 0 && L.g.n[1] % 8 == 0) {
+        const dim3 grid((unsigned)(L.g.n[0] / 32), (unsigned)(L.g.n[1] / 8),
+                        (unsigned)((L.g.n[2] + kProlongZ - 1) / kProlongZ));
+        CDI_PROF(KC_PROLONG0, s, (k_prolong0_3<<<grid, dim3(32, 8), 0, s>>>(L.g, C.g, C.e, e)));
+    } else {
+        CDI_PROF(KC_PROLONG0, s, (k_prolong<DIM><<<blocks_for(L.g.N), kThreads, 0, s>>>(L.g, C.g, C.e, e)));
+    }
+    ++g_launches;
+}
+
 // One V-cycle from level l.  On level 0 (when the single-CTA tail does not
 // take it) the first sweep starts from e = 0 and the last one adds e to p;
 // returns whether p has been updated.
@@ -564,13 +732,9 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
             cur = out;
         }
         MGLevel& C = mg.lv[1];
-        CDI_PROF(KC_RESTRICT0, s,
-                 (k_resid_restrict0<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.rho0, buf[cur], L.r, C.r,
-                                                                                C.e)));
-        ++g_launches;
+        launch_restrict0<DIM>(L, C, buf[cur], s);
         vcycle_rec<T, DIM>(mg, p, 1, npre, npost, s);
-        CDI_PROF(KC_PROLONG0, s, (k_prolong<DIM><<<nb, kThreads, 0, s>>>(L.g, C.g, C.e, buf[cur])));
-        ++g_launches;
+        launch_prolong0<DIM>(L, C, buf[cur], s);
         for (int it = 0; it < npost; ++it) {
             const int out = 1 - cur;
             CDI_PROF(KC_RBGS0, s,
@@ -611,16 +775,18 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
             sweep(col, (l == 0 && it == 0 && col == 0) ? kSweepFromZero : kSweepPlain);
     MGLevel& C = mg.lv[l + 1];
     if (l == 0)
-        CDI_PROF(KC_RESTRICT0, s,
-                 (k_resid_restrict0<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.rho0, L.e, L.r, C.r,
-                                                                                C.e)));
+        launch_restrict0<DIM>(L, C, L.e, s);
     else
         k_resid_restrict<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r,
                                                                      C.r, C.e);
     ++g_launches;
     vcycle_rec<T, DIM>(mg, p, l + 1, npre, npost, s);
-    CDI_PROF(l == 0 ? KC_PROLONG0 : -1, s, (k_prolong<DIM><<<nb, kThreads, 0, s>>>(L.g, C.g, C.e, L.e)));
-    ++g_launches;
+    if (l == 0) {
+        launch_prolong0<DIM>(L, C, L.e, s);
+    } else {
+        k_prolong<DIM><<<nb, kThreads, 0, s>>>(L.g, C.g, C.e, L.e);
+        ++g_launches;
+    }
     for (int it = 0; it < npost; ++it)
         for (int col = 0; col < 2; ++col)
             sweep(col, (l == 0 && it == npost - 1 && col == 1) ? kSweepUpdate : kSweepPlain);
@@ -704,6 +870,9 @@ void launch_project(const Geom& g, const PhysDev& ph, const T* phi, T* const* us
     const PT<T>* pp = reinterpret_cast<const PT<T>*>(p);
     if (g.D == 2)
         k_project<T, 2><<<blocks_for(g.N), kThreads, 0, s>>>(g, ph, phi, us[0], us[1], nullptr, (T)cdt, pp);
+    else if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0)
+        k_project3<T><<<dim3((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kProjectZ - 1) / kProjectZ)),
+                        dim3(32, 8), 0, s>>>(g, ph, phi, us[0], us[1], us[2], (T)cdt, pp);
     else
         k_project<T, 3><<<blocks_for(g.N), kThreads, 0, s>>>(g, ph, phi, us[0], us[1], us[2], (T)cdt, pp);
     prof_after(on, s);

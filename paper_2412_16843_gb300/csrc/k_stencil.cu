@@ -150,6 +150,44 @@ __global__ void __launch_bounds__(256) k_cell3(Geom g, PhysDev ph, const T* __re
     }
 }
 
+// 3D phi right-hand side and mass flux with the arithmetic of ops::phi_rhs_at
+// (faces of axes x, y, z in that order; the low face flux and the high face
+// flux from ops::phi_flux, zero on the walls): one thread per (x, y) column
+// marching over kCellZ planes, neighbour offsets formed once.
+template <typename T>
+__global__ void __launch_bounds__(256) k_phi_rhs3(Geom g, PhysDev ph, StageFields<T> f) {
+    using Ld = ops::LdPlain;
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long NP = g.NP;
+    const long dm[2] = {i == 0 ? nx - 1 : -1, j == 0 ? (long)(ny - 1) * nx : -(long)nx};
+    const long dp[2] = {i == nx - 1 ? -(long)(nx - 1) : 1, j == ny - 1 ? -(long)(ny - 1) * nx : (long)nx};
+    const T ih = g_ih<T>(g);
+    const PhysT<T>& Q = phys<T>(ph);
+    const T eps = Q.eps, delta = Q.delta, drho = Q.drho, rho2 = Q.rho2;
+    const T gamma = stage_gamma(f);
+    const long pidx = (long)i + (long)nx * j;
+    const int k0 = blockIdx.z * kCellZ, k1 = min(k0 + kCellZ, nz);
+    for (int k = k0; k < k1; ++k) {
+        const long c = pidx + (long)k * NP;
+        T div = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T* ua = f.u[a];
+            const T* na = f.nh[a];
+            T Flo = T(0), Fhi = T(0);
+            const T ulo = __ldg(ua + c);
+            const bool wlo = a == 2 && k == 0, whi = a == 2 && k == nz - 1;
+            const long cL = a < 2 ? c + dm[a] : c - NP, cR = a < 2 ? c + dp[a] : c + NP;
+            if (!wlo) Flo = ops::phi_flux<Ld>(f.phi, na, cL, c, ulo, gamma, eps, ih, delta);
+            if (!whi) Fhi = ops::phi_flux<Ld>(f.phi, na, c, cR, __ldg(ua + cR), gamma, eps, ih, delta);
+            div += Fhi - Flo;
+            f.m[a][c] = wlo ? T(0) : drho * Flo + rho2 * ulo;
+        }
+        f.rphi[c] = -div * ih;
+    }
+}
+
 // 3D momentum right-hand side with the arithmetic of ops::mom_at (the same
 // terms in the same order), one thread per (x, y) column marching over kMomZ
 // planes: the neighbour offsets (periodic wraps in x and y) are formed once
@@ -280,7 +318,12 @@ void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaS
         }
         CDI_PROF(KC_WALL, s, (k_wall<T, 3><<<wall_blocks(g), kWallThreads, 0, s>>>(
                                  g, ph, f.phi, f.psi, f.u[0], f.u[1], f.wuY, f.wghost, f.wmuw)));
-        CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));
+        if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
+            const dim3 grid((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kCellZ - 1) / kCellZ));
+            CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs3<T><<<grid, dim3(32, 8), 0, s>>>(g, ph, f)));
+        } else {
+            CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));
+        }
         if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
             const dim3 grid((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kMomZ - 1) / kMomZ));
             CDI_PROF(KC_MOM, s, (k_mom3<T><<<grid, dim3(32, 8), 0, s>>>(g, ph, f)));
