@@ -37,6 +37,8 @@ METRIC = "Mcell-steps/s per full CDI+NS step, learned/batched vs plain, same acc
 UNIT = "Mcell-steps/s"
 WORKLOAD = "drop3d_512x256x256_fp32mixed"
 PRESSURE_TOL = 1e-8
+SMOOTHING_3D = (1, 2)   # V(1,2): the library's 3D default, measured fastest a step
+SMOOTHING_2D = (1, 1)
 
 
 def parse():
@@ -61,32 +63,44 @@ def workload(nx=512):
 # algorithmic bytes per launch of the kernels the roofline can name
 # (unique words each launch must read or write at least once)
 # ---------------------------------------------------------------------------
-def vcycle_words(D):
+def vcycle_words(D, sweeps=4):
     """Words per finest-level cell of one V-cycle (the per-unit figure of the
-    measurement contract): on the finest level 4 smoothing sweeps x 4 words (p
-    read and write, f, phi), the residual 4, the restriction 1 + 2^-D, the
-    prolongation and correction 2 + 2^-D; the whole hierarchy weighs
-    1/(1 - 2^-D) of the finest level (about 31 words in 2D, 27 in 3D)."""
-    fine = 4 * 4 + 4 + (1 + 2.0 ** -D) + (2 + 2.0 ** -D)
+    measurement contract): on the finest level `sweeps` smoothing sweeps x 4
+    words (p read and write, f, phi; the contract's V(2,2) cycle has 4), the
+    residual 4, the restriction 1 + 2^-D, the prolongation and correction
+    2 + 2^-D; the whole hierarchy weighs 1/(1 - 2^-D) of the finest level
+    (with 4 sweeps about 31 words in 2D, 27 in 3D)."""
+    fine = sweeps * 4 + 4 + (1 + 2.0 ** -D) + (2 + 2.0 ** -D)
     return fine / (1 - 2.0 ** -D)
 
 
-def step_bytes(D, N, word, vcycles_per_step):
+def step_bytes(D, N, word, vcycles_per_step, sweeps=4):
     """Algorithmic bytes of one full step, B = W [4 * 5(1+D) + 4 ((D+1) + (2D+1)
     + N_V V_D)] per cell: per RK stage the fused stencil minimum (read the stage
     state and y^n, read+write the accumulator, write the next stage: 5(1+D)
     words), per pressure solve the divergence (D velocity components read, f
-    written: D+1 words), the projection (2D+1) and N_V V-cycles of V_D words;
-    W is the state word size."""
+    written: D+1 words), the projection (2D+1) and N_V V-cycles of V_D words
+    (V_D with the cycle's own number of finest-level sweeps); W is the state
+    word size."""
     nv_per_solve = vcycles_per_step / 4.0
-    words = 4 * 5 * (1 + D) + 4 * ((D + 1) + (2 * D + 1) + nv_per_solve * vcycle_words(D))
+    words = 4 * 5 * (1 + D) + 4 * ((D + 1) + (2 * D + 1) + nv_per_solve * vcycle_words(D, sweeps))
     return N * word * words
 
 
-def algorithmic_bytes(kernel, dim, N, NP, word):
+def onepass_sweep_words(sweeps):
+    """FP32 words a cell of one launch of the 3D one-pass finest-level sweep,
+    averaged over the launches of one V-cycle with `sweeps` sweeps: the first
+    reads rho and r and writes e (3), the plain ones also read the old e (4),
+    the last one also reads and writes the double-float p (4 + 4)."""
+    return (3 + 4 * (sweeps - 2) + 8) / sweeps
+
+
+def algorithmic_bytes(kernel, dim, N, NP, word, sweeps=3):
     D = dim
     words = {
-        "rbgs0": 2.5 * N,  # one colour: rho, the other colour's e, own r, own e written
+        # 3D: one-pass sweeps (both colours a launch); 2D: one colour a launch (rho, the other
+        # colour's e, own r, own e written)
+        "rbgs0": onepass_sweep_words(sweeps) * N if D == 3 else 2.5 * N,
         # double-float residual: p (2 FP32 words), f, the densities the coefficients come from, r written
         "resid": 5 * N,
         "mom": (3 * D + 2) * N + NP,                           # u, m, phi, mu_c in; rhs of every component out
@@ -298,7 +312,7 @@ def kernel_rooflines(s, wl, hbm, steps=2):
         ms, n = s.profile_stop()
         if not n:
             continue
-        nbytes = algorithmic_bytes(kc, wl.dim, wl.cells, wl.n[0] * wl.n[1], 4)
+        nbytes = algorithmic_bytes(kc, wl.dim, wl.cells, wl.n[0] * wl.n[1], 4, sum(SMOOTHING_3D))
         avg = ms / n / 1e3
         out[kc] = {"launches": n, "avg_launch_us": avg * 1e6, "algorithmic_bytes_per_launch": nbytes,
                    "achieved": nbytes / avg / 1e9, "frac": nbytes / avg / 1e9 / hbm,
@@ -321,6 +335,7 @@ def gpu_arm(args, rank, world, local_rank):
     s = cdi.from_workload(wl, precision=cdi.FP32_MIXED, tol=PRESSURE_TOL, max_vcycles=100)
     s.set_exec(cdi.EXEC_KERNELS)
     s.set_solver(PRESSURE_TOL, 100, cdi.WARM_PREV)
+    s.set_smoothing(*SMOOTHING_3D)
     stream = s.stream
 
     s.step(wl.dt, args.warmup)
@@ -378,14 +393,15 @@ def gpu_arm(args, rank, world, local_rank):
         return
     hbm, peak_kind = peaks()
     # the contract's algorithmic bytes of every timed step with its own V-cycle count
-    nbytes = sum(step_bytes(wl.dim, wl.cells, 4, c) for c in cyc)
+    nbytes = sum(step_bytes(wl.dim, wl.cells, 4, c, sum(SMOOTHING_3D)) for c in cyc)
     achieved = nbytes / (ms / 1e3) / 1e9
     per_kernel = kernel_rooflines(s, wl, hbm)
     roof = {"bound": "hbm", "kernel": "step", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic_for("step_wide"), "peak_source": peak_kind,
             "algorithmic_bytes_per_step": nbytes / args.steps, "avg_step_ms": ms / args.steps,
             "what": "one full step (all its launches) timed with CUDA events on the library's stream; "
-                    "bytes from the per-cell formula with each timed step's own V-cycle count",
+                    "bytes from the per-cell formula with each timed step's own V-cycle count and the "
+                    "cycle's %d finest-level sweeps" % sum(SMOOTHING_3D),
             "kernels": per_kernel}
     del s
     torch.cuda.empty_cache()
@@ -405,6 +421,7 @@ def gpu_arm(args, rank, world, local_rank):
                    "pressure_tol": PRESSURE_TOL, "vcycles_per_step": float(np.mean(cyc)),
                    "vcycles_per_step_min_max": [int(min(cyc)), int(max(cyc))],
                    "exec": "kernels", "warm_start": "previous pressure",
+                   "smoothing": "V(%d,%d)" % SMOOTHING_3D,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "not flushed: every field (134 MB) is larger than the 129 MB L2"},
         "clocks": clk,
@@ -564,7 +581,7 @@ def forms_report(steps=30):
         ms = _timed_steps(one, steps, flush)
         kms, kn = s.profile_stop()
         word = 8 if prec == cdi.FP64 else 4
-        nbytes = step_bytes(2, wl.cells, word, cyc / steps)
+        nbytes = step_bytes(2, wl.cells, word, cyc / steps, sum(SMOOTHING_2D))
         ach = nbytes / (kms / max(kn, 1) / 1e3) / 1e9
         out[name] = {"value": wl.cells * steps / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / steps,
                      "pressure_tol": PRESSURE_TOL, "vcycles_per_step": cyc / steps, "exec": "persistent",
@@ -614,7 +631,7 @@ def forms_report(steps=30):
         s.step(wl.dt, 1)
         cyc3.append(s.last_stats()["total_cycles_call"])
     ms3 = _timed_steps(one3, k3, flush)
-    nbytes = sum(step_bytes(3, wl.cells, 4, c) for c in cyc3)
+    nbytes = sum(step_bytes(3, wl.cells, 4, c, sum(SMOOTHING_3D)) for c in cyc3)
     ach = nbytes / (ms3 / 1e3) / 1e9
     out["fp32_mixed_drop3d_256"] = {"value": wl.cells * k3 / (ms3 / 1e3) / 1e6, "unit": UNIT,
                                     "ms_per_step": ms3 / k3, "vcycles_per_step": float(np.mean(cyc3)),

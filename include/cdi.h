@@ -208,7 +208,7 @@ cdi_status cdi_launches_per_step(cdi_ctx* ctx, long* launches);
 cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
 
 /* Red-black Gauss-Seidel sweeps before and after the coarse-grid correction
- * on every multigrid level (each in [1, 4]; default 1 and 1 in 2D, 2 and 2 in
+ * on every multigrid level (each in [1, 4]; default 1 and 1 in 2D, 1 and 2 in
  * 3D: measured fastest per step of a single 2D or 3D grid; in batched
  * execution, where an instance's barriers are CTA barriers, 2 and 2 measured
  * faster on the 2D sweep).  The solve

@@ -308,7 +308,11 @@ cdi_status need_bound(cdi_ctx* c) {
 
 // Multigrid solve of div(beta grad p) = f on level 0 (f already mean-free,
 // its norm in S_FNORM, coefficients set); p holds the first guess.
-size_t pick_tail(const cdi_ctx* c, size_t budget, int* lt_out, PersistLayout* L);
+size_t pick_tail(const cdi_ctx* c, size_t budget, int* lt_out, PersistLayout* L, long max_cells = 1L << 40);
+// launch-per-kernel path: the largest level the single-CTA tail takes.  One CTA
+// sweeping 8192 cells (32 x 16 x 16 on the 512x256x256 grid) took 77 us a
+// V-cycle; such a level runs faster as grid-wide launches.
+constexpr long kTailMaxCells = 2048;
 cdi_status smem_optin(cdi_ctx* c, size_t* bytes);
 
 // Launch-per-kernel path: the coarse levels of every V-cycle that fit in one
@@ -326,7 +330,7 @@ cdi_status kernels_tail_setup(cdi_ctx* c) {
     const size_t budget = optin > 8192 ? optin - 4096 : 0;
     int lt = 0;
     PersistLayout lay{};
-    const size_t sm = pick_tail(c, budget, &lt, &lay);
+    const size_t sm = pick_tail(c, budget, &lt, &lay, kTailMaxCells);
     c->mg.tail_args = nullptr;
     if (sm <= budget) {
         InstArgs<float> A{};
@@ -526,11 +530,11 @@ cdi_status step_once(cdi_ctx* c, double dt) {
 
 // First multigrid level that one CTA solves in shared memory (the largest
 // FP32 tail that fits the budget) and its layout.
-size_t pick_tail(const cdi_ctx* c, size_t budget, int* lt_out, PersistLayout* L) {
+size_t pick_tail(const cdi_ctx* c, size_t budget, int* lt_out, PersistLayout* L, long max_cells) {
     int lt = c->mg.nlev - 1;
     for (int l = 0; l < c->mg.nlev; ++l) {
         PersistLayout t{};
-        if (persist_tail_layout(c->g, c->mg, l, t) <= budget) {
+        if (c->mg.lv[l].g.N <= max_cells && persist_tail_layout(c->g, c->mg, l, t) <= budget) {
             lt = l;
             break;
         }
@@ -694,7 +698,9 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     for (int a = 0; a < 3; ++a) c->L[a] = L[a];
     c->precision = precision;
     // V(1,1) in 2D, where the small grids are bound by the barriers of each sweep; V(2,2) in 3D
-    c->npre = c->npost = (dim == 2) ? 1 : 2;
+    // measured fastest a step: V(1,1) on single 2D grids, V(1,2) on 3D grids
+    c->npre = 1;
+    c->npost = (dim == 2) ? 1 : 2;
     // one clamp rule for both precisions, representable in FP32 (1 - delta
     // must differ from 1): phi in [1e-6, 1 - 1e-6] for psi and every phi(1-phi)
     // factor, |grad psi| floored at 1e-6

@@ -32,5 +32,16 @@ def test_step_bytes_scale_with_cells_and_vcycles():
 
 
 def test_level0_sweep_bytes():
-    # one colour pass: rho N, the other colour's e N/2, own r N/2, own e written N/2, FP32
-    assert bench.algorithmic_bytes("rbgs0", 3, 1000, 100, 8) == pytest.approx(2.5 * 1000 * 4)
+    # 2D, one colour pass: rho N, the other colour's e N/2, own r N/2, own e written N/2, FP32
+    assert bench.algorithmic_bytes("rbgs0", 2, 1000, 100, 8) == pytest.approx(2.5 * 1000 * 4)
+    # 3D one-pass sweeps of a V(1,2) cycle: from zero 3 words, plain 4, with the p update 8
+    assert bench.algorithmic_bytes("rbgs0", 3, 1000, 100, 8, 3) == pytest.approx(5 * 1000 * 4)
+    assert bench.onepass_sweep_words(4) == pytest.approx((3 + 4 + 4 + 8) / 4)
+
+
+def test_vcycle_words_with_the_cycles_own_sweeps():
+    # V(1,2): 3 sweeps of 4 words, residual 4, restriction 1 + 1/8, prolongation 2 + 1/8 in 3D
+    assert bench.vcycle_words(3, 3) == pytest.approx((12 + 4 + 1.125 + 2.125) / 0.875)
+    # one fewer sweep removes 4 words on the finest level, 4 / (1 - 2^-D) over the hierarchy
+    assert bench.vcycle_words(3, 4) - bench.vcycle_words(3, 3) == pytest.approx(4 / 0.875)
+    assert bench.step_bytes(3, 10, 4, 20, 3) < bench.step_bytes(3, 10, 4, 20, 4)
