@@ -222,11 +222,16 @@ cdi_status cdi_set_smoothing(cdi_ctx* ctx, int npre, int npost);
  * red-black Gauss-Seidel sweep as one launch that marches along z over
  * 64 x 16 tiles with planes staged in shared memory, reading the correction
  * from one buffer and writing it to another (both colours in one pass over
- * memory; needs nx a multiple of 64 and ny of 16); CDI_SWEEP_COLOUR runs
- * one launch per colour; CDI_SWEEP_AUTO (default) takes the one-pass sweep
- * where the grid has enough tiles to fill the GPU.  Both compute the same
- * red-then-black update (each cell's terms in the same order). */
-enum { CDI_SWEEP_AUTO = 0, CDI_SWEEP_ONEPASS = 1, CDI_SWEEP_COLOUR = 2 };
+ * memory; needs nx a multiple of 64 and ny of 16); tiles whose halo lies
+ * inside the grid stage each plane with TMA copies, the tiles on the periodic
+ * seams with 16-byte cp.async copies; CDI_SWEEP_ONEPASS_CPASYNC is the same
+ * sweep with cp.async staging on every tile; CDI_SWEEP_COLOUR runs one
+ * launch per colour; CDI_SWEEP_AUTO (default) takes the one-pass sweep where
+ * the grid has enough tiles to fill the GPU.  All compute the same
+ * red-then-black update (each cell's terms in the same order).  A staged
+ * copy that does not complete within its bounded wait (1 s) makes cdi_step
+ * return CDI_ETIMEOUT. */
+enum { CDI_SWEEP_AUTO = 0, CDI_SWEEP_ONEPASS = 1, CDI_SWEEP_COLOUR = 2, CDI_SWEEP_ONEPASS_CPASYNC = 3 };
 cdi_status cdi_set_level0_sweep(cdi_ctx* ctx, int mode);
 
 /* Longest wait (nanoseconds, 0 .. 6e10; default 2e9) of a grid barrier in the

@@ -24,7 +24,7 @@ FP64, FP32_MIXED = 0, 1
 WALL_LO, WALL_HI, WALL_BOTH = 0, 1, 2
 WARM_PREV, WARM_ZERO, WARM_EXTRAP, WARM_UNET = 0, 1, 2, 3
 EXEC_PERSISTENT, EXEC_KERNELS, EXEC_AUTO = 0, 1, 2
-SWEEP_AUTO, SWEEP_ONEPASS, SWEEP_COLOUR = 0, 1, 2
+SWEEP_AUTO, SWEEP_ONEPASS, SWEEP_COLOUR, SWEEP_ONEPASS_CPASYNC = 0, 1, 2, 3
 MODELS = {"1A": 0, "1B": 1, "2A": 2, "2B": 3, "3A": 4, "3B": 5, "4A": 6, "4B": 7}
 
 _lib = None

@@ -72,6 +72,7 @@ struct cdi_ctx {
     bool persist_ready = false;
     void* tail_dev = nullptr;  // launch-per-kernel path: descriptor of the V-cycle's shared-memory tail
     bool tail_ready = false;
+    SweepMaps smaps{};         // tensor maps of the one-pass sweep (encoded with the tail)
     // launch-per-kernel path: one V-cycle plus its residual norm as a CUDA graph per form
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
@@ -323,9 +324,12 @@ cdi_status kernels_tail_setup(cdi_ctx* c) {
     size_t optin = 0;
     cdi_status st = smem_optin(c, &optin);
     if (st) return st;
+    c->mg.maps = nullptr;
     if (c->mg.lv[0].e2) {
         st = cuda_check(c, sweep0_prepare(), "one-pass sweep setup");
         if (st) return st;
+        sweep0_encode_maps(c->mg.lv[0], &c->smaps);
+        if (c->smaps.ok) c->mg.maps = &c->smaps;
     }
     const size_t budget = optin > 8192 ? optin - 4096 : 0;
     int lt = 0;
@@ -422,6 +426,10 @@ cdi_status mg_solve(cdi_ctx* c) {
         vcycle_and_residual<T>(c);
         st = read_scalars(c);
         if (st) return st;
+        if (c->host_scal[S_TMAERR] != 0.0) {
+            cudaMemsetAsync(mg.scal + S_TMAERR, 0, sizeof(double), s);
+            return fail(c, CDI_ETIMEOUT, "one-pass sweep: a staged copy did not complete within its bounded wait");
+        }
         rn = c->host_scal[S_RNORM];
         ++cyc;
         if (!std::isfinite(rn)) return fail(c, CDI_ENAN, "non-finite pressure residual");
@@ -981,8 +989,11 @@ cdi_status cdi_set_smoothing(cdi_ctx* c, int npre, int npost) {
 
 cdi_status cdi_set_level0_sweep(cdi_ctx* c, int mode) {
     if (!c) return fail(nullptr, CDI_EINVAL, "null context");
-    if (mode != CDI_SWEEP_AUTO && mode != CDI_SWEEP_ONEPASS && mode != CDI_SWEEP_COLOUR)
-        return fail(c, CDI_EINVAL, "sweep mode must be CDI_SWEEP_AUTO, CDI_SWEEP_ONEPASS or CDI_SWEEP_COLOUR");
+    if (mode != CDI_SWEEP_AUTO && mode != CDI_SWEEP_ONEPASS && mode != CDI_SWEEP_COLOUR &&
+        mode != CDI_SWEEP_ONEPASS_CPASYNC)
+        return fail(c, CDI_EINVAL,
+                    "sweep mode must be CDI_SWEEP_AUTO, CDI_SWEEP_ONEPASS, CDI_SWEEP_COLOUR or "
+                    "CDI_SWEEP_ONEPASS_CPASYNC");
     c->mg.sweep_mode = mode;
     // the V-cycle graphs hold the launches of the previous choice
     for (int k = 0; k < 2; ++k)

@@ -9,6 +9,7 @@
 // is entry c of every component.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -238,13 +239,26 @@ struct MG {
     int tail_lt;
     size_t tail_smem;
     // launch-per-kernel path, 3D level 0: 0 one-pass sweeps where the grid
-    // fills the GPU, 1 one-pass sweeps wherever the tile shape fits, 2 colour passes
+    // fills the GPU, 1 one-pass sweeps wherever the tile shape fits, 2 colour
+    // passes, 3 one-pass sweeps staged by cp.async only
     int sweep_mode;
+    // tensor maps of the one-pass sweep's level-0 arrays (host memory; null
+    // or not encoded: cp.async staging)
+    const struct SweepMaps* maps;
+};
+
+// TMA tensor maps of the level-0 arrays the one-pass 3D sweep stages: cell
+// densities, both correction buffers and the residual, each an (nx, ny, nz)
+// FP32 array, box of 72 cells x 20 rows (18 for r) of one z plane
+struct SweepMaps {
+    CUtensorMap rho, e, e2, r;
+    bool ok;
 };
 
 // scalar slots in MG::scal
 enum { S_MEAN = 0, S_FNORM = 1, S_RNORM = 2, S_MASS = 3, S_UMAX = 4, S_GAMMA = 5,
-       S_THETA = 6, S_WETTED = 7, S_BADIN = 8 /* nonzero: an uploaded value was not finite */, S_NSCAL = 16 };
+       S_THETA = 6, S_WETTED = 7, S_BADIN = 8 /* nonzero: an uploaded value was not finite */,
+       S_TMAERR = 9 /* nonzero: a bounded wait for a staged copy ran out */, S_NSCAL = 16 };
 // slots in MG::scalf: the means of f and p as double-floats (FP32-mixed form) and gamma
 enum { SF_FMEAN_HI = 0, SF_FMEAN_LO = 1, SF_GAMMA = 2, SF_PMEAN_HI = 4, SF_PMEAN_LO = 5, SF_NSCAL = 8 };
 
@@ -288,9 +302,10 @@ enum SweepMode { kSweepPlain = 0, kSweepFromZero = 1, kSweepUpdate = 2 };
 bool sweep0_supported(const Geom& g);  // the tile shape fits the grid
 bool sweep0_auto(const Geom& g);       // it fits and the grid fills the GPU
 cudaError_t sweep0_prepare();
+void sweep0_encode_maps(const MGLevel& L0, SweepMaps* maps);  // maps->ok false if TMA is unavailable
 template <typename T>
-void launch_sweep0(const Geom& g, const float* rho, const float* ein, float* eout, const float* r, int mode,
-                   PT<T>* p, cudaStream_t s);
+void launch_sweep0(const MGLevel& L0, const SweepMaps* maps, const float* ein, float* eout, int mode, PT<T>* p,
+                   double* err, cudaStream_t s);
 // the single-CTA shared-memory tail of a V-cycle as its own launch (k_persist.cu)
 cudaError_t tail_prepare(int dim, size_t smem);
 cudaError_t launch_tail(const void* inst_args, int dim, size_t smem, cudaStream_t s);

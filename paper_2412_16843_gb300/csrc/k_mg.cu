@@ -718,16 +718,19 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
     const unsigned nb = blocks_for(L.g.N);
     const unsigned nbh = blocks_for(L.g.N / 2);
     const int kc_rbgs = (l == 0) ? KC_RBGS0 : KC_RBGS;
-    if (DIM == 3 && l == 0 && L.e2 && (mg.sweep_mode == 1 || (mg.sweep_mode == 0 && sweep0_auto(L.g)))) {
+    if (DIM == 3 && l == 0 && L.e2 &&
+        (mg.sweep_mode == 1 || mg.sweep_mode == 3 || (mg.sweep_mode == 0 && sweep0_auto(L.g)))) {
         // one-pass sweeps (k_sweep.cu), alternating between the two correction
         // buffers: the first starts from e = 0, the last adds e to p
         float* buf[2] = {L.e, L.e2};
+        const SweepMaps* maps = mg.sweep_mode == 3 ? nullptr : mg.maps;
+        double* err = mg.scal + S_TMAERR;
         int cur = -1;
         for (int it = 0; it < npre; ++it) {
             const int out = cur == 0 ? 1 : 0;
             CDI_PROF(KC_RBGS0, s,
-                     launch_sweep0<T>(L.g, L.rho0, cur < 0 ? nullptr : buf[cur], buf[out], L.r,
-                                      cur < 0 ? kSweepFromZero : kSweepPlain, p, s));
+                     launch_sweep0<T>(L, maps, cur < 0 ? nullptr : buf[cur], buf[out],
+                                      cur < 0 ? kSweepFromZero : kSweepPlain, p, err, s));
             ++g_launches;
             cur = out;
         }
@@ -738,8 +741,8 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
         for (int it = 0; it < npost; ++it) {
             const int out = 1 - cur;
             CDI_PROF(KC_RBGS0, s,
-                     launch_sweep0<T>(L.g, L.rho0, buf[cur], buf[out], L.r,
-                                      it == npost - 1 ? kSweepUpdate : kSweepPlain, p, s));
+                     launch_sweep0<T>(L, maps, buf[cur], buf[out], it == npost - 1 ? kSweepUpdate : kSweepPlain,
+                                      p, err, s));
             ++g_launches;
             cur = out;
         }

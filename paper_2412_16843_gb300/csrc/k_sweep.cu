@@ -23,6 +23,14 @@
 // terms, are those of k_rbgs0 (x-, x+, y-, y+, z-, z+), so the result equals
 // a red pass followed by a black pass.
 //
+// Staging.  Tiles whose halo lies inside the grid (every tile but those on
+// the periodic seams of x and y) load each staged plane with one TMA copy per
+// array (cp.async.bulk.tensor of a 72 x 20 box of rho and the old e, a 72 x 18
+// box of r, issued by one thread and completed on the plane's mbarrier, every
+// wait bounded); the box lands in shared memory in exactly the layout below,
+// so both stagings feed the same arithmetic.  Seam tiles, whose halo wraps
+// around the grid, keep the per-thread 16-byte cp.async copies.
+//
 // Threads: a thread owns a cell pair (2p, 2p+1) of one tile row (each pair
 // holds one red and one black cell of a plane).  A warp covers 16 pairs of
 // two adjacent rows: the colour of the pair's red cell flips from one row to
@@ -31,6 +39,9 @@
 // (red and black updates), warps 16..17 the ring rows -1 and 16 (red only),
 // warp 18 the red ring cell of each row left or right of the tile.
 #include "ops.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 
@@ -47,12 +58,20 @@ constexpr int kRR = kTY + 2;                       // staged r rows: -1..kTY
 constexpr int kEPlane = 2 * kEP * kER;             // floats per staged e or rho plane
 constexpr int kRPlane = 2 * kEP * kRR;
 constexpr int kRowF = 2 * kEP;                     // floats per staged row
-constexpr int kESlots = 6, kRSlots = 4;            // ring buffers (planes k-1..k+2 in use, two in flight)
+// ring buffers: e / rho planes k-1..k+2 in use and two in flight; r planes k,
+// k+1 in use and two in flight.  Both rings have six slots, so the z loop
+// unrolls by six and every slot index is a compile-time constant.
+constexpr int kESlots = 6, kRSlots = 6;
 constexpr int kPD = 2;                             // planes loaded ahead of use
 constexpr int kSweepWarps = kTY + 3;               // 19
 constexpr int kSweepThreads = kSweepWarps * 32;    // 608
-constexpr size_t kSweepSmem = (size_t)(2 * kESlots * kEPlane + kRSlots * kRPlane) * sizeof(float);
+// an r slot padded to a multiple of 128 bytes (TMA destinations are 128-byte aligned)
+constexpr int kRSlotF = (kRPlane * 4 + 127) / 128 * 32;
+constexpr int kSlotsF = 2 * kESlots * kEPlane + kRSlots * kRSlotF;   // floats of the staged planes
+constexpr size_t kSweepSmem = (size_t)kSlotsF * sizeof(float) + kESlots * sizeof(unsigned long long);
+constexpr unsigned kEBoxBytes = kEPlane * 4, kRBoxBytes = kRPlane * 4;   // one TMA box of e / rho, of r
 static_assert(kEQ * kER <= kSweepThreads && kEQ * kRR <= kSweepThreads, "one staged quad per thread");
+static_assert(kEPlane * 4 % 128 == 0 && kRSlotF * 4 % 128 == 0, "slots start on 128-byte boundaries");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -62,28 +81,78 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Gauss-Seidel value of the staged cell at float index fi of plane (E, H)
-// (old or new e, rho), with the planes below / above (null through a wall)
-// and the cell's r: e = (sum_nb b e_nb - r h^2) / sum_nb b, b = 2 / (rho_c +
-// rho_nb), terms in the order x-, x+, y-, y+, z-, z+
-__device__ __forceinline__ float cell_update(const float* E, const float* H, const float* Em, const float* Hm,
-                                             const float* Ep, const float* Hp, int fi, float rcen, float h2) {
-    const float rc = H[fi];
-    const float b0 = __fdividef(2.f, rc + H[fi - 1]), b1 = __fdividef(2.f, rc + H[fi + 1]);
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+// the issuing thread's arrival; the phase completes once `bytes` have landed
+__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes) {
+    if (bytes)
+        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                     "r"(bytes)
+                     : "memory");
+    else
+        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for the phase of the given parity; gives up (false) only after 2^20
+// polls and one second
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (long polls = 0;; ++polls) {
+        if (mbar_try(bar, parity)) return true;
+        if (polls > (1L << 20) && globaltimer() - t0 > 1000000000ull) return false;
+    }
+}
+// one z plane (box 72 x rows x 1) of a 3D FP32 tensor into shared memory, completed on mbarrier bar
+__device__ __forceinline__ void tma_plane(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+// order this thread's generic shared-memory writes before later TMA writes to the same bytes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// Gauss-Seidel value of the staged cell at float index fi of the e plane E
+// (old or new e; its rho plane lies kESlots e planes further on), with the
+// planes below / above DM / DP floats away (taken when lo / hi: not through a
+// wall) and the cell's r: e = (sum_nb b e_nb - r h^2) / sum_nb b, b = 2 /
+// (rho_c + rho_nb), terms in the order x-, x+, y-, y+, z-, z+
+template <int DM, int DP>
+__device__ __forceinline__ float cell_update(const float* E, int fi, bool lo, bool hi, float rcen, float h2) {
+    constexpr int HO = kESlots * kEPlane;
+    const float rc = E[HO + fi];
+    const float b0 = __fdividef(2.f, rc + E[HO + fi - 1]), b1 = __fdividef(2.f, rc + E[HO + fi + 1]);
     float bsum = b0 + b1;
     float off = b0 * E[fi - 1] + b1 * E[fi + 1];
-    const float b2 = __fdividef(2.f, rc + H[fi - kRowF]), b3 = __fdividef(2.f, rc + H[fi + kRowF]);
+    const float b2 = __fdividef(2.f, rc + E[HO + fi - kRowF]), b3 = __fdividef(2.f, rc + E[HO + fi + kRowF]);
     bsum += b2 + b3;
     off += b2 * E[fi - kRowF] + b3 * E[fi + kRowF];
-    if (Em) {
-        const float b = __fdividef(2.f, rc + Hm[fi]);
+    if (lo) {
+        const float b = __fdividef(2.f, rc + E[HO + DM + fi]);
         bsum += b;
-        off += b * Em[fi];
+        off += b * E[DM + fi];
     }
-    if (Ep) {
-        const float b = __fdividef(2.f, rc + Hp[fi]);
+    if (hi) {
+        const float b = __fdividef(2.f, rc + E[HO + DP + fi]);
         bsum += b;
-        off += b * Ep[fi];
+        off += b * E[DP + fi];
     }
     return __fdividef(off - rcen * h2, bsum);
 }
@@ -101,26 +170,38 @@ __device__ __forceinline__ void p_add_pair(float2* p, float2 e) {
     *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
 
-__device__ __forceinline__ int next_slot(int s, int n) { return s + 1 == n ? 0 : s + 1; }
+template <int V>
+struct IC {
+    static constexpr int value = V;
+};
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kSweepThreads, 2)
     k_sweep0(Geom g, const float* __restrict__ rho, const float* __restrict__ ein, float* __restrict__ eout,
-             const float* __restrict__ r, float h2, PT<T>* __restrict__ p, int zchunk) {
-    extern __shared__ float smf[];
+             const float* __restrict__ r, float h2, PT<T>* __restrict__ p, int zchunk,
+             const __grid_constant__ CUtensorMap tm_rho, const __grid_constant__ CUtensorMap tm_e,
+             const __grid_constant__ CUtensorMap tm_r, int use_tma, double* __restrict__ err) {
+    extern __shared__ __align__(128) float smf[];
     float* Es = smf;                                 // [kESlots][kER][kEP][2] old e, then new red values
     float* Rh = Es + kESlots * kEPlane;              // [kESlots][kER][kEP][2] rho
-    float* Rs = Rh + kESlots * kEPlane;              // [kRSlots][kRR][kEP][2] r
+    float* Rs = Rh + kESlots * kEPlane;              // [kRSlots][kRR][kEP][2] r (slots kRSlotF floats apart)
+    const unsigned bar0 = smem_u32(smf + kSlotsF);   // [kESlots] mbarriers, one per e / rho slot
     const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
     const long NP = g.NP;
     const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(z0 + zchunk, nz);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // ring-buffer slots: plane z sits in slot (z - (z0 - 2)) mod kESlots (e, rho)
-    // and (z - (z0 - 2)) mod kRSlots (r)
-    auto eslot = [&](int z) { return (z - z0 + 2) % kESlots; };
-    auto rslot = [&](int z) { return (z - z0 + 2) % kRSlots; };
+    // TMA staging: the tile's halo boxes lie inside the grid (no periodic wrap)
+    const bool tma = use_tma && x0 >= 4 && x0 + kTX + 4 <= nx && y0 >= 2 && y0 + kTY + 2 <= ny &&
+                     (smem_u32(smf) & 127u) == 0;
+    if (tma && tid == 0) {
+        for (int i = 0; i < kESlots; ++i) mbar_init(bar0 + 8u * i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        fence_proxy_async();
+    }
+    __syncthreads();
+    bool timed_out = false;
 
     // The staging pattern of every plane is the same: thread tid copies at most
     // one quad (4 cells, 16 bytes) of the e / rho grid (rows -2..kTY+1, pairs
@@ -147,30 +228,48 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
         r_off = quad_off(q, row - 1);
         r_sm = row * kRowF + 4 * q;
     }
-    // stage e / rho plane z and r plane zr (planes outside the wall-bounded
-    // domain, or beyond what this chunk reads, are skipped); one commit group
-    // per call, possibly empty
-    auto issue = [&](int z, int zr) {
-        if (has_e && z >= 0 && z < nz && z <= z1 + 1) {
-            const int sl = eslot(z);
-            const long o = (long)z * NP + e_off;
-            cp_async16(Rh + sl * kEPlane + e_sm, rho + o);
-            if (MODE == kSweepFromZero)
-                *reinterpret_cast<float4*>(Es + sl * kEPlane + e_sm) = make_float4(0.f, 0.f, 0.f, 0.f);
-            else
-                cp_async16(Es + sl * kEPlane + e_sm, ein + o);
+    // Stage e / rho plane z into e slot es and r plane zr into r slot rs
+    // (planes outside the wall-bounded domain, or beyond what this chunk
+    // reads, are skipped).  Plane z sits in slot (z - z0 + 2) mod 6, and so
+    // does r plane zr.  cp.async: one commit group per call, possibly empty.
+    // TMA: thread 0 arms mbarrier es with the bytes of the call's boxes and
+    // issues them (an empty call just arrives).
+    auto issue = [&](int z, int zr, int es, int rs) {
+        const bool ce = z >= 0 && z < nz && z <= z1 + 1, cr = zr >= 0 && zr < nz && zr <= z1;
+        if (MODE == kSweepFromZero && ce && has_e)
+            *reinterpret_cast<float4*>(Es + es * kEPlane + e_sm) = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tma) {
+            if (tid == 0) {
+                const unsigned bar = bar0 + 8u * es;
+                mbar_arrive_tx(bar, (ce ? (MODE == kSweepFromZero ? 1u : 2u) * kEBoxBytes : 0u) + (cr ? kRBoxBytes : 0u));
+                if (ce) {
+                    tma_plane(smem_u32(Rh + es * kEPlane), &tm_rho, x0 - 4, y0 - 2, z, bar);
+                    if (MODE != kSweepFromZero) tma_plane(smem_u32(Es + es * kEPlane), &tm_e, x0 - 4, y0 - 2, z, bar);
+                }
+                if (cr) tma_plane(smem_u32(Rs + rs * kRSlotF), &tm_r, x0 - 4, y0 - 1, zr, bar);
+            }
+            return;
         }
-        if (has_r && zr >= 0 && zr < nz && zr <= z1) cp_async16(Rs + rslot(zr) * kRPlane + r_sm, r + (long)zr * NP + r_off);
+        if (has_e && ce) {
+            const long o = (long)z * NP + e_off;
+            cp_async16(Rh + es * kEPlane + e_sm, rho + o);
+            if (MODE != kSweepFromZero) cp_async16(Es + es * kEPlane + e_sm, ein + o);
+        }
+        if (has_r && cr) cp_async16(Rs + rs * kRSlotF + r_sm, r + (long)zr * NP + r_off);
         cp_async_commit();
     };
-    // prologue: e / rho planes z0-2 and z0-1, then group m (m = 0, 1, ...) holds
-    // e / rho plane z0+m and r plane z0-1+m; step k = z0-2+m reads groups <= m
-    issue(z0 - 2, -1);
-    issue(z0 - 1, -1);
-    for (int m = 0; m < kPD; ++m) issue(z0 + m, z0 - 1 + m);
+    // prologue: e / rho planes z0-2 .. z0+1 (slots 0..3) and r planes z0-1, z0
+    // (slots 1, 2); with TMA the first step's planes z0-2, z0-1 are waited for here
+    issue(z0 - 2, -1, 0, 0);
+    issue(z0 - 1, -1, 1, 0);
+    issue(z0, z0 - 1, 2, 1);
+    issue(z0 + 1, z0, 3, 2);
+    if (tma)
+        for (int j = 0; j < 2; ++j)
+            if (!mbar_wait_bounded(bar0 + 8u * j, 0u)) timed_out = true;
 
     // this thread's pair: red update on rows -1..kTY (warps 0..kTY+1), black
-    // update on rows 0..kTY-1 (warps 2..kTY+1); warp kTY+2: the ring cells
+    // update on rows 0..kTY-1 (warps 0..kTY-1); warp kTY+2: the ring cells
     const int half = lane >> 4, sub = lane & 15;
     int red_row = -1, pc = 0;   // staged r row (tile row + 1) and staged pair (tile pair + 2)
     if (warp < kTY) {           // tile rows 0..kTY-1: red and black updates
@@ -184,22 +283,16 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
     }
     const bool black_thread = warp < kTY;
     const int jrel = red_row - 1;  // tile row of the pair
-    // slots of planes k-1, k, k+1 (e / rho) and of r planes k, k+1 at the
-    // current step, and the slots the step's loads fill (e / rho plane k+4, r
-    // plane k+3); global offsets of those planes
-    int sm1 = eslot(z0 - 3 + kESlots), s0 = eslot(z0 - 2), sp1 = eslot(z0 - 1);
-    int r0 = rslot(z0 - 2 + kRSlots), rp1 = rslot(z0 - 1);
-    for (int k = z0 - 2; k < z1; ++k) {
-        cp_async_wait<kPD - 1>();
-        __syncthreads();  // e / rho planes <= k+2 and r planes <= k+1 are staged
-        // e / rho plane k-2 and r plane k-1 were last read by step k-1's black
-        // update: their slots take the planes two steps ahead
-        issue(k + 2 + kPD, k + 1 + kPD);
-        const int sp2 = next_slot(sp1, kESlots);
-        // red cells of plane kr = k+1 on the tile and its one-cell ring
-        const int kr = k + 1;
-        if (kr >= 0 && kr < nz && red_row >= 0) {
-            const int y = y0 + red_row - 1;
+    // The colour of a cell flips from one plane to the next, so the thread's
+    // red cell (staged float index fr, r index rr) and the parity tb of its
+    // black cell take one value on the even steps of the z march and another
+    // on the odd ones.
+    int fr[2] = {0, 0}, rr[2] = {0, 0}, tb[2] = {0, 0};
+    if (red_row >= 0) {
+        const int y = y0 + red_row - 1;
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            const int kr = z0 - 1 + par;  // red plane of the first (par 0) or second step
             int pcr = pc, t;
             if (warp < kTY + 2) {
                 t = (y + kr) & 1;
@@ -209,39 +302,82 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
                 pcr = left ? 1 : kTP + 2;
                 t = left ? 1 : 0;
             }
-            const int fi = (red_row + 1) * kRowF + 2 * pcr + t;
-            const float* E = Es + sp1 * kEPlane;
-            const float* H = Rh + sp1 * kEPlane;
-            const float rcen = Rs[rp1 * kRPlane + red_row * kRowF + 2 * pcr + t];
-            const float v = cell_update(E, H, kr > 0 ? Es + s0 * kEPlane : nullptr, Rh + s0 * kEPlane,
-                                        kr < nz - 1 ? Es + sp2 * kEPlane : nullptr, Rh + sp2 * kEPlane, fi, rcen,
-                                        h2);
-            Es[sp1 * kEPlane + fi] = v;
+            fr[par] = (red_row + 1) * kRowF + 2 * pcr + t;
+            rr[par] = red_row * kRowF + 2 * pcr + t;
+            tb[par] = (y0 + jrel + kr) & 1;
+        }
+    }
+    const int fb = (jrel + 2) * kRowF + 2 * pc;  // staged float index of the pair
+    const int rb = (jrel + 1) * kRowF + 2 * pc;
+    // this thread's output pair of plane z0 (black threads); advanced by one
+    // plane per black update
+    const long cb = (long)z0 * NP + (long)(x0 + 2 * (pc - 2)) + (long)nx * (y0 + jrel);
+    float2* o2 = reinterpret_cast<float2*>(eout) + (black_thread ? cb >> 1 : 0);
+    PT<T>* pp = p + (black_thread && MODE == kSweepUpdate ? cb : 0);
+    const long NPh = NP >> 1;
+
+    // Step k = z0 - 2 + 6 m + u of the march: red cells of plane k + 1, then
+    // black cells of plane k.  e / rho plane k + j sits in slot (u + j) mod 6
+    // and r plane k + j in slot (u + j) mod 6.  With TMA, plane k + 2 is call
+    // 6 m + u + 2 of mbarrier (u + 2) mod 6, phase m + (u >= 4).
+    auto step = [&](auto uc, int k, unsigned ph) {
+        constexpr int u = decltype(uc)::value;
+        constexpr int sM = (u + 5) % 6, s0 = u, s1 = (u + 1) % 6, s2 = (u + 2) % 6;
+        if (tma) {
+            if (!mbar_wait_bounded(bar0 + 8u * s2, ph ^ (u >= 4 ? 1u : 0u))) timed_out = true;
+        } else {
+            cp_async_wait<kPD - 1>();
+        }
+        __syncthreads();  // e / rho planes <= k+2 and r planes <= k+1 are staged
+        // e / rho plane k-2 and r plane k-3 were last read before this step:
+        // their slots take the planes two steps ahead
+        issue(k + 2 + kPD, k + 1 + kPD, (u + 4) % 6, (u + 3) % 6);
+        // red cells of plane kr = k+1 on the tile and its one-cell ring
+        const int kr = k + 1;
+        if (kr >= 0 && kr < nz && red_row >= 0) {
+            const int fi = fr[u & 1];
+            const float rcen = Rs[s1 * kRSlotF + rr[u & 1]];
+            const float v = cell_update<(s0 - s1) * kEPlane, (s2 - s1) * kEPlane>(Es + s1 * kEPlane, fi, kr > 0,
+                                                                                  kr < nz - 1, rcen, h2);
+            Es[s1 * kEPlane + fi] = v;
+            // the slot is refilled by TMA later on: order this generic write before it
+            if (MODE != kSweepFromZero && tma) fence_proxy_async();
         }
         __syncthreads();  // the red values of plane k+1 are visible
         // black cells of plane k on the tile, written out with their red partners
         if (k >= z0 && black_thread) {
-            const int t = (y0 + jrel + k + 1) & 1;
-            const int fb = (jrel + 2) * kRowF + 2 * pc;
-            const float* E = Es + s0 * kEPlane;
-            const float* H = Rh + s0 * kEPlane;
-            const float rcen = Rs[r0 * kRPlane + (jrel + 1) * kRowF + 2 * pc + t];
-            const float v = cell_update(E, H, k > 0 ? Es + sm1 * kEPlane : nullptr, Rh + sm1 * kEPlane,
-                                        k < nz - 1 ? Es + sp1 * kEPlane : nullptr, Rh + sp1 * kEPlane, fb + t, rcen,
-                                        h2);
-            const float red = E[fb + 1 - t];  // the pair's red value is in place
+            const int t = tb[u & 1];
+            const float rcen = Rs[s0 * kRSlotF + rb + t];
+            const float v = cell_update<(sM - s0) * kEPlane, (s1 - s0) * kEPlane>(Es + s0 * kEPlane, fb + t, k > 0,
+                                                                                  k < nz - 1, rcen, h2);
+            const float red = Es[s0 * kEPlane + fb + 1 - t];  // the pair's red value is in place
             const float2 out = t == 0 ? make_float2(v, red) : make_float2(red, v);
-            const long c = (long)k * NP + (long)(x0 + 2 * (pc - 2)) + (long)nx * (y0 + jrel);
-            reinterpret_cast<float2*>(eout)[c >> 1] = out;
-            if (MODE == kSweepUpdate) p_add_pair(p + c, out);
+            *o2 = out;
+            o2 += NPh;
+            if (MODE == kSweepUpdate) {
+                p_add_pair(pp, out);
+                pp += NP;
+            }
         }
-        sm1 = s0;
-        s0 = sp1;
-        sp1 = sp2;
-        r0 = rp1;
-        rp1 = next_slot(rp1, kRSlots);
+    };
+    unsigned ph = 0;
+    for (int kb = z0 - 2; kb < z1; kb += 6, ph ^= 1u) {
+        step(IC<0>{}, kb, ph);
+        if (kb + 1 >= z1) break;
+        step(IC<1>{}, kb + 1, ph);
+        if (kb + 2 >= z1) break;
+        step(IC<2>{}, kb + 2, ph);
+        if (kb + 3 >= z1) break;
+        step(IC<3>{}, kb + 3, ph);
+        if (kb + 4 >= z1) break;
+        step(IC<4>{}, kb + 4, ph);
+        if (kb + 5 >= z1) break;
+        step(IC<5>{}, kb + 5, ph);
     }
-    cp_async_wait<0>();
+    // every call that staged bytes was waited for above (the calls after the
+    // last wait stage nothing: their planes lie beyond z1 + 1)
+    if (!tma) cp_async_wait<0>();
+    if (timed_out) *err = 1.0;
 }
 
 }  // namespace
@@ -308,25 +444,76 @@ cudaError_t sweep0_prepare() {
     return cudaSuccess;
 }
 
+namespace {
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (no link against the driver library); null if unavailable
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && f)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+// (nx, ny, nz) FP32 array, x fastest; box kRowF x rows x 1, no swizzle (the
+// box lands row after row, kRowF floats a row), zero fill outside the grid
+bool encode_plane_map(CUtensorMap* m, const float* base, const Geom& g, int rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn || !base) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.n[0] * sizeof(float), (cuuint64_t)g.NP * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)kRowF, (cuuint32_t)rows, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+}  // namespace
+
+void sweep0_encode_maps(const MGLevel& L, SweepMaps* m) {
+    *m = SweepMaps{};
+    if (!sweep0_supported(L.g) || !L.e2) return;
+    m->ok = encode_plane_map(&m->rho, L.rho0, L.g, kER) && encode_plane_map(&m->e, L.e, L.g, kER) &&
+            encode_plane_map(&m->e2, L.e2, L.g, kER) && encode_plane_map(&m->r, L.r, L.g, kRR);
+}
+
 // one full red-black sweep of level 0: ein -> eout (ein unused when from_zero),
-// and p += eout when update
+// and p += eout when update; interior tiles stage with TMA when maps is
+// non-null and encoded, a wait that runs out sets *err
 template <typename T>
-void launch_sweep0(const Geom& g, const float* rho, const float* ein, float* eout, const float* r, int mode, PT<T>* p,
-                   cudaStream_t s) {
+void launch_sweep0(const MGLevel& L, const SweepMaps* maps, const float* ein, float* eout, int mode, PT<T>* p,
+                   double* err, cudaStream_t s) {
+    const Geom& g = L.g;
     const int zchunk = sweep0_zchunk(g);
     const dim3 grid((unsigned)(g.n[0] / kTX), (unsigned)(g.n[1] / kTY), (unsigned)((g.n[2] + zchunk - 1) / zchunk));
     const float h2 = (float)(g.h * g.h);
+    static const SweepMaps none{};
+    const bool tma = maps && maps->ok;
+    const SweepMaps& m = tma ? *maps : none;
+    const CUtensorMap& me = (ein == L.e2) ? m.e2 : m.e;
+    const int ut = tma ? 1 : 0;
     if (mode == kSweepFromZero)
-        k_sweep0<T, kSweepFromZero><<<grid, kSweepThreads, kSweepSmem, s>>>(g, rho, ein, eout, r, h2, p, zchunk);
+        k_sweep0<T, kSweepFromZero><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2, p, zchunk,
+                                                                            m.rho, me, m.r, ut, err);
     else if (mode == kSweepUpdate)
-        k_sweep0<T, kSweepUpdate><<<grid, kSweepThreads, kSweepSmem, s>>>(g, rho, ein, eout, r, h2, p, zchunk);
+        k_sweep0<T, kSweepUpdate><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2, p, zchunk,
+                                                                          m.rho, me, m.r, ut, err);
     else
-        k_sweep0<T, kSweepPlain><<<grid, kSweepThreads, kSweepSmem, s>>>(g, rho, ein, eout, r, h2, p, zchunk);
+        k_sweep0<T, kSweepPlain><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2, p, zchunk,
+                                                                         m.rho, me, m.r, ut, err);
 }
 
-template void launch_sweep0<double>(const Geom&, const float*, const float*, float*, const float*, int, double*,
+template void launch_sweep0<double>(const MGLevel&, const SweepMaps*, const float*, float*, int, double*, double*,
                                     cudaStream_t);
-template void launch_sweep0<float>(const Geom&, const float*, const float*, float*, const float*, int, float2*,
+template void launch_sweep0<float>(const MGLevel&, const SweepMaps*, const float*, float*, int, float2*, double*,
                                    cudaStream_t);
 
 }  // namespace cdi
