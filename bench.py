@@ -91,8 +91,9 @@ def onepass_sweep_words(sweeps):
     """FP32 words a cell of one launch of the 3D one-pass finest-level sweep,
     averaged over the launches of one V-cycle with `sweeps` sweeps: the first
     reads rho and r and writes e (3), the plain ones also read the old e (4),
-    the last one also reads and writes the double-float p (4 + 4)."""
-    return (3 + 4 * (sweeps - 2) + 8) / sweeps
+    the last one reads rho, r and the old e and reads and writes the
+    double-float p instead of writing e (3 + 4)."""
+    return (3 + 4 * (sweeps - 2) + 7) / sweeps
 
 
 def algorithmic_bytes(kernel, dim, N, NP, word, sweeps=3):

@@ -325,6 +325,8 @@ cdi_status kernels_tail_setup(cdi_ctx* c) {
     cdi_status st = smem_optin(c, &optin);
     if (st) return st;
     c->mg.maps = nullptr;
+    st = cuda_check(c, resid_tile_prepare(), "tiled residual setup");
+    if (st) return st;
     if (c->mg.lv[0].e2) {
         st = cuda_check(c, sweep0_prepare(), "one-pass sweep setup");
         if (st) return st;

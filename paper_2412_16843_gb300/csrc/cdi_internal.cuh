@@ -298,7 +298,8 @@ void launch_p_extrap(const Geom& g, MG& mg, const double* hnew, const double* ho
 // correction is zero (not read); the last, which also adds the correction to p
 enum SweepMode { kSweepPlain = 0, kSweepFromZero = 1, kSweepUpdate = 2 };
 // one-pass red-black sweep of the 3D level 0 (k_sweep.cu): ein -> eout in one
-// launch (ein unused from zero; the update mode also adds eout to p)
+// launch (ein unused from zero; the update mode adds the new e to p instead
+// of writing eout)
 bool sweep0_supported(const Geom& g);  // the tile shape fits the grid
 bool sweep0_auto(const Geom& g);       // it fits and the grid fills the GPU
 cudaError_t sweep0_prepare();
@@ -306,6 +307,11 @@ void sweep0_encode_maps(const MGLevel& L0, SweepMaps* maps);  // maps->ok false 
 template <typename T>
 void launch_sweep0(const MGLevel& L0, const SweepMaps* maps, const float* ein, float* eout, int mode, PT<T>* p,
                    double* err, cudaStream_t s);
+// tiled level-0 residual of the FP32-mixed form on 3D grids (k_resid.cu): r
+// and one |r|^2 partial a CTA (at most max_parts); returns the partial count
+bool resid_tile_supported(const Geom& g, int max_parts);
+cudaError_t resid_tile_prepare();
+unsigned launch_resid_tile(const MGLevel& L0, const float* fmean_df, double* part, int max_parts, cudaStream_t s);
 // the single-CTA shared-memory tail of a V-cycle as its own launch (k_persist.cu)
 cudaError_t tail_prepare(int dim, size_t smem);
 cudaError_t launch_tail(const void* inst_args, int dim, size_t smem, cudaStream_t s);

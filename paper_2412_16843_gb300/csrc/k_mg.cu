@@ -202,9 +202,12 @@ __global__ void k_rbgs(Geom g, const float* b0, const float* b1, const float* b2
 
 // Level-0 red-black sweep of one colour on a (x/2, y, z) thread grid: thread
 // (ix, j, k) updates cell i = 2 ix + ((colour + j + k) & 1) of row (j, k), so
-// no index is recovered by division.  Coefficients 2 / (rho_c + rho_nb) from
-// the FP32 cell densities, zero through the walls (the last axis); the update
-// e_c = (sum b e_nb - r h^2) / sum b is the Gauss-Seidel step of apply_L_rho.
+// no index is recovered by division.  Coefficients b = 2 / (rho_c + rho_nb)
+// from the FP32 cell densities, zero through the walls (the last axis); the
+// update e_c = (sum b e_nb - r h^2) / sum b (the Gauss-Seidel step of
+// apply_L_rho) is formed with the half coefficients b' = 1 / (rho_c + rho_nb)
+// as (sum b' e_nb - r h^2 / 2) / sum b', reciprocals by ops::rcp_approx: the
+// arithmetic, term for term, of the one-pass sweep (k_sweep.cu).
 // kSweepFromZero: the first red pass of a V-cycle, whose neighbours are all
 // zero (e is not cleared beforehand: every cell of e is written before it is
 // read).  kSweepUpdate: the last black pass, which also adds the now final
@@ -213,7 +216,7 @@ constexpr int kSweepX = 64, kSweepY = 4;
 template <typename T, int DIM, int MODE>
 __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float* __restrict__ rho,
                                                              float* __restrict__ e, const float* __restrict__ r,
-                                                             int colour, float h2, PT<T>* __restrict__ p) {
+                                                             int colour, float h2h, PT<T>* __restrict__ p) {
     const int nx = g.n[0], ny = g.n[1];
     const int ix = blockIdx.x * kSweepX + threadIdx.x;
     const int j = blockIdx.y * kSweepY + threadIdx.y;
@@ -228,40 +231,40 @@ __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float
     const long xm = row + (i == 0 ? nx - 1 : i - 1), xp = row + (i == nx - 1 ? 0 : i + 1);
     float bsum, off;
     {
-        const float b0 = __fdividef(2.f, rc + rho[xm]), b1 = __fdividef(2.f, rc + rho[xp]);
+        const float b0 = ops::rcp_approx(rc + rho[xm]), b1 = ops::rcp_approx(rc + rho[xp]);
         bsum = b0 + b1;
         off = b0 * en(xm) + b1 * en(xp);
     }
     if (DIM == 2) {  // y is the wall axis
         if (j > 0) {
-            const float b = __fdividef(2.f, rc + rho[c - nx]);
+            const float b = ops::rcp_approx(rc + rho[c - nx]);
             bsum += b;
             off += b * en(c - nx);
         }
         if (j < ny - 1) {
-            const float b = __fdividef(2.f, rc + rho[c + nx]);
+            const float b = ops::rcp_approx(rc + rho[c + nx]);
             bsum += b;
             off += b * en(c + nx);
         }
     } else {
         const long ym = (j == 0) ? c + (long)(ny - 1) * nx : c - nx;
         const long yp = (j == ny - 1) ? c - (long)(ny - 1) * nx : c + nx;
-        const float b2 = __fdividef(2.f, rc + rho[ym]), b3 = __fdividef(2.f, rc + rho[yp]);
+        const float b2 = ops::rcp_approx(rc + rho[ym]), b3 = ops::rcp_approx(rc + rho[yp]);
         bsum += b2 + b3;
         off += b2 * en(ym) + b3 * en(yp);
         const long np = g.NP;
         if (k > 0) {
-            const float b = __fdividef(2.f, rc + rho[c - np]);
+            const float b = ops::rcp_approx(rc + rho[c - np]);
             bsum += b;
             off += b * en(c - np);
         }
         if (k < g.n[2] - 1) {
-            const float b = __fdividef(2.f, rc + rho[c + np]);
+            const float b = ops::rcp_approx(rc + rho[c + np]);
             bsum += b;
             off += b * en(c + np);
         }
     }
-    const float ec = __fdividef(off - r[c] * h2, bsum);
+    const float ec = (off - r[c] * h2h) * ops::rcp_approx(bsum);
     e[c] = ec;
     if (MODE == kSweepUpdate) {
         const long co = c ^ 1;  // the pair's other cell (row starts are even: nx is even)
@@ -752,21 +755,21 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
     const dim3 sweep_grid((unsigned)((L.g.n[0] / 2 + kSweepX - 1) / kSweepX),
                           (unsigned)((L.g.n[1] + kSweepY - 1) / kSweepY), (unsigned)(DIM == 3 ? L.g.n[2] : 1));
     const dim3 sweep_block(kSweepX, kSweepY);
-    const float h2 = (float)(L.g.h * L.g.h);
+    const float h2h = 0.5f * (float)(L.g.h * L.g.h);
     auto sweep = [&](int col, int mode) {
         if (l == 0) {
             if (mode == kSweepFromZero)
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepFromZero><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                              col, h2, p)));
+                                                                                              col, h2h, p)));
             else if (mode == kSweepUpdate)
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepUpdate><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                            col, h2, p)));
+                                                                                            col, h2h, p)));
             else
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepPlain><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                           col, h2, p)));
+                                                                                           col, h2h, p)));
         } else {
             CDI_PROF(kc_rbgs, s,
                      (k_rbgs<DIM><<<nbh, kThreads, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r, col)));
@@ -808,13 +811,22 @@ void launch_vcycle(const Geom& g, MG& mg, int npre, int npost, cudaStream_t s) {
     }
 }
 
+// residual and |r|^2 partials: the tiled kernel (k_resid.cu) for the
+// FP32-mixed form on 3D grids of 64 x 16 tiles (not with the colour-pass
+// smoother, which keeps the per-cell kernel: the two are compared bit for bit),
+// else one thread a cell
 template <typename T>
 void launch_resid_norm(const Geom& g, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.D == 2 ? (const void*)k_resid<T, 2> : (const void*)k_resid<T, 3>, g.N);
     const float* fm = sizeof(T) == 8 ? nullptr : mg.scalf + SF_FMEAN_HI;
+    unsigned G;
     const bool on = prof_before(KC_RESID, s);
-    if (g.D == 2) k_resid<T, 2><<<G, kThreads, 0, s>>>(mg.lv[0], fm, mg.partials);
-    else k_resid<T, 3><<<G, kThreads, 0, s>>>(mg.lv[0], fm, mg.partials);
+    if (sizeof(T) == 4 && mg.sweep_mode != 2 && resid_tile_supported(g, kPartials)) {
+        G = launch_resid_tile(mg.lv[0], fm, mg.partials, kPartials, s);
+    } else {
+        G = red_blocks(g.D == 2 ? (const void*)k_resid<T, 2> : (const void*)k_resid<T, 3>, g.N);
+        if (g.D == 2) k_resid<T, 2><<<G, kThreads, 0, s>>>(mg.lv[0], fm, mg.partials);
+        else k_resid<T, 3><<<G, kThreads, 0, s>>>(mg.lv[0], fm, mg.partials);
+    }
     prof_after(on, s);
     k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G, 1.0, mg.scal + S_RNORM, 1);
     g_launches += 2;

@@ -39,8 +39,8 @@
 // (red and black updates), warps 16..17 the ring rows -1 and 16 (red only),
 // warp 18 the red ring cell of each row left or right of the tile.
 #include "ops.cuh"
+#include "stage.cuh"
 
-#include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <cmath>
@@ -48,6 +48,8 @@
 namespace cdi {
 
 namespace {
+
+using namespace stage;
 
 constexpr int kTX = 64, kTY = 16;                  // tile of cells in x, y
 constexpr int kTP = kTX / 2;                       // pairs in x (32 = warp width)
@@ -73,88 +75,34 @@ constexpr unsigned kEBoxBytes = kEPlane * 4, kRBoxBytes = kRPlane * 4;   // one 
 static_assert(kEQ * kER <= kSweepThreads && kEQ * kRR <= kSweepThreads, "one staged quad per thread");
 static_assert(kEPlane * 4 % 128 == 0 && kRSlotF * 4 % 128 == 0, "slots start on 128-byte boundaries");
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-// the issuing thread's arrival; the phase completes once `bytes` have landed
-__device__ __forceinline__ void mbar_arrive_tx(unsigned bar, unsigned bytes) {
-    if (bytes)
-        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
-                     "r"(bytes)
-                     : "memory");
-    else
-        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// wait for the phase of the given parity; gives up (false) only after 2^20
-// polls and one second
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (long polls = 0;; ++polls) {
-        if (mbar_try(bar, parity)) return true;
-        if (polls > (1L << 20) && globaltimer() - t0 > 1000000000ull) return false;
-    }
-}
-// one z plane (box 72 x rows x 1) of a 3D FP32 tensor into shared memory, completed on mbarrier bar
-__device__ __forceinline__ void tma_plane(unsigned dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];\n" ::"r"(dst),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-// order this thread's generic shared-memory writes before later TMA writes to the same bytes
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-
 // Gauss-Seidel value of the staged cell at float index fi of the e plane E
 // (old or new e; its rho plane lies kESlots e planes further on), with the
 // planes below / above DM / DP floats away (taken when lo / hi: not through a
-// wall) and the cell's r: e = (sum_nb b e_nb - r h^2) / sum_nb b, b = 2 /
-// (rho_c + rho_nb), terms in the order x-, x+, y-, y+, z-, z+
+// wall) and the cell's r: e = (sum_nb b e_nb - r h^2) / sum_nb b with b = 2 /
+// (rho_c + rho_nb), formed as (sum_nb b' e_nb - r h^2 / 2) / sum_nb b' with
+// b' = b / 2 = 1 / (rho_c + rho_nb) (ops::rcp_approx), terms in the order x-,
+// x+, y-, y+, z-, z+; h2h = h^2 / 2
 template <int DM, int DP>
-__device__ __forceinline__ float cell_update(const float* E, int fi, bool lo, bool hi, float rcen, float h2) {
+__device__ __forceinline__ float cell_update(const float* E, int fi, bool lo, bool hi, float rcen, float h2h) {
     constexpr int HO = kESlots * kEPlane;
     const float rc = E[HO + fi];
-    const float b0 = __fdividef(2.f, rc + E[HO + fi - 1]), b1 = __fdividef(2.f, rc + E[HO + fi + 1]);
+    const float b0 = ops::rcp_approx(rc + E[HO + fi - 1]), b1 = ops::rcp_approx(rc + E[HO + fi + 1]);
     float bsum = b0 + b1;
     float off = b0 * E[fi - 1] + b1 * E[fi + 1];
-    const float b2 = __fdividef(2.f, rc + E[HO + fi - kRowF]), b3 = __fdividef(2.f, rc + E[HO + fi + kRowF]);
+    const float b2 = ops::rcp_approx(rc + E[HO + fi - kRowF]), b3 = ops::rcp_approx(rc + E[HO + fi + kRowF]);
     bsum += b2 + b3;
     off += b2 * E[fi - kRowF] + b3 * E[fi + kRowF];
     if (lo) {
-        const float b = __fdividef(2.f, rc + E[HO + DM + fi]);
+        const float b = ops::rcp_approx(rc + E[HO + DM + fi]);
         bsum += b;
         off += b * E[DM + fi];
     }
     if (hi) {
-        const float b = __fdividef(2.f, rc + E[HO + DP + fi]);
+        const float b = ops::rcp_approx(rc + E[HO + DP + fi]);
         bsum += b;
         off += b * E[DP + fi];
     }
-    return __fdividef(off - rcen * h2, bsum);
+    return (off - rcen * h2h) * ops::rcp_approx(bsum);
 }
 
 // p[0] += e.x, p[1] += e.y for two cells of a pair (16-byte aligned)
@@ -178,7 +126,7 @@ struct IC {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kSweepThreads, 2)
     k_sweep0(Geom g, const float* __restrict__ rho, const float* __restrict__ ein, float* __restrict__ eout,
-             const float* __restrict__ r, float h2, PT<T>* __restrict__ p, int zchunk,
+             const float* __restrict__ r, float h2h, PT<T>* __restrict__ p, int zchunk,
              const __grid_constant__ CUtensorMap tm_rho, const __grid_constant__ CUtensorMap tm_e,
              const __grid_constant__ CUtensorMap tm_r, int use_tma, double* __restrict__ err) {
     extern __shared__ __align__(128) float smf[];
@@ -338,7 +286,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
             const int fi = fr[u & 1];
             const float rcen = Rs[s1 * kRSlotF + rr[u & 1]];
             const float v = cell_update<(s0 - s1) * kEPlane, (s2 - s1) * kEPlane>(Es + s1 * kEPlane, fi, kr > 0,
-                                                                                  kr < nz - 1, rcen, h2);
+                                                                                  kr < nz - 1, rcen, h2h);
             Es[s1 * kEPlane + fi] = v;
             // the slot is refilled by TMA later on: order this generic write before it
             if (MODE != kSweepFromZero && tma) fence_proxy_async();
@@ -349,14 +297,15 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
             const int t = tb[u & 1];
             const float rcen = Rs[s0 * kRSlotF + rb + t];
             const float v = cell_update<(sM - s0) * kEPlane, (s1 - s0) * kEPlane>(Es + s0 * kEPlane, fb + t, k > 0,
-                                                                                  k < nz - 1, rcen, h2);
+                                                                                  k < nz - 1, rcen, h2h);
             const float red = Es[s0 * kEPlane + fb + 1 - t];  // the pair's red value is in place
             const float2 out = t == 0 ? make_float2(v, red) : make_float2(red, v);
-            *o2 = out;
-            o2 += NPh;
-            if (MODE == kSweepUpdate) {
+            if (MODE == kSweepUpdate) {  // the V-cycle's last sweep: e is not read again
                 p_add_pair(pp, out);
                 pp += NP;
+            } else {
+                *o2 = out;
+                o2 += NPh;
             }
         }
     };
@@ -486,7 +435,7 @@ void sweep0_encode_maps(const MGLevel& L, SweepMaps* m) {
 }
 
 // one full red-black sweep of level 0: ein -> eout (ein unused when from_zero),
-// and p += eout when update; interior tiles stage with TMA when maps is
+// or, in update mode, p += the new e (eout not written: nothing reads it); interior tiles stage with TMA when maps is
 // non-null and encoded, a wait that runs out sets *err
 template <typename T>
 void launch_sweep0(const MGLevel& L, const SweepMaps* maps, const float* ein, float* eout, int mode, PT<T>* p,
@@ -494,20 +443,20 @@ void launch_sweep0(const MGLevel& L, const SweepMaps* maps, const float* ein, fl
     const Geom& g = L.g;
     const int zchunk = sweep0_zchunk(g);
     const dim3 grid((unsigned)(g.n[0] / kTX), (unsigned)(g.n[1] / kTY), (unsigned)((g.n[2] + zchunk - 1) / zchunk));
-    const float h2 = (float)(g.h * g.h);
+    const float h2h = 0.5f * (float)(g.h * g.h);
     static const SweepMaps none{};
     const bool tma = maps && maps->ok;
     const SweepMaps& m = tma ? *maps : none;
     const CUtensorMap& me = (ein == L.e2) ? m.e2 : m.e;
     const int ut = tma ? 1 : 0;
     if (mode == kSweepFromZero)
-        k_sweep0<T, kSweepFromZero><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2, p, zchunk,
+        k_sweep0<T, kSweepFromZero><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, p, zchunk,
                                                                             m.rho, me, m.r, ut, err);
     else if (mode == kSweepUpdate)
-        k_sweep0<T, kSweepUpdate><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2, p, zchunk,
+        k_sweep0<T, kSweepUpdate><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, p, zchunk,
                                                                           m.rho, me, m.r, ut, err);
     else
-        k_sweep0<T, kSweepPlain><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2, p, zchunk,
+        k_sweep0<T, kSweepPlain><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, p, zchunk,
                                                                          m.rho, me, m.r, ut, err);
 }
 

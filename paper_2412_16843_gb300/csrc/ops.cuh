@@ -651,6 +651,16 @@ __device__ __forceinline__ long colour_cell(const Geom& g, int colour, long k) {
 // is then never stored: a Gauss-Seidel step does not read its own cell)
 enum StepNb { kNbStored = 0, kNbZero = 1, kNbProlong = 2 };
 
+// 1 / x by the hardware approximation (rcp.approx.ftz.f32: relative error
+// below 2^-23, subnormals flushed), for the finest-level smoother's face
+// coefficients, which only precondition (the defect correction iterates to the
+// tolerance regardless)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // quotient of a smoothing step: the fast FP32 division (a preconditioner's
 // arithmetic; the defect correction iterates to the tolerance regardless)
 __device__ __forceinline__ float step_div(float a, float b) { return __fdividef(a, b); }
@@ -812,6 +822,17 @@ __device__ __forceinline__ void df_acc_term(float b, float2 x, float2 y, float& 
     Sl = __fadd_rn(Sl, __fadd_rn(se, te));
 }
 
+// (f - mean) - S / h^2 for the double-float flux sum S = (Sh, Sl), rounded to FP32
+__device__ __forceinline__ float resid_df_finish(float Sh, float Sl, float ih2f, float fc, float2 fmean) {
+    float ah, al;
+    dfl::two_prod(Sh, ih2f, ah, al);
+    al = __fmaf_rn(Sl, ih2f, al);
+    float r1, e1, r2, e2;
+    dfl::two_sum(fc, -fmean.x, r1, e1);
+    dfl::two_sum(r1, -ah, r2, e2);
+    return __fadd_rn(r2, __fadd_rn(__fsub_rn(e1, fmean.y), __fsub_rn(e2, al)));
+}
+
 // Residual (f - mean) - A p of the FP32-mixed form at cell c, with the FP32
 // face coefficients bf and 1/h^2 of the V-cycles, accumulated in double-float
 // (error about 2^-44 of the largest flux term, far below any tolerance a
@@ -839,13 +860,7 @@ __device__ __forceinline__ float resid_df_at(const Geom& g, const float* const* 
         df_acc_term(bm, L::ld(p + lo), pc, Sh, Sl);
         df_acc_term(bp, L::ld(p + hi), pc, Sh, Sl);
     }
-    float ah, al;
-    dfl::two_prod(Sh, g.ih2f, ah, al);
-    al = __fmaf_rn(Sl, g.ih2f, al);
-    float r1, e1, r2, e2;
-    dfl::two_sum(L::ld(f + c), -fmean.x, r1, e1);
-    dfl::two_sum(r1, -ah, r2, e2);
-    return __fadd_rn(r2, __fadd_rn(__fsub_rn(e1, fmean.y), __fsub_rn(e2, al)));
+    return resid_df_finish(Sh, Sl, g.ih2f, L::ld(f + c), fmean);
 }
 
 // level-0 residual of either form (fmean: the mean of f, FP32-mixed form only)
