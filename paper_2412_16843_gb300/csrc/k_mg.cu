@@ -280,12 +280,14 @@ __global__ void k_resid_restrict0(Geom gf, Geom gc, const float* rho0, const flo
     if (t < gc.N) ops::resid_restrict_rho_at<Ld, DIM>(gf, gc, rho0, e, r, rc, ec, t);
 }
 
-// Level-0 -> level-1 restriction of the residual of 3D grids with the
-// arithmetic of ops::resid_restrict_rho_at (children in the order z, y, x;
-// each child's stencil x, y, z with its coefficients 2 / (rho_c + rho_nb)):
-// one thread per coarse (x, y) column marching over a z chunk, the fine
-// neighbour offsets formed once.  r_c = mean of the children's f - A e,
-// e_c = 0.  Coarse blocks of 32 x 8 columns.
+// Level-0 -> level-1 restriction of the residual of 3D grids in the order of
+// ops::resid_restrict_rho_at (children in the order z, y, x; each child's
+// stencil x, y, z) with the finest-level smoother's coefficients: half
+// coefficients b' = 1 / (rho_c + rho_nb) by ops::rcp_approx against 2 / h^2,
+// so the coarse correction targets the operator the one-pass sweep and the
+// colour passes smooth.  One thread per coarse (x, y) column marching over a
+// z chunk, the fine neighbour offsets formed once.  r_c = mean of the
+// children's f - A e, e_c = 0.  Coarse blocks of 32 x 8 columns.
 constexpr int kRestrictZ = 4;
 __global__ void __launch_bounds__(256) k_restrict0_3(Geom gf, Geom gc, const float* __restrict__ rho,
                                                      const float* __restrict__ e, const float* __restrict__ r,
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(256) k_restrict0_3(Geom gf, Geom gc, const flo
     const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y;
     const int nx = gf.n[0], ny = gf.n[1], nz = gf.n[2];
     const long NP = gf.NP;
-    const float ih2 = gf.ih2f;
+    const float ih2 = 2.f * gf.ih2f;  // half coefficients b' = b / 2: 2 / h^2
     // offsets of the x and y neighbours of the children 2I + t0, 2J + t1
     long xm[2], xp[2], ym[2], yp[2];
     xm[0] = 2 * I == 0 ? nx - 1 : -1;
@@ -321,23 +323,23 @@ __global__ void __launch_bounds__(256) k_restrict0_3(Geom gf, Geom gc, const flo
                     float diag = 0.f, off = 0.f;
                     {
                         const long lo = c + xm[t0], hi = c + xp[t0];
-                        const float bm = 1.f * __fdividef(2.f, rcen + __ldg(rho + lo));
-                        const float bp = 1.f * __fdividef(2.f, rcen + __ldg(rho + hi));
+                        const float bm = ops::rcp_approx(rcen + __ldg(rho + lo));
+                        const float bp = ops::rcp_approx(rcen + __ldg(rho + hi));
                         diag += (bm + bp) * ih2;
                         off += (bm * __ldg(e + lo) + bp * __ldg(e + hi)) * ih2;
                     }
                     {
                         const long lo = c + ym[t1], hi = c + yp[t1];
-                        const float bm = 1.f * __fdividef(2.f, rcen + __ldg(rho + lo));
-                        const float bp = 1.f * __fdividef(2.f, rcen + __ldg(rho + hi));
+                        const float bm = ops::rcp_approx(rcen + __ldg(rho + lo));
+                        const float bp = ops::rcp_approx(rcen + __ldg(rho + hi));
                         diag += (bm + bp) * ih2;
                         off += (bm * __ldg(e + lo) + bp * __ldg(e + hi)) * ih2;
                     }
                     {
                         const bool wlo = k == 0, whi = k == nz - 1;
                         const long lo = wlo ? c : c - NP, hi = whi ? c : c + NP;
-                        const float bm = (wlo ? 0.f : 1.f) * __fdividef(2.f, rcen + __ldg(rho + lo));
-                        const float bp = (whi ? 0.f : 1.f) * __fdividef(2.f, rcen + __ldg(rho + hi));
+                        const float bm = (wlo ? 0.f : 1.f) * ops::rcp_approx(rcen + __ldg(rho + lo));
+                        const float bp = (whi ? 0.f : 1.f) * ops::rcp_approx(rcen + __ldg(rho + hi));
                         const float pm = wlo ? 0.f : __ldg(e + lo);
                         const float pp = whi ? 0.f : __ldg(e + hi);
                         diag += (bm + bp) * ih2;
@@ -354,9 +356,11 @@ __global__ void __launch_bounds__(256) k_restrict0_3(Geom gf, Geom gc, const flo
 
 // Level-1 -> level-0 prolongation of 3D grids with the arithmetic of
 // ops::prolong_val (trilinear weights 3/4, 1/4; coarse neighbours in the order
-// z, y, x), one thread per fine (x, y) column marching over a z chunk, the
-// coarse column indices formed once: e += P e_c.  Fine blocks of 32 x 8.
-constexpr int kProlongZ = 8;
+// z, y, x), one thread per fine (x, y) column marching over a z chunk: the
+// four coarse columns' values of coarse planes K-1, K, K+1 are held in
+// registers (fine planes 2K and 2K+1 use K with K-1 and with K+1), so each
+// coarse value is loaded once per thread: e += P e_c.  Fine blocks of 32 x 8.
+constexpr int kProlongZ = 16;  // fine planes a thread (even)
 __global__ void __launch_bounds__(256) k_prolong0_3(Geom gf, Geom gc, const float* __restrict__ ecoarse,
                                                     float* __restrict__ e) {
     const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
@@ -371,23 +375,48 @@ __global__ void __launch_bounds__(256) k_prolong0_3(Geom gf, Geom gc, const floa
     if (Iy[1] < 0) Iy[1] += ncy;
     else if (Iy[1] >= ncy) Iy[1] -= ncy;
     const float w[2] = {0.75f, 0.25f};
-    const long cbase = (long)i + (long)gf.n[0] * j;
-    const int k0 = blockIdx.z * kProlongZ, k1 = min(k0 + kProlongZ, gf.n[2]);
-    for (int k = k0; k < k1; ++k) {
-        int Iz[2];
-        Iz[0] = k >> 1;
-        Iz[1] = min(max((k & 1) ? Iz[0] + 1 : Iz[0] - 1, 0), ncz - 1);
+    long col[4];  // coarse column (t1, t0) at index 2 t1 + t0
+#pragma unroll
+    for (int t1 = 0; t1 < 2; ++t1)
+#pragma unroll
+        for (int t0 = 0; t0 < 2; ++t0) col[2 * t1 + t0] = (long)Ix[t0] + (long)ncx * Iy[t1];
+    const long ncp = gc.NP;
+    // the four columns' values of coarse plane K (clamped to the grid: the
+    // prolongation's wall rule)
+    auto load = [&](int K, float* v) {
+        const long o = (long)min(max(K, 0), ncz - 1) * ncp;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldg(ecoarse + col[q] + o);
+    };
+    float* ef = e + (long)i + (long)gf.n[0] * j;
+    // fine cell of plane k from coarse planes Iz0 = k / 2 (va) and Iz1 (vb)
+    auto fine = [&](int k, const float* va, const float* vb) {
         float s = 0.f;
 #pragma unroll
-        for (int t2 = 0; t2 < 2; ++t2)
+        for (int t2 = 0; t2 < 2; ++t2) {
+            const float* vv = t2 == 0 ? va : vb;
 #pragma unroll
             for (int t1 = 0; t1 < 2; ++t1)
 #pragma unroll
-                for (int t0 = 0; t0 < 2; ++t0)
-                    s += w[t0] * w[t1] * w[t2] *
-                         __ldg(ecoarse + (long)Ix[t0] + (long)ncx * (Iy[t1] + (long)ncy * Iz[t2]));
-        const long c = cbase + (long)k * gf.NP;
-        e[c] = e[c] + s;
+                for (int t0 = 0; t0 < 2; ++t0) s += w[t0] * w[t1] * w[t2] * vv[2 * t1 + t0];
+        }
+        float* c = ef + (long)k * gf.NP;
+        *c = *c + s;
+    };
+    const int k0 = blockIdx.z * kProlongZ, k1 = min(k0 + kProlongZ, gf.n[2]);
+    float vm[4], v0[4], vp[4];
+    load((k0 >> 1) - 1, vm);
+    load(k0 >> 1, v0);
+    load((k0 >> 1) + 1, vp);
+    for (int k = k0; k < k1; k += 2) {
+        fine(k, v0, vm);                      // even plane: K and K-1
+        if (k + 1 < k1) fine(k + 1, v0, vp);  // odd plane: K and K+1
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            vm[q] = v0[q];
+            v0[q] = vp[q];
+        }
+        load((k >> 1) + 2, vp);
     }
 }
 
