@@ -357,9 +357,10 @@ __global__ void __launch_bounds__(256) k_restrict0_3(Geom gf, Geom gc, const flo
 // Level-1 -> level-0 prolongation of 3D grids with the arithmetic of
 // ops::prolong_val (trilinear weights 3/4, 1/4; coarse neighbours in the order
 // z, y, x), one thread per fine (x, y) column marching over a z chunk: the
-// four coarse columns' values of coarse planes K-1, K, K+1 are held in
+// four coarse columns' values of coarse planes K-1 .. K+2 are held in
 // registers (fine planes 2K and 2K+1 use K with K-1 and with K+1), so each
-// coarse value is loaded once per thread: e += P e_c.  Fine blocks of 32 x 8.
+// coarse value is loaded once per thread, and the fine values of four planes
+// are loaded together: e += P e_c.  Fine blocks of 32 x 8.
 constexpr int kProlongZ = 16;  // fine planes a thread (even)
 __global__ void __launch_bounds__(256) k_prolong0_3(Geom gf, Geom gc, const float* __restrict__ ecoarse,
                                                     float* __restrict__ e) {
@@ -389,8 +390,8 @@ __global__ void __launch_bounds__(256) k_prolong0_3(Geom gf, Geom gc, const floa
         for (int q = 0; q < 4; ++q) v[q] = __ldg(ecoarse + col[q] + o);
     };
     float* ef = e + (long)i + (long)gf.n[0] * j;
-    // fine cell of plane k from coarse planes Iz0 = k / 2 (va) and Iz1 (vb)
-    auto fine = [&](int k, const float* va, const float* vb) {
+    // correction of a fine cell from coarse planes Iz0 = k / 2 (va) and Iz1 (vb)
+    auto corr = [&](const float* va, const float* vb) {
         float s = 0.f;
 #pragma unroll
         for (int t2 = 0; t2 < 2; ++t2) {
@@ -400,23 +401,37 @@ __global__ void __launch_bounds__(256) k_prolong0_3(Geom gf, Geom gc, const floa
 #pragma unroll
                 for (int t0 = 0; t0 < 2; ++t0) s += w[t0] * w[t1] * w[t2] * vv[2 * t1 + t0];
         }
-        float* c = ef + (long)k * gf.NP;
-        *c = *c + s;
+        return s;
     };
+    // four fine planes 2K .. 2K+3 an iteration (their e loads issued together):
+    // coarse planes K-1 .. K+2 in vm, v0, vp, vq
     const int k0 = blockIdx.z * kProlongZ, k1 = min(k0 + kProlongZ, gf.n[2]);
-    float vm[4], v0[4], vp[4];
+    const long NP = gf.NP;
+    float vm[4], v0[4], vp[4], vq[4];
     load((k0 >> 1) - 1, vm);
     load(k0 >> 1, v0);
     load((k0 >> 1) + 1, vp);
-    for (int k = k0; k < k1; k += 2) {
-        fine(k, v0, vm);                      // even plane: K and K-1
-        if (k + 1 < k1) fine(k + 1, v0, vp);  // odd plane: K and K+1
+    load((k0 >> 1) + 2, vq);
+    for (int k = k0; k < k1; k += 4) {
+        float* c = ef + (long)k * NP;
+        const int nq = min(4, k1 - k);  // 2 or 4 (every extent of a coarsened grid is even)
+        float o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = q < nq ? c[q * NP] : 0.f;
+        o[0] += corr(v0, vm);  // plane 2K: K and K-1
+        o[1] += corr(v0, vp);  // 2K+1: K and K+1
+        o[2] += corr(vp, v0);  // 2K+2: K+1 and K
+        o[3] += corr(vp, vq);  // 2K+3: K+1 and K+2
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < nq) c[q * NP] = o[q];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            vm[q] = v0[q];
-            v0[q] = vp[q];
+            vm[q] = vp[q];
+            v0[q] = vq[q];
         }
-        load((k >> 1) + 2, vp);
+        load((k >> 1) + 3, vp);
+        load((k >> 1) + 4, vq);
     }
 }
 

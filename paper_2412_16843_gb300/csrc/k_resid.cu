@@ -15,7 +15,8 @@
 // cell's six neighbours and faces then come from shared memory at fixed
 // offsets, so no index is recovered by division and every global access is a
 // whole coalesced quad.  The z- face of a plane is the z+ face of the plane
-// below, staged once.
+// below, staged once, and its flux is that plane's z+ flux negated (the flux
+// is odd in its two pressures, so the sum is unchanged to the bit).
 //
 // Threads: 512 (16 warps); warp w computes tile row w, lane l the cells
 // x0 + l and x0 + 32 + l (32 consecutive double-floats a warp access: free of
@@ -144,6 +145,7 @@ __global__ void __launch_bounds__(kQThreads, kResidPerSM)
     float* rout = r + (long)z0 * NP + (long)nx * (y0 + warp) + x0 + lane;
     const float ih2 = g.ih2f;
     float acc = 0.f;
+    float zt[2] = {0.f, 0.f}, zte[2] = {0.f, 0.f};  // z+ flux of the previous plane, per cell
 
     // plane k = z0 + 6 m + u: p plane k + j in slot (u + j + 1) mod 6, f / b0 /
     // b1 plane k in slot u mod 2, b2 plane k + j in slot (u + j) mod 3
@@ -175,8 +177,19 @@ __global__ void __launch_bounds__(kQThreads, kResidPerSM)
             ops::df_acc_term(B0[jc + 1], P0[jp + 1], pc, Sh, Sl);
             ops::df_acc_term(B1[jc], P0[jp - kPW], pc, Sh, Sl);
             ops::df_acc_term(B1[jc + kCW], P0[jp + kPW], pc, Sh, Sl);
-            ops::df_acc_term(Z0[jc], lo ? Pm[jp] : pc, pc, Sh, Sl);
-            ops::df_acc_term(Z1[jc], hi ? Pp[jp] : pc, pc, Sh, Sl);
+            // the z- flux is the z+ flux of the plane below with its sign
+            // flipped (exactly: the flux is odd in its two pressures), except
+            // on the chunk's first plane
+            float t, te;
+            if (k == z0) {
+                ops::df_term(Z0[jc], lo ? Pm[jp] : pc, pc, t, te);
+            } else {
+                t = -zt[i];
+                te = -zte[i];
+            }
+            ops::df_acc(t, te, Sh, Sl);
+            ops::df_term(Z1[jc], hi ? Pp[jp] : pc, pc, zt[i], zte[i]);
+            ops::df_acc(zt[i], zte[i], Sh, Sl);
             const float v = ops::resid_df_finish(Sh, Sl, ih2, F[jc], fmean);
             rout[32 * i] = v;
             acc += v * v;

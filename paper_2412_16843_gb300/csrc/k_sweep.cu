@@ -77,15 +77,14 @@ static_assert(kEPlane * 4 % 128 == 0 && kRSlotF * 4 % 128 == 0, "slots start on 
 
 // Gauss-Seidel value of the staged cell at float index fi of the e plane E
 // (old or new e; its rho plane lies kESlots e planes further on), with the
-// planes below / above DM / DP floats away (taken when lo / hi: not through a
-// wall) and the cell's r: e = (sum_nb b e_nb - r h^2) / sum_nb b with b = 2 /
+// cell's rho rc, the rho and e of the cells below (hm, em) and above (hp, ep)
+// (taken when lo / hi: not through a wall) and the cell's r: e = (sum_nb b e_nb - r h^2) / sum_nb b with b = 2 /
 // (rho_c + rho_nb), formed as (sum_nb b' e_nb - r h^2 / 2) / sum_nb b' with
 // b' = b / 2 = 1 / (rho_c + rho_nb) (ops::rcp_approx), terms in the order x-,
 // x+, y-, y+, z-, z+; h2h = h^2 / 2
-template <int DM, int DP>
-__device__ __forceinline__ float cell_update(const float* E, int fi, bool lo, bool hi, float rcen, float h2h) {
+__device__ __forceinline__ float cell_update(const float* E, int fi, float rc, bool lo, float hm, float em, bool hi,
+                                             float hp, float ep, float rcen, float h2h) {
     constexpr int HO = kESlots * kEPlane;
-    const float rc = E[HO + fi];
     const float b0 = ops::rcp_approx(rc + E[HO + fi - 1]), b1 = ops::rcp_approx(rc + E[HO + fi + 1]);
     float bsum = b0 + b1;
     float off = b0 * E[fi - 1] + b1 * E[fi + 1];
@@ -93,14 +92,14 @@ __device__ __forceinline__ float cell_update(const float* E, int fi, bool lo, bo
     bsum += b2 + b3;
     off += b2 * E[fi - kRowF] + b3 * E[fi + kRowF];
     if (lo) {
-        const float b = ops::rcp_approx(rc + E[HO + DM + fi]);
+        const float b = ops::rcp_approx(rc + hm);
         bsum += b;
-        off += b * E[DM + fi];
+        off += b * em;
     }
     if (hi) {
-        const float b = ops::rcp_approx(rc + E[HO + DP + fi]);
+        const float b = ops::rcp_approx(rc + hp);
         bsum += b;
-        off += b * E[DP + fi];
+        off += b * ep;
     }
     return (off - rcen * h2h) * ops::rcp_approx(bsum);
 }
@@ -268,6 +267,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
     // black cells of plane k.  e / rho plane k + j sits in slot (u + j) mod 6
     // and r plane k + j in slot (u + j) mod 6.  With TMA, plane k + 2 is call
     // 6 m + u + 2 of mbarrier (u + 2) mod 6, phase m + (u >= 4).
+    float prev_red = 0.f;  // this thread's red value of the previous step
     auto step = [&](auto uc, int k, unsigned ph) {
         constexpr int u = decltype(uc)::value;
         constexpr int sM = (u + 5) % 6, s0 = u, s1 = (u + 1) % 6, s2 = (u + 2) % 6;
@@ -280,14 +280,26 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
         // e / rho plane k-2 and r plane k-3 were last read before this step:
         // their slots take the planes two steps ahead
         issue(k + 2 + kPD, k + 1 + kPD, (u + 4) % 6, (u + 3) % 6);
-        // red cells of plane kr = k+1 on the tile and its one-cell ring
+        // red cells of plane kr = k+1 on the tile and its one-cell ring.  A
+        // tile thread's black cell of plane k lies in the same column (x, y) as
+        // its red cell of plane k+1, and the pair's red cell of plane k is the
+        // one it updated in the previous step: those values pass in registers.
+        constexpr int HO = kESlots * kEPlane;
         const int kr = k + 1;
-        if (kr >= 0 && kr < nz && red_row >= 0) {
+        float v_red = 0.f, rc_red = 0.f, hm_red = 0.f;
+        const bool red_here = kr >= 0 && kr < nz;
+        if (red_here && red_row >= 0) {
             const int fi = fr[u & 1];
+            const float* E = Es + s1 * kEPlane;
+            const bool lo = kr > 0, hi = kr < nz - 1;
+            rc_red = E[HO + fi];
+            hm_red = lo ? Es[HO + s0 * kEPlane + fi] : 0.f;
+            const float em = lo ? Es[s0 * kEPlane + fi] : 0.f;
+            const float hp = hi ? Es[HO + s2 * kEPlane + fi] : 0.f;
+            const float ep = hi ? Es[s2 * kEPlane + fi] : 0.f;
             const float rcen = Rs[s1 * kRSlotF + rr[u & 1]];
-            const float v = cell_update<(s0 - s1) * kEPlane, (s2 - s1) * kEPlane>(Es + s1 * kEPlane, fi, kr > 0,
-                                                                                  kr < nz - 1, rcen, h2h);
-            Es[s1 * kEPlane + fi] = v;
+            v_red = cell_update(E, fi, rc_red, lo, hm_red, em, hi, hp, ep, rcen, h2h);
+            Es[s1 * kEPlane + fi] = v_red;
             // the slot is refilled by TMA later on: order this generic write before it
             if (MODE != kSweepFromZero && tma) fence_proxy_async();
         }
@@ -295,10 +307,15 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
         // black cells of plane k on the tile, written out with their red partners
         if (k >= z0 && black_thread) {
             const int t = tb[u & 1];
+            const int fi = fb + t;  // = fr[u & 1]
+            const float* E = Es + s0 * kEPlane;
+            const bool lo = k > 0, hi = k < nz - 1;  // hi: the red update of plane k+1 ran
+            const float rc = red_here ? hm_red : E[HO + fi];
+            const float hm = lo ? Es[HO + sM * kEPlane + fi] : 0.f;
+            const float em = lo ? Es[sM * kEPlane + fi] : 0.f;
             const float rcen = Rs[s0 * kRSlotF + rb + t];
-            const float v = cell_update<(sM - s0) * kEPlane, (s1 - s0) * kEPlane>(Es + s0 * kEPlane, fb + t, k > 0,
-                                                                                  k < nz - 1, rcen, h2h);
-            const float red = Es[s0 * kEPlane + fb + 1 - t];  // the pair's red value is in place
+            const float v = cell_update(E, fi, rc, lo, hm, em, hi, rc_red, v_red, rcen, h2h);
+            const float red = prev_red;  // the pair's red value of plane k
             const float2 out = t == 0 ? make_float2(v, red) : make_float2(red, v);
             if (MODE == kSweepUpdate) {  // the V-cycle's last sweep: e is not read again
                 p_add_pair(pp, out);
@@ -308,6 +325,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
                 o2 += NPh;
             }
         }
+        prev_red = v_red;
     };
     unsigned ph = 0;
     for (int kb = z0 - 2; kb < z1; kb += 6, ph ^= 1u) {

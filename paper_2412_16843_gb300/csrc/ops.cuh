@@ -807,19 +807,28 @@ template <> struct SumAcc<float> {
     __device__ __forceinline__ double value() const { return dfl::to_double(s); }
 };
 
-// S += b (x - y) for double-floats x, y, an FP32 coefficient b and the
-// double-float accumulator (Sh, Sl)
-__device__ __forceinline__ void df_acc_term(float b, float2 x, float2 y, float& Sh, float& Sl) {
+// the flux b (x - y) for double-floats x, y and an FP32 coefficient b, as an
+// unevaluated sum t + te (every step is odd in (x, y): swapping them negates t
+// and te exactly)
+__device__ __forceinline__ void df_term(float b, float2 x, float2 y, float& t, float& te) {
     float d, de;
     dfl::two_sum(x.x, -y.x, d, de);
     const float dl = __fadd_rn(de, __fsub_rn(x.y, y.y));
-    float t, te;
     dfl::two_prod(b, d, t, te);
     te = __fmaf_rn(b, dl, te);
+}
+// (Sh, Sl) += t + te
+__device__ __forceinline__ void df_acc(float t, float te, float& Sh, float& Sl) {
     float s2, se;
     dfl::two_sum(Sh, t, s2, se);
     Sh = s2;
     Sl = __fadd_rn(Sl, __fadd_rn(se, te));
+}
+// S += b (x - y) into the double-float accumulator (Sh, Sl)
+__device__ __forceinline__ void df_acc_term(float b, float2 x, float2 y, float& Sh, float& Sl) {
+    float t, te;
+    df_term(b, x, y, t, te);
+    df_acc(t, te, Sh, Sl);
 }
 
 // (f - mean) - S / h^2 for the double-float flux sum S = (Sh, Sl), rounded to FP32
