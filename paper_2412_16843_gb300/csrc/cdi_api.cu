@@ -711,6 +711,7 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     // measured fastest a step: V(1,1) on single 2D grids, V(1,2) on 3D grids
     c->npre = 1;
     c->npost = (dim == 2) ? 1 : 2;
+    c->mg.omega = 1.f;
     // one clamp rule for both precisions, representable in FP32 (1 - delta
     // must differ from 1): phi in [1e-6, 1 - 1e-6] for psi and every phi(1-phi)
     // factor, |grad psi| floored at 1e-6
@@ -781,6 +782,10 @@ cdi_status cdi_bind_workspace(cdi_ctx* c, void* dev_ptr, size_t bytes, void* str
     if (!c->host_scal) {
         cdi_status st = cuda_check(c, cudaMallocHost((void**)&c->host_scal, S_NSCAL * sizeof(double)),
                                    "cudaMallocHost");
+        if (st) return st;
+    }
+    if (mom_tile_supported(c->g)) {
+        cdi_status st = cuda_check(c, mom_tile_prepare(), "tiled momentum setup");
         if (st) return st;
     }
     cdi_status st = cuda_check(c, cudaMemsetAsync(c->ws, 0, c->ws_bytes - 256, c->stream), "cudaMemsetAsync");
@@ -971,6 +976,19 @@ cdi_status cdi_last_pressure(cdi_ctx* c, double* f, double* p) {
     }
     if (p) st = download_level0(c, p, true);
     return st;
+}
+
+cdi_status cdi_set_relaxation(cdi_ctx* c, double omega) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    if (!(omega > 0.0 && omega < 2.0)) return fail(c, CDI_EINVAL, "relaxation must lie in (0, 2)");
+    c->mg.omega = (float)omega;
+    // the V-cycle graphs hold the kernels' arguments
+    for (int k = 0; k < 2; ++k)
+        if (c->vc_exec[k]) {
+            cudaGraphExecDestroy(c->vc_exec[k]);
+            c->vc_exec[k] = nullptr;
+        }
+    return CDI_OK;
 }
 
 cdi_status cdi_set_smoothing(cdi_ctx* c, int npre, int npost) {

@@ -242,6 +242,9 @@ struct MG {
     // fills the GPU, 1 one-pass sweeps wherever the tile shape fits, 2 colour
     // passes, 3 one-pass sweeps staged by cp.async only
     int sweep_mode;
+    // relaxation of the finest level's red-black sweeps on the launch-per-kernel
+    // path: e <- e + omega (e_GS - e); 1 is Gauss-Seidel
+    float omega;
     // tensor maps of the one-pass sweep's level-0 arrays (host memory; null
     // or not encoded: cp.async staging)
     const struct SweepMaps* maps;
@@ -305,8 +308,14 @@ bool sweep0_auto(const Geom& g);       // it fits and the grid fills the GPU
 cudaError_t sweep0_prepare();
 void sweep0_encode_maps(const MGLevel& L0, SweepMaps* maps);  // maps->ok false if TMA is unavailable
 template <typename T>
-void launch_sweep0(const MGLevel& L0, const SweepMaps* maps, const float* ein, float* eout, int mode, PT<T>* p,
-                   double* err, cudaStream_t s);
+void launch_sweep0(const MGLevel& L0, const SweepMaps* maps, const float* ein, float* eout, int mode, float omega,
+                   PT<T>* p, double* err, cudaStream_t s);
+// tiled 3D momentum right-hand side (k_mom.cu): nx a multiple of 32, ny of 8;
+// mom_tile_prepare sets its shared-memory size (once per process and device)
+bool mom_tile_supported(const Geom& g);
+cudaError_t mom_tile_prepare();
+template <typename T>
+void launch_mom_tile(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaStream_t s);
 // tiled level-0 residual of the FP32-mixed form on 3D grids (k_resid.cu): r
 // and one |r|^2 partial a CTA (at most max_parts); returns the partial count
 bool resid_tile_supported(const Geom& g, int max_parts);

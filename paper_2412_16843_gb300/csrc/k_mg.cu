@@ -10,9 +10,12 @@
 //                    adjacent cells, zero on the walls
 //   k_resid          residual r = f - A p in the form's precision, |r|^2,
 //                    FP32 copy of r
-//   k_rbgs           FP32 red-black Gauss-Seidel sweep of A e = r
+//   k_rbgs_rows      FP32 red-black Gauss-Seidel colour pass of A e = r on a
+//                    coarse level (row-mapped; level 0: k_rbgs0, or the
+//                    one-pass sweep of k_sweep.cu)
 //   k_resid_restrict FP32 residual and its restriction (mean of the 2^D children)
-//   k_prolong        FP32 cell-centred (bi/tri)linear prolongation
+//   k_prolong        FP32 cell-centred (bi/tri)linear prolongation (3D grids of
+//                    32 x 8 columns: k_prolong0_3)
 //   k_coarse         FP64 dense solve of the coarsest level in one CTA
 //   k_update         p += e (FP64, or double-float in the FP32-mixed form) where
 //                    the V-cycle's last level-0 sweep does not add it
@@ -192,12 +195,54 @@ __global__ void k_resid(MGLevel L0, const float* fmean_df, double* part) {
     if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
+// row-mapped colour passes (k_rbgs_rows, k_rbgs0): blocks of 64 pairs x 4 rows
+constexpr int kSweepX = 64, kSweepY = 4;
+
+// One colour of a coarse level's red-black sweep with the arithmetic of
+// ops::rbgs_at (stencil_L's terms x, y, z with the stored face coefficients,
+// then step_div) on the row-mapped thread grid of k_rbgs0: thread (ix, j, k)
+// updates cell 2 ix + ((colour + j + k) & 1) of row (j, k), so no index is
+// decoded.
 template <int DIM>
-__global__ void k_rbgs(Geom g, const float* b0, const float* b1, const float* b2, float* e, const float* r,
-                       int colour) {
-    const float* beta[3] = {b0, b1, b2};
-    long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < g.N / 2) ops::rbgs_at<Ld, float, DIM>(g, beta, e, r, ops::colour_cell(g, colour, k));
+__global__ void __launch_bounds__(kSweepX * kSweepY)
+    k_rbgs_rows(Geom g, const float* __restrict__ b0, const float* __restrict__ b1, const float* __restrict__ b2,
+                float* __restrict__ e, const float* __restrict__ r, int colour) {
+    const int nx = g.n[0], ny = g.n[1];
+    const int ix = blockIdx.x * kSweepX + threadIdx.x;
+    const int j = blockIdx.y * kSweepY + threadIdx.y;
+    const int k = (DIM == 3) ? (int)blockIdx.z : 0;
+    if (2 * ix >= nx || j >= ny) return;
+    const int i = 2 * ix + ((colour + j + k) & 1);
+    const long row = (long)nx * ((long)j + (long)ny * k);
+    const long c = row + i;
+    const float ih2 = g.ih2f;
+    float diag = 0.f, off = 0.f;
+    {  // x (periodic)
+        const long lo = row + (i == 0 ? nx - 1 : i - 1), hi = row + (i == nx - 1 ? 0 : i + 1);
+        const float bm = b0[c], bp = b0[hi];
+        diag += (bm + bp) * ih2;
+        off += (bm * e[lo] + bp * e[hi]) * ih2;
+    }
+    if (DIM == 3) {  // y (periodic), then z (walls)
+        const long lo = (j == 0) ? c + (long)(ny - 1) * nx : c - nx;
+        const long hi = (j == ny - 1) ? c - (long)(ny - 1) * nx : c + nx;
+        const float bm = b1[c], bp = b1[hi];
+        diag += (bm + bp) * ih2;
+        off += (bm * e[lo] + bp * e[hi]) * ih2;
+        const long np = g.NP;
+        const bool wlo = k == 0, whi = k == g.n[2] - 1;
+        const float bmz = b2[c], bpz = b2[c + np];
+        const float pm = wlo ? 0.f : e[c - np], pp = whi ? 0.f : e[c + np];
+        diag += (bmz + bpz) * ih2;
+        off += (bmz * pm + bpz * pp) * ih2;
+    } else {  // y (walls)
+        const bool wlo = j == 0, whi = j == ny - 1;
+        const float bm = b1[c], bp = b1[c + nx];
+        const float pm = wlo ? 0.f : e[c - nx], pp = whi ? 0.f : e[c + nx];
+        diag += (bm + bp) * ih2;
+        off += (bm * pm + bp * pp) * ih2;
+    }
+    e[c] = ops::step_div(off - r[c], diag);
 }
 
 // Level-0 red-black sweep of one colour on a (x/2, y, z) thread grid: thread
@@ -212,11 +257,11 @@ __global__ void k_rbgs(Geom g, const float* b0, const float* b1, const float* b2
 // zero (e is not cleared beforehand: every cell of e is written before it is
 // read).  kSweepUpdate: the last black pass, which also adds the now final
 // correction of both cells of the thread's pair (2 ix, 2 ix + 1) to p.
-constexpr int kSweepX = 64, kSweepY = 4;
 template <typename T, int DIM, int MODE>
 __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float* __restrict__ rho,
                                                              float* __restrict__ e, const float* __restrict__ r,
-                                                             int colour, float h2h, PT<T>* __restrict__ p) {
+                                                             int colour, float h2h, float omega,
+                                                             PT<T>* __restrict__ p) {
     const int nx = g.n[0], ny = g.n[1];
     const int ix = blockIdx.x * kSweepX + threadIdx.x;
     const int j = blockIdx.y * kSweepY + threadIdx.y;
@@ -264,7 +309,11 @@ __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float
             off += b * en(c + np);
         }
     }
-    const float ec = (off - r[c] * h2h) * ops::rcp_approx(bsum);
+    float ec = (off - r[c] * h2h) * ops::rcp_approx(bsum);
+    if (omega != 1.f) {  // over-relaxation from the cell's old value
+        const float eo = MODE == kSweepFromZero ? 0.f : e[c];
+        ec = eo + omega * (ec - eo);
+    }
     e[c] = ec;
     if (MODE == kSweepUpdate) {
         const long co = c ^ 1;  // the pair's other cell (row starts are even: nx is even)
@@ -777,7 +826,7 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
             const int out = cur == 0 ? 1 : 0;
             CDI_PROF(KC_RBGS0, s,
                      launch_sweep0<T>(L, maps, cur < 0 ? nullptr : buf[cur], buf[out],
-                                      cur < 0 ? kSweepFromZero : kSweepPlain, p, err, s));
+                                      cur < 0 ? kSweepFromZero : kSweepPlain, mg.omega, p, err, s));
             ++g_launches;
             cur = out;
         }
@@ -789,7 +838,7 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
             const int out = 1 - cur;
             CDI_PROF(KC_RBGS0, s,
                      launch_sweep0<T>(L, maps, buf[cur], buf[out], it == npost - 1 ? kSweepUpdate : kSweepPlain,
-                                      p, err, s));
+                                      mg.omega, p, err, s));
             ++g_launches;
             cur = out;
         }
@@ -805,18 +854,19 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
             if (mode == kSweepFromZero)
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepFromZero><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                              col, h2h, p)));
+                                                                                              col, h2h, mg.omega, p)));
             else if (mode == kSweepUpdate)
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepUpdate><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                            col, h2h, p)));
+                                                                                            col, h2h, mg.omega, p)));
             else
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepPlain><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                           col, h2h, p)));
+                                                                                           col, h2h, mg.omega, p)));
         } else {
             CDI_PROF(kc_rbgs, s,
-                     (k_rbgs<DIM><<<nbh, kThreads, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r, col)));
+                     (k_rbgs_rows<DIM><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r,
+                                                                           col)));
         }
         ++g_launches;
     };
@@ -831,12 +881,7 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
                                                                      C.r, C.e);
     ++g_launches;
     vcycle_rec<T, DIM>(mg, p, l + 1, npre, npost, s);
-    if (l == 0) {
-        launch_prolong0<DIM>(L, C, L.e, s);
-    } else {
-        k_prolong<DIM><<<nb, kThreads, 0, s>>>(L.g, C.g, C.e, L.e);
-        ++g_launches;
-    }
+    launch_prolong0<DIM>(L, C, L.e, s);  // any level: the column kernel where the shape fits
     for (int it = 0; it < npost; ++it)
         for (int col = 0; col < 2; ++col)
             sweep(col, (l == 0 && it == npost - 1 && col == 1) ? kSweepUpdate : kSweepPlain);

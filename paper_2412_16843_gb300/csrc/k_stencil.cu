@@ -188,89 +188,6 @@ __global__ void __launch_bounds__(256) k_phi_rhs3(Geom g, PhysDev ph, StageField
     }
 }
 
-// 3D momentum right-hand side with the arithmetic of ops::mom_at (the same
-// terms in the same order), one thread per (x, y) column marching over kMomZ
-// planes: the neighbour offsets (periodic wraps in x and y) are formed once
-// per thread instead of decoding and shifting a cell index for each of the
-// ~150 neighbour reads of a cell.  Blocks of 32 x 8 columns; nx a multiple of
-// 32 and ny of 8.
-constexpr int kMomZ = 8;
-template <typename T>
-__global__ void __launch_bounds__(256, 3) k_mom3(Geom g, PhysDev ph, StageFields<T> f) {
-    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const long NP = g.NP;
-    const T ih = g_ih<T>(g);
-    const T dmu = phys<T>(ph).dmu, mu2 = phys<T>(ph).mu2;
-    // offsets of the low (0) and high (1) neighbour along each axis
-    long d[3][2];
-    d[0][0] = i == 0 ? nx - 1 : -1;
-    d[0][1] = i == nx - 1 ? -(long)(nx - 1) : 1;
-    d[1][0] = j == 0 ? (long)(ny - 1) * nx : -(long)nx;
-    d[1][1] = j == ny - 1 ? -(long)(ny - 1) * nx : (long)nx;
-    d[2][0] = -NP;
-    d[2][1] = NP;
-    const T* phi = f.phi;
-    auto mu = [&](long cc) { return dmu * __ldg(phi + cc) + mu2; };
-    const long pidx = (long)i + (long)nx * j;
-    const int k0 = blockIdx.z * kMomZ, k1 = min(k0 + kMomZ, nz);
-    for (int k = k0; k < k1; ++k) {
-        const long c = pidx + (long)k * NP;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const T* ua = f.u[a];
-            if (a == 2 && k == 0) { f.rm[a][c] = T(0); continue; }  // wall face
-            const long ea = d[a][0];                               // c - e_a = c + ea
-            const long cR = c, cL = c + ea;
-            T adv = T(0), vis = T(0);
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                if (b == a) {
-                    const long fRlo = c, fRhi = c + d[a][1], fLlo = cL, fLhi = c;
-                    const T* ma = f.m[a];
-                    const T uRlo = __ldg(ua + fRlo), uRhi = __ldg(ua + fRhi), uLlo = __ldg(ua + fLlo);
-                    T mbR = T(0.5) * (__ldg(ma + fRlo) + __ldg(ma + fRhi)), ubR = T(0.5) * (uRlo + uRhi);
-                    T mbL = T(0.5) * (__ldg(ma + fLlo) + __ldg(ma + fLhi)), ubL = T(0.5) * (uLlo + uRlo);
-                    T tR = T(2) * mu(cR) * (uRhi - uRlo) * ih;
-                    T tL = T(2) * mu(cL) * (uRlo - uLlo) * ih;
-                    adv -= (mbR * ubR - mbL * ubL) * ih;
-                    vis += (tR - tL) * ih;
-                } else {
-                    T conv[2], tau[2];
-#pragma unroll
-                    for (int side = 0; side < 2; ++side) {
-                        if (b == 2 && ((side == 0 && k == 0) || (side == 1 && k == nz - 1))) {
-                            const int s = side;  // the edge lies on wall s
-                            const long o = ((long)s * 2 + a) * NP + pidx;
-                            const T ug = __ldg(f.wghost + o), muw = __ldg(f.wmuw + o);
-                            const T u0 = __ldg(ua + c);
-                            conv[side] = T(0);
-                            tau[side] = (s == 0) ? muw * (u0 - ug) * ih : muw * (ug - u0) * ih;
-                            continue;
-                        }
-                        const long chi = side == 0 ? c : c + d[b][1];
-                        const long clo = side == 0 ? c + d[b][0] : c;
-                        const long chiA = chi + ea, cloA = clo + ea;
-                        const T uhi = __ldg(ua + chi), ulo = __ldg(ua + clo);
-                        const T ub = T(0.5) * (ulo + uhi);
-                        const T mb = T(0.5) * (__ldg(f.m[b] + chi) + __ldg(f.m[b] + chiA));
-                        conv[side] = mb * ub;
-                        const T me = T(0.25) * (mu(chi) + mu(chiA) + mu(clo) + mu(cloA));
-                        const T dub = (uhi - ulo) * ih;
-                        const T dua = (__ldg(f.u[b] + chi) - __ldg(f.u[b] + chiA)) * ih;
-                        tau[side] = me * (dub + dua);
-                    }
-                    adv -= (conv[1] - conv[0]) * ih;
-                    vis += (tau[1] - tau[0]) * ih;
-                }
-            }
-            // energy-based surface tension on the face (Eq. EB)
-            const T st = T(0.5) * (__ldg(f.muc + cL) + __ldg(f.muc + cR)) * (__ldg(phi + cR) - __ldg(phi + cL)) * ih;
-            f.rm[a][c] = adv + vis + st;
-        }
-    }
-}
-
 template <typename T>
 __global__ void k_stage_phi(long N, T b, T cdt, T dt, int first, int last, const T* phi0, const T* rphi, T* acc,
                             T* phik) {
@@ -324,9 +241,8 @@ void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaS
         } else {
             CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));
         }
-        if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
-            const dim3 grid((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kMomZ - 1) / kMomZ));
-            CDI_PROF(KC_MOM, s, (k_mom3<T><<<grid, dim3(32, 8), 0, s>>>(g, ph, f)));
+        if (mom_tile_supported(g)) {
+            CDI_PROF(KC_MOM, s, launch_mom_tile<T>(g, ph, f, s));
         } else {
             CDI_PROF(KC_MOM, s, (k_mom<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));
         }

@@ -125,7 +125,7 @@ struct IC {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kSweepThreads, 2)
     k_sweep0(Geom g, const float* __restrict__ rho, const float* __restrict__ ein, float* __restrict__ eout,
-             const float* __restrict__ r, float h2h, PT<T>* __restrict__ p, int zchunk,
+             const float* __restrict__ r, float h2h, float omega, PT<T>* __restrict__ p, int zchunk,
              const __grid_constant__ CUtensorMap tm_rho, const __grid_constant__ CUtensorMap tm_e,
              const __grid_constant__ CUtensorMap tm_r, int use_tma, double* __restrict__ err) {
     extern __shared__ __align__(128) float smf[];
@@ -299,6 +299,10 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
             const float ep = hi ? Es[s2 * kEPlane + fi] : 0.f;
             const float rcen = Rs[s1 * kRSlotF + rr[u & 1]];
             v_red = cell_update(E, fi, rc_red, lo, hm_red, em, hi, hp, ep, rcen, h2h);
+            if (omega != 1.f) {  // over-relaxation from the cell's old value
+                const float eo = E[fi];
+                v_red = eo + omega * (v_red - eo);
+            }
             Es[s1 * kEPlane + fi] = v_red;
             // the slot is refilled by TMA later on: order this generic write before it
             if (MODE != kSweepFromZero && tma) fence_proxy_async();
@@ -314,7 +318,11 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
             const float hm = lo ? Es[HO + sM * kEPlane + fi] : 0.f;
             const float em = lo ? Es[sM * kEPlane + fi] : 0.f;
             const float rcen = Rs[s0 * kRSlotF + rb + t];
-            const float v = cell_update(E, fi, rc, lo, hm, em, hi, rc_red, v_red, rcen, h2h);
+            float v = cell_update(E, fi, rc, lo, hm, em, hi, rc_red, v_red, rcen, h2h);
+            if (omega != 1.f) {
+                const float eo = E[fi];
+                v = eo + omega * (v - eo);
+            }
             const float red = prev_red;  // the pair's red value of plane k
             const float2 out = t == 0 ? make_float2(v, red) : make_float2(red, v);
             if (MODE == kSweepUpdate) {  // the V-cycle's last sweep: e is not read again
@@ -456,8 +464,8 @@ void sweep0_encode_maps(const MGLevel& L, SweepMaps* m) {
 // or, in update mode, p += the new e (eout not written: nothing reads it); interior tiles stage with TMA when maps is
 // non-null and encoded, a wait that runs out sets *err
 template <typename T>
-void launch_sweep0(const MGLevel& L, const SweepMaps* maps, const float* ein, float* eout, int mode, PT<T>* p,
-                   double* err, cudaStream_t s) {
+void launch_sweep0(const MGLevel& L, const SweepMaps* maps, const float* ein, float* eout, int mode, float omega,
+                   PT<T>* p, double* err, cudaStream_t s) {
     const Geom& g = L.g;
     const int zchunk = sweep0_zchunk(g);
     const dim3 grid((unsigned)(g.n[0] / kTX), (unsigned)(g.n[1] / kTY), (unsigned)((g.n[2] + zchunk - 1) / zchunk));
@@ -468,19 +476,19 @@ void launch_sweep0(const MGLevel& L, const SweepMaps* maps, const float* ein, fl
     const CUtensorMap& me = (ein == L.e2) ? m.e2 : m.e;
     const int ut = tma ? 1 : 0;
     if (mode == kSweepFromZero)
-        k_sweep0<T, kSweepFromZero><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, p, zchunk,
+        k_sweep0<T, kSweepFromZero><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, omega, p, zchunk,
                                                                             m.rho, me, m.r, ut, err);
     else if (mode == kSweepUpdate)
-        k_sweep0<T, kSweepUpdate><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, p, zchunk,
+        k_sweep0<T, kSweepUpdate><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, omega, p, zchunk,
                                                                           m.rho, me, m.r, ut, err);
     else
-        k_sweep0<T, kSweepPlain><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, p, zchunk,
+        k_sweep0<T, kSweepPlain><<<grid, kSweepThreads, kSweepSmem, s>>>(g, L.rho0, ein, eout, L.r, h2h, omega, p, zchunk,
                                                                          m.rho, me, m.r, ut, err);
 }
 
-template void launch_sweep0<double>(const MGLevel&, const SweepMaps*, const float*, float*, int, double*, double*,
-                                    cudaStream_t);
-template void launch_sweep0<float>(const MGLevel&, const SweepMaps*, const float*, float*, int, float2*, double*,
-                                   cudaStream_t);
+template void launch_sweep0<double>(const MGLevel&, const SweepMaps*, const float*, float*, int, float, double*,
+                                    double*, cudaStream_t);
+template void launch_sweep0<float>(const MGLevel&, const SweepMaps*, const float*, float*, int, float, float2*,
+                                   double*, cudaStream_t);
 
 }  // namespace cdi
