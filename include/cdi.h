@@ -218,8 +218,9 @@ cdi_status cdi_set_smoothing(cdi_ctx* ctx, int npre, int npost);
 
 /* Relaxation factor omega of the finest level's red-black sweeps on the
  * launch-per-kernel path: each update is e <- e + omega (e_GS - e), e_GS the
- * Gauss-Seidel value (omega in (0, 2); default 1: Gauss-Seidel).  A
- * preconditioner setting: the solve still iterates to its tolerance. */
+ * Gauss-Seidel value (omega in (0, 2); default 1.15 on 3D grids, 1 on 2D
+ * grids, where 1 is Gauss-Seidel).  A preconditioner setting: the solve
+ * still iterates to its tolerance. */
 cdi_status cdi_set_relaxation(cdi_ctx* ctx, double omega);
 
 /* Smoother kernel of the finest multigrid level of 3D grids on the

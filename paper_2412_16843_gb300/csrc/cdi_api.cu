@@ -225,11 +225,30 @@ unsigned nblk(long n) { return (unsigned)((n + 255) / 256); }
 // copy a host double array into a device field of the context's precision;
 // a value that is not finite (found on the device while converting or by a
 // check of the copy) returns CDI_ENAN, leaving the field undefined
+// Device address of a host buffer that kernels may read and write directly
+// (page-locked and mapped into the device's address space, e.g. from
+// cudaHostAlloc or a pinned torch tensor), or null for pageable memory, which
+// is copied through the staging buffer instead.
+const void* host_alias(const void* p) {
+    cudaPointerAttributes a{};
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 cdi_status upload(cdi_ctx* c, void* dst, const double* src, long n, const char* what) {
     double* bad = c->mg.scal + S_BADIN;
     cdi_status st = cuda_check(c, cudaMemsetAsync(bad, 0, sizeof(double), c->stream), "cudaMemsetAsync");
     if (st) return st;
-    if (c->precision == CDI_FP64) {
+    // mapped host memory: one pass that reads the host array over the link,
+    // checks it and stores it in the field's type
+    const double* hs = static_cast<const double*>(host_alias(src));
+    if (hs) {
+        if (c->precision == CDI_FP64) k_from_double<double><<<nblk(n), 256, 0, c->stream>>>(n, hs, (double*)dst, bad);
+        else k_from_double<float><<<nblk(n), 256, 0, c->stream>>>(n, hs, (float*)dst, bad);
+    } else if (c->precision == CDI_FP64) {
         st = cuda_check(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->stream),
                         "cudaMemcpyAsync(H2D)");
         if (st) return st;
@@ -251,7 +270,10 @@ cdi_status upload(cdi_ctx* c, void* dst, const double* src, long n, const char* 
 
 cdi_status download(cdi_ctx* c, double* dst, const void* src, long n) {
     if (!dst) return CDI_OK;
-    if (c->precision == CDI_FP64) {
+    double* hd = static_cast<double*>(const_cast<void*>(host_alias(dst)));
+    if (hd && c->precision != CDI_FP64) {  // mapped host memory: convert straight into it
+        k_to_double<float><<<nblk(n), 256, 0, c->stream>>>(n, (const float*)src, hd);
+    } else if (c->precision == CDI_FP64) {
         cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                                    "cudaMemcpyAsync(D2H)");
         if (st) return st;
@@ -269,14 +291,18 @@ cdi_status download(cdi_ctx* c, double* dst, const void* src, long n) {
 cdi_status download_level0(cdi_ctx* c, double* dst, bool pressure) {
     const Geom& g = c->g;
     const double* src = pressure ? c->mg.lv[0].p : c->mg.lv[0].f;
+    double* hd = static_cast<double*>(const_cast<void*>(host_alias(dst)));
     if (c->precision != CDI_FP64) {
-        if (pressure) launch_p_to_double(g, c->mg, c->xfer, c->stream);
-        else launch_f_to_double(g, c->mg, c->xfer, c->stream);
+        double* to = hd ? hd : c->xfer;  // mapped host memory: convert straight into it
+        if (pressure) launch_p_to_double(g, c->mg, to, c->stream);
+        else launch_f_to_double(g, c->mg, to, c->stream);
         src = c->xfer;
     }
-    cdi_status st = cuda_check(c, cudaMemcpyAsync(dst, src, g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                               "cudaMemcpyAsync(D2H)");
-    if (st) return st;
+    if (!hd || c->precision == CDI_FP64) {
+        cdi_status st = cuda_check(
+            c, cudaMemcpyAsync(dst, src, g.N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync(D2H)");
+        if (st) return st;
+    }
     return cuda_check(c, cudaStreamSynchronize(c->stream), "download");
 }
 
@@ -711,7 +737,9 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     // measured fastest a step: V(1,1) on single 2D grids, V(1,2) on 3D grids
     c->npre = 1;
     c->npost = (dim == 2) ? 1 : 2;
-    c->mg.omega = 1.f;
+    // 3D: over-relaxed finest-level sweeps, measured 4 % fewer V-cycles a step
+    // on the 512x256x256 drop for omega 1.1 .. 1.3 (1.4: more)
+    c->mg.omega = (dim == 3) ? 1.15f : 1.f;
     // one clamp rule for both precisions, representable in FP32 (1 - delta
     // must differ from 1): phi in [1e-6, 1 - 1e-6] for psi and every phi(1-phi)
     // factor, |grad psi| floored at 1e-6

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kSweepX * kSweepY)
 template <typename T, int DIM, int MODE>
 __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float* __restrict__ rho,
                                                              float* __restrict__ e, const float* __restrict__ r,
-                                                             int colour, float h2h, float omega,
+                                                             int colour, float h2h, float omega, int own_zero,
                                                              PT<T>* __restrict__ p) {
     const int nx = g.n[0], ny = g.n[1];
     const int ix = blockIdx.x * kSweepX + threadIdx.x;
@@ -309,11 +309,9 @@ __global__ void __launch_bounds__(kSweepX * kSweepY) k_rbgs0(Geom g, const float
             off += b * en(c + np);
         }
     }
-    float ec = (off - r[c] * h2h) * ops::rcp_approx(bsum);
-    if (omega != 1.f) {  // over-relaxation from the cell's old value
-        const float eo = MODE == kSweepFromZero ? 0.f : e[c];
-        ec = eo + omega * (ec - eo);
-    }
+    float ec = __fmul_rn(off - r[c] * h2h, ops::rcp_approx(bsum));
+    // over-relaxation from the cell's old value (zero in the first sweep of a V-cycle)
+    if (omega != 1.f) ec = ops::relax(MODE == kSweepFromZero || own_zero ? 0.f : e[c], ec, omega);
     e[c] = ec;
     if (MODE == kSweepUpdate) {
         const long co = c ^ 1;  // the pair's other cell (row starts are even: nx is even)
@@ -391,6 +389,72 @@ __global__ void __launch_bounds__(256) k_restrict0_3(Geom gf, Geom gc, const flo
                         const float bp = (whi ? 0.f : 1.f) * ops::rcp_approx(rcen + __ldg(rho + hi));
                         const float pm = wlo ? 0.f : __ldg(e + lo);
                         const float pp = whi ? 0.f : __ldg(e + hi);
+                        diag += (bm + bp) * ih2;
+                        off += (bm * pm + bp * pp) * ih2;
+                    }
+                    const float Lp = off - diag * __ldg(e + c);
+                    s += __ldg(r + c) - Lp;
+                }
+        const long t = tbase + (long)K * gc.NP;
+        rc[t] = s * (1.f / 8.f);
+        ec[t] = 0.f;
+    }
+}
+
+// Residual restriction of a coarse 3D level (stored face coefficients) with
+// the arithmetic of ops::resid_restrict_at (children in the order z, y, x;
+// each child's stencil_L terms x, y, z), one thread per coarse (x, y) column
+// marching over a z chunk with the fine neighbour offsets formed once:
+// r_c = mean of the children's r - A e, e_c = 0.  Coarse blocks of 32 x 8.
+__global__ void __launch_bounds__(256) k_restrict_bf3(Geom gf, Geom gc, const float* __restrict__ b0,
+                                                      const float* __restrict__ b1, const float* __restrict__ b2,
+                                                      const float* __restrict__ e, const float* __restrict__ r,
+                                                      float* __restrict__ rc, float* __restrict__ ec) {
+    const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y;
+    const int nx = gf.n[0], ny = gf.n[1], nz = gf.n[2];
+    const long NP = gf.NP;
+    const float ih2 = gf.ih2f;
+    // offsets of the x and y neighbours of the children 2I + t0, 2J + t1
+    long xm[2], xp[2], ym[2], yp[2];
+    xm[0] = 2 * I == 0 ? nx - 1 : -1;
+    xp[0] = 1;
+    xm[1] = -1;
+    xp[1] = 2 * I + 1 == nx - 1 ? -(long)(nx - 1) : 1;
+    ym[0] = 2 * J == 0 ? (long)(ny - 1) * nx : -(long)nx;
+    yp[0] = nx;
+    ym[1] = -(long)nx;
+    yp[1] = 2 * J + 1 == ny - 1 ? -(long)(ny - 1) * nx : (long)nx;
+    const long cbase = 2L * I + (long)nx * (2L * J);
+    const long tbase = (long)I + (long)gc.n[0] * J;
+    const int K0 = blockIdx.z * kRestrictZ, K1 = min(K0 + kRestrictZ, gc.n[2]);
+    for (int K = K0; K < K1; ++K) {
+        float s = 0.f;
+#pragma unroll
+        for (int t2 = 0; t2 < 2; ++t2)
+#pragma unroll
+            for (int t1 = 0; t1 < 2; ++t1)
+#pragma unroll
+                for (int t0 = 0; t0 < 2; ++t0) {
+                    const int k = 2 * K + t2;
+                    const long c = cbase + t0 + (long)nx * t1 + (long)k * NP;
+                    float diag = 0.f, off = 0.f;
+                    {
+                        const long lo = c + xm[t0], hi = c + xp[t0];
+                        const float bm = __ldg(b0 + c), bp = __ldg(b0 + hi);
+                        diag += (bm + bp) * ih2;
+                        off += (bm * __ldg(e + lo) + bp * __ldg(e + hi)) * ih2;
+                    }
+                    {
+                        const long lo = c + ym[t1], hi = c + yp[t1];
+                        const float bm = __ldg(b1 + c), bp = __ldg(b1 + hi);
+                        diag += (bm + bp) * ih2;
+                        off += (bm * __ldg(e + lo) + bp * __ldg(e + hi)) * ih2;
+                    }
+                    {
+                        const bool wlo = k == 0, whi = k == nz - 1;
+                        const float bm = __ldg(b2 + c), bp = __ldg(b2 + c + NP);
+                        const float pm = wlo ? 0.f : __ldg(e + c - NP);
+                        const float pp = whi ? 0.f : __ldg(e + c + NP);
                         diag += (bm + bp) * ih2;
                         off += (bm * pm + bp * pp) * ih2;
                     }
@@ -785,7 +849,8 @@ static void launch_restrict0(const MGLevel& L, MGLevel& C, const float* e, cudaS
 }
 template <int DIM>
 static void launch_prolong0(const MGLevel& L, const MGLevel& C, float* e, cudaStream_t s) {
-    if (DIM == 3 && L.g.n[0] % 32 == 0 && L.g.n[1] % 8 == 0) {
+    // the column kernel where its grid fills the GPU (smaller levels: one thread a cell)
+    if (DIM == 3 && L.g.n[0] % 32 == 0 && L.g.n[1] % 8 == 0 && L.g.N >= (1L << 21)) {
         const dim3 grid((unsigned)(L.g.n[0] / 32), (unsigned)(L.g.n[1] / 8),
                         (unsigned)((L.g.n[2] + kProlongZ - 1) / kProlongZ));
         CDI_PROF(KC_PROLONG0, s, (k_prolong0_3<<<grid, dim3(32, 8), 0, s>>>(L.g, C.g, C.e, e)));
@@ -849,20 +914,21 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
                           (unsigned)((L.g.n[1] + kSweepY - 1) / kSweepY), (unsigned)(DIM == 3 ? L.g.n[2] : 1));
     const dim3 sweep_block(kSweepX, kSweepY);
     const float h2h = 0.5f * (float)(L.g.h * L.g.h);
-    auto sweep = [&](int col, int mode) {
+    // first: a pass of the V-cycle's first sweep, whose old correction is zero
+    auto sweep = [&](int col, int mode, int first = 0) {
         if (l == 0) {
             if (mode == kSweepFromZero)
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepFromZero><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                              col, h2h, mg.omega, p)));
+                                                                                              col, h2h, mg.omega, first, p)));
             else if (mode == kSweepUpdate)
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepUpdate><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                            col, h2h, mg.omega, p)));
+                                                                                            col, h2h, mg.omega, first, p)));
             else
                 CDI_PROF(kc_rbgs, s,
                          (k_rbgs0<T, DIM, kSweepPlain><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.rho0, L.e, L.r,
-                                                                                           col, h2h, mg.omega, p)));
+                                                                                           col, h2h, mg.omega, first, p)));
         } else {
             CDI_PROF(kc_rbgs, s,
                      (k_rbgs_rows<DIM><<<sweep_grid, sweep_block, 0, s>>>(L.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r,
@@ -872,14 +938,20 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
     };
     for (int it = 0; it < npre; ++it)
         for (int col = 0; col < 2; ++col)
-            sweep(col, (l == 0 && it == 0 && col == 0) ? kSweepFromZero : kSweepPlain);
+            sweep(col, (l == 0 && it == 0 && col == 0) ? kSweepFromZero : kSweepPlain, l == 0 && it == 0);
     MGLevel& C = mg.lv[l + 1];
-    if (l == 0)
+    if (l == 0) {
         launch_restrict0<DIM>(L, C, L.e, s);
-    else
-        k_resid_restrict<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r,
-                                                                     C.r, C.e);
-    ++g_launches;
+    } else {
+        if (DIM == 3 && C.g.n[0] % 32 == 0 && C.g.n[1] % 8 == 0 && L.g.N >= (1L << 21))
+            k_restrict_bf3<<<dim3((unsigned)(C.g.n[0] / 32), (unsigned)(C.g.n[1] / 8),
+                                  (unsigned)((C.g.n[2] + kRestrictZ - 1) / kRestrictZ)),
+                             dim3(32, 8), 0, s>>>(L.g, C.g, L.bf[0], L.bf[1], L.bf[2], L.e, L.r, C.r, C.e);
+        else
+            k_resid_restrict<DIM><<<blocks_for(C.g.N), kThreads, 0, s>>>(L.g, C.g, L.bf[0], L.bf[1], L.bf[2], L.e,
+                                                                         L.r, C.r, C.e);
+        ++g_launches;
+    }
     vcycle_rec<T, DIM>(mg, p, l + 1, npre, npost, s);
     launch_prolong0<DIM>(L, C, L.e, s);  // any level: the column kernel where the shape fits
     for (int it = 0; it < npost; ++it)

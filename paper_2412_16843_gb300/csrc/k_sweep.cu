@@ -101,7 +101,7 @@ __device__ __forceinline__ float cell_update(const float* E, int fi, float rc, b
         bsum += b;
         off += b * ep;
     }
-    return (off - rcen * h2h) * ops::rcp_approx(bsum);
+    return __fmul_rn(off - rcen * h2h, ops::rcp_approx(bsum));
 }
 
 // p[0] += e.x, p[1] += e.y for two cells of a pair (16-byte aligned)
@@ -299,10 +299,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
             const float ep = hi ? Es[s2 * kEPlane + fi] : 0.f;
             const float rcen = Rs[s1 * kRSlotF + rr[u & 1]];
             v_red = cell_update(E, fi, rc_red, lo, hm_red, em, hi, hp, ep, rcen, h2h);
-            if (omega != 1.f) {  // over-relaxation from the cell's old value
-                const float eo = E[fi];
-                v_red = eo + omega * (v_red - eo);
-            }
+            if (omega != 1.f) v_red = ops::relax(E[fi], v_red, omega);  // over-relaxation from the old value
             Es[s1 * kEPlane + fi] = v_red;
             // the slot is refilled by TMA later on: order this generic write before it
             if (MODE != kSweepFromZero && tma) fence_proxy_async();
@@ -319,10 +316,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
             const float em = lo ? Es[sM * kEPlane + fi] : 0.f;
             const float rcen = Rs[s0 * kRSlotF + rb + t];
             float v = cell_update(E, fi, rc, lo, hm, em, hi, rc_red, v_red, rcen, h2h);
-            if (omega != 1.f) {
-                const float eo = E[fi];
-                v = eo + omega * (v - eo);
-            }
+            if (omega != 1.f) v = ops::relax(E[fi], v, omega);
             const float red = prev_red;  // the pair's red value of plane k
             const float2 out = t == 0 ? make_float2(v, red) : make_float2(red, v);
             if (MODE == kSweepUpdate) {  // the V-cycle's last sweep: e is not read again

@@ -661,6 +661,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// over-relaxed update e + omega (e_gs - e) from the old value e, every
+// rounding explicit (no contraction with the producer of e_gs)
+__device__ __forceinline__ float relax(float e, float egs, float omega) {
+    return __fmaf_rn(omega, __fsub_rn(egs, e), e);
+}
+
 // quotient of a smoothing step: the fast FP32 division (a preconditioner's
 // arithmetic; the defect correction iterates to the tolerance regardless)
 __device__ __forceinline__ float step_div(float a, float b) { return __fdividef(a, b); }
