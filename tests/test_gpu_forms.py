@@ -150,6 +150,14 @@ def test_pinned_host_buffers_give_the_same_state(precision):
         s.get_fields(fields)
         out.append([np.array(fields[0]), [np.array(v) for v in fields[1]], np.array(fields[2])])
         if pinned:
+            # a pinned array that starts 8 bytes past a 16-byte boundary
+            buf = torch.empty(phi.size + 1, dtype=torch.float64, pin_memory=True).numpy()
+            off = buf[1:].reshape(phi.shape)
+            off[...] = fields[0]
+            s.set_phi(off)
+            back = np.empty(s.cell_shape)
+            s.get_fields((back, [np.empty(s.face_shape(a)) for a in range(3)], np.empty(s.cell_shape)))
+            assert np.array_equal(back, fields[0])
             phi[3, 4, 5] = np.nan
             with pytest.raises(cdi.CdiError) as ei:
                 s.set_phi(phi)
