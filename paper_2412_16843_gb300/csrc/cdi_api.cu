@@ -222,7 +222,6 @@ __global__ void k_zero_wall_planes(long N, long NP, T* __restrict__ w) {
 
 unsigned nblk(long n) { return (unsigned)((n + 255) / 256); }
 
-
 // copy a host double array into a device field of the context's precision;
 // a value that is not finite (found on the device while converting or by a
 // check of the copy) returns CDI_ENAN, leaving the field undefined
