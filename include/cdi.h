@@ -373,10 +373,15 @@ cdi_status cdi_unet_forward_device(cdi_unet* net, const float* x, float* y);
 cdi_status cdi_unet_train_step(cdi_unet* net, const double* x, const double* target,
                                double lr, double* loss, double* grads);
 
-/* Kernel of the 3x3x3 convolutions (forward and data gradient): 1 (default)
- * the tcgen05 implicit GEMM (M = 128 voxels, accumulator in tensor memory,
- * input tile with halo staged once in shared memory for all 27 taps); 0 the
- * warp-level mma.sync implicit GEMM.  Both compute the same sums in FP32. */
+/* Kernels of the convolutions: 1 (default) the tcgen05 implicit GEMMs: the
+ * 3x3x3 forward and data gradient (M = 128 voxels, accumulator in tensor
+ * memory, input tile with halo staged once in shared memory for all 27 taps)
+ * and every layer's weight and bias gradient (M = 128 rows of taps x input
+ * channels plus a row of ones, N = output channels, K = voxels; voxel splits
+ * added in a fixed order, no atomics); 0 the warp-level mma.sync implicit
+ * GEMMs (weight gradients summed with FP32 atomics); 2 the tcgen05
+ * convolutions with the mma.sync weight gradients (to compare the two weight
+ * gradients on the same forward pass).  All compute the same sums in FP32. */
 cdi_status cdi_unet_set_conv_kernel(cdi_unet* net, int tensor_core);
 
 /* Last error of the network (NULL: of the last failed cdi_unet_create). */

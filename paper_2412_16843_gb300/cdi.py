@@ -456,9 +456,13 @@ class Unet:
         self._check(self.lib.cdi_unet_forward(self.h, _dp(xa), _dp(y)))
         return y
 
-    def set_conv_kernel(self, tensor_core: bool):
-        """3x3x3 convolutions on tcgen05 (True, default) or mma.sync (False)."""
-        self._check(self.lib.cdi_unet_set_conv_kernel(self.h, 1 if tensor_core else 0))
+    def set_conv_kernel(self, tensor_core):
+        """Convolutions and weight gradients on tcgen05 (True or 1, default),
+        everything on mma.sync (False or 0), or tcgen05 convolutions with the
+        mma.sync weight gradients (2)."""
+        mode = tensor_core if isinstance(tensor_core, int) and not isinstance(tensor_core, bool) else (
+            1 if tensor_core else 0)
+        self._check(self.lib.cdi_unet_set_conv_kernel(self.h, mode))
 
     def forward_device(self, x, y):
         """Device forward pass: torch float32 tensors x (..., 2) and y (...) on

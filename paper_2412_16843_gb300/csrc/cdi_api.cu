@@ -374,6 +374,7 @@ cdi_status kernels_tail_setup(cdi_ctx* c) {
         A.npre = c->npre;
         A.npost = c->npost;
         A.ainv = c->mg.ainv;
+        A.tail_bf_stored = 1;  // launch_mg_coef restricts the coefficients of every level once per solve
         st = cuda_check(c, cudaMemcpyAsync(c->tail_dev, &A, sizeof A, cudaMemcpyHostToDevice, c->stream),
                         "cudaMemcpyAsync(tail)");
         if (st) return st;

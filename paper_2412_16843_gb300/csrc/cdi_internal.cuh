@@ -392,6 +392,7 @@ struct __align__(16) InstArgs : PersistLayout {
     const float* ainv; // coarsest-level inverse in global memory (launch-per-kernel tail), or null:
                        // the tail inverts in shared memory at the first V-cycle of each solve
     void* colq;        // extrapolated wall-column quantities, [2 NP] (ops::ColQ<T>)
+    int tail_bf_stored;  // nonzero: the tail's top level's coefficients are in lv[lt].bf already
 };
 
 template <typename T>

@@ -134,6 +134,49 @@ __global__ void k_div(Geom g, const T* u0, const T* u1, const T* u2, T inv_cdt, 
     if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
+// k_div on FP32 3D grids with nx a multiple of 4: four cells of one x row an
+// iteration on float4 words (the x+ face of the fourth is the next quad's
+// first word, or the row's first across the periodic seam), the terms of
+// div_at in its order; the same fixed grid and per-block sums
+__global__ void k_div4(Geom g, const float* __restrict__ u0, const float* __restrict__ u1,
+                       const float* __restrict__ u2, float inv_cdt, float* __restrict__ f, double* part) {
+    const float ih = g.ihf;
+    const int nx = g.n[0], ny = g.n[1];
+    const long nq = g.N / 4;
+    ops::SumAcc<float> acc;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += stride) {
+        const long c = 4 * t;
+        const long line = c / nx;
+        const int i0 = (int)(c - line * nx);
+        const int j = (int)(line % ny);
+        const long row = line * nx;
+        const float4 a0 = __ldg(reinterpret_cast<const float4*>(u0 + c));
+        const float xe = __ldg(u0 + (i0 + 4 == nx ? row : c + 4));
+        const long yp = (j == ny - 1) ? c - (long)(ny - 1) * nx : c + nx;
+        const float4 b0 = __ldg(reinterpret_cast<const float4*>(u1 + c));
+        const float4 b1 = __ldg(reinterpret_cast<const float4*>(u1 + yp));
+        const float4 z0 = __ldg(reinterpret_cast<const float4*>(u2 + c));
+        const float4 z1 = __ldg(reinterpret_cast<const float4*>(u2 + c + g.NP));
+        const float ax[5] = {a0.x, a0.y, a0.z, a0.w, xe};
+        const float by0[4] = {b0.x, b0.y, b0.z, b0.w}, by1[4] = {b1.x, b1.y, b1.z, b1.w};
+        const float zz0[4] = {z0.x, z0.y, z0.z, z0.w}, zz1[4] = {z1.x, z1.y, z1.z, z1.w};
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float div = 0.f;
+            div += ax[e + 1] - ax[e];
+            div += by1[e] - by0[e];
+            div += zz1[e] - zz0[e];
+            o[e] = div * ih * inv_cdt;
+            acc.add(o[e]);
+        }
+        *reinterpret_cast<float4*>(f + c) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    const double a = block_sum(acc.value());
+    if (threadIdx.x == 0) part[blockIdx.x] = a;
+}
+
 // FP64 form: f -= mean, |f|^2
 __global__ void k_sub_mean_sq(long N, double* f, const double* mean_p, double* part) {
     const double mean = *mean_p;
@@ -168,6 +211,56 @@ __global__ void k_coef0(Geom g, PhysDev ph, const T* phi, double* b0, double* b1
     float* bf[3] = {f0, f1, f2};
     long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < g.N + g.NP) ops::coef0_at<Ld, T, DIM>(g, ph, phi, bs, bf, rho0, t);
+}
+
+// k_coef0 of the FP32-mixed form on 3D grids with nx a multiple of 4: four
+// cells of one x row a thread on float4 words (64 x-quads x 4 rows of one z
+// plane a block), the arithmetic of coef0_at term for term; the top plane's
+// threads also clear the high wall's faces above them
+constexpr int kCoefX = 64, kCoefY = 4;
+__global__ void __launch_bounds__(kCoefX * kCoefY)
+    k_coef0_4(Geom g, PhysDev ph, const float* __restrict__ phi, float* f0, float* f1, float* f2, float* rho0) {
+    const int q = blockIdx.x * kCoefX + threadIdx.x, j = blockIdx.y * kCoefY + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], k = blockIdx.z;
+    if (4 * q >= nx || j >= ny) return;
+    const long row = (long)nx * ((long)j + (long)ny * k);
+    const long c = row + 4L * q;
+    const float dr = phys<float>(ph).drho, rho2 = phys<float>(ph).rho2;
+    const float4 pc4 = __ldg(reinterpret_cast<const float4*>(phi + c));
+    const float pc[4] = {pc4.x, pc4.y, pc4.z, pc4.w};
+    *reinterpret_cast<float4*>(rho0 + c) =
+        make_float4(dr * pc[0] + rho2, dr * pc[1] + rho2, dr * pc[2] + rho2, dr * pc[3] + rho2);
+    float* bf[3] = {f0, f1, f2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a == 2 && k == 0) {  // low wall faces
+            *reinterpret_cast<float4*>(f2 + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        float pl[4];
+        if (a == 0) {
+            pl[0] = __ldg(phi + (q == 0 ? row + nx - 1 : c - 1));
+            pl[1] = pc[0];
+            pl[2] = pc[1];
+            pl[3] = pc[2];
+        } else {
+            const long cL = a == 1 ? ((j == 0) ? c + (long)(ny - 1) * nx : c - nx) : c - g.NP;
+            const float4 l4 = __ldg(reinterpret_cast<const float4*>(phi + cL));
+            pl[0] = l4.x;
+            pl[1] = l4.y;
+            pl[2] = l4.z;
+            pl[3] = l4.w;
+        }
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float rf = 0.5f * ((dr * pl[e] + rho2) + (dr * pc[e] + rho2));
+            o[e] = 1.f / rf;
+        }
+        *reinterpret_cast<float4*>(bf[a] + c) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    if (k == g.n[2] - 1)  // high wall faces
+        *reinterpret_cast<float4*>(f2 + c + g.NP) = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 template <int DIM>
@@ -615,6 +708,17 @@ __global__ void k_sub_mean_p(long N, PT<T>* p, const double* mean, const float* 
     else p[c] = ops::dfl::sub(p[c], make_float2(mean_df[0], mean_df[1]));
 }
 
+// the FP32-mixed form's p -= mean on 16-byte words (two double-float cells a
+// thread; N even)
+__global__ void k_sub_mean_p2(long N2, float4* p, const float* mean_df) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N2) return;
+    const float2 m = make_float2(mean_df[0], mean_df[1]);
+    const float4 v = p[t];
+    const float2 a = ops::dfl::sub(make_float2(v.x, v.y), m), b = ops::dfl::sub(make_float2(v.z, v.w), m);
+    p[t] = make_float4(a.x, a.y, b.x, b.y);
+}
+
 template <typename T>
 __global__ void k_p_extrap(long N, PT<T>* p, const PT<T>* hnew, const PT<T>* hold) {
     long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -661,6 +765,9 @@ __global__ void __launch_bounds__(256) k_project3(Geom g, PhysDev ph, const T* _
     const T ih = g_ih<T>(g), dr = phys<T>(ph).drho, rho2 = phys<T>(ph).rho2;
     const long pidx = (long)i + (long)nx * j;
     const int k0 = blockIdx.z * kProjectZ, k1 = min(k0 + kProjectZ, nz);
+    // the cell below (the z face's other side): the previous plane's values
+    T phib = k0 > 0 ? __ldg(phi + pidx + (long)(k0 - 1) * NP) : T(0);
+    PT<T> pb = k0 > 0 ? __ldg(p + pidx + (long)(k0 - 1) * NP) : PT<T>{};
     for (int k = k0; k < k1; ++k) {
         const long c = pidx + (long)k * NP;
         const T phic = __ldg(phi + c);
@@ -669,11 +776,15 @@ __global__ void __launch_bounds__(256) k_project3(Geom g, PhysDev ph, const T* _
         for (int a = 0; a < 3; ++a) {
             if (a == 2 && k == 0) continue;  // wall face stays zero
             const long cL = c + dm[a];
-            const T rf = T(0.5) * ((dr * __ldg(phi + cL) + rho2) + (dr * phic + rho2));
+            const T phiL = a == 2 ? phib : __ldg(phi + cL);
+            const PT<T> pL = a == 2 ? pb : __ldg(p + cL);
+            const T rf = T(0.5) * ((dr * phiL + rho2) + (dr * phic + rho2));
             const T beta = T(1) / rf;
-            const T dpv = ops::p_diff(pc, __ldg(p + cL)) * ih;
+            const T dpv = ops::p_diff(pc, pL) * ih;
             us[a][c] = us[a][c] - cdt * beta * dpv;
         }
+        phib = phic;
+        pb = pc;
     }
 }
 
@@ -770,9 +881,19 @@ __global__ void k_contact_line(int D, int nx, int nlines, double h, const double
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_div(const Geom& g, const T* const* us, double inv_cdt, MG& mg, cudaStream_t s) {
-    const unsigned G = red_blocks(g.D == 2 ? (const void*)k_div<T, 2> : (const void*)k_div<T, 3>, g.N);
     const bool on = prof_before(KC_DIV, s);
     FT<T>* f = ops::fbuf<T>(mg.lv[0]);
+    if constexpr (sizeof(T) == 4) {
+        if (g.D == 3 && g.n[0] % 4 == 0) {
+            const unsigned G4 = red_blocks((const void*)k_div4, g.N / 4);
+            k_div4<<<G4, kThreads, 0, s>>>(g, us[0], us[1], us[2], (float)inv_cdt, f, mg.partials);
+            prof_after(on, s);
+            k_final_sum<<<1, 1024, 0, s>>>(mg.partials, (int)G4, 1.0 / (double)g.N, mg.scal + S_MEAN, 0);
+            g_launches += 2;
+            return;
+        }
+    }
+    const unsigned G = red_blocks(g.D == 2 ? (const void*)k_div<T, 2> : (const void*)k_div<T, 3>, g.N);
     if (g.D == 2)
         k_div<T, 2><<<G, kThreads, 0, s>>>(g, us[0], us[1], nullptr, (T)inv_cdt, f, mg.partials);
     else
@@ -810,7 +931,13 @@ void launch_sub_mean_and_norm(const Geom& g, MG& mg, cudaStream_t s) {
 template <typename T>
 void launch_mg_coef(const Geom& g, const PhysDev& ph, const T* phi, MG& mg, cudaStream_t s) {
     MGLevel& L0 = mg.lv[0];
-    if (g.D == 2)
+    bool vec = false;
+    if constexpr (sizeof(T) == 4) vec = g.D == 3 && g.n[0] % 4 == 0;
+    if (vec)
+        k_coef0_4<<<dim3((unsigned)((g.n[0] / 4 + kCoefX - 1) / kCoefX), (unsigned)((g.n[1] + kCoefY - 1) / kCoefY),
+                         (unsigned)g.n[2]),
+                    dim3(kCoefX, kCoefY), 0, s>>>(g, ph, (const float*)phi, L0.bf[0], L0.bf[1], L0.bf[2], L0.rho0);
+    else if (g.D == 2)
         k_coef0<T, 2><<<blocks_for(g.N + g.NP), kThreads, 0, s>>>(g, ph, phi, L0.beta[0], L0.beta[1],
                                                                   nullptr, L0.bf[0], L0.bf[1], nullptr, L0.rho0);
     else
@@ -1007,8 +1134,12 @@ void launch_p_mean_remove(const Geom& g, MG& mg, cudaStream_t s) {
         k_mean_df<<<1, 1, 0, s>>>(mg.scal + S_MEAN, mg.scalf + SF_PMEAN_HI);
         ++g_launches;
     }
-    k_sub_mean_p<T><<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<T>(mg.lv[0]), mg.scal + S_MEAN,
-                                                        mg.scalf + SF_PMEAN_HI);
+    if (sizeof(T) == 4 && g.N % 2 == 0)
+        k_sub_mean_p2<<<blocks_for(g.N / 2), kThreads, 0, s>>>(g.N / 2, reinterpret_cast<float4*>(mg.lv[0].p),
+                                                                mg.scalf + SF_PMEAN_HI);
+    else
+        k_sub_mean_p<T><<<blocks_for(g.N), kThreads, 0, s>>>(g.N, ops::pbuf<T>(mg.lv[0]), mg.scal + S_MEAN,
+                                                            mg.scalf + SF_PMEAN_HI);
     g_launches += 3;
 }
 

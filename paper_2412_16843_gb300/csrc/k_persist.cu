@@ -204,11 +204,20 @@ __device__ void tail_vcycle(const InstArgs<T>& A, bool first, float* sm) {
         // coefficients of the tail levels (constant during one solve)
         const SmLevel top = sm_level<T, DIM>(A, sm, lt);
         const int ntop = (int)(top.g.N + top.g.NP);
-        if (lt == 0) {
+        if (lt == 0 || A.tail_bf_stored) {
+            // stored by an earlier phase or kernel of this solve: copied in
             for (int a = 0; a < DIM; ++a) {
                 const int nf = (int)(top.g.N + (a == DIM - 1 ? top.g.NP : 0));
-                const float* src = A.lv[0].bf[a];
-                for (int t = t0; t < nf; t += nt) top.b[a][t] = __ldcg(src + t);
+                const float* src = A.lv[lt].bf[a];
+                constexpr int U = 4;  // loads in flight per thread before the stores
+                for (int c0 = t0; c0 < nf; c0 += U * nt) {
+                    float v[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) v[u] = (c0 + u * nt < nf) ? __ldcg(src + c0 + u * nt) : 0.f;
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (c0 + u * nt < nf) top.b[a][c0 + u * nt] = v[u];
+                }
             }
         } else {
             const MGLevel F = A.lv[lt - 1];

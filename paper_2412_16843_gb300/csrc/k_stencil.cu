@@ -207,6 +207,125 @@ __global__ void k_stage_mom(Geom g, PhysDev ph, T b, T cdt, T dt, int first, int
     if (c < g.N) ops::stage_mom_at<Ld, T, DIM>(g, ph, b, cdt, dt, first, last, phi0, phik, u0.p, rm.p, acc.p, uk.p, c);
 }
 
+// FP32 3D grids with nx a multiple of 4: the elementwise stage kernels on
+// float4 words (four cells of one x row a thread, 16-byte loads and stores),
+// with the arithmetic of psi_at, stage_phi_at and stage_mom_at term for term.
+// Thread block: 64 x-quads x 4 rows of one z plane, so no index is decoded.
+constexpr int kVecX = 64, kVecY = 4;
+__device__ __forceinline__ float v4(const float4& a, int e) { return e == 0 ? a.x : e == 1 ? a.y : e == 2 ? a.z : a.w; }
+
+__global__ void __launch_bounds__(kVecX * kVecY) k_psi4(Geom g, PhysDev ph, const float* __restrict__ phi,
+                                                        float* __restrict__ psi) {
+    const int q = blockIdx.x * kVecX + threadIdx.x, j = blockIdx.y * kVecY + threadIdx.y;
+    if (4 * q >= g.n[0] || j >= g.n[1]) return;
+    const long c = 4L * q + (long)g.n[0] * ((long)j + (long)g.n[1] * blockIdx.z);
+    const PhysT<float>& P = phys<float>(ph);
+    const float4 f = __ldg(reinterpret_cast<const float4*>(phi + c));
+    float o[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float pt = clampv(v4(f, e), P.delta, 1.f - P.delta);
+        o[e] = P.eps * log(pt / (1.f - pt));
+    }
+    *reinterpret_cast<float4*>(psi + c) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+__global__ void __launch_bounds__(kVecX * kVecY) k_stage_phi4(Geom g, float b, float cdt, float dt, int first,
+                                                              int last, const float* __restrict__ phi0,
+                                                              const float* __restrict__ rphi, float* acc,
+                                                              float* phik) {
+    const int q = blockIdx.x * kVecX + threadIdx.x, j = blockIdx.y * kVecY + threadIdx.y;
+    if (4 * q >= g.n[0] || j >= g.n[1]) return;
+    const long c = 4L * q + (long)g.n[0] * ((long)j + (long)g.n[1] * blockIdx.z);
+    const float4 k4 = __ldg(reinterpret_cast<const float4*>(rphi + c));
+    const float4 p4 = __ldg(reinterpret_cast<const float4*>(phi0 + c));
+    const float4 a4 = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(acc + c);
+    float ao[4], po[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float k = v4(k4, e);
+        const float a = first ? b * k : v4(a4, e) + b * k;
+        ao[e] = a;
+        po[e] = last ? v4(p4, e) + dt * a : v4(p4, e) + cdt * k;
+    }
+    *reinterpret_cast<float4*>(acc + c) = make_float4(ao[0], ao[1], ao[2], ao[3]);
+    *reinterpret_cast<float4*>(phik + c) = make_float4(po[0], po[1], po[2], po[3]);
+}
+
+// the three faces of four cells: the low neighbours' phi (x: the word before,
+// or the row's last cell across the periodic seam; y, z: the quads one row and
+// one plane back, y periodic, z skipped on the wall plane)
+__global__ void __launch_bounds__(kVecX * kVecY)
+    k_stage_mom4(Geom g, PhysDev ph, float b, float cdt, float dt, int first, int last,
+                 const float* __restrict__ phi0, const float* __restrict__ phik, Ptr3<const float> u0,
+                 Ptr3<const float> rm, Ptr3<float> acc, Ptr3<float> uk) {
+    const int q = blockIdx.x * kVecX + threadIdx.x, j = blockIdx.y * kVecY + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], k = blockIdx.z;
+    if (4 * q >= nx || j >= ny) return;
+    const long row = (long)nx * ((long)j + (long)ny * k);
+    const long c = row + 4L * q;
+    const float drho = phys<float>(ph).drho, rho2 = phys<float>(ph).rho2;
+    const long xm = (q == 0) ? row + nx - 1 : c - 1;
+    const long ym = (j == 0) ? c + (long)(ny - 1) * nx : c - nx;
+    const float4 p0c = __ldg(reinterpret_cast<const float4*>(phi0 + c));
+    const float4 pkc = __ldg(reinterpret_cast<const float4*>(phik + c));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float* ua = uk.p[a];
+        float* aa = acc.p[a];
+        if (a == 2 && k == 0) {  // the wall face
+            *reinterpret_cast<float4*>(ua + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(aa + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        float p0L[4], pkL[4];
+        if (a == 0) {
+            p0L[0] = __ldg(phi0 + xm);
+            pkL[0] = __ldg(phik + xm);
+#pragma unroll
+            for (int e = 1; e < 4; ++e) {
+                p0L[e] = v4(p0c, e - 1);
+                pkL[e] = v4(pkc, e - 1);
+            }
+        } else {
+            const long cL = a == 1 ? ym : c - g.NP;
+            const float4 x0 = __ldg(reinterpret_cast<const float4*>(phi0 + cL));
+            const float4 xk = __ldg(reinterpret_cast<const float4*>(phik + cL));
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                p0L[e] = v4(x0, e);
+                pkL[e] = v4(xk, e);
+            }
+        }
+        const float4 uo = __ldg(reinterpret_cast<const float4*>(u0.p[a] + c));
+        const float4 kk = __ldg(reinterpret_cast<const float4*>(rm.p[a] + c));
+        const float4 ao = first ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(aa + c);
+        float an[4], un[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float rf0 = 0.5f * ((drho * p0L[e] + rho2) + (drho * v4(p0c, e) + rho2));
+            const float M0 = rf0 * v4(uo, e);
+            const float kv = v4(kk, e);
+            const float ac = first ? b * kv : v4(ao, e) + b * kv;
+            an[e] = ac;
+            const float Mv = last ? M0 + dt * ac : M0 + cdt * kv;
+            const float rfk = 0.5f * ((drho * pkL[e] + rho2) + (drho * v4(pkc, e) + rho2));
+            un[e] = Mv / rfk;
+        }
+        *reinterpret_cast<float4*>(aa + c) = make_float4(an[0], an[1], an[2], an[3]);
+        *reinterpret_cast<float4*>(ua + c) = make_float4(un[0], un[1], un[2], un[3]);
+    }
+}
+
+template <typename T>
+inline bool vec4_ok(const Geom& g) {
+    return sizeof(T) == 4 && g.D == 3 && g.n[0] % 4 == 0;
+}
+inline dim3 vec4_grid(const Geom& g) {
+    return dim3((unsigned)((g.n[0] / 4 + kVecX - 1) / kVecX), (unsigned)((g.n[1] + kVecY - 1) / kVecY),
+                (unsigned)g.n[2]);
+}
+
 }  // namespace
 
 // wall columns are FP64-heavy and few: small blocks spread them over the SMs
@@ -216,7 +335,14 @@ inline unsigned wall_blocks(const Geom& g) { return (unsigned)((2 * g.NP + kWall
 template <typename T>
 void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaStream_t s) {
     const unsigned nb = blocks_for(g.N);
-    CDI_PROF(KC_PSI, s, (k_psi<T><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi)));
+    if constexpr (sizeof(T) == 4) {
+        if (vec4_ok<T>(g))
+            CDI_PROF(KC_PSI, s, (k_psi4<<<vec4_grid(g), dim3(kVecX, kVecY), 0, s>>>(g, ph, f.phi, f.psi)));
+        else
+            CDI_PROF(KC_PSI, s, (k_psi<T><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi)));
+    } else {
+        CDI_PROF(KC_PSI, s, (k_psi<T><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi)));
+    }
     if (g.D == 2) {
         CDI_PROF(KC_CELL, s,
                  (k_cell<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f.phi, f.psi, f.nh[0], f.nh[1], nullptr, f.muc)));
@@ -259,10 +385,22 @@ void launch_stage_update(const Geom& g, const PhysDev& ph, int stage, double dt,
     const int first = stage == 0, last = stage == 3;
     const double cn = last ? 1.0 : ck[stage + 1];
     const unsigned nb = blocks_for(g.N);
-    CDI_PROF(KC_STAGE_PHI, s, (k_stage_phi<T><<<nb, kThreads, 0, s>>>(g.N, (T)bk[stage], (T)(cn * dt), (T)dt, first,
-                                                                       last, phi0, rphi, accphi, phik)));
     Ptr3<const T> pu0{{u0[0], u0[1], u0[2]}}, prm{{rm[0], rm[1], rm[2]}};
     Ptr3<T> pacc{{accm[0], accm[1], accm[2]}}, puk{{uk[0], uk[1], uk[2]}};
+    if constexpr (sizeof(T) == 4) {
+        if (vec4_ok<T>(g)) {
+            const dim3 grid = vec4_grid(g), block(kVecX, kVecY);
+            CDI_PROF(KC_STAGE_PHI, s, (k_stage_phi4<<<grid, block, 0, s>>>(g, (T)bk[stage], (T)(cn * dt), (T)dt,
+                                                                            first, last, phi0, rphi, accphi, phik)));
+            CDI_PROF(KC_STAGE_MOM, s, (k_stage_mom4<<<grid, block, 0, s>>>(g, ph, (T)bk[stage], (T)(cn * dt), (T)dt,
+                                                                            first, last, phi0, phik, pu0, prm, pacc,
+                                                                            puk)));
+            g_launches += 2;
+            return;
+        }
+    }
+    CDI_PROF(KC_STAGE_PHI, s, (k_stage_phi<T><<<nb, kThreads, 0, s>>>(g.N, (T)bk[stage], (T)(cn * dt), (T)dt, first,
+                                                                       last, phi0, rphi, accphi, phik)));
     if (g.D == 2)
         CDI_PROF(KC_STAGE_MOM, s, (k_stage_mom<T, 2><<<nb, kThreads, 0, s>>>(
                                       g, ph, (T)bk[stage], (T)(cn * dt), (T)dt, first, last, phi0, phik, pu0, prm,

@@ -678,6 +678,218 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(CG g, const bf16* __rest
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Weight and bias gradients on the tcgen05 tensor cores.
+//
+// dW[t][co][ci] = sum_v x[v + off(t)][ci] dy[v][co] and dB[co] = sum_v dy[v][co]
+// form one GEMM D[m][n] = sum_k A[m][k] B[n][k]: rows m = t Cin_pad + ci
+// (taps x padded input channels), then one row of ones (m = R = taps
+// Cin_pad) whose product is the bias gradient, further rows zero; columns n =
+// output channels (N = Cout_pad); K = voxels.  A CTA takes a block of 128
+// rows and a contiguous range of voxel chunks (a K split), accumulates
+// D[128][N] in tensor memory over chunks of kWgK voxels (eight MMAs of K =
+// 16 each, M = 128) and stores it as FP32 partial sums; k_wgrad_reduce adds
+// the splits in a fixed order, so no atomics are involved.  The operands
+// arrive channels-last, so staging transposes them into the canonical K-major
+// layout without swizzling (a core matrix is 8 rows of 16 bytes: 8 voxels of
+// one row): a thread loads the 16-byte 8-channel groups of 8 voxels and
+// stores eight 16-byte core-matrix rows, one per channel, after an 8 x 8
+// transpose in registers.  Core matrices of consecutive row groups are
+// kWgSbo = 272 bytes apart (not 256), so the eight threads of a store phase
+// hit different bank groups.  Chunks are double-buffered: the MMAs of one
+// chunk run while the next one is staged.  Waits are bounded and tensor
+// memory is released under the same rules as in k_conv_tc.
+// ---------------------------------------------------------------------------
+constexpr int kWgK = 128;        // voxels per chunk
+constexpr int kWgThreads = 128;
+constexpr int kWgSbo = 272;      // bytes between the core matrices of consecutive 8-row groups
+constexpr int kWgAStep = 16 * kWgSbo;   // bytes of one K = 16 step of A (16 row groups)
+constexpr int kWgABytes = (kWgK / 16) * kWgAStep;
+constexpr int kWgMaxCtas = 304;  // row blocks x splits of a launch (about two per SM)
+
+__host__ __device__ constexpr int wg_bstep(int N) { return (N / 8) * kWgSbo; }
+__host__ __device__ constexpr int wg_buf_bytes(int N) { return kWgABytes + (kWgK / 16) * wg_bstep(N); }
+
+// 8 x 8 transpose of BF16 values: in[e] holds channels 0..7 of voxel e, out[j]
+// voxels 0..7 of channel j (element i of a 16-byte group in bytes 2i, 2i+1)
+__device__ __forceinline__ void transpose8(const uint4* in, uint4* out) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(in);  // w[4 e + k]: channels 2k (low), 2k+1 of voxel e
+    uint32_t* o = reinterpret_cast<uint32_t*>(out);              // o[4 j + m]: voxels 2m (low), 2m+1 of channel j
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t a = w[4 * (2 * m) + k], b = w[4 * (2 * m + 1) + k];
+            o[4 * (2 * k) + m] = __byte_perm(a, b, 0x5410);
+            o[4 * (2 * k + 1) + m] = __byte_perm(a, b, 0x7632);
+        }
+}
+
+// Partial GEMM of row block blockIdx.x over voxel chunks [blockIdx.y cps,
+// (blockIdx.y + 1) cps) into part[(split nrb + rb) 128 + row][N] (FP32).
+// x: [voxel][cin_pad], dy: [voxel][N]; N a multiple of 16 in [16, 128].
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(CG g, const bf16* __restrict__ x, int cin_pad, int ntaps,
+                                                         const bf16* __restrict__ dy, int N, int cps,
+                                                         float* __restrict__ part, int ncols, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rb = blockIdx.x, nrb = gridDim.x;
+    const int bstep = wg_bstep(N), bufb = wg_buf_bytes(N);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = idesc_bf16(128, N);
+
+    const int R = ntaps * cin_pad;  // weight rows; row R is the row of ones
+    const int nchunks = (g.N + kWgK - 1) / kWgK;
+    const int ch0 = blockIdx.y * cps, nch = max(0, min(ch0 + cps, nchunks) - ch0);
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    bool unconfirmed[2] = {false, false};
+    uint32_t uphase[2] = {0u, 0u};
+    auto wait_mma = [&](int b) {
+        if (pending[b]) {
+            if (!mbar_wait_bounded(&mbar[b], phase[b])) {
+                s_abort = 1;
+                atomicExch(err, 1);
+                unconfirmed[b] = true;
+                uphase[b] = phase[b];
+            }
+            phase[b] ^= 1u;
+            pending[b] = false;
+        }
+    };
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    // stage chunk ch0 + c into buffer b
+    auto stage = [&](int c, int b) {
+        unsigned char* A = smem + b * bufb;
+        unsigned char* B = A + kWgABytes;
+        const int vbase = (ch0 + c) * kWgK;
+        // A: 16 row groups x kWgK / 8 voxel octets (consecutive threads: consecutive row groups)
+        for (int u = tid; u < 16 * (kWgK / 8); u += kWgThreads) {
+            const int gq = u & 15, o = u >> 4;
+            const int row0 = rb * 128 + gq * 8;
+            uint4 in[8];
+            if (row0 < R) {
+                const int tap = row0 / cin_pad, ci0 = row0 - tap * cin_pad;
+                int dz, dyy, dx;
+                tap_off(tap, ntaps, dz, dyy, dx);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int n = nbr(g, vox(g, vbase + 8 * o + e), dz, dyy, dx);
+                    in[e] = n >= 0 ? __ldg(reinterpret_cast<const uint4*>(x + (size_t)n * cin_pad + ci0)) : zero4;
+                }
+            } else {
+                // the row of ones (channel 0 of the group starting at row R), then zeros
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    in[e] = zero4;
+                    if (row0 == R && vbase + 8 * o + e < g.N) in[e].x = 0x3F80u;  // BF16 1.0 in element 0
+                }
+            }
+            uint4 out[8];
+            transpose8(in, out);
+            unsigned char* dst = A + (o >> 1) * kWgAStep + gq * kWgSbo + (o & 1) * 128;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(dst + j * 16) = out[j];
+        }
+        // B: N / 8 column groups x kWgK / 8 voxel octets
+        const int ng = N >> 3;
+        for (int u = tid; u < ng * (kWgK / 8); u += kWgThreads) {
+            const int gq = u % ng, o = u / ng;
+            uint4 in[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int v = vbase + 8 * o + e;
+                in[e] = v < g.N ? __ldg(reinterpret_cast<const uint4*>(dy + (size_t)v * N + gq * 8)) : zero4;
+            }
+            uint4 out[8];
+            transpose8(in, out);
+            unsigned char* dst = B + (o >> 1) * bstep + gq * kWgSbo + (o & 1) * 128;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(dst + j * 16) = out[j];
+        }
+    };
+
+    for (int c = 0; c < nch; ++c) {
+        const int b = c & 1;
+        wait_mma(b);  // the MMAs of chunk c - 2 read this buffer
+        stage(c, b);
+        fence_proxy_async();
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(smem + b * bufb), b0 = a0 + kWgABytes;
+#pragma unroll
+            for (int q = 0; q < kWgK / 16; ++q) {
+                const uint64_t ad = smem_desc(a0 + (uint32_t)(q * kWgAStep), 128, kWgSbo);
+                const uint64_t bd = smem_desc(b0 + (uint32_t)(q * bstep), 128, kWgSbo);
+                tc_mma(tmem, ad, bd, idesc, (c == 0 && q == 0) ? 0u : 1u);
+            }
+            tc_commit(&mbar[b]);
+        }
+        pending[b] = true;
+    }
+    for (int b = 0; b < 2; ++b) wait_mma(b);
+    __syncthreads();
+    if (!s_abort && nch > 0) {
+        tc_fence_after();
+        const int row = warp * 32 + lane;
+        float* dst = part + ((size_t)(blockIdx.y * nrb + rb) * 128 + row) * N;
+        for (int c0 = 0; c0 < N; c0 += 8) {
+            float v[8];
+            tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            *reinterpret_cast<float4*>(dst + c0) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(dst + c0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        }
+    }
+    // a phase whose wait gave up must be seen complete before the dealloc
+    for (int b = 0; b < 2; ++b)
+        if (unconfirmed[b] && !mbar_drain(&mbar[b], uphase[b])) atomicMax(err, 2);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// dW[t][co][ci] (ci < cin, co < cout) and dB[co] from the partial sums of the
+// nsplit voxel splits, added in split order
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int nsplit, int nrb, int N, int ntaps, int cin_pad,
+                               int cin, int cout, float* __restrict__ dW, float* __restrict__ dB) {
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int R = ntaps * cin_pad;
+    if (t >= (long)(R + 1) * cout) return;
+    const int n = (int)(t % cout);
+    const int m = (int)(t / cout);  // row, 0 .. R
+    const int rb = m >> 7, row = m & 127;
+    float s = 0.f;
+    for (int k = 0; k < nsplit; ++k) s += part[((size_t)(k * nrb + rb) * 128 + row) * N + n];
+    if (m == R) {
+        dB[n] = s;
+        return;
+    }
+    const int tap = m / cin_pad, ci = m - tap * cin_pad;
+    if (ci < cin) dW[((size_t)tap * cout + n) * cin + ci] = s;
+}
+
 }  // namespace
 }  // namespace cdi
 
@@ -698,11 +910,13 @@ struct cdi_unet {
     bf16 *x, *e0, *p0, *e1, *p1, *e2, *p2, *b, *c2, *d2, *c1, *d1, *c0, *d0;
     bf16 *gy, *gd0, *gc0, *gd1, *gc1, *gd2, *gc2, *gb, *gp2, *ge2, *gp1, *ge1, *gp0, *ge0;
     float *y, *t, *part;
+    float* wpart;  // FP32 partial sums of the tcgen05 weight gradients (voxel splits x rows x columns)
     double* x2;  // host-input staging [N][2]
     double* sd;  // prediction scales (FP64 and FP32 copies)
     float* sf;
     int* tc_err;          // set by a tcgen05 convolution whose bounded wait ran out
     bool use_tc = true;   // 3x3x3 convolutions on tcgen05 (else mma.sync)
+    bool wgrad_tc = true; // weight and bias gradients on tcgen05 (else mma.sync with FP32 atomics)
     long adam_t = 0;
     bool weights_ready = false;
     std::string err;
@@ -728,6 +942,25 @@ struct UCarver {
         return p;
     }
 };
+
+// level of the grid each layer works on (e0 e1 e2 b d2 d1 d0 head)
+constexpr int kLevelOf[kLayers] = {0, 1, 2, 3, 2, 1, 0, 0};
+
+// work split of the tcgen05 weight gradient of one layer: row blocks of 128
+// (taps x padded input channels, plus the row of ones), voxel splits of cps
+// chunks each (every split holds at least one chunk), about kWgMaxCtas CTAs
+struct WgPlan {
+    int nrb, nsplit, cps;
+};
+WgPlan wg_plan(int l, long nvox, int ci_pad) {
+    WgPlan p;
+    p.nrb = (kTaps[l] * ci_pad + 1 + 127) / 128;
+    const int nchunks = (int)std::max(1L, (nvox + kWgK - 1) / kWgK);
+    const int s = std::max(1, std::min(nchunks, (kWgMaxCtas + p.nrb - 1) / p.nrb));
+    p.cps = (nchunks + s - 1) / s;
+    p.nsplit = (nchunks + p.cps - 1) / p.cps;
+    return p;
+}
 
 void unet_carve(cdi_unet* u, char* base, size_t* total) {
     UCarver cv{base};
@@ -780,6 +1013,12 @@ void unet_carve(cdi_unet* u, char* base, size_t* total) {
     u->y = (float*)cv.take((size_t)N0 * 4);
     u->t = (float*)cv.take((size_t)N0 * 4);
     u->part = (float*)cv.take(256);
+    size_t wp = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const WgPlan p = wg_plan(l, u->g[kLevelOf[l]].N, pad16(kCin[l]));
+        wp = std::max(wp, (size_t)p.nsplit * p.nrb * 128 * pad16(kCout[l]));
+    }
+    u->wpart = (float*)cv.take(wp * 4);
     u->sd = (double*)cv.take(4 * sizeof(double));
     u->sf = (float*)cv.take(4 * sizeof(float));
     u->tc_err = (int*)cv.take(sizeof(int));
@@ -866,7 +1105,28 @@ void conv_dgrad(cdi_unet* u, int l, const CG& gl, const bf16* dy, bf16* dx) {
 #undef DG_CASE
 }
 
+// weight and bias gradients of layer l on the tcgen05 tensor cores (no atomics)
+void wgrad_tc(cdi_unet* u, int l, const CG& gl, const bf16* in, const bf16* dy) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * wg_buf_bytes(128));
+        attr = true;
+    }
+    const int N = u->co_pad[l];
+    const WgPlan p = wg_plan(l, gl.N, u->ci_pad[l]);
+    const int ncols = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+    k_wgrad_tc<<<dim3((unsigned)p.nrb, (unsigned)p.nsplit), kWgThreads, 2 * (size_t)wg_buf_bytes(N), u->stream>>>(
+        gl, in, u->ci_pad[l], kTaps[l], dy, N, p.cps, u->wpart, ncols, u->tc_err);
+    const long nt = (long)(kTaps[l] * u->ci_pad[l] + 1) * kCout[l];
+    k_wgrad_reduce<<<blocks(nt), 256, 0, u->stream>>>(u->wpart, p.nsplit, p.nrb, N, kTaps[l], u->ci_pad[l], kCin[l],
+                                                      kCout[l], u->gW[l], u->gB[l]);
+}
+
 void conv_wgrad(cdi_unet* u, int l, const CG& gl, const bf16* in, const bf16* dy) {
+    if (u->wgrad_tc) {
+        wgrad_tc(u, l, gl, in, dy);
+        return;
+    }
     const int chunk = 1024;
     dim3 grid((unsigned)kTaps[l], (unsigned)((u->co_pad[l] + 15) / 16), (unsigned)((gl.N + chunk - 1) / chunk));
     const int nf = u->ci_pad[l] / 8;
@@ -1233,8 +1493,9 @@ cdi_status cdi_unet_train_step(cdi_unet* u, const double* x_host, const double* 
 
 cdi_status cdi_unet_set_conv_kernel(cdi_unet* u, int tensor_core) {
     if (!u) return ufail(nullptr, CDI_EINVAL, "null network");
-    if (tensor_core != 0 && tensor_core != 1) return ufail(u, CDI_EINVAL, "tensor_core must be 0 or 1");
-    u->use_tc = tensor_core == 1;
+    if (tensor_core < 0 || tensor_core > 2) return ufail(u, CDI_EINVAL, "tensor_core must be 0, 1 or 2");
+    u->use_tc = tensor_core != 0;
+    u->wgrad_tc = tensor_core == 1;
     return CDI_OK;
 }
 

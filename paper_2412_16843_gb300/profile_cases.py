@@ -2,6 +2,7 @@
 (run the same command once without ncu first):
 
     python -m paper_2412_16843_gb300.profile_cases unet 128     # network forward passes at 128^3
+    python -m paper_2412_16843_gb300.profile_cases train 64     # 3 network training steps at 64^3
     python -m paper_2412_16843_gb300.profile_cases batch 64     # 64-instance FP32-mixed sweep, 3 steps
     python -m paper_2412_16843_gb300.profile_cases drop3d 256   # 3D drop, FP32-mixed, separate kernels, 2 steps
     python -m paper_2412_16843_gb300.profile_cases wide 512 1   # 512x256x256 drop, FP32-mixed, previous-pressure
@@ -28,6 +29,17 @@ def main(argv):
             net.forward_device(x, y)
         torch.cuda.synchronize()
         print('unet ok', float(y.abs().mean()))
+    elif mode == 'train':
+        n = int(argv[2]) if len(argv) > 2 else 64
+        net = cdi.Unet((n, n, n))
+        net.set_params(inputs.unet_initial_params(0))
+        rng = np.random.default_rng(0)
+        x = rng.standard_normal((n, n, n, 2))
+        t = rng.standard_normal((n, n, n))
+        for _ in range(3):
+            loss = net.train_step(x, t, lr=1e-3)
+        torch.cuda.synchronize()
+        print('train ok', loss)
     elif mode == 'batch':
         k = int(argv[2]) if len(argv) > 2 else 64
         wls = inputs.sweep_2d(n_inst=k)

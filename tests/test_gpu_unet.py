@@ -230,6 +230,33 @@ def test_tensor_core_and_warp_mma_convolutions_agree(n):
     assert relnorm(g_tc, g_mma) < 1e-2
 
 
+@pytest.mark.parametrize("n", [(16, 8, 8), (24, 40, 16)], ids=["16x8x8", "24x40x16"])
+def test_tcgen05_weight_gradients_match_mma_sync(n):
+    """The same forward pass (tcgen05 convolutions) with the weight and bias
+    gradients of every layer from the tcgen05 voxel-reduction GEMM (row of
+    ones for the bias, fixed-order split sums) or from the mma.sync kernel
+    with FP32 atomics: both sum the same BF16 products in FP32, so every
+    entry agrees to accumulation-order round-off, 1e-4 of the layer's
+    largest entry.  The 24x40x16 grid's coarse levels (3x5x2 voxels at the
+    bottleneck) have extents that are not multiples of 8."""
+    shape = (n[2], n[1], n[0])
+    P, x, t = random_case(shape, 5)
+    grads = []
+    for mode in (1, 2):
+        net = cdi.Unet(n)
+        net.set_conv_kernel(mode)
+        net.set_params(flat(P))
+        _, g = net.train_step(x, t[..., 0], lr=0.0, want_grads=True)
+        grads.append(unflat(g))
+    g_tc, g_mma = grads
+    for name, _, _, _ in ref.LAYERS:
+        for part in (".w", ".b"):
+            a, b = g_tc[name + part], g_mma[name + part]
+            m = np.abs(a - b).max() / np.abs(b).max()
+            print("%-7s max diff / max %.3e" % (name + part, m))
+            assert m < 1e-4, (name + part, m)
+
+
 def test_fused_decoder_inputs_match_stored_ones():
     """Inference gathers the decoder inputs [up(coarser), skip] while staging
     the convolution tiles; training stores them.  Both feed the same BF16
