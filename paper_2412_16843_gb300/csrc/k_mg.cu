@@ -788,6 +788,71 @@ __global__ void __launch_bounds__(256) k_project3(Geom g, PhysDev ph, const T* _
     }
 }
 
+// k_project3 of the FP32-mixed form with nx a multiple of 4: four cells of one
+// x row a thread on float4 words (double-float p: two float4 words), the
+// arithmetic of project_at term for term; 64 x-quads x 4 rows of one z plane
+// a block (kCoefX x kCoefY)
+__global__ void __launch_bounds__(kCoefX * kCoefY)
+    k_project4(Geom g, PhysDev ph, const float* __restrict__ phi, float* u0, float* u1, float* u2, float cdt,
+               const float2* __restrict__ p) {
+    const int q = blockIdx.x * kCoefX + threadIdx.x, j = blockIdx.y * kCoefY + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], k = blockIdx.z;
+    if (4 * q >= nx || j >= ny) return;
+    const long row = (long)nx * ((long)j + (long)ny * k);
+    const long c = row + 4L * q;
+    const float ih = g.ihf, dr = phys<float>(ph).drho, rho2 = phys<float>(ph).rho2;
+    auto ld4 = [](const float* a, long i, float* v) {
+        const float4 w = __ldg(reinterpret_cast<const float4*>(a + i));
+        v[0] = w.x;
+        v[1] = w.y;
+        v[2] = w.z;
+        v[3] = w.w;
+    };
+    auto ldp4 = [](const float2* a, long i, float2* v) {
+        const float4 w0 = __ldg(reinterpret_cast<const float4*>(a + i));
+        const float4 w1 = __ldg(reinterpret_cast<const float4*>(a + i + 2));
+        v[0] = make_float2(w0.x, w0.y);
+        v[1] = make_float2(w0.z, w0.w);
+        v[2] = make_float2(w1.x, w1.y);
+        v[3] = make_float2(w1.z, w1.w);
+    };
+    float phic[4];
+    float2 pc[4];
+    ld4(phi, c, phic);
+    ldp4(p, c, pc);
+    float* us[3] = {u0, u1, u2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a == 2 && k == 0) continue;  // wall face stays zero
+        float phiL[4];
+        float2 pL[4];
+        if (a == 0) {
+            const long xm = q == 0 ? row + nx - 1 : c - 1;
+            phiL[0] = __ldg(phi + xm);
+            pL[0] = __ldg(p + xm);
+#pragma unroll
+            for (int e = 1; e < 4; ++e) {
+                phiL[e] = phic[e - 1];
+                pL[e] = pc[e - 1];
+            }
+        } else {
+            const long cL = a == 1 ? ((j == 0) ? c + (long)(ny - 1) * nx : c - nx) : c - g.NP;
+            ld4(phi, cL, phiL);
+            ldp4(p, cL, pL);
+        }
+        float4 u = *reinterpret_cast<const float4*>(us[a] + c);
+        float uv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float rf = 0.5f * ((dr * phiL[e] + rho2) + (dr * phic[e] + rho2));
+            const float beta = 1.f / rf;
+            const float dpv = ops::p_diff(pc[e], pL[e]) * ih;
+            uv[e] = uv[e] - cdt * beta * dpv;
+        }
+        *reinterpret_cast<float4*>(us[a] + c) = make_float4(uv[0], uv[1], uv[2], uv[3]);
+    }
+}
+
 template <typename T>
 __global__ void k_mass_partial(long N, const T* phi, double* part) {
     double acc = 0.0;
@@ -1175,7 +1240,14 @@ void launch_project(const Geom& g, const PhysDev& ph, const T* phi, T* const* us
                     cudaStream_t s) {
     const bool on = prof_before(KC_PROJECT, s);
     const PT<T>* pp = reinterpret_cast<const PT<T>*>(p);
-    if (g.D == 2)
+    bool vec = false;
+    if constexpr (sizeof(T) == 4) vec = g.D == 3 && g.n[0] % 4 == 0;
+    if (vec)
+        k_project4<<<dim3((unsigned)((g.n[0] / 4 + kCoefX - 1) / kCoefX), (unsigned)((g.n[1] + kCoefY - 1) / kCoefY),
+                          (unsigned)g.n[2]),
+                     dim3(kCoefX, kCoefY), 0, s>>>(g, ph, (const float*)phi, (float*)us[0], (float*)us[1],
+                                                   (float*)us[2], (float)cdt, (const float2*)pp);
+    else if (g.D == 2)
         k_project<T, 2><<<blocks_for(g.N), kThreads, 0, s>>>(g, ph, phi, us[0], us[1], nullptr, (T)cdt, pp);
     else if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0)
         k_project3<T><<<dim3((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kProjectZ - 1) / kProjectZ)),

@@ -317,6 +317,197 @@ __global__ void __launch_bounds__(kVecX * kVecY)
     }
 }
 
+__device__ __forceinline__ void ld4(const float* a, long i, float* v) {
+    const float4 w = __ldg(reinterpret_cast<const float4*>(a + i));
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+}
+__device__ __forceinline__ void st4(float* a, long i, const float* v) {
+    *reinterpret_cast<float4*>(a + i) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// k_cell3 on float4 words: four cells of one x row a thread (the x
+// neighbours of the end cells are the words before and after the quad, across
+// the periodic seam at the row ends), the terms of k_cell3 in its order
+__global__ void __launch_bounds__(kVecX * kVecY)
+    k_cell4(Geom g, PhysDev ph, const float* __restrict__ phi, const float* __restrict__ psi, float* __restrict__ nh0,
+            float* __restrict__ nh1, float* __restrict__ nh2, float* __restrict__ muc) {
+    const int q = blockIdx.x * kVecX + threadIdx.x, j = blockIdx.y * kVecY + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], k = blockIdx.z;
+    if (4 * q >= nx || j >= ny) return;
+    const long NP = g.NP;
+    const long row = (long)nx * ((long)j + (long)ny * k);
+    const long c = row + 4L * q;
+    const float ih = g.ihf;
+    const float half_ih = 0.5f * ih, ih2 = ih * ih;
+    const PhysT<float>& Q = phys<float>(ph);
+    const float delta = Q.delta, eps = Q.eps;
+    float s0[4], sx[6], ym[4], yp[4], z1[4], z2[4], z3[4], ph4[4];
+    ld4(psi, c, s0);
+    sx[0] = __ldg(psi + (q == 0 ? row + nx - 1 : c - 1));
+    sx[5] = __ldg(psi + (4 * q + 4 == nx ? row : c + 4));
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sx[e + 1] = s0[e];
+    ld4(psi, (j == 0) ? c + (long)(ny - 1) * nx : c - nx, ym);
+    ld4(psi, (j == ny - 1) ? c - (long)(ny - 1) * nx : c + nx, yp);
+    if (k == 0) {
+        ld4(psi, c + NP, z1);
+        ld4(psi, c + 2 * NP, z2);
+        ld4(psi, c + 3 * NP, z3);
+    } else if (k == nz - 1) {
+        ld4(psi, c - NP, z1);
+        ld4(psi, c - 2 * NP, z2);
+        ld4(psi, c - 3 * NP, z3);
+    } else {
+        ld4(psi, c - NP, z1);  // below
+        ld4(psi, c + NP, z2);  // above
+    }
+    ld4(phi, c, ph4);
+    float o0[4], o1[4], o2[4], om[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float gb[3], grad2 = 0.f, lap = 0.f;
+        {  // x
+            const float sm = sx[e], sp = sx[e + 2];
+            const float d1 = (sp - sm) * half_ih, d2 = (sp - 2.f * s0[e] + sm) * ih2;
+            gb[0] = d1;
+            grad2 += d1 * d1;
+            lap += d2;
+        }
+        {  // y
+            const float sm = ym[e], sp = yp[e];
+            const float d1 = (sp - sm) * half_ih, d2 = (sp - 2.f * s0[e] + sm) * ih2;
+            gb[1] = d1;
+            grad2 += d1 * d1;
+            lap += d2;
+        }
+        {  // z: the wall axis
+            float d1, d2;
+            if (k == 0) {
+                d1 = (-3.f * s0[e] + 4.f * z1[e] - z2[e]) * half_ih;
+                d2 = (2.f * s0[e] - 5.f * z1[e] + 4.f * z2[e] - z3[e]) * ih2;
+            } else if (k == nz - 1) {
+                d1 = (3.f * s0[e] - 4.f * z1[e] + z2[e]) * half_ih;
+                d2 = (2.f * s0[e] - 5.f * z1[e] + 4.f * z2[e] - z3[e]) * ih2;
+            } else {
+                const float sm = z1[e], sp = z2[e];
+                d1 = (sp - sm) * half_ih;
+                d2 = (sp - 2.f * s0[e] + sm) * ih2;
+            }
+            gb[2] = d1;
+            grad2 += d1 * d1;
+            lap += d2;
+        }
+        const float pt = clampv(ph4[e], delta, 1.f - delta);
+        const float P = pt * (1.f - pt);
+        om[e] = 6.f * Q.sigma * (P * (1.f - 2.f * pt) * (1.f - grad2) / eps - P * lap);
+        const float igm = 1.f / (sqrtf(grad2) + Q.tau);
+        o0[e] = gb[0] * igm;
+        o1[e] = gb[1] * igm;
+        o2[e] = gb[2] * igm;
+    }
+    st4(muc, c, om);
+    st4(nh0, c, o0);
+    st4(nh1, c, o1);
+    st4(nh2, c, o2);
+}
+
+// k_phi_rhs3 on float4 words: four cells of one x row a thread; the five x
+// faces of the quad are formed once each (the high face of one cell is the
+// low face of the next), each face by ops::phi_flux_v, the terms of
+// k_phi_rhs3 in its order
+__global__ void __launch_bounds__(kVecX * kVecY) k_phi_rhs4(Geom g, PhysDev ph, StageFields<float> f) {
+    const int q = blockIdx.x * kVecX + threadIdx.x, j = blockIdx.y * kVecY + threadIdx.y;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2], k = blockIdx.z;
+    if (4 * q >= nx || j >= ny) return;
+    const long NP = g.NP;
+    const long row = (long)nx * ((long)j + (long)ny * k);
+    const long c = row + 4L * q;
+    const float ih = g.ihf;
+    const PhysT<float>& Q = phys<float>(ph);
+    const float eps = Q.eps, delta = Q.delta, drho = Q.drho, rho2 = Q.rho2;
+    const float gamma = stage_gamma(f);
+    const long xm = q == 0 ? row + nx - 1 : c - 1, xp = 4 * q + 4 == nx ? row : c + 4;
+    float pc[4], nc[4], ul[4];
+    ld4(f.phi, c, pc);
+    float div[4] = {0.f, 0.f, 0.f, 0.f};
+    {  // x: faces e = 0..4 between cells e-1 and e of the quad
+        float fx[6], nx6[6], F[5];
+        ld4(f.nh[0], c, nc);
+        ld4(f.u[0], c, ul);
+        fx[0] = __ldg(f.phi + xm);
+        nx6[0] = __ldg(f.nh[0] + xm);
+        fx[5] = __ldg(f.phi + xp);
+        nx6[5] = __ldg(f.nh[0] + xp);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            fx[e + 1] = pc[e];
+            nx6[e + 1] = nc[e];
+        }
+        const float u4 = __ldg(f.u[0] + xp);
+#pragma unroll
+        for (int e = 0; e < 5; ++e)
+            F[e] = ops::phi_flux_v(fx[e], fx[e + 1], nx6[e], nx6[e + 1], e < 4 ? ul[e] : u4, gamma, eps, ih, delta);
+        float m[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            div[e] += F[e + 1] - F[e];
+            m[e] = drho * F[e] + rho2 * ul[e];
+        }
+        st4(f.m[0], c, m);
+    }
+    {  // y (periodic)
+        const long cL = (j == 0) ? c + (long)(ny - 1) * nx : c - nx;
+        const long cR = (j == ny - 1) ? c - (long)(ny - 1) * nx : c + nx;
+        float fL[4], fR[4], nL[4], nR[4], uR[4], m[4];
+        ld4(f.nh[1], c, nc);
+        ld4(f.u[1], c, ul);
+        ld4(f.phi, cL, fL);
+        ld4(f.nh[1], cL, nL);
+        ld4(f.phi, cR, fR);
+        ld4(f.nh[1], cR, nR);
+        ld4(f.u[1], cR, uR);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float Flo = ops::phi_flux_v(fL[e], pc[e], nL[e], nc[e], ul[e], gamma, eps, ih, delta);
+            const float Fhi = ops::phi_flux_v(pc[e], fR[e], nc[e], nR[e], uR[e], gamma, eps, ih, delta);
+            div[e] += Fhi - Flo;
+            m[e] = drho * Flo + rho2 * ul[e];
+        }
+        st4(f.m[1], c, m);
+    }
+    {  // z (walls: no flux through the wall faces)
+        const bool wlo = k == 0, whi = k == nz - 1;
+        float fL[4], fR[4], nL[4], nR[4], uR[4], m[4];
+        ld4(f.nh[2], c, nc);
+        ld4(f.u[2], c, ul);
+        if (!wlo) {
+            ld4(f.phi, c - NP, fL);
+            ld4(f.nh[2], c - NP, nL);
+        }
+        if (!whi) {
+            ld4(f.phi, c + NP, fR);
+            ld4(f.nh[2], c + NP, nR);
+            ld4(f.u[2], c + NP, uR);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float Flo = 0.f, Fhi = 0.f;
+            if (!wlo) Flo = ops::phi_flux_v(fL[e], pc[e], nL[e], nc[e], ul[e], gamma, eps, ih, delta);
+            if (!whi) Fhi = ops::phi_flux_v(pc[e], fR[e], nc[e], nR[e], uR[e], gamma, eps, ih, delta);
+            div[e] += Fhi - Flo;
+            m[e] = wlo ? 0.f : drho * Flo + rho2 * ul[e];
+        }
+        st4(f.m[2], c, m);
+    }
+    float r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r[e] = -div[e] * ih;
+    st4(f.rphi, c, r);
+}
+
 template <typename T>
 inline bool vec4_ok(const Geom& g) {
     return sizeof(T) == 4 && g.D == 3 && g.n[0] % 4 == 0;
@@ -351,7 +542,14 @@ void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaS
         CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f)));
         CDI_PROF(KC_MOM, s, (k_mom<T, 2><<<nb, kThreads, 0, s>>>(g, ph, f)));
     } else {
-        if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
+        bool vec = false;
+        if constexpr (sizeof(T) == 4) vec = vec4_ok<T>(g);
+        if (vec) {
+            CDI_PROF(KC_CELL, s,
+                     (k_cell4<<<vec4_grid(g), dim3(kVecX, kVecY), 0, s>>>(
+                         g, ph, (const float*)f.phi, (const float*)f.psi, (float*)f.nh[0], (float*)f.nh[1],
+                         (float*)f.nh[2], (float*)f.muc)));
+        } else if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
             const dim3 grid((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kCellZ - 1) / kCellZ));
             CDI_PROF(KC_CELL, s,
                      (k_cell3<T><<<grid, dim3(32, 8), 0, s>>>(g, ph, f.phi, f.psi, f.nh[0], f.nh[1], f.nh[2], f.muc)));
@@ -361,11 +559,17 @@ void launch_rhs(const Geom& g, const PhysDev& ph, const StageFields<T>& f, cudaS
         }
         CDI_PROF(KC_WALL, s, (k_wall<T, 3><<<wall_blocks(g), kWallThreads, 0, s>>>(
                                  g, ph, f.phi, f.psi, f.u[0], f.u[1], f.wuY, f.wghost, f.wmuw)));
-        if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
-            const dim3 grid((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8), (unsigned)((g.n[2] + kCellZ - 1) / kCellZ));
-            CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs3<T><<<grid, dim3(32, 8), 0, s>>>(g, ph, f)));
-        } else {
-            CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));
+        if constexpr (sizeof(T) == 4) {
+            if (vec) CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs4<<<vec4_grid(g), dim3(kVecX, kVecY), 0, s>>>(g, ph, f)));
+        }
+        if (!vec) {
+            if (g.n[0] % 32 == 0 && g.n[1] % 8 == 0) {
+                const dim3 grid((unsigned)(g.n[0] / 32), (unsigned)(g.n[1] / 8),
+                                (unsigned)((g.n[2] + kCellZ - 1) / kCellZ));
+                CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs3<T><<<grid, dim3(32, 8), 0, s>>>(g, ph, f)));
+            } else {
+                CDI_PROF(KC_PHI_RHS, s, (k_phi_rhs<T, 3><<<nb, kThreads, 0, s>>>(g, ph, f)));
+            }
         }
         if (mom_tile_supported(g)) {
             CDI_PROF(KC_MOM, s, launch_mom_tile<T>(g, ph, f, s));

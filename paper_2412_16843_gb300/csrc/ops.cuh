@@ -324,14 +324,19 @@ __device__ void wall_from_colq_at(const Geom& g, const PhysDev& ph, const ColQ<T
 // ---------------------------------------------------------------------------
 // a3: phi flux and the consistent mass flux
 // ---------------------------------------------------------------------------
+// flux of the face between cells L and R from their phi, normal component and
+// the face velocity
+template <typename T>
+__device__ __forceinline__ T phi_flux_v(T fL, T fR, T nL, T nR, T uf, T gamma, T eps, T ih, T delta) {
+    const T pb = T(0.5) * (fL + fR);
+    const T pc = clampv(pb, delta, T(1) - delta);
+    const T nb = T(0.5) * (nL + nR);
+    return uf * pb - gamma * (eps * (fR - fL) * ih - pc * (T(1) - pc) * nb);
+}
 template <class L, typename T>
 __device__ __forceinline__ T phi_flux(const T* phi, const T* nh, long cL, long cR, T uf, T gamma, T eps, T ih,
                                       T delta) {
-    const T fL = L::ld(phi + cL), fR = L::ld(phi + cR);
-    const T pb = T(0.5) * (fL + fR);
-    const T pc = clampv(pb, delta, T(1) - delta);
-    const T nb = T(0.5) * (L::ld(nh + cL) + L::ld(nh + cR));
-    return uf * pb - gamma * (eps * (fR - fL) * ih - pc * (T(1) - pc) * nb);
+    return phi_flux_v(L::ld(phi + cL), L::ld(phi + cR), L::ld(nh + cL), L::ld(nh + cR), uf, gamma, eps, ih, delta);
 }
 
 template <class L, typename T, int DIM>
