@@ -78,6 +78,14 @@ struct cdi_ctx {
     cudaGraphExec_t vc_exec[2] = {nullptr, nullptr};
     long vc_nodes[2] = {0, 0};
     bool vc_graph_failed = false;
+    // launch-per-kernel path: a whole pressure solve (first residual, the
+    // V-cycles in a conditional while node, mean removal) as one CUDA graph
+    // per form; tolerance and cycle limit are baked into its kernels
+    cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
+    long solve_nodes[2][3] = {{0, 0, 0}, {0, 0, 0}};  // before, per V-cycle, after the loop
+    double solve_tol[2] = {0.0, 0.0};
+    int solve_max[2] = {0, 0};
+    bool solve_graph_failed = false;
     PersistLayout playout{};
     int persist_lt = 0;
     size_t persist_smem = 0;
@@ -105,6 +113,21 @@ cdi_status fail(cdi_ctx* c, cdi_status st, const std::string& msg) {
 cdi_status cuda_check(cdi_ctx* c, cudaError_t e, const char* what) {
     if (e == cudaSuccess) return CDI_OK;
     return fail(c, CDI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// The cached CUDA graphs hold kernel arguments (sweep counts, relaxation,
+// sweep form, tolerance, buffers): dropped whenever one of them changes.
+void drop_graphs(cdi_ctx* c) {
+    for (int k = 0; k < 2; ++k) {
+        if (c->vc_exec[k]) {
+            cudaGraphExecDestroy(c->vc_exec[k]);
+            c->vc_exec[k] = nullptr;
+        }
+        if (c->solve_exec[k]) {
+            cudaGraphExecDestroy(c->solve_exec[k]);
+            c->solve_exec[k] = nullptr;
+        }
+    }
 }
 
 size_t esize(const cdi_ctx* c) { return c->precision == CDI_FP64 ? sizeof(double) : sizeof(float); }
@@ -431,6 +454,154 @@ void vcycle_and_residual(cdi_ctx* c) {
     launch_resid_norm<T>(g, mg, c->stream);
 }
 
+// Device-side control of the V-cycle loop: the tests of the host loop in
+// mg_solve (f finite and nonzero, residual above tol |f|, staged-copy
+// timeout, finite residual, cycle limit), in the same order and the same FP64
+// arithmetic, set the condition of the solve graph's while node.
+__global__ void k_solve_begin(double* scal, cudaGraphConditionalHandle h, double tol, int max_cycles) {
+    const double fn = scal[S_FNORM], rn = scal[S_RNORM];
+    unsigned go = 0;
+    double end = kSolveRan;
+    if (!isfinite(fn) || !isfinite(rn)) end = kSolveNanF;
+    else if (fn == 0.0) end = kSolveZeroF;
+    else go = (rn > tol * fn && 0 < max_cycles) ? 1u : 0u;
+    scal[S_CYC] = 0.0;
+    scal[S_SOLVE] = end;
+    cudaGraphSetConditional(h, go);
+}
+
+__global__ void k_solve_next(double* scal, cudaGraphConditionalHandle h, double tol, int max_cycles) {
+    const double fn = scal[S_FNORM], rn = scal[S_RNORM];
+    const double cyc = scal[S_CYC] + 1.0;
+    unsigned go = 0;
+    if (scal[S_TMAERR] != 0.0) scal[S_SOLVE] = kSolveTma;
+    else if (!isfinite(rn)) scal[S_SOLVE] = kSolveNanR;
+    else go = (rn > tol * fn && cyc < (double)max_cycles) ? 1u : 0u;
+    scal[S_CYC] = cyc;
+    cudaGraphSetConditional(h, go);
+}
+
+// a zero right-hand side has the constant solutions: p = 0 (both forms keep 8
+// bytes a cell, and all-zero bytes are zero in both)
+__global__ void k_zero_p_if_zero_f(long n, double* p, const double* scal) {
+    if (scal[S_SOLVE] != (double)kSolveZeroF) return;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) p[i] = 0.0;
+}
+
+// The whole pressure solve as one CUDA graph: the first guess's residual norm
+// and the loop's first test, a conditional while node whose body is one
+// V-cycle, the residual norm after it and the next test, then p = 0 for a zero
+// f and the mean removal.  The host waits once per solve instead of once per
+// V-cycle.  false: the graph could not be built (the caller falls back to the
+// host-driven loop).
+template <typename T>
+bool build_solve_graph(cdi_ctx* c, int k) {
+    const Geom& g = c->g;
+    MG& mg = c->mg;
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+    cudaStream_t cs = c->cap_stream;
+    const long l0 = g_launches;
+    long n_before = 0, n_body = 0, n_after = 0;
+    cudaGraph_t G = nullptr, body = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    bool ok = cudaGraphCreate(&G, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+    if (ok) ok = cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        launch_resid_norm<T>(g, mg, cs);
+        k_solve_begin<<<1, 1, 0, cs>>>(mg.scal, h, c->tol, c->max_vcycles);
+        ++g_launches;
+        n_before = g_launches - l0;
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        bool node_ok = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd) == cudaSuccess &&
+                       cst == cudaStreamCaptureStatusActive;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t wn = nullptr;
+        node_ok = node_ok && cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &np) == cudaSuccess;
+        node_ok = node_ok && cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1,
+                                                                 cudaStreamSetCaptureDependencies) == cudaSuccess;
+        if (node_ok) body = np.conditional.phGraph_out[0];
+        const long l1 = g_launches;
+        k_zero_p_if_zero_f<<<2 * 152, 256, 0, cs>>>(g.N, mg.lv[0].p, mg.scal);
+        ++g_launches;
+        launch_p_mean_remove<T>(g, mg, cs);
+        n_after = g_launches - l1;
+        cudaGraph_t out = nullptr;
+        ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && node_ok && body;
+    }
+    if (ok) {
+        const long l2 = g_launches;
+        ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+            launch_vcycle<T>(g, mg, c->npre, c->npost, cs);
+            launch_resid_norm<T>(g, mg, cs);
+            k_solve_next<<<1, 1, 0, cs>>>(mg.scal, h, c->tol, c->max_vcycles);
+            ++g_launches;
+            cudaGraph_t out = nullptr;
+            ok = cudaStreamEndCapture(cs, &out) == cudaSuccess;
+        }
+        n_body = g_launches - l2;
+    }
+    g_launches = l0;
+    cudaGraphExec_t ex = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&ex, G, 0) == cudaSuccess;
+    if (G) cudaGraphDestroy(G);
+    if (!ok) {
+        cudaGetLastError();
+        if (ex) cudaGraphExecDestroy(ex);
+        return false;
+    }
+    c->solve_exec[k] = ex;
+    c->solve_nodes[k][0] = n_before;
+    c->solve_nodes[k][1] = n_body;
+    c->solve_nodes[k][2] = n_after;
+    c->solve_tol[k] = c->tol;
+    c->solve_max[k] = c->max_vcycles;
+    return true;
+}
+
+// Outcome of a solve-graph launch: one wait, then the statuses and statistics
+// of the host loop.
+cdi_status finish_solve_graph(cdi_ctx* c, int k) {
+    cdi_status st = read_scalars(c);
+    if (st) return st;
+    const double* hs = c->host_scal;
+    const double fn = hs[S_FNORM], rn = hs[S_RNORM];
+    const int cyc = (int)hs[S_CYC];
+    const int end = (int)hs[S_SOLVE];
+    g_launches += c->solve_nodes[k][0] + (long)cyc * c->solve_nodes[k][1] + c->solve_nodes[k][2];
+    if (end == kSolveNanF) return fail(c, CDI_ENAN, "non-finite pressure right-hand side");
+    if (end == kSolveZeroF) {
+        c->last_cycles = 0;
+        c->last_resid = 0.0;
+        return CDI_OK;
+    }
+    if (end == kSolveTma) {
+        cudaMemsetAsync(c->mg.scal + S_TMAERR, 0, sizeof(double), c->stream);
+        return fail(c, CDI_ETIMEOUT, "one-pass sweep: a staged copy did not complete within its bounded wait");
+    }
+    if (end == kSolveNanR) return fail(c, CDI_ENAN, "non-finite pressure residual");
+    c->last_cycles = cyc;
+    c->last_resid = rn / fn;
+    if (cyc > c->max_cycles_step) c->max_cycles_step = cyc;
+    c->total_cycles_call += cyc;
+    if (rn > c->tol * fn) {
+        char b[160];
+        snprintf(b, sizeof b, "pressure solve: %d V-cycles left relative residual %.3e > tol %.3e", cyc, rn / fn,
+                 c->tol);
+        return fail(c, CDI_ENOCONV, b);
+    }
+    return CDI_OK;
+}
+
 template <typename T>
 cdi_status mg_solve(cdi_ctx* c) {
     const Geom& g = c->g;
@@ -438,6 +609,19 @@ cdi_status mg_solve(cdi_ctx* c) {
     MG& mg = c->mg;
     cdi_status st0 = kernels_tail_setup(c);
     if (st0) return st0;
+    const int k = sizeof(T) == 8 ? 0 : 1;
+    if (g_prof.target < 0 && !c->solve_graph_failed) {
+        if (c->solve_exec[k] && (c->solve_tol[k] != c->tol || c->solve_max[k] != c->max_vcycles)) {
+            cudaGraphExecDestroy(c->solve_exec[k]);
+            c->solve_exec[k] = nullptr;
+        }
+        if (!c->solve_exec[k] && !build_solve_graph<T>(c, k)) c->solve_graph_failed = true;
+        if (c->solve_exec[k]) {
+            if (cudaGraphLaunch(c->solve_exec[k], s) == cudaSuccess) return finish_solve_graph(c, k);
+            cudaGetLastError();
+            c->solve_graph_failed = true;
+        }
+    }
     launch_resid_norm<T>(g, mg, s);
     cdi_status st = read_scalars(c);
     if (st) return st;
@@ -803,11 +987,7 @@ cdi_status cdi_bind_workspace(cdi_ctx* c, void* dev_ptr, size_t bytes, void* str
     carve(c, c->ws, &total);
     c->mg.tail_args = nullptr;
     c->tail_ready = false;
-    for (int k = 0; k < 2; ++k)
-        if (c->vc_exec[k]) {
-            cudaGraphExecDestroy(c->vc_exec[k]);
-            c->vc_exec[k] = nullptr;
-        }
+    drop_graphs(c);
     if (!c->host_scal) {
         cdi_status st = cuda_check(c, cudaMallocHost((void**)&c->host_scal, S_NSCAL * sizeof(double)),
                                    "cudaMallocHost");
@@ -1012,11 +1192,7 @@ cdi_status cdi_set_relaxation(cdi_ctx* c, double omega) {
     if (!(omega > 0.0 && omega < 2.0)) return fail(c, CDI_EINVAL, "relaxation must lie in (0, 2)");
     c->mg.omega = (float)omega;
     // the V-cycle graphs hold the kernels' arguments
-    for (int k = 0; k < 2; ++k)
-        if (c->vc_exec[k]) {
-            cudaGraphExecDestroy(c->vc_exec[k]);
-            c->vc_exec[k] = nullptr;
-        }
+    drop_graphs(c);
     return CDI_OK;
 }
 
@@ -1028,11 +1204,7 @@ cdi_status cdi_set_smoothing(cdi_ctx* c, int npre, int npost) {
     // the launch-per-kernel tail descriptor and V-cycle graphs hold the sweep counts
     c->tail_ready = false;
     c->mg.tail_args = nullptr;
-    for (int k = 0; k < 2; ++k)
-        if (c->vc_exec[k]) {
-            cudaGraphExecDestroy(c->vc_exec[k]);
-            c->vc_exec[k] = nullptr;
-        }
+    drop_graphs(c);
     return CDI_OK;
 }
 
@@ -1045,11 +1217,7 @@ cdi_status cdi_set_level0_sweep(cdi_ctx* c, int mode) {
                     "CDI_SWEEP_ONEPASS_CPASYNC");
     c->mg.sweep_mode = mode;
     // the V-cycle graphs hold the launches of the previous choice
-    for (int k = 0; k < 2; ++k)
-        if (c->vc_exec[k]) {
-            cudaGraphExecDestroy(c->vc_exec[k]);
-            c->vc_exec[k] = nullptr;
-        }
+    drop_graphs(c);
     return CDI_OK;
 }
 
@@ -1251,8 +1419,7 @@ const char* cdi_last_error(const cdi_ctx* c) {
 
 void cdi_destroy(cdi_ctx* c) {
     if (!c) return;
-    for (int k = 0; k < 2; ++k)
-        if (c->vc_exec[k]) cudaGraphExecDestroy(c->vc_exec[k]);
+    drop_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->host_scal) cudaFreeHost(c->host_scal);
     delete c;

@@ -261,7 +261,13 @@ struct SweepMaps {
 // scalar slots in MG::scal
 enum { S_MEAN = 0, S_FNORM = 1, S_RNORM = 2, S_MASS = 3, S_UMAX = 4, S_GAMMA = 5,
        S_THETA = 6, S_WETTED = 7, S_BADIN = 8 /* nonzero: an uploaded value was not finite */,
-       S_TMAERR = 9 /* nonzero: a bounded wait for a staged copy ran out */, S_NSCAL = 16 };
+       S_TMAERR = 9 /* nonzero: a bounded wait for a staged copy ran out */,
+       S_CYC = 10 /* V-cycles of the device-controlled solve */,
+       S_SOLVE = 11 /* how the device-controlled solve ended (SolveEnd) */, S_NSCAL = 16 };
+// S_SOLVE values: the loop ran (converged or out of cycles: the host compares
+// the residual), f was zero, f or the residual was not finite, a staged copy
+// of the one-pass sweep timed out
+enum SolveEnd { kSolveRan = 0, kSolveZeroF = 1, kSolveNanF = 2, kSolveNanR = 3, kSolveTma = 4 };
 // slots in MG::scalf: the means of f and p as double-floats (FP32-mixed form) and gamma
 enum { SF_FMEAN_HI = 0, SF_FMEAN_LO = 1, SF_GAMMA = 2, SF_PMEAN_HI = 4, SF_PMEAN_LO = 5, SF_NSCAL = 8 };
 

@@ -325,6 +325,55 @@ def test_onepass_sweep_is_bitwise_colour_passes(precision, omega):
     assert np.array_equal(p_a, p_b)
 
 
+@pytest.mark.parametrize("precision", [cdi.FP64, cdi.FP32_MIXED], ids=["fp64", "fp32_mixed"])
+def test_device_controlled_solve_is_bitwise_host_loop(precision):
+    """The launch-per-kernel pressure solve runs as one CUDA graph whose V-cycle
+    loop is a conditional while node, its tests taken on the device.  While the
+    event profiler is on, the host drives the same loop one V-cycle at a time.
+    4 steps of the 256x64x64 drop give bit-identical fields and the same V-cycle
+    counts either way."""
+    n = (256, 64, 64)
+    out = []
+    for profiled in (False, True):
+        g, _, _ = _drop3d_solver(n, precision, cdi.SWEEP_AUTO, tol=1e-10)
+        if profiled:
+            g.profile_start("resid", 1 << 14)
+        cyc = []
+        for _ in range(4):
+            g.step(5e-5, 1)
+            cyc.append(g.last_stats()["total_cycles_call"])
+        if profiled:
+            _, launches = g.profile_stop()
+            assert launches > 0
+        out.append((g.get_fields(), cyc))
+    ((phi_a, vel_a, p_a), cyc_a), ((phi_b, vel_b, p_b), cyc_b) = out
+    assert cyc_a == cyc_b and min(cyc_a) > 0
+    assert np.array_equal(phi_a, phi_b)
+    for a in range(3):
+        assert np.array_equal(vel_a[a], vel_b[a]), a
+    assert np.array_equal(p_a, p_b)
+
+
+def test_device_controlled_solve_zero_rhs():
+    """A fluid at rest with uniform phi has f = 0 in every solve: the graph's
+    first test skips the loop, p is set to zero, no V-cycle runs."""
+    n = (64, 32, 32)
+    h = 1.0 / 32
+    g = cdi.Solver(3, n, tuple(x * h for x in n), precision=cdi.FP32_MIXED)
+    g.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, 1.0)
+    g.set_solver(1e-8, 100)
+    g.set_wall(cdi.WALL_BOTH, math.radians(60), h, 0.0)
+    g.set_exec(cdi.EXEC_KERNELS)
+    g.set_state(np.ones(g.cell_shape))
+    g.step(1e-4, 3)
+    st = g.last_stats()
+    assert st["total_cycles_call"] == 0 and st["resid"] == 0.0
+    phi, vel, p = g.get_fields()
+    assert np.all(p == 0.0) and np.all(phi == 1.0)
+    for a in range(3):
+        assert np.all(vel[a] == 0.0), a
+
+
 @EXEC_MODES
 def test_couette_full_size_512x128_parity(exec_mode):
     """The full 512x128 Couette workload in the launch configuration the bench
