@@ -297,27 +297,34 @@ def reference_arm(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------
 ROOF_KERNELS = ("rbgs0", "resid", "mom")
+# the other kernel classes of the step, timed the same way (time per step; bytes where the
+# per-launch count is defined above)
+BREAKDOWN_KERNELS = ("resid_restrict0", "prolong0", "rbgs", "coarse", "phi_rhs", "cell", "psi", "wall",
+                     "stage_phi", "stage_mom", "div", "project")
 
 
-def kernel_rooflines(s, wl, hbm, steps=2):
+def kernel_rooflines(s, wl, hbm, steps=2, classes=ROOF_KERNELS):
     """Per-launch device time of the largest kernels of the step (launch
     profiler: CUDA events on the library's stream around each launch; the
-    V-cycle then runs without its graph) over `steps` steps, against each
-    kernel's algorithmic bytes."""
+    pressure solve then runs without its graphs) over `steps` steps, against
+    each kernel's algorithmic bytes where that is defined."""
     import torch
     out = {}
-    for kc in ROOF_KERNELS:
+    for kc in classes:
         s.profile_start(kc, 1 << 14)
         s.step(wl.dt, steps)
         torch.cuda.synchronize()
         ms, n = s.profile_stop()
         if not n:
             continue
-        nbytes = algorithmic_bytes(kc, wl.dim, wl.cells, wl.n[0] * wl.n[1], 4, sum(SMOOTHING_3D))
         avg = ms / n / 1e3
-        out[kc] = {"launches": n, "avg_launch_us": avg * 1e6, "algorithmic_bytes_per_launch": nbytes,
-                   "achieved": nbytes / avg / 1e9, "frac": nbytes / avg / 1e9 / hbm,
-                   "ms_per_step": ms / steps}
+        out[kc] = {"launches": n, "avg_launch_us": avg * 1e6, "ms_per_step": ms / steps}
+        try:
+            nbytes = algorithmic_bytes(kc, wl.dim, wl.cells, wl.n[0] * wl.n[1], 4, sum(SMOOTHING_3D))
+        except KeyError:
+            continue
+        out[kc].update({"algorithmic_bytes_per_launch": nbytes, "achieved": nbytes / avg / 1e9,
+                        "frac": nbytes / avg / 1e9 / hbm})
     return out
 
 
@@ -397,13 +404,14 @@ def gpu_arm(args, rank, world, local_rank):
     nbytes = sum(step_bytes(wl.dim, wl.cells, 4, c, sum(SMOOTHING_3D)) for c in cyc)
     achieved = nbytes / (ms / 1e3) / 1e9
     per_kernel = kernel_rooflines(s, wl, hbm)
+    breakdown = kernel_rooflines(s, wl, hbm, classes=BREAKDOWN_KERNELS)
     roof = {"bound": "hbm", "kernel": "step", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic_for("step_wide"), "peak_source": peak_kind,
             "algorithmic_bytes_per_step": nbytes / args.steps, "avg_step_ms": ms / args.steps,
             "what": "one full step (all its launches) timed with CUDA events on the library's stream; "
                     "bytes from the per-cell formula with each timed step's own V-cycle count and the "
                     "cycle's %d finest-level sweeps" % sum(SMOOTHING_3D),
-            "kernels": per_kernel}
+            "kernels": per_kernel, "other_kernels": breakdown}
     del s
     torch.cuda.empty_cache()
     forms = None

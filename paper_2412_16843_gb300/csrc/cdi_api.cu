@@ -86,6 +86,9 @@ struct cdi_ctx {
     double solve_tol[2] = {0.0, 0.0};
     int solve_max[2] = {0, 0};
     bool solve_graph_failed = false;
+    // launch-per-kernel path: the level-0 pressure still carries the constant
+    // its V-cycles added (removed when p is read out)
+    bool p_mean_pending = false;
     PersistLayout playout{};
     int persist_lt = 0;
     size_t persist_smem = 0;
@@ -313,6 +316,11 @@ cdi_status download(cdi_ctx* c, double* dst, const void* src, long n) {
 // (the FP32-mixed form converts through the staging buffer)
 cdi_status download_level0(cdi_ctx* c, double* dst, bool pressure) {
     const Geom& g = c->g;
+    if (pressure && c->p_mean_pending) {
+        if (c->precision == CDI_FP64) launch_p_mean_remove<double>(g, c->mg, c->stream);
+        else launch_p_mean_remove<float>(g, c->mg, c->stream);
+        c->p_mean_pending = false;
+    }
     const double* src = pressure ? c->mg.lv[0].p : c->mg.lv[0].f;
     double* hd = static_cast<double*>(const_cast<void*>(host_alias(dst)));
     if (c->precision != CDI_FP64) {
@@ -491,8 +499,7 @@ __global__ void k_zero_p_if_zero_f(long n, double* p, const double* scal) {
 // The whole pressure solve as one CUDA graph: the first guess's residual norm
 // and the loop's first test, a conditional while node whose body is one
 // V-cycle, the residual norm after it and the next test, then p = 0 for a zero
-// f and the mean removal.  The host waits once per solve instead of once per
-// V-cycle.  false: the graph could not be built (the caller falls back to the
+// f.  The host waits once per solve instead of once per V-cycle.  false: the graph could not be built (the caller falls back to the
 // host-driven loop).
 template <typename T>
 bool build_solve_graph(cdi_ctx* c, int k) {
@@ -531,7 +538,6 @@ bool build_solve_graph(cdi_ctx* c, int k) {
         const long l1 = g_launches;
         k_zero_p_if_zero_f<<<2 * 152, 256, 0, cs>>>(g.N, mg.lv[0].p, mg.scal);
         ++g_launches;
-        launch_p_mean_remove<T>(g, mg, cs);
         n_after = g_launches - l1;
         cudaGraph_t out = nullptr;
         ok = cudaStreamEndCapture(cs, &out) == cudaSuccess && node_ok && body;
@@ -589,6 +595,7 @@ cdi_status finish_solve_graph(cdi_ctx* c, int k) {
         return fail(c, CDI_ETIMEOUT, "one-pass sweep: a staged copy did not complete within its bounded wait");
     }
     if (end == kSolveNanR) return fail(c, CDI_ENAN, "non-finite pressure residual");
+    c->p_mean_pending = true;
     c->last_cycles = cyc;
     c->last_resid = rn / fn;
     if (cyc > c->max_cycles_step) c->max_cycles_step = cyc;
@@ -657,7 +664,10 @@ cdi_status mg_solve(cdi_ctx* c) {
                  c->tol);
         return fail(c, CDI_ENOCONV, b);
     }
-    launch_p_mean_remove<T>(g, mg, s);
+    // p is determined up to a constant (periodic axes, Neumann walls) and
+    // nothing in the step reads more than its differences, so the zero-mean
+    // normalisation waits until p is read out (download_level0)
+    c->p_mean_pending = true;
     return CDI_OK;
 }
 
@@ -876,6 +886,7 @@ cdi_status step_persist(cdi_ctx* c, double dt, int nsteps) {
     if (st) return st;
     st = cuda_check(c, cudaStreamSynchronize(c->stream), "persistent step");
     if (st) return st;
+    c->p_mean_pending = false;  // the persistent kernel leaves p zero-mean after every solve
     return apply_stats(c, h.st, "");
 }
 
