@@ -216,6 +216,17 @@ cdi_status cdi_set_exec(cdi_ctx* ctx, int mode);
  * V-cycles per solve. */
 cdi_status cdi_set_smoothing(cdi_ctx* ctx, int npre, int npost);
 
+/* Red-black sweeps before and after the coarse-grid correction on the levels
+ * below the finest that the launch-per-kernel V-cycle runs as separate
+ * launches (the levels the single-CTA tail takes, and the persistent and
+ * batched kernels, keep the counts of cdi_set_smoothing).  Each in [0, 4]
+ * with npre + npost >= 1; npre = npost = -1 (the default) takes the counts of
+ * cdi_set_smoothing.  On these levels every sweep is two launches of a few
+ * microseconds, so the counts trade launches against V-cycles per solve; the
+ * solve still iterates to its tolerance.  Returns CDI_EINVAL outside those
+ * ranges. */
+cdi_status cdi_set_coarse_smoothing(cdi_ctx* ctx, int npre, int npost);
+
 /* Relaxation factor omega of the finest level's red-black sweeps on the
  * launch-per-kernel path: each update is e <- e + omega (e_GS - e), e_GS the
  * Gauss-Seidel value (omega in (0, 2); default 1.15 on 3D grids, 1 on 2D

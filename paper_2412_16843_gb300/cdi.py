@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         "cdi_set_exec": [P, I],
         "cdi_set_barrier_timeout": [P, ctypes.c_longlong],
         "cdi_set_smoothing": [P, I, I],
+        "cdi_set_coarse_smoothing": [P, I, I],
         "cdi_set_relaxation": [P, D],
         "cdi_set_level0_sweep": [P, I],
         "cdi_launches_per_step": [P, ctypes.POINTER(ctypes.c_long)],
@@ -292,6 +293,9 @@ class Solver:
 
     def set_smoothing(self, npre: int, npost: int):
         self._check(self.lib.cdi_set_smoothing(self.h, npre, npost))
+
+    def set_coarse_smoothing(self, npre: int, npost: int):
+        self._check(self.lib.cdi_set_coarse_smoothing(self.h, npre, npost))
 
     def set_relaxation(self, omega: float):
         self._check(self.lib.cdi_set_relaxation(self.h, float(omega)))

@@ -936,6 +936,8 @@ cdi_status cdi_init_grid(cdi_ctx** out, int dim, int nx, int ny, int nz, double 
     // 3D: over-relaxed finest-level sweeps, measured 4 % fewer V-cycles a step
     // on the 512x256x256 drop for omega 1.1 .. 1.3 (1.4: more)
     c->mg.omega = (dim == 3) ? 1.15f : 1.f;
+    c->mg.cpre = -1;
+    c->mg.cpost = -1;
     // one clamp rule for both precisions, representable in FP32 (1 - delta
     // must differ from 1): phi in [1e-6, 1 - 1e-6] for psi and every phi(1-phi)
     // factor, |grad psi| floored at 1e-6
@@ -1216,6 +1218,17 @@ cdi_status cdi_set_smoothing(cdi_ctx* c, int npre, int npost) {
     c->tail_ready = false;
     c->mg.tail_args = nullptr;
     drop_graphs(c);
+    return CDI_OK;
+}
+
+cdi_status cdi_set_coarse_smoothing(cdi_ctx* c, int npre, int npost) {
+    if (!c) return fail(nullptr, CDI_EINVAL, "null context");
+    const bool dflt = npre == -1 && npost == -1;
+    if (!dflt && (npre < 0 || npre > 4 || npost < 0 || npost > 4 || npre + npost < 1))
+        return fail(c, CDI_EINVAL, "coarse sweeps must lie in [0, 4] with at least one, or both be -1");
+    c->mg.cpre = npre;
+    c->mg.cpost = npost;
+    drop_graphs(c);  // the graphs hold the launches of the previous counts
     return CDI_OK;
 }
 

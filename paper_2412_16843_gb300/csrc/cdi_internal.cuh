@@ -245,6 +245,10 @@ struct MG {
     // relaxation of the finest level's red-black sweeps on the launch-per-kernel
     // path: e <- e + omega (e_GS - e); 1 is Gauss-Seidel
     float omega;
+    // launch-per-kernel path: sweeps before / after the coarse-grid correction
+    // on the levels below the finest that run as separate launches (-1: the
+    // finest level's counts)
+    int cpre, cpost;
     // tensor maps of the one-pass sweep's level-0 arrays (host memory; null
     // or not encoded: cp.async staging)
     const struct SweepMaps* maps;

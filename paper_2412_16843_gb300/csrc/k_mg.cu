@@ -1128,7 +1128,10 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
         }
         ++g_launches;
     };
-    for (int it = 0; it < npre; ++it)
+    // the coarser levels' own counts, when set
+    const int lpre = (l > 0 && mg.cpre >= 0) ? mg.cpre : npre;
+    const int lpost = (l > 0 && mg.cpost >= 0) ? mg.cpost : npost;
+    for (int it = 0; it < lpre; ++it)
         for (int col = 0; col < 2; ++col)
             sweep(col, (l == 0 && it == 0 && col == 0) ? kSweepFromZero : kSweepPlain, l == 0 && it == 0);
     MGLevel& C = mg.lv[l + 1];
@@ -1146,9 +1149,9 @@ static bool vcycle_rec(MG& mg, PT<T>* p, int l, int npre, int npost, cudaStream_
     }
     vcycle_rec<T, DIM>(mg, p, l + 1, npre, npost, s);
     launch_prolong0<DIM>(L, C, L.e, s);  // any level: the column kernel where the shape fits
-    for (int it = 0; it < npost; ++it)
+    for (int it = 0; it < lpost; ++it)
         for (int col = 0; col < 2; ++col)
-            sweep(col, (l == 0 && it == npost - 1 && col == 1) ? kSweepUpdate : kSweepPlain);
+            sweep(col, (l == 0 && it == lpost - 1 && col == 1) ? kSweepUpdate : kSweepPlain);
     return l == 0;
 }
 

@@ -519,3 +519,41 @@ def test_smoothing_counts_change_cycles_not_the_solution(exec_mode):
     for bad in ((0, 1), (1, 5)):
         with pytest.raises(cdi.CdiError):
             g.set_smoothing(*bad)
+
+
+def test_coarse_smoothing_counts_change_cycles_not_the_solution():
+    """Sweeps on the coarser separately launched levels (cdi_set_coarse_smoothing,
+    launch-per-kernel path): a 64x32x32 3D drop in FP64 (level 1, 8192 cells,
+    runs as separate launches; the single-CTA tail takes the levels below it)
+    matches the oracle within the FP64 bar after 5 steps with the finest
+    level's counts, with V(1,1) and with V(0,1) on level 1; out-of-range counts
+    are rejected and (-1, -1) restores the default."""
+    n = (64, 32, 32)
+    h = 1.0 / 32
+    L = tuple(x * h for x in n)
+    phi = inputs.add_noise(inputs.cap_phi_3d(*n, h, 0.3, math.pi / 2, 1.0, 0.5, h), 1e-3, 99)
+    o = oracle.Oracle(3, n, L)
+    o.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, 1.0)
+    o.set_solver(1e-12, 100)
+    o.set_wall_slip_length(2, math.radians(60), h, 0.0)
+    o.set_state(phi)
+    o.step(5e-5, 5)
+    phi_o, vel_o, _ = o.get_state()
+    for coarse in ((-1, -1), (1, 1), (0, 1)):
+        g = cdi.Solver(3, n, L, precision=cdi.FP64)
+        g.set_fluids(1.0, 0.1, 0.05, 0.005, 1.0, h, 1.0)
+        g.set_solver(1e-12, 100)
+        g.set_wall(cdi.WALL_BOTH, math.radians(60), h, 0.0)
+        g.set_exec(cdi.EXEC_KERNELS)
+        g.set_coarse_smoothing(*coarse)
+        g.set_state(phi)
+        g.step(5e-5, 5)
+        assert g.last_stats()["resid"] <= 1e-12
+        phi_g, vel_g, _ = g.get_fields()
+        assert rel(phi_g, phi_o) < 1e-11, coarse
+        for a in range(3):
+            assert rel(vel_g[a], vel_o[a]) < 1e-10, (coarse, a)
+    for bad in ((0, 0), (1, 5), (-1, 1)):
+        with pytest.raises(cdi.CdiError):
+            g.set_coarse_smoothing(*bad)
+    g.set_coarse_smoothing(-1, -1)
