@@ -57,6 +57,11 @@ def test_init_and_host_side_setters(lib):
     assert lib.cdi_set_wall_beta(h, 0, 1.0, float("inf")) == 1
     assert lib.cdi_set_model(h, 9) == 1
     assert lib.cdi_set_solver(h, 1e-10, 0, 0) == 1
+    assert lib.cdi_set_smoothing(h, 0, 1) == 1 and lib.cdi_set_smoothing(h, 1, 5) == 1
+    assert lib.cdi_set_smoothing(h, 1, 2) == 0
+    for bad in ((0, 0), (1, 5), (-1, 1), (5, 0)):
+        assert lib.cdi_set_coarse_smoothing(h, *bad) == 1, bad
+    assert lib.cdi_set_coarse_smoothing(h, 0, 1) == 0 and lib.cdi_set_coarse_smoothing(h, -1, -1) == 0
     # no workspace bound yet: state calls refuse
     assert lib.cdi_step(h, 1e-4, 1) == 2
     m = ctypes.c_double()
