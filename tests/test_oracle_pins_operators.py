@@ -16,6 +16,12 @@ closed forms the mathematics fixes.
   integral of u^Y converges at second order to the value that Eq. (integral
   constraint u_slip) fixes, -(sigma/beta)(cos theta - cos theta_eq) for a
   right contact line with tau = +x.
+  On a 3D wall the slip is a tangential vector: with the contact line oblique to
+  the grid (in-wall normal along (1, 2)) each tangential component, summed
+  along a grid line that crosses the contact line, must converge to the same
+  constraint value (the line element along the normal is cos or sin of the
+  direction times h), which pins the second tangential component, the
+  direction of the slip vector and the tangential gradient inside |grad psi|.
   A planar profile wider than eps (|grad psi| != 1, kappa != 0) separates
   the |grad psi| forms (B) from the equilibrium forms (A) and pins the
   curvature correction of Models 3 and 4 by a closed-form integral.
@@ -291,6 +297,58 @@ def test_slip_model_integral_constraint_planar(model):
         errs.append(abs(uY[win].sum() * h - exact) / abs(exact))
     assert errs[-1] < 5e-3, errs
     assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.5, errs
+
+
+def _oblique_3d(nx, ny, nz, h, theta, eps, a, b, s0):
+    """3D planar interface at contact angle theta on the low wall whose contact
+    line is sigma = s0, sigma = (a x + b y)/|(a, b)| (fluid 1 on the side of
+    smaller sigma), and a mirrored interface half a period of sigma away, so
+    the field is periodic in x and y (a Lx = b Ly is the period of a x + b y)."""
+    x = inputs.cell_centres(nx, h)[None, None, :]
+    y = inputs.cell_centres(ny, h)[None, :, None]
+    z = inputs.cell_centres(nz, h)[:, None, None]
+    c = math.hypot(a, b)
+    P = nx * h * a / c
+    v = ((a * x + b * y) / c - s0 + P / 4) % P - P / 4   # right line at v = 0, left one at v = P/2
+    pr = 0.5 * (1 + np.tanh((-math.sin(theta) * v - math.cos(theta) * z) / (2 * eps)))
+    pl = 0.5 * (1 + np.tanh((math.sin(theta) * (v - P / 2) - math.cos(theta) * z) / (2 * eps)))
+    return pr + pl, P
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_slip_model_integral_constraint_oblique_3d(model):
+    """Eq. (integral constraint u_slip) on a 3D wall with the contact line
+    oblique to the grid (in-wall normal (1, 2)/sqrt 5, theta = 70 deg,
+    theta_eq = 50 deg, eps fixed): in every grid row the sum of the x component
+    of u^Y times h over the right contact line, and in every grid column the
+    sum of the y component, converge at second order to
+    -(sigma/beta)(cos theta - cos theta_eq)."""
+    th, th_eq = math.radians(70.0), math.radians(50.0)
+    sigma, beta, eps, L, a, b, nz = 1.0, 10.0, 0.05, 4.0, 1, 2, 8
+    exact = -(sigma / beta) * (math.cos(th) - math.cos(th_eq))
+    c = math.hypot(a, b)
+    errs = []
+    for nx in (256, 512):
+        h = L / nx
+        ny = nx * a // b
+        o = oracle.Oracle(3, (nx, ny, nz), (L, ny * h, nz * h))
+        o.set_fluids(1.0, 1.0, 0.1, 0.1, sigma, eps, 1.0)
+        o.set_wall(2, th_eq, beta, beta)
+        o.set_model(model)
+        s0 = 0.6 * L * a / c
+        phi, P = _oblique_3d(nx, ny, nz, h, th, eps, a, b, s0)
+        o.set_state(phi)
+        uY, _, _ = o.eval_wall()
+        wrap = lambda d: (d + P / 2) % P - P / 2
+        # x component on x faces (x = i h, cell-centre y), y component on y faces
+        sx = (a * np.arange(nx)[None, :] * h + b * inputs.cell_centres(ny, h)[:, None]) / c
+        sy = (a * inputs.cell_centres(nx, h)[None, :] + b * np.arange(ny)[:, None] * h) / c
+        Ix = (uY[0, 0] * (np.abs(wrap(sx - s0)) < P / 4)).sum(axis=1) * h
+        Iy = (uY[0, 1] * (np.abs(wrap(sy - s0)) < P / 4)).sum(axis=0) * h
+        errs.append((np.abs(Ix - exact).max() / abs(exact), np.abs(Iy - exact).max() / abs(exact)))
+    for comp in range(2):
+        assert errs[-1][comp] < 1.5e-3, errs
+        assert errs[0][comp] / errs[1][comp] > 3.3, errs
 
 
 @pytest.mark.parametrize("model", MODELS)
