@@ -79,8 +79,9 @@ struct cdi_ctx {
     long vc_nodes[2] = {0, 0};
     bool vc_graph_failed = false;
     // launch-per-kernel path: a whole pressure solve (first residual, the
-    // V-cycles in a conditional while node, mean removal) as one CUDA graph
-    // per form; tolerance and cycle limit are baked into its kernels
+    // V-cycles in a conditional while node, the zero right-hand side guard) as
+    // one CUDA graph per form; tolerance and cycle limit are baked into its
+    // kernels
     cudaGraphExec_t solve_exec[2] = {nullptr, nullptr};
     long solve_nodes[2][3] = {{0, 0, 0}, {0, 0, 0}};  // before, per V-cycle, after the loop
     double solve_tol[2] = {0.0, 0.0};
@@ -499,8 +500,9 @@ __global__ void k_zero_p_if_zero_f(long n, double* p, const double* scal) {
 // The whole pressure solve as one CUDA graph: the first guess's residual norm
 // and the loop's first test, a conditional while node whose body is one
 // V-cycle, the residual norm after it and the next test, then p = 0 for a zero
-// f.  The host waits once per solve instead of once per V-cycle.  false: the graph could not be built (the caller falls back to the
-// host-driven loop).
+// f.  The host waits once per solve instead of once per V-cycle.  Returns
+// false when the graph could not be built (the caller then drives the loop
+// from the host).
 template <typename T>
 bool build_solve_graph(cdi_ctx* c, int k) {
     const Geom& g = c->g;
