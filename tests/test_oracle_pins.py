@@ -85,6 +85,26 @@ def test_stationary_tanh_profile_rhs_converges_second_order():
     assert errs[0] / errs[1] > 3.6 and errs[1] / errs[2] > 3.8, errs
 
 
+def test_stationary_circular_profile_rhs_converges_second_order():
+    """Eq. (CDI) at rest on a curved interface: for the circular tanh profile
+    psi = R - r, so eps grad phi = phi(1-phi) grad psi = phi(1-phi) n and the
+    regularisation flux vanishes in the continuum.  The face normal of the
+    discrete flux (mean of the two cell normals, reading R2) keeps the
+    divergence at second order where the normal turns; a normal taken from one
+    cell would leave a first-order residue."""
+    errs = []
+    R, eps = 0.25, 0.02
+    for n in (64, 128, 256):
+        o, h = make2d(n, n, sigma=0.0, eps=eps, gamma=1.0)
+        x = inputs.cell_centres(n, h)
+        X, Y = np.meshgrid(x, x)
+        r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+        o.set_state(0.5 * (1 + np.tanh((R - r) / (2 * eps))))
+        rphi, _ = o.eval_rhs(gamma=1.0)
+        errs.append(np.abs(rphi).max())
+    assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.5, errs
+
+
 def test_central_advection_modified_wavenumber():
     """With gamma = 0 the phi flux is u phi_f; for phi = 0.5 + 0.1 sin(kx) and
     uniform u, -div F = -U 0.1 cos(k x_i) sin(k h)/h exactly."""

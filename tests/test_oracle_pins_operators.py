@@ -299,6 +299,66 @@ def test_slip_model_integral_constraint_planar(model):
     assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.5, errs
 
 
+@pytest.mark.parametrize("model", MODELS)
+def test_slip_model_vanishes_at_equilibrium_angle_high_wall(model):
+    """The high wall (inward normal -y) of the same planar interfaces: the
+    lines cross the channel, so fluid 1 meets the high wall at pi - theta.
+    With theta_eq = pi - theta there, the bracket of every model vanishes as on
+    the low wall (psi models to round-off, here 1e-9 of the slip scale because
+    the mirrored line's tails reach the high wall's window; phi models at
+    second order), which pins the sign of the one-sided normal derivatives of
+    the high wall."""
+    th = math.radians(55.0)
+    sigma, beta, eps = 1.0, 10.0, 0.03
+    scale = 6 * sigma / beta * 0.0625 / eps
+    vals = []
+    for nx in (128, 256, 512):
+        h = 2.0 / nx
+        ny = nx // 8
+        o = oracle.Oracle(2, (nx, ny), (2.0, ny * h))
+        o.set_fluids(1.0, 1.0, 0.1, 0.1, sigma, eps, 1.0)
+        o.set_wall(0, th, beta, beta)
+        o.set_wall(1, math.pi - th, beta, beta)
+        o.set_model(model)
+        o.set_state(_tilted(nx, ny, h, 1.4, th, eps))
+        uY, _, _ = o.eval_wall()
+        x = np.arange(nx) * h
+        xt = 1.4 - ny * h / math.tan(th)      # where the right line meets the high wall
+        win = np.abs(x - xt) < 0.3
+        vals.append(np.abs(uY[1, 0][win]).max() / scale)
+    if model in PSI_MODELS:
+        assert max(vals) < 1e-9, vals
+    else:
+        assert vals[0] / vals[1] > 3.3 and vals[1] / vals[2] > 3.6, vals
+        assert vals[-1] < 2e-3, vals
+
+
+def test_wall_curvature_extrapolation_second_order():
+    """Reading R4: kappa_p (= kappa in 2D, Eq. curvature) is extrapolated to
+    the wall linearly from the first two cell rows.  For a circle crossing the
+    wall, psi = R - r and kappa = 1/r in the continuum, so with eps fixed the
+    wall value at each column near the contact line converges to 1/r at the
+    wall point at second order (a copy of the first row would be first order)."""
+    R, yc, eps = 0.3, -0.1, 0.03
+    errs = []
+    for nx in (128, 256, 512):
+        h = 1.0 / nx
+        ny = nx // 2
+        o = oracle.Oracle(2, (nx, ny), (1.0, ny * h))
+        o.set_fluids(1.0, 1.0, 0.1, 0.1, 1.0, eps, 1.0)
+        o.set_wall(2, math.pi / 2, 10.0, 10.0)
+        x = inputs.cell_centres(nx, h)
+        y = inputs.cell_centres(ny, h)
+        X, Y = np.meshgrid(x, y)
+        r = np.sqrt((X - 0.5) ** 2 + (Y - yc) ** 2)
+        o.set_state(0.5 * (1 + np.tanh((R - r) / (2 * eps))))
+        _, kpw = o.wall_columns()
+        rw = np.sqrt((x - 0.5) ** 2 + yc ** 2)
+        near = np.abs(rw - R) < 2 * eps
+        errs.append(np.abs(kpw[0][near] - 1 / rw[near]).max())
+    assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.5, errs
+
+
 def _oblique_3d(nx, ny, nz, h, theta, eps, a, b, s0):
     """3D planar interface at contact angle theta on the low wall whose contact
     line is sigma = s0, sigma = (a x + b y)/|(a, b)| (fluid 1 on the side of
