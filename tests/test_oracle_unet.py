@@ -77,6 +77,21 @@ def test_first_adam_step_closed_form():
     assert np.allclose(P["w"], [1.0 - 0.01 * 0.5 / (0.5 + 1e-8), -2.0 + 0.01 * 4.0 / (4.0 + 1e-8), 3.0])
 
 
+def test_adam_bias_correction_with_a_constant_gradient():
+    """Kingma and Ba's bias correction makes both moment estimates of a
+    constant gradient exact at every step (m_hat = g, v_hat = g^2), so each of
+    many steps moves a parameter by exactly -lr g / (|g| + eps); a correction
+    with the wrong power of beta1 or beta2 after the first step would not."""
+    g = np.array([0.5, -4.0, 2.0e-3])
+    P = {"w": np.array([1.0, -2.0, 3.0])}
+    st = {}
+    want = P["w"].copy()
+    for _ in range(12):
+        unet.adam_step(P, {"w": g}, st, lr=0.01)
+        want = want - 0.01 * g / (np.abs(g) + 1e-8)
+        assert np.allclose(P["w"], want, rtol=0, atol=1e-13)
+
+
 def test_bf16_round_ties_and_bounds():
     e = 2.0 ** -8          # half the bfloat16 spacing at 1
     vals = np.array([1.0, 3.0, 1 + e, 1 + 3 * e, 1 + e + 2.0 ** -20, -(1 + e), 2.0 ** -130, 65504.0])
