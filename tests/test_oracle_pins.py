@@ -540,6 +540,40 @@ def test_in_plane_curvature_on_spherical_cap_3d(theta_deg):
     assert errs[1] < errs[0] / 1.7
 
 
+@pytest.mark.parametrize("theta_deg", [60, 90, 120])
+def test_in_plane_curvature_of_wider_profile_on_spherical_cap_3d(theta_deg):
+    """R13 with |grad psi| != 1: for phi = (1 + tanh(r (R - rho)/(2 eps)))/2
+    (r = 0.8, a profile wider than the phase-field equilibrium) psi = r (R - rho),
+    so Eq. (curvature) gives kappa = (1 - 2 phi)(1 - r^2)/eps + 2 r/rho, while
+    the normal curvature along the in-plane tangent, -(s.H s)/|grad psi| with H
+    the Hessian of psi, stays the geometric 1/rho.  Hence kappa_p =
+    (1 - 2 phi)(1 - r^2)/eps + (2 r - 1)/rho, and the wall value near the
+    contact line (|psi_w| < 0.3 eps, rho_w = R - psi_w/r) converges to it at
+    second order with eps fixed.  Leaving |grad psi| out of the normal
+    curvature shifts it by (1 - r)/rho (about 20 % here)."""
+    th = math.radians(theta_deg)
+    R, rf, eps = 0.3, 0.8, 0.04
+    errs = []
+    for n in (48, 96):
+        h = 1.0 / n
+        dims = (n, n, n // 2)
+        x = inputs.cell_centres(dims[0], h)[None, None, :]
+        y = inputs.cell_centres(dims[1], h)[None, :, None]
+        z = inputs.cell_centres(dims[2], h)[:, None, None]
+        rho = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2 + (z + R * math.cos(th)) ** 2)
+        o = oracle.Oracle(3, dims, tuple(d * h for d in dims))
+        o.set_fluids(1.0, 1.0, 0.1, 0.1, 1.0, eps, 0.0)
+        o.set_state(0.5 * (1 + np.tanh(rf * (R - rho) / (2 * eps))))
+        psiw, kpw = o.wall_columns()
+        near = np.abs(psiw[0]) < 0.3 * eps
+        assert near.sum() > 100
+        pw = psiw[0][near]
+        phw = 1 / (1 + np.exp(-pw / eps))
+        want = (1 - 2 * phw) * (1 - rf ** 2) / eps + (2 * rf - 1) / (R - pw / rf)
+        errs.append(np.abs(kpw[0][near] / want - 1).max())
+    assert errs[1] < 0.025 and errs[1] < errs[0] / 3.0, errs
+
+
 def test_adaptive_gamma_is_the_printed_factor_times_the_largest_velocity(golden):
     """Sec. 5.1 (and 5.2): gamma = 2.5 |u|_max, the factor the paper prints.
     With gamma < 0 the oracle takes that rule, floored at -gamma (reading
