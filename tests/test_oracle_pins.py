@@ -439,6 +439,32 @@ def test_model4a_3d_spherical_cap_spurious_slip_decreases():
     assert vals[0] / vals[1] > 1.8, vals
 
 
+@pytest.mark.parametrize("model", ["4A", "4B"])
+def test_model4_3d_spherical_cap_spurious_slip_second_order_fixed_eps(model):
+    """The same prescribed spherical cap with eps fixed: near the contact line
+    (|psi_w| < 2 eps) the continuum slip of Models 4A and 4B is zero, and the
+    discrete slip (both tangential components) falls at second order in h
+    (ratio (144/96)^2 = 2.25 between the two grids).  The |grad psi| of Model
+    4B takes the other tangential gradient extrapolated linearly to the wall; a
+    copy of the first row would cut the order below 1.7."""
+    th = math.radians(60.0)
+    eps = 0.04
+    R = inputs.cap_radius(0.3, th, dim=3)
+    vals = []
+    for n in (96, 144):
+        h = 1.0 / n
+        o = oracle.Oracle(3, (n, n, n // 2), (1.0, 1.0, 0.5))
+        o.set_fluids(1, 1, 0.1, 0.1, 1.0, eps, 1.0)
+        o.set_wall(2, th, 10.0, 10.0)
+        o.set_model(model)
+        o.set_state(inputs.cap_phi_3d(n, n, n // 2, h, R, th, 0.5, 0.5, eps))
+        uY, _, _ = o.eval_wall()
+        psiw, _ = o.wall_columns()
+        near = np.abs(psiw[0]) < 2 * eps
+        vals.append(max(np.abs(uY[0, 0][near]).max(), np.abs(uY[0, 1][near]).max()))
+    assert vals[0] / vals[1] > 2.0 and vals[1] < 3e-4, vals
+
+
 # ---------------------------------------------------------------------------
 # a9: contact angle and wetted length
 # ---------------------------------------------------------------------------
