@@ -48,6 +48,24 @@ def test_psi_is_signed_distance_of_tanh_profile():
     assert np.abs(out["muc"][:, inner]).max() < 1e-6
 
 
+def test_uniform_field_normal_curvature_and_chemical_potential():
+    """Where phi is uniform (inside either fluid, or clamped far from the
+    interface) grad psi = 0 up to the round-off of the one-sided wall-row
+    stencils.  Reading R2, n = grad psi / (|grad psi| + tau), then gives a
+    normal of at most round-off / tau; Eq. (curvature) reduces to
+    kappa = (1 - 2 phi)/eps and Eq. (chemical potential) to
+    mu_c = 6 sigma phi (1 - phi)(1 - 2 phi)/eps, with phi clamped to
+    [delta, 1 - delta] (reading R3, delta = 1e-6)."""
+    eps, sigma = 0.05, 1.0
+    o, h = make2d(32, 16, sigma=sigma, eps=eps)
+    for val in (0.3, 1e-9, 1.0 - 1e-9):
+        out = o.eval_psi(np.full((16, 32), val))
+        assert np.abs(out["nx"]).max() < 1e-7 and np.abs(out["ny"]).max() < 1e-7, val
+        p = min(max(val, 1e-6), 1.0 - 1e-6)
+        assert np.allclose(out["kappa"], (1 - 2 * p) / eps, rtol=1e-12, atol=0), val
+        assert np.allclose(out["muc"], 6 * sigma * p * (1 - p) * (1 - 2 * p) / eps, rtol=1e-9, atol=0), val
+
+
 def test_curvature_and_chemical_potential_of_circle_converge_second_order():
     """For a circular tanh interface, psi = R - r so |grad psi| = 1 and
     lap psi = -1/r: kappa -> 1/r and mu_c -> 6 sigma phi(1-phi)/r (Eqs. curvature,
