@@ -69,9 +69,10 @@ enum { CDI_WALL_LO = 0, CDI_WALL_HI = 1, CDI_WALL_BOTH = 2 };
  * the prediction of the network attached with cdi_set_warm_unet
  * (launch-per-kernel execution) */
 enum { CDI_WARM_PREV = 0, CDI_WARM_ZERO = 1, CDI_WARM_EXTRAP = 2, CDI_WARM_UNET = 3 };
-/* how cdi_step runs: one persistent cooperative launch per call, one launch
- * per stencil / multigrid kernel with host-side convergence tests, or
- * (default) the first for grids up to 2^20 cells and the second above */
+/* how cdi_step runs: one persistent cooperative launch per call; one launch
+ * per stencil kernel with each pressure solve one CUDA graph, its V-cycle
+ * loop decided on the device (the host waits once per solve); or (default)
+ * the first for grids up to 2^20 cells and the second above */
 enum { CDI_EXEC_PERSISTENT = 0, CDI_EXEC_KERNELS = 1, CDI_EXEC_AUTO = 2 };
 /* slip models of Sec. 3, Eqs. (Model 1A) .. (Model 4B); 4A is the default */
 enum { CDI_MODEL_1A = 0, CDI_MODEL_1B, CDI_MODEL_2A, CDI_MODEL_2B,
@@ -166,7 +167,8 @@ cdi_status cdi_mass(cdi_ctx* ctx, double* mass_out);
 cdi_status cdi_contact_angle(cdi_ctx* ctx, int wall, double* theta_rad,
                              double* wetted_len);
 
-/* Copy the state to host memory (any pointer may be NULL). */
+/* Copy the state to host memory (any pointer may be NULL); p with its mean
+ * removed (mean(p) = 0). */
 cdi_status cdi_get_fields(cdi_ctx* ctx, double* phi, double* u, double* v,
                           double* w, double* p);
 
