@@ -884,10 +884,13 @@ static void contact_line(const Solver& S, int s, double* theta, double* wetted) 
     for (int line = 0; line < nlines; ++line) {
         const long base = (long)line * nx;
         auto phw = [&](int i) { return w.phiw[s][base + wrap(i, nx)]; };
-        // wall gradient of psi at column i: central in x, extrapolated normal part
-        auto grad_at = [&](int i, double& gn, double& gt) {
+        // wall gradient of psi at column i: central in x (and, in 3D, in y
+        // across the neighbouring lines), extrapolated normal part
+        const long bup = (long)((line + 1) % nlines) * nx, bdn = (long)((line + nlines - 1) % nlines) * nx;
+        auto grad_at = [&](int i, double& gn, double& gt, double& gy) {
             gn = w.dnw[s][base + wrap(i, nx)];
             gt = (w.psiw[s][base + wrap(i + 1, nx)] - w.psiw[s][base + wrap(i - 1, nx)]) / (2.0 * h);
+            gy = (g.D == 3) ? (w.psiw[s][bup + wrap(i, nx)] - w.psiw[s][bdn + wrap(i, nx)]) / (2.0 * h) : 0.0;
         };
         int i0 = 0;
         for (int i = 1; i < nx; ++i) if (phw(i) < phw(i0)) i0 = i;
@@ -901,11 +904,13 @@ static void contact_line(const Solver& S, int s, double* theta, double* wetted) 
             if (!crossing) continue;
             double t = (0.5 - a0) / (a1 - a0);
             double x = ((double)ip + 0.5 + t) * h;
-            double gn0, gt0, gn1, gt1;
-            grad_at(ip, gn0, gt0);
-            grad_at(ic, gn1, gt1);
-            double gn = gn0 + t * (gn1 - gn0), gt = gt0 + t * (gt1 - gt0);
-            double th = std::acos(clampd(-gn / std::sqrt(gn * gn + gt * gt), -1.0, 1.0));
+            double gn0, gt0, gy0, gn1, gt1, gy1;
+            grad_at(ip, gn0, gt0, gy0);
+            grad_at(ic, gn1, gt1, gy1);
+            double gn = gn0 + t * (gn1 - gn0), gt = gt0 + t * (gt1 - gt0), gy = gy0 + t * (gy1 - gy0);
+            // theta = acos(-d_n psi / |grad psi|) with the whole wall gradient
+            double gm = (g.D == 3) ? std::sqrt(gn * gn + gt * gt + gy * gy) : std::sqrt(gn * gn + gt * gt);
+            double th = std::acos(clampd(-gn / gm, -1.0, 1.0));
             if (!have_l) { xl = x; thl = th; have_l = true; }
             else { xr = x; thr = th; have_r = true; }
         }

@@ -894,6 +894,8 @@ __global__ void k_contact_line(int D, int nx, int nlines, double h, const double
     double th_sum = 0.0, cnt = 0.0, len_sum = 0.0;
     for (int line = threadIdx.x; line < nlines; line += blockDim.x) {
         const long base = (long)line * nx;
+        // the neighbouring lines (3D: the y derivative of the wall psi)
+        const long bup = (long)((line + 1) % nlines) * nx, bdn = (long)((line + nlines - 1) % nlines) * nx;
         auto wrapi = [&](int i) { i %= nx; return i < 0 ? i + nx : i; };
         int i0 = 0;
         for (int i = 1; i < nx; ++i)
@@ -911,7 +913,17 @@ __global__ void k_contact_line(int D, int nx, int nlines, double h, const double
             const double gt0 = (psw[base + wrapi(ip + 1)] - psw[base + wrapi(ip - 1)]) / (2.0 * h);
             const double gt1 = (psw[base + wrapi(ic + 1)] - psw[base + wrapi(ic - 1)]) / (2.0 * h);
             const double gn = gn0 + t * (gn1 - gn0), gt = gt0 + t * (gt1 - gt0);
-            double cv = -gn / sqrt(gn * gn + gt * gt);
+            // theta = acos(-d_n psi / |grad psi|) with the whole wall gradient
+            double gm;
+            if (D == 3) {
+                const double gy0 = (psw[bup + wrapi(ip)] - psw[bdn + wrapi(ip)]) / (2.0 * h);
+                const double gy1 = (psw[bup + wrapi(ic)] - psw[bdn + wrapi(ic)]) / (2.0 * h);
+                const double gy = gy0 + t * (gy1 - gy0);
+                gm = sqrt(gn * gn + gt * gt + gy * gy);
+            } else {
+                gm = sqrt(gn * gn + gt * gt);
+            }
+            double cv = -gn / gm;
             cv = fmin(fmax(cv, -1.0), 1.0);
             const double th = acos(cv);
             if (!have_l) { xl = x; thl = th; have_l = true; }

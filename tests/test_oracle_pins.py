@@ -502,6 +502,27 @@ def test_contact_angle_of_prescribed_cap(th_deg):
     assert abs(L - 2 * R * math.sin(th)) / (2 * R * math.sin(th)) < 0.01
 
 
+@pytest.mark.parametrize("th_deg", [60.0, 90.0, 120.0])
+def test_contact_angle_of_prescribed_spherical_cap_3d(th_deg):
+    """Reading R12 in 3D: the angle is the mean over the x lines of the wall
+    that cross the contact line, and the wetted length is the equivalent base
+    diameter 2 sqrt(A/pi) of the wetted area A (the summed chord lengths times
+    h).  For a spherical cap of radius R the base is a circle of diameter
+    2 R sin(theta)."""
+    n = 96
+    h = 1.0 / n
+    th = math.radians(th_deg)
+    eps = 1.0 * h
+    R = 0.25
+    dims = (n, n, n // 2)
+    o = oracle.Oracle(3, dims, tuple(d * h for d in dims))
+    o.set_fluids(1.0, 1.0, 0.1, 0.1, 1.0, eps, 1.0)
+    o.set_state(inputs.cap_phi_3d(*dims, h, R, th, 0.5, 0.5, eps))
+    theta, L = o.contact_angle(0)
+    assert abs(math.degrees(theta) - th_deg) < 2.0, math.degrees(theta)
+    assert abs(L - 2 * R * math.sin(th)) / (2 * R * math.sin(th)) < 0.01, L
+
+
 def test_equilibrium_drop_relaxes_toward_theta_eq():
     """Sec. 5.1: a 90 deg half disc with theta_eq = 60 deg spreads: the contact
     angle falls toward 60 deg and the wetted length grows toward the exact cap
