@@ -375,6 +375,37 @@ def _oblique_3d(nx, ny, nz, h, theta, eps, a, b, s0):
     return pr + pl, P
 
 
+@pytest.mark.parametrize("model", ["1A", "1B", "3A", "3B"])
+def test_phi_slip_models_vanish_at_equilibrium_angle_oblique_3d(model):
+    """The phi models on the oblique 3D wall at theta = theta_eq = 55 deg:
+    their bracket vanishes in the continuum, and the discrete slip (both
+    tangential components, at every face near the right contact line) falls
+    at second order with eps fixed.  Their |grad phi| takes the other
+    tangential phi gradient extrapolated linearly to the wall; a copy of the
+    first row would leave a first-order error."""
+    th = math.radians(55.0)
+    sigma, beta, eps, L, a, b, nz = 1.0, 10.0, 0.05, 4.0, 1, 2, 8
+    c = math.hypot(a, b)
+    vals = []
+    for nx in (256, 512):
+        h = L / nx
+        ny = nx * a // b
+        o = oracle.Oracle(3, (nx, ny, nz), (L, ny * h, nz * h))
+        o.set_fluids(1.0, 1.0, 0.1, 0.1, sigma, eps, 1.0)
+        o.set_wall(2, th, beta, beta)
+        o.set_model(model)
+        s0 = 0.6 * L * a / c
+        phi, P = _oblique_3d(nx, ny, nz, h, th, eps, a, b, s0)
+        o.set_state(phi)
+        uY, _, _ = o.eval_wall()
+        wrap = lambda d: (d + P / 2) % P - P / 2
+        sx = (a * np.arange(nx)[None, :] * h + b * inputs.cell_centres(ny, h)[:, None]) / c
+        sy = (a * inputs.cell_centres(nx, h)[None, :] + b * np.arange(ny)[:, None] * h) / c
+        vals.append(max(np.abs(uY[0, 0][np.abs(wrap(sx - s0)) < P / 4]).max(),
+                        np.abs(uY[0, 1][np.abs(wrap(sy - s0)) < P / 4]).max()))
+    assert vals[0] / vals[1] > 3.3 and vals[1] < 1.5e-3, vals
+
+
 @pytest.mark.parametrize("model", MODELS)
 def test_slip_model_integral_constraint_oblique_3d(model):
     """Eq. (integral constraint u_slip) on a 3D wall with the contact line
